@@ -1,0 +1,259 @@
+"""Seeded synthetic workloads for the GLL Poisson solver.
+
+This module only *describes* problems: a structured element grid on the unit
+square/cube, a smooth deformation map, a right-hand side f and Dirichlet data g
+given as closed-form functions of the physical coordinates, all with seeded
+random parameters.  It contains none of the solver's arithmetic: no quadrature,
+no basis, no operator.  The caller supplies the undeformed node positions
+(wherever its own GLL nodes put them) and gets back physical coordinates and
+nodal samples of f and g.  Both the CUDA path and the CPU oracle consume the
+same workload objects, so their inputs agree up to the rounding of their own
+node computations.
+
+Sign convention: the solver treats -Laplace(u) = f (weak form of Sec. 2.1,
+integral of grad u . grad v = integral of f v), so a manufactured solution u
+comes with f = -Laplace(u).
+
+Workloads (seeds are numpy.random.default_rng(2504_10710 + 1000*cfg + i)):
+  * ``square_sine``      4x4 undeformed elements, p=4, u = sin(pi x) sin(pi y).
+  * ``terrain2d``        64x64 elements, p=8, y' = y + A sin(2 pi x)(1-y), A=0.1,
+                         f = sum of 16 seeded Fourier modes, seeded smooth g.
+  * ``terrain3d``        16^3 elements, p=7,
+                         z' = z + 0.15 sin(2 pi x) cos(2 pi y)(1-z), 32 seeded
+                         right-hand sides, g = 0.
+  * ``table1_problem1``  one element, -Laplace(u) = 1, u = 0 on the boundary.
+  * ``table1_problem3``  one element, u = sin(8 pi / (x + y + pi/10)).
+  * ``random2d/3d``      any element grid / order / amplitude, for parity tests.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, Sequence
+
+import numpy as np
+
+SEED_BASE = 2504_10710
+
+
+def rng_for(cfg_id: int, i: int = 0) -> np.random.Generator:
+    return np.random.default_rng(SEED_BASE + 1000 * cfg_id + i)
+
+
+@dataclass
+class Workload:
+    """A problem description: grid, map, f and g (closed forms, seeded)."""
+
+    name: str
+    dim: int
+    nelem: tuple          # elements per physical axis (x, y[, z])
+    order: int            # GLL order p of the finest level
+    map: Callable         # (X, Y[, Z]) undeformed -> tuple of physical coords
+    rhs: Sequence[Callable]  # one f(x, y[, z]) per right-hand side
+    dirichlet: Callable   # g(x, y[, z]); only boundary samples are used
+    exact: Callable | None = None  # exact solution when manufactured
+    params: dict = field(default_factory=dict)
+
+    @property
+    def nrhs(self) -> int:
+        return len(self.rhs)
+
+    def grid_shape(self, order: int | None = None) -> tuple:
+        """Global node array shape, slowest axis first: (Nz, Ny, Nx)."""
+        p = self.order if order is None else order
+        return tuple(self.nelem[a] * p + 1 for a in reversed(range(self.dim)))
+
+    def ndof(self) -> int:
+        return int(np.prod(self.grid_shape()))
+
+    # ---- sampling helpers (the caller provides the 1-D node positions) ----
+    def undeformed_nodes(self, ref_nodes: np.ndarray) -> list[np.ndarray]:
+        """Global undeformed coordinates from reference nodes in [-1, 1].
+
+        Returns one array per physical axis, each of the global grid shape,
+        for the unit square/cube split into ``nelem`` equal elements.
+        """
+        p = len(ref_nodes) - 1
+        lines = []
+        for a in range(self.dim):
+            E = self.nelem[a]
+            t = np.empty(E * p + 1)
+            for e in range(E):
+                t[e * p:(e + 1) * p + 1] = (e + 0.5 * (np.asarray(ref_nodes) + 1.0)) / E
+            t[0], t[-1] = 0.0, 1.0
+            lines.append(t)
+        # meshgrid with 'ij' indexing in slowest-first order
+        grids = np.meshgrid(*[lines[a] for a in reversed(range(self.dim))], indexing="ij")
+        return [grids[self.dim - 1 - a] for a in range(self.dim)]
+
+    def coords(self, ref_nodes: np.ndarray) -> np.ndarray:
+        """Physical coordinates, shape (dim, *grid)."""
+        und = self.undeformed_nodes(ref_nodes)
+        return np.stack(self.map(*und))
+
+    def sample_rhs(self, coords: np.ndarray) -> np.ndarray:
+        """f samples, shape (nrhs, *grid)."""
+        return np.stack([f(*coords) for f in self.rhs])
+
+    def sample_dirichlet(self, coords: np.ndarray) -> np.ndarray:
+        return np.asarray(self.dirichlet(*coords), dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# maps
+# --------------------------------------------------------------------------
+def terrain2d_map(amp: float):
+    def m(X, Y):
+        return X, Y + amp * np.sin(2 * np.pi * X) * (1.0 - Y)
+    return m
+
+
+def terrain3d_map(amp: float):
+    def m(X, Y, Z):
+        return X, Y, Z + amp * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y) * (1.0 - Z)
+    return m
+
+
+def identity_map(*X):
+    return X
+
+
+# --------------------------------------------------------------------------
+# right-hand sides and Dirichlet data
+# --------------------------------------------------------------------------
+def fourier_rhs_2d(rng: np.random.Generator, nmodes: int = 16, kmax: int = 8):
+    a = rng.standard_normal(nmodes)
+    m = rng.integers(1, kmax + 1, nmodes)
+    n = rng.integers(1, kmax + 1, nmodes)
+
+    def f(x, y):
+        out = np.zeros_like(x, dtype=np.float64)
+        for k in range(nmodes):
+            out += a[k] * np.sin(np.pi * m[k] * x) * np.sin(np.pi * n[k] * y)
+        return out
+    return f, dict(a=a.tolist(), m=m.tolist(), n=n.tolist())
+
+
+def fourier_rhs_3d(rng: np.random.Generator, nmodes: int = 16, kmax: int = 8):
+    a = rng.standard_normal(nmodes)
+    ks = rng.integers(1, kmax + 1, (nmodes, 3))
+
+    def f(x, y, z):
+        out = np.zeros_like(x, dtype=np.float64)
+        for k in range(nmodes):
+            out += (a[k] * np.sin(np.pi * ks[k, 0] * x) * np.sin(np.pi * ks[k, 1] * y)
+                    * np.sin(np.pi * ks[k, 2] * z))
+        return out
+    return f, dict(a=a.tolist(), k=ks.tolist())
+
+
+def smooth_dirichlet_2d(rng: np.random.Generator, nmodes: int = 4):
+    b = rng.standard_normal(nmodes)
+    c = rng.integers(0, 4, nmodes)
+    d = rng.integers(0, 4, nmodes)
+    th = rng.uniform(0.0, 2 * np.pi, nmodes)
+
+    def g(x, y):
+        out = np.zeros_like(x, dtype=np.float64)
+        for k in range(nmodes):
+            out += b[k] * np.cos(np.pi * (c[k] * x + d[k] * y) + th[k])
+        return out
+    return g, dict(b=b.tolist(), c=c.tolist(), d=d.tolist(), theta=th.tolist())
+
+
+def smooth_dirichlet_3d(rng: np.random.Generator, nmodes: int = 4):
+    b = rng.standard_normal(nmodes)
+    c = rng.integers(0, 4, (nmodes, 3))
+    th = rng.uniform(0.0, 2 * np.pi, nmodes)
+
+    def g(x, y, z):
+        out = np.zeros_like(x, dtype=np.float64)
+        for k in range(nmodes):
+            out += b[k] * np.cos(np.pi * (c[k, 0] * x + c[k, 1] * y + c[k, 2] * z) + th[k])
+        return out
+    return g, dict(b=b.tolist(), c=c.tolist(), theta=th.tolist())
+
+
+def _zero(*x):
+    return np.zeros_like(x[0], dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------
+def square_sine() -> Workload:
+    """4x4 undeformed elements, p = 4; u = sin(pi x) sin(pi y), g = 0."""
+    def u(x, y):
+        return np.sin(np.pi * x) * np.sin(np.pi * y)
+
+    def f(x, y):
+        return 2 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y)
+    return Workload("square_sine_4x4_p4", 2, (4, 4), 4, identity_map, [f], _zero, exact=u)
+
+
+def terrain2d(nelem: int = 64, order: int = 8, amp: float = 0.1) -> Workload:
+    """Terrain-deformed unit square, 16 random Fourier modes, random smooth g."""
+    f, fp = fourier_rhs_2d(rng_for(1, 0))
+    g, gp = smooth_dirichlet_2d(rng_for(1, 1))
+    return Workload(f"terrain2d_{nelem}x{nelem}_p{order}", 2, (nelem, nelem), order,
+                    terrain2d_map(amp), [f], g, params=dict(amp=amp, f=fp, g=gp))
+
+
+def terrain3d(nelem: int = 16, order: int = 7, nrhs: int = 32, amp: float = 0.15) -> Workload:
+    """Hex mesh with a deformed bottom face, ``nrhs`` seeded right-hand sides, g = 0."""
+    fs = []
+    fps = []
+    for j in range(nrhs):
+        f, fp = fourier_rhs_3d(rng_for(2, j))
+        fs.append(f)
+        fps.append(fp)
+    return Workload(f"terrain3d_{nelem}^3_p{order}_x{nrhs}", 3, (nelem,) * 3, order,
+                    terrain3d_map(amp), fs, _zero, params=dict(amp=amp, f=fps))
+
+
+def table1_problem1(order: int) -> Workload:
+    """Single element on [0,1]^2, -Laplace(u) = 1 (the paper's Lap u = -1), g = 0."""
+    def f(x, y):
+        return np.ones_like(x, dtype=np.float64)
+    return Workload(f"table1_p1_p{order}", 2, (1, 1), order, identity_map, [f], _zero)
+
+
+def table1_problem3(order: int) -> Workload:
+    """Single element, u = sin(8 pi / (x + y + pi/10)), non-homogeneous Dirichlet."""
+    c = np.pi / 10.0
+
+    def u(x, y):
+        return np.sin(8 * np.pi / (x + y + c))
+
+    def f(x, y):
+        s = x + y + c
+        # Laplace(u) = 2 * u''(s) with u(s) = sin(8 pi / s)
+        d2 = (-(64 * np.pi ** 2) / s ** 4 * np.sin(8 * np.pi / s)
+              + (16 * np.pi) / s ** 3 * np.cos(8 * np.pi / s))
+        return -2.0 * d2
+    return Workload(f"table1_p3_p{order}", 2, (1, 1), order, identity_map, [f], u, exact=u)
+
+
+def random2d(nelem: Sequence[int], order: int, amp: float = 0.1, seed: int = 0,
+             nrhs: int = 1) -> Workload:
+    """Deformed 2-D grid of any size for parity tests (cfg2 map and generators)."""
+    fs = [fourier_rhs_2d(rng_for(7, 2 * seed + 17 * j))[0] for j in range(nrhs)]
+    g, _ = smooth_dirichlet_2d(rng_for(7, 2 * seed + 1))
+    ne = tuple(int(n) for n in nelem)
+    return Workload(f"random2d_{ne[0]}x{ne[1]}_p{order}_s{seed}", 2, ne, order,
+                    terrain2d_map(amp), fs, g, params=dict(amp=amp, seed=seed))
+
+
+def random3d(nelem: Sequence[int], order: int, amp: float = 0.15, seed: int = 0,
+             nrhs: int = 1) -> Workload:
+    """Deformed 3-D grid of any size for parity tests (cfg3 map and generators)."""
+    fs = [fourier_rhs_3d(rng_for(8, 2 * seed + 17 * j))[0] for j in range(nrhs)]
+    g, _ = smooth_dirichlet_3d(rng_for(8, 2 * seed + 1))
+    ne = tuple(int(n) for n in nelem)
+    return Workload(f"random3d_{'x'.join(map(str, ne))}_p{order}_s{seed}", 3, ne, order,
+                    terrain3d_map(amp), fs, g, params=dict(amp=amp, seed=seed))
+
+
+def random_field(shape, seed: int) -> np.ndarray:
+    """Seeded N(0,1) nodal field, e.g. a vector to apply an operator to."""
+    return np.random.default_rng(SEED_BASE + 9000 + seed).standard_normal(shape)
