@@ -1,0 +1,315 @@
+"""Benchmark: solved DOF/s to a 1e-10 relative residual on the 2-D
+terrain-deformed GLL Poisson problem (64x64 elements, p = 8, 263,169 nodes),
+FP32 gamma-cycle inside FP64 flexible CG, one GB300.
+
+One step = one complete solve (lifting, outer iterations to tolerance,
+u = w + v) with f and g already resident on the device.  The FP64-plain form
+is measured the same way and reported beside it.  L2 is flushed (a 256 MB
+write) between timed steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank solves its own replica of the problem
+(independent problems, no collective on the data path); value = all ranks'
+DOF / max-over-ranks time.  --impl reference times the FP64 CPU oracle (the
+slow plain implementation the GPU path is checked against).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solved DOF/s to 1e-10 rel. residual (FP32-gamma vs FP64 plain)"
+WORKLOAD = "terrain2d 64x64 quads p=8 (263,169 nodes), y'=y+0.1 sin(2 pi x)(1-y), 16 random Fourier modes"
+GAMMA, ALPHA = 1, 0.5
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_problem(wl, glls):
+    prob, coords = glls.problem_for(wl, glls.SMOOTHER_GLL, glls.RESTRICT_TRANSPOSE)
+    f = wl.sample_rhs(coords)[0]
+    g = wl.sample_dirichlet(coords)
+    return prob, f, g
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import __graft_entry__
+    from paper_2504_10710_gb300 import glls, inputs
+
+    __graft_entry__.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    wl = inputs.terrain2d()
+    prob, f, g = make_problem(wl, glls)
+    N = prob.N
+    stream = torch.cuda.current_stream()
+    f_d = torch.tensor(f.ravel(), dtype=torch.float64, device="cuda")
+    g_d = torch.tensor(g.ravel(), dtype=torch.float64, device="cuda")
+    u_d = torch.zeros(N, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    prob.set_rhs(f_d, stream)
+    prob.set_dirichlet(g_d, stream)
+
+    def timed(precision, steps, warmup, clocks=None):
+        o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=precision, use_graph=1)
+        its = []
+        for _ in range(warmup):
+            prob.solve(u_d, o, stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        if clocks:
+            clocks.start()
+        ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = prob.solve(u_d, o, stream)
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+            its.append(st.iterations)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        return ms / steps, its, clk
+
+    clocks = ClockSampler(dev)
+    ms_mixed, its_mixed, clk = timed(glls.PREC_MIXED, args.steps, args.warmup, clocks)
+    ms_fp64, its_fp64, _ = timed(glls.PREC_FP64, max(3, args.steps // 2), 2)
+    u_mixed = np.zeros(N)
+    prob.solve(u_mixed, glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED))
+    u_fp64 = np.zeros(N)
+    prob.solve(u_fp64, glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_FP64))
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    f_h = torch.tensor(f.ravel(), dtype=torch.float64).pin_memory()
+    g_h = torch.tensor(g.ravel(), dtype=torch.float64).pin_memory()
+    u_h = torch.zeros(N, dtype=torch.float64).pin_memory()
+    o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED)
+    e2e = []
+    for k in range(args.warmup + max(3, args.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prob.set_rhs(f_h.numpy())
+        prob.set_dirichlet(g_h.numpy())
+        prob.solve(u_h.numpy(), o)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e.append(t1 - t0)
+    e2e_s = float(np.mean(e2e))
+
+    # dominant kernel: the fine-level FP32 line-smoothing step (apply + CR
+    # line solve), timed alone with CUDA events over repeated launches
+    roof = kernel_roofline(prob, glls, torch, stream, N)
+
+    # max over ranks
+    ms_step = ms_mixed
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * N / (ms_step / 1e3)
+    res = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 gamma-cycle / f64 outer", "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "dof": N, "nrhs": 1, "gamma": GAMMA, "alpha": ALPHA, "smoother": "GLL band-1",
+                   "restriction": "P^T", "levels": [8, 4, 2, 1], "tol": 1e-10, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "iterations_mixed": int(np.median(its_mixed)),
+        "fp64_plain": {"value": world * N / (ms_fp64 / 1e3), "ms_per_step": ms_fp64, "iterations": int(np.median(its_fp64))},
+        "mixed_over_fp64": ms_fp64 / ms_mixed,
+        "e2e": {"value": world * N / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": 2 * 8 * N, "d2h_bytes_per_step": 8 * N},
+        "clocks": clk,
+        "roofline": roof,
+        "gpu_launches": None,
+    }
+    return res, (u_mixed, u_fp64, wl)
+
+
+def kernel_roofline(prob, glls, torch, stream, N):
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    L = prob.levels - 1
+    shape = prob.level_shape(L)
+    x = torch.zeros(N, dtype=torch.float32, device="cuda")
+    r = torch.randn(shape, dtype=torch.float32, device="cuda")
+    r[0, :] = 0
+    r[-1, :] = 0
+    r[:, 0] = 0
+    r[:, -1] = 0
+    r = r.reshape(-1).contiguous()
+    for _ in range(3):
+        prob.smooth(L, 0, 0.5, r, x, stream)
+    reps = 50
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        prob.smooth(L, 0, 0.5, r, x, stream)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    # algorithmic bytes of one fine-level FP32 smoothing step (apply + line solve):
+    # apply reads x (4N) and G (3 * E * 81 * 4), writes y (4N); line solve reads
+    # r, y, diag, off (16N), reads and writes x (8N)
+    E = 64 * 64
+    bytes_alg = 4 * N + 3 * E * 81 * 4 + 4 * N + 16 * N + 8 * N
+    ach = bytes_alg / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": "fine-level FP32 smoothing step (apply_kernel + line_kernel)",
+            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "ms_per_launch": ms, "algorithmic_bytes": bytes_alg,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s",
+            "note": "working set (~12 MB) is L2-resident; timed standalone with CUDA events"}
+
+
+def oracle_baseline(wl, u_ref_gpu=None):
+    from oracle import solve as osolve
+    t0 = time.perf_counter()
+    fine, h = osolve.build(wl, restriction="transpose")
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = osolve.solve(wl, gamma=GAMMA, alpha=ALPHA, tol=1e-10, maxit=200, hierarchy=h)
+    ts = time.perf_counter() - t0
+    N = fine.N
+    out = {"value": N / ts, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+           "sample": f"one full FP64 solve of the same workload ({r.iterations[0]} FCG iterations, {ts:.1f} s; "
+                     f"setup {tb:.1f} s excluded)"}
+    return out, r
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_2504_10710_gb300 import inputs
+        wl = inputs.terrain2d()
+        from oracle import solve as osolve
+        fine, h = osolve.build(wl, restriction="transpose")
+        times = []
+        its = []
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            r = osolve.solve(wl, gamma=GAMMA, alpha=ALPHA, tol=1e-10, maxit=200, hierarchy=h)
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t0)
+                its.append(r.iterations[0])
+        ms = 1e3 * float(np.mean(times))
+        val = fine.N / (ms / 1e3)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": val, "unit": "DOF/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "dof": fine.N, "gamma": GAMMA, "alpha": ALPHA, "tol": 1e-10},
+            "iterations": int(np.median(its)),
+            "cpu_baseline": {"value": val, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                             "sample": "one full FP64 oracle solve of the workload per step"},
+            "e2e": {"value": val, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+    res, (u_mixed, u_fp64, wl) = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            cb, r = oracle_baseline(wl)
+            res["cpu_baseline"] = cb
+            ref = r.u[0].ravel()
+            res["parity_vs_oracle"] = {
+                "fp64_rel_err": float(np.abs(u_fp64 - ref).max() / np.abs(ref).max()),
+                "mixed_rel_err": float(np.abs(u_mixed - ref).max() / np.abs(ref).max()),
+                "oracle_iterations": r.iterations[0]}
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * glls.h - C ABI of the GB300 (sm_103a) GLL spectral-element Poisson solver:
+ * outer Krylov (flexible CG) preconditioned by a p-multigrid gamma-cycle with
+ * line smoothers solved by cyclic reduction.
+ *
+ * Paper passages (arXiv 2504.10710):
+ *   Sec. 2.2, eq. (discreteBilinear)   stiffness A_p, diagonal mass M_p
+ *   Sec. 2.3                            Dirichlet lifting f0 = M f - A v, u = w + v
+ *   Def. 3.1, Def. 3.2, Fig. 4          band-1 line systems, line preconditioners
+ *   Algorithm 1, Prop. 3.7, Thm. 3.8,
+ *   Cor. 3.9                            cyclic reduction as a direct multigrid
+ *   Sec. 3.3, Def. 3.12, Algorithm 2    p-transfers, gamma-cycle, M_0^-1 = A_0^-1
+ *
+ * Conventions for every entry point:
+ *   - Return value: GLLS_OK (0) or a negative glls_status.  The message of the
+ *     last error on the calling thread is returned by glls_last_error().  No
+ *     call aborts the process or throws across the ABI.
+ *   - Nodal vectors use the global lexicographic grid of their level, x
+ *     fastest ("left-right, bottom-top", Fig. 4): index = (k*Ny + j)*Nx + i,
+ *     with N_a = nelem[a]*p_level + 1 nodes along axis a, boundary included.
+ *     Vectors handed to level operations must be zero on the boundary nodes
+ *     (the unknowns are the interior nodes; boundary values are Dirichlet).
+ *   - "Device" pointers are CUDA global-memory pointers on the problem's device
+ *     (e.g. torch tensor data_ptr()); "host" pointers are ordinary memory.  The
+ *     caller owns every buffer it passes; the library copies what it keeps.
+ *   - stream: a cudaStream_t (NULL = legacy default stream).  Device-pointer
+ *     operations are asynchronous on that stream unless stated otherwise.
+ *   - Levels are numbered 0 (coarsest, p = 1 on multi-element grids, p = 2 on
+ *     a single element) to L (finest), with p_{l-1} = floor(p_l / 2).
+ */
+#ifndef GLLS_H
+#define GLLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GLLS_OK = 0,
+    GLLS_ERR_INVALID = -1,        /* bad argument, size, level or axis */
+    GLLS_ERR_OOM = -2,            /* device or host allocation failed */
+    GLLS_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+    GLLS_ERR_NOT_CONVERGED = -4,  /* max_iter reached; last iterate returned */
+    GLLS_ERR_BREAKDOWN = -5,      /* p.Ap <= 0, NaN/Inf, zero pivot, bad Jacobian */
+    GLLS_ERR_TIMEOUT = -6,
+    GLLS_ERR_BUDGET = -7
+} glls_status;
+
+enum { GLLS_PREC_FP64 = 0, GLLS_PREC_MIXED = 1 };          /* gamma-cycle in FP64, or FP32 */
+enum { GLLS_SMOOTHER_GLL = 0, GLLS_SMOOTHER_FEM = 1 };     /* line systems from A_p or A~_p */
+enum { GLLS_RESTRICT_TRANSPOSE = 0, GLLS_RESTRICT_INTERP = 1 };
+enum { GLLS_KRYLOV_FCG = 0, GLLS_KRYLOV_PCG = 1 };
+
+typedef struct glls_problem glls_problem;   /* opaque, library-owned */
+
+/* Mesh of a structured grid of dim-dimensional GLL elements of order `order`.
+ * coords: HOST array [dim][N] of physical node coordinates on the fine grid
+ * (x-coordinates of all nodes, then y, then z), i.e. the isoparametric map
+ * sampled at the GLL nodes (glls_gll gives the reference nodes). */
+typedef struct {
+    int dim;              /* 2 or 3 */
+    int nelem[3];         /* elements along x, y, z (z ignored in 2-D) */
+    int order;            /* p >= 1 (p >= 2 for a single element) */
+    const double* coords; /* host, [dim][N] */
+    int smoother;         /* GLLS_SMOOTHER_* */
+    int restriction;      /* GLLS_RESTRICT_* */
+    int device;           /* CUDA device ordinal */
+} glls_mesh_desc;
+
+typedef struct {
+    double tol;      /* stop when ||r_k||_2 <= tol ||r_0||_2 (interior nodes, x0 = 0) */
+    int max_iter;    /* outer iterations */
+    int gamma;       /* coarse visits per level visit, >= 1 (Algorithm 2) */
+    int m;           /* smoothing steps per direction, >= 1 */
+    double alpha;    /* damping of the line smoothing step */
+    int precision;   /* GLLS_PREC_FP64 or GLLS_PREC_MIXED */
+    int krylov;      /* GLLS_KRYLOV_FCG (Polak-Ribiere beta) or _PCG (Fletcher-Reeves) */
+    int use_graph;   /* 1: replay the outer iteration as a captured CUDA graph */
+    int check_every; /* read the residual back every k iterations (>= 1) */
+} glls_solve_opts;
+
+typedef struct {
+    int iterations;
+    double rel_residual;
+    double setup_ms;
+    double solve_ms;
+    int status;
+} glls_stats;
+
+typedef struct {
+    int dim, levels;            /* number of levels L + 1 */
+    int order[8];               /* p per level, index 0 = coarsest */
+    int nodes[8][3];            /* nodes per axis per level */
+    long long ndof[8];          /* total nodes per level */
+    long long coarse_unknowns;  /* interior unknowns of level 0 */
+    size_t device_bytes;        /* device memory held by the problem */
+} glls_info;
+
+/* Reference GLL(p) nodes and weights (Def. 2.1); xi, rho: host arrays of p+1. */
+glls_status glls_gll(int p, double* xi, double* rho);
+
+/* Build every level: geometry factors, line bands, CR-ready data, transfers and
+ * the coarsest-level factor, and upload them to the device.  Synchronous. */
+glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out);
+void glls_problem_destroy(glls_problem* prob);
+glls_status glls_problem_info(const glls_problem* prob, glls_info* out);
+
+/* Dirichlet data g (N fine-grid values; only boundary entries are read) and
+ * right-hand side f (N nodal values; M f is formed inside).  on_device selects
+ * how the pointer is read; with on_device = 0 the copy is synchronous. */
+glls_status glls_set_dirichlet(glls_problem* prob, const double* g, int on_device, void* stream);
+glls_status glls_set_rhs(glls_problem* prob, const double* f, int on_device, void* stream);
+
+/* Solve A u = M f with u = g on the boundary (Sec. 2.3): lifting, outer Krylov
+ * to opts->tol, u = w + v.  u: N values (device or host per on_device).  Host
+ * output makes the call synchronous.  Returns GLLS_ERR_NOT_CONVERGED (u holds
+ * the last iterate) or GLLS_ERR_BREAKDOWN; stats may be NULL. */
+glls_status glls_solve(glls_problem* prob, const glls_solve_opts* opts, double* u, int on_device,
+                       void* stream, glls_stats* stats);
+
+/* ---- level operations on device vectors (parity tests, custom drivers) ----
+ * Each exists as _f64 and _f32; the FP32 variant uses the FP32 copies of the
+ * level data (the mixed-precision gamma-cycle). */
+
+/* y = A_l x on interior rows (boundary rows of y set to 0), eq. (discreteBilinear). */
+glls_status glls_apply_f64(glls_problem* prob, int level, const double* x, double* y, void* stream);
+glls_status glls_apply_f32(glls_problem* prob, int level, const float* x, float* y, void* stream);
+
+/* x = B_s^-1 g: every interior grid line along axis s solved by cyclic
+ * reduction (Def. 3.2, Cor. 3.9); x is written on interior nodes only. */
+glls_status glls_line_solve_f64(glls_problem* prob, int level, int axis, const double* g, double* x, void* stream);
+glls_status glls_line_solve_f32(glls_problem* prob, int level, int axis, const float* g, float* x, void* stream);
+
+/* One damped line-smoothing step x <- x + alpha B_s^-1 (r - A_l x) (Algorithm 2). */
+glls_status glls_smooth_f64(glls_problem* prob, int level, int axis, double alpha, const double* r, double* x, void* stream);
+glls_status glls_smooth_f32(glls_problem* prob, int level, int axis, float alpha, const float* r, float* x, void* stream);
+
+/* rc = R_l (r - A_l x) on level l-1 (coarse boundary rows 0), Sec. 3.3. level >= 1. */
+glls_status glls_restrict_f64(glls_problem* prob, int level, const double* r, const double* x, double* rc, void* stream);
+glls_status glls_restrict_f32(glls_problem* prob, int level, const float* r, const float* x, float* rc, void* stream);
+
+/* x += P_l e, e on level l-1, x on level l (Sec. 3.3). level >= 1. */
+glls_status glls_prolong_add_f64(glls_problem* prob, int level, const double* e, double* x, void* stream);
+glls_status glls_prolong_add_f32(glls_problem* prob, int level, const float* e, float* x, void* stream);
+
+/* e = A_0^-1 r on the coarsest level (M_0^-1 of Algorithm 2). */
+glls_status glls_coarse_solve_f64(glls_problem* prob, const double* r, double* e, void* stream);
+glls_status glls_coarse_solve_f32(glls_problem* prob, const float* r, float* e, void* stream);
+
+/* z = M_L^-1 r: one gamma-cycle on the finest level (Algorithm 2, x0 = 0),
+ * using opts->gamma, opts->m, opts->alpha. */
+glls_status glls_precondition_f64(glls_problem* prob, const glls_solve_opts* opts, const double* r, double* z, void* stream);
+glls_status glls_precondition_f32(glls_problem* prob, const glls_solve_opts* opts, const float* r, float* z, void* stream);
+
+/* f0 = M f - A v on interior nodes (0 on the boundary), v = g on the boundary
+ * and 0 inside (Sec. 2.3); f, g, f0: fine-grid device vectors. */
+glls_status glls_lift_f64(glls_problem* prob, const double* f, const double* g, double* f0, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* glls_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLLS_H */

@@ -1,0 +1,605 @@
+// C ABI of the GLL p-multigrid solver (include/glls.h): problem set-up and
+// upload, the gamma-cycle driver (Algorithm 2) and the outer flexible CG.
+#include "../../include/glls.h"
+#include "device.cuh"
+#include "setup.h"
+
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+using namespace glls;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+glls_status fail(glls_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? GLLS_ERR_OOM : GLLS_ERR_CUDA,            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+template <typename T>
+struct LevelStore {
+    DevLevel<T> dev;
+    T* r = nullptr;    // level right-hand side (coarse levels)
+    T* x = nullptr;    // level iterate
+    T* y = nullptr;    // A x scratch
+    T* t1 = nullptr;   // transfer temporaries
+    T* t2 = nullptr;
+};
+
+}  // namespace
+
+struct glls_problem {
+    int device = 0;
+    int dim = 2;
+    int nelem[3] = {1, 1, 1};
+    int p = 1;
+    int smoother = 0, restriction = 0;
+    std::vector<int> orders;
+    std::vector<LevelStore<double>> L64;
+    std::vector<LevelStore<float>> L32;
+    DevCoarse<double> C64;
+    DevCoarse<float> C32;
+    long long N = 0;       // fine nodes
+    long long N0 = 0;      // coarsest nodes
+    // fine-level FP64 solve state
+    double *f = nullptr, *g = nullptr, *v = nullptr, *f0 = nullptr;
+    const double* mass = nullptr;
+    double *xk = nullptr, *rk = nullptr, *pk = nullptr, *qk = nullptr, *zk = nullptr, *yk = nullptr;
+    double *S = nullptr, *part = nullptr, *hostS = nullptr;
+    float *r32 = nullptr, *z32 = nullptr;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    double setup_ms = 0.0;
+    cudaStream_t capture_stream = nullptr;
+    // cached graph of one outer iteration
+    cudaGraphExec_t iter_exec = nullptr;
+    int g_gamma = -1, g_m = -1, g_prec = -1, g_krylov = -1;
+    double g_alpha = 0.0;
+    bool has_rhs = false, has_dirichlet = false;
+
+    template <typename T>
+    cudaError_t alloc(T** ptr, size_t count) {
+        void* p_ = nullptr;
+        cudaError_t e = cudaMalloc(&p_, sizeof(T) * (count ? count : 1));
+        if (e != cudaSuccess) return e;
+        allocs.push_back(p_);
+        bytes += sizeof(T) * (count ? count : 1);
+        *ptr = static_cast<T*>(p_);
+        return cudaSuccess;
+    }
+    template <typename T, typename S>
+    cudaError_t upload(const T** dst, const std::vector<S>& src) {
+        T* d = nullptr;
+        cudaError_t e = alloc(&d, src.size());
+        if (e != cudaSuccess) return e;
+        std::vector<T> tmp(src.begin(), src.end());
+        e = cudaMemcpy(d, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice);
+        *dst = d;
+        return e;
+    }
+};
+
+namespace {
+
+template <typename T>
+glls_status upload_levels(glls_problem* P, const std::vector<LevelHost>& H, std::vector<LevelStore<T>>& out) {
+    out.assign(H.size(), LevelStore<T>());
+    for (size_t l = 0; l < H.size(); ++l) {
+        const LevelHost& h = H[l];
+        LevelStore<T>& s = out[l];
+        DevLevel<T>& d = s.dev;
+        d.dim = h.dim;
+        d.p = h.p;
+        d.n1 = h.p + 1;
+        d.nloc = h.nloc;
+        d.ncomp = h.ncomp;
+        for (int a = 0; a < 3; ++a) { d.ne[a] = h.ne[a]; d.n[a] = h.n[a]; }
+        d.N = h.N;
+        d.E = h.E;
+        CK(P->upload(&d.G, h.G));
+        CK(P->upload(&d.D, h.D));
+        CK(P->upload(&d.diag, h.diag));
+        for (int a = 0; a < h.dim; ++a) CK(P->upload(&d.off[a], h.off[a]));
+        if (l > 0) {
+            for (int a = 0; a < h.dim; ++a) {
+                const Band1D* bs[2] = {&h.P[a], &h.R[a]};
+                DevBand<T>* ds[2] = {&d.P[a], &d.R[a]};
+                for (int k = 0; k < 2; ++k) {
+                    ds[k]->rows = bs[k]->rows;
+                    ds[k]->cols = bs[k]->cols;
+                    ds[k]->width = bs[k]->width;
+                    CK(P->upload(&ds[k]->start, bs[k]->start));
+                    CK(P->upload(&ds[k]->coef, bs[k]->coef));
+                }
+            }
+        }
+        CK(P->alloc(&s.r, h.N));
+        CK(P->alloc(&s.x, h.N));
+        CK(P->alloc(&s.y, h.N));
+        CK(P->alloc(&s.t1, h.N));
+        CK(P->alloc(&s.t2, h.N));
+        CK(cudaMemset(s.r, 0, sizeof(T) * h.N));
+        CK(cudaMemset(s.x, 0, sizeof(T) * h.N));
+    }
+    return GLLS_OK;
+}
+
+template <typename T>
+std::vector<LevelStore<T>>& levels_of(glls_problem* P);
+template <>
+std::vector<LevelStore<double>>& levels_of<double>(glls_problem* P) { return P->L64; }
+template <>
+std::vector<LevelStore<float>>& levels_of<float>(glls_problem* P) { return P->L32; }
+template <typename T>
+const DevCoarse<T>& coarse_of(glls_problem* P);
+template <>
+const DevCoarse<double>& coarse_of<double>(glls_problem* P) { return P->C64; }
+template <>
+const DevCoarse<float>& coarse_of<float>(glls_problem* P) { return P->C32; }
+
+// rc = R_l (r - y) on level l-1
+template <typename T>
+void restrict_residual(glls_problem* P, int l, const T* r, const T* y, T* rc, cudaStream_t st) {
+    auto& Ls = levels_of<T>(P);
+    const DevLevel<T>& F = Ls[l].dev;
+    const DevLevel<T>& C = Ls[l - 1].dev;
+    int cur[3] = {F.n[0], F.n[1], F.n[2]};
+    const T* in = r;
+    const T* in2 = y;
+    for (int a = 0; a < F.dim; ++a) {
+        int nxt[3] = {cur[0], cur[1], cur[2]};
+        nxt[a] = C.n[a];
+        const bool last = a == F.dim - 1;
+        T* out = last ? rc : (a % 2 == 0 ? Ls[l].t1 : Ls[l].t2);
+        launch_transfer<T>(F.R[a], a, cur, nxt, in, in2, out, false, last, st);
+        in = out;
+        in2 = nullptr;
+        for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
+    }
+}
+
+// x += P_l e
+template <typename T>
+void prolong_add(glls_problem* P, int l, const T* e, T* x, cudaStream_t st) {
+    auto& Ls = levels_of<T>(P);
+    const DevLevel<T>& F = Ls[l].dev;
+    const DevLevel<T>& C = Ls[l - 1].dev;
+    int cur[3] = {C.n[0], C.n[1], C.n[2]};
+    const T* in = e;
+    for (int a = 0; a < F.dim; ++a) {
+        int nxt[3] = {cur[0], cur[1], cur[2]};
+        nxt[a] = F.n[a];
+        const bool last = a == F.dim - 1;
+        T* out = last ? x : (a % 2 == 0 ? Ls[l].t1 : Ls[l].t2);
+        launch_transfer<T>(F.P[a], a, cur, nxt, in, nullptr, out, last, false, st);
+        in = out;
+        for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
+    }
+}
+
+// x <- x + alpha B_s^-1 (r - A x); x_is_zero skips the apply
+template <typename T>
+void smooth(glls_problem* P, int l, int s, T alpha, const T* r, T* x, bool x_is_zero, cudaStream_t st) {
+    auto& Ls = levels_of<T>(P);
+    if (x_is_zero) {
+        launch_line_solve<T>(Ls[l].dev, s, 1, nullptr, r, nullptr, x, alpha, st);
+    } else {
+        launch_apply<T>(Ls[l].dev, x, Ls[l].y, true, st);
+        launch_line_solve<T>(Ls[l].dev, s, 1, nullptr, r, Ls[l].y, x, alpha, st);
+    }
+}
+
+// Algorithm 2: x = M_l^-1 r from x0 = 0
+template <typename T>
+void cycle(glls_problem* P, int l, const T* r, T* x, int gamma, int m, T alpha, cudaStream_t st) {
+    auto& Ls = levels_of<T>(P);
+    if (l == 0) {
+        launch_coarse<T>(coarse_of<T>(P), Ls[0].dev.N, r, x, st);
+        return;
+    }
+    const int d = Ls[l].dev.dim;
+    cudaMemsetAsync(x, 0, sizeof(T) * Ls[l].dev.N, st);
+    bool zero = true;
+    for (int s = 0; s < d; ++s)
+        for (int k = 0; k < m; ++k) {
+            smooth<T>(P, l, s, alpha, r, x, zero, st);
+            zero = false;
+        }
+    for (int g = 0; g < gamma; ++g) {
+        launch_apply<T>(Ls[l].dev, x, Ls[l].y, true, st);
+        restrict_residual<T>(P, l, r, Ls[l].y, Ls[l - 1].r, st);
+        cycle<T>(P, l - 1, Ls[l - 1].r, Ls[l - 1].x, gamma, m, alpha, st);
+        prolong_add<T>(P, l, Ls[l - 1].x, x, st);
+        for (int s = d - 1; s >= 0; --s)
+            for (int k = 0; k < m; ++k) smooth<T>(P, l, s, alpha, r, x, false, st);
+    }
+}
+
+glls_status check_level(glls_problem* P, int level, bool need_coarser) {
+    if (!P) return fail(GLLS_ERR_INVALID, "null problem");
+    if (level < 0 || level >= (int)P->L64.size()) return fail(GLLS_ERR_INVALID, "level out of range");
+    if (need_coarser && level < 1) return fail(GLLS_ERR_INVALID, "level must be >= 1");
+    return GLLS_OK;
+}
+
+glls_status check_opts(const glls_solve_opts* o) {
+    if (!o) return fail(GLLS_ERR_INVALID, "null options");
+    if (o->gamma < 1 || o->gamma > 16) return fail(GLLS_ERR_INVALID, "gamma must be in 1..16");
+    if (o->m < 1 || o->m > 16) return fail(GLLS_ERR_INVALID, "m must be in 1..16");
+    if (!(o->alpha > 0.0)) return fail(GLLS_ERR_INVALID, "alpha must be > 0");
+    if (o->precision != GLLS_PREC_FP64 && o->precision != GLLS_PREC_MIXED)
+        return fail(GLLS_ERR_INVALID, "bad precision");
+    if (o->krylov != GLLS_KRYLOV_FCG && o->krylov != GLLS_KRYLOV_PCG) return fail(GLLS_ERR_INVALID, "bad krylov");
+    if (o->max_iter < 1) return fail(GLLS_ERR_INVALID, "max_iter must be >= 1");
+    if (!(o->tol > 0.0)) return fail(GLLS_ERR_INVALID, "tol must be > 0");
+    return GLLS_OK;
+}
+
+// z = M^-1 r for the outer iteration (FP64 in, FP64 out)
+void precondition_outer(glls_problem* P, const glls_solve_opts* o, const double* r, double* z, cudaStream_t st) {
+    const int L = (int)P->L64.size() - 1;
+    if (o->precision == GLLS_PREC_MIXED) {
+        launch_cast<double, float>(r, P->r32, P->N, st);
+        cycle<float>(P, L, P->r32, P->z32, o->gamma, o->m, (float)o->alpha, st);
+        launch_cast<float, double>(P->z32, z, P->N, st);
+    } else {
+        cycle<double>(P, L, r, z, o->gamma, o->m, o->alpha, st);
+    }
+}
+
+// Body of one outer iteration, in the order
+//   z = M r; (r.z, z.q); p = z + beta p; rz <- rz_new; q = A p; p.q; x, r update; r.r
+void outer_iteration(glls_problem* P, const glls_solve_opts* o, cudaStream_t st) {
+    const int L = (int)P->L64.size() - 1;
+    const long long N = P->N;
+    precondition_outer(P, o, P->rk, P->zk, st);
+    launch_dots(P->rk, P->zk, P->zk, P->qk, 2, N, P->part, P->S, S_RZNEW, S_ZQ, st);
+    launch_fcg_direction(P->pk, P->zk, N, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, st);
+    launch_fcg_rotate(P->S, st);
+    launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st);
+    launch_dots(P->pk, P->qk, nullptr, nullptr, 1, N, P->part, P->S, S_PQ, S_PQ, st);
+    launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, P->part, P->S, st);
+}
+
+glls_status get_iteration_graph(glls_problem* P, const glls_solve_opts* o) {
+    if (P->iter_exec && P->g_gamma == o->gamma && P->g_m == o->m && P->g_prec == o->precision &&
+        P->g_krylov == o->krylov && P->g_alpha == o->alpha)
+        return GLLS_OK;
+    if (P->iter_exec) {
+        cudaGraphExecDestroy(P->iter_exec);
+        P->iter_exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(P->capture_stream, cudaStreamCaptureModeThreadLocal));
+    outer_iteration(P, o, P->capture_stream);
+    CK(cudaStreamEndCapture(P->capture_stream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&P->iter_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    P->g_gamma = o->gamma;
+    P->g_m = o->m;
+    P->g_prec = o->precision;
+    P->g_krylov = o->krylov;
+    P->g_alpha = o->alpha;
+    return GLLS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* glls_last_error(void) { return g_last_error.c_str(); }
+
+glls_status glls_gll(int p, double* xi, double* rho) {
+    if (p < 1 || p > 64 || !xi) return fail(GLLS_ERR_INVALID, "glls_gll: need 1 <= p <= 64 and xi != NULL");
+    std::vector<double> w;
+    std::vector<double> x = gll_nodes(p, &w);
+    std::memcpy(xi, x.data(), sizeof(double) * (p + 1));
+    if (rho) std::memcpy(rho, w.data(), sizeof(double) * (p + 1));
+    return GLLS_OK;
+}
+
+glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) {
+    if (!desc || !out) return fail(GLLS_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (desc->dim != 2 && desc->dim != 3) return fail(GLLS_ERR_INVALID, "dim must be 2 or 3");
+    if (desc->order < 1 || desc->order > 24) return fail(GLLS_ERR_INVALID, "order must be in 1..24");
+    for (int a = 0; a < desc->dim; ++a)
+        if (desc->nelem[a] < 1 || desc->nelem[a] > 4096) return fail(GLLS_ERR_INVALID, "nelem out of range");
+    if (!desc->coords) return fail(GLLS_ERR_INVALID, "coords is NULL");
+    bool multi = desc->nelem[0] > 1 || desc->nelem[1] > 1 || (desc->dim == 3 && desc->nelem[2] > 1);
+    if (!multi && desc->order < 2) return fail(GLLS_ERR_INVALID, "a single element needs order >= 2");
+    if (desc->smoother != GLLS_SMOOTHER_GLL && desc->smoother != GLLS_SMOOTHER_FEM)
+        return fail(GLLS_ERR_INVALID, "bad smoother");
+    if (desc->restriction != GLLS_RESTRICT_TRANSPOSE && desc->restriction != GLLS_RESTRICT_INTERP)
+        return fail(GLLS_ERR_INVALID, "bad restriction");
+    auto t0 = std::chrono::steady_clock::now();
+    CK(cudaSetDevice(desc->device));
+    static std::once_flag once;
+    static bool attrs_ok = false;
+    std::call_once(once, [] { attrs_ok = init_kernel_attributes(); });
+    if (!attrs_ok) return fail(GLLS_ERR_CUDA, "could not set kernel shared-memory attributes");
+
+    std::unique_ptr<glls_problem> P(new glls_problem());
+    P->device = desc->device;
+    P->dim = desc->dim;
+    P->p = desc->order;
+    P->smoother = desc->smoother;
+    P->restriction = desc->restriction;
+    for (int a = 0; a < 3; ++a) P->nelem[a] = a < desc->dim ? desc->nelem[a] : 1;
+    std::vector<LevelHost> H;
+    std::string err = build_levels(desc->dim, P->nelem, desc->order, desc->coords, desc->smoother,
+                                   desc->restriction, H);
+    if (!err.empty()) return fail(GLLS_ERR_BREAKDOWN, err);
+    for (auto& h : H) {
+        P->orders.push_back(h.p);
+        for (long long i = 0; i < h.N; ++i) {
+            // zero pivots would break cyclic reduction without pivoting
+            bool inner = true;
+            long long I = i % h.n[0], J = (i / h.n[0]) % h.n[1], K = i / ((long long)h.n[0] * h.n[1]);
+            if (I == 0 || I == h.n[0] - 1 || J == 0 || J == h.n[1] - 1 ||
+                (h.dim == 3 && (K == 0 || K == h.n[2] - 1)))
+                inner = false;
+            if (inner && !(h.diag[i] > 0.0)) return fail(GLLS_ERR_BREAKDOWN, "non-positive line-system diagonal");
+        }
+    }
+    CoarseHost C;
+    err = build_coarse(H[0], C);
+    if (!err.empty()) return fail(GLLS_ERR_BREAKDOWN, err);
+
+    glls_status st = upload_levels<double>(P.get(), H, P->L64);
+    if (st != GLLS_OK) return st;
+    st = upload_levels<float>(P.get(), H, P->L32);
+    if (st != GLLS_OK) return st;
+    P->C64.n = C.n;
+    P->C32.n = C.n;
+    CK(P->upload(&P->C64.index, C.index));
+    P->C32.index = P->C64.index;
+    CK(P->upload(&P->C64.inv, C.inv));
+    CK(P->upload(&P->C32.inv, C.inv));
+    if ((size_t)C.n * sizeof(double) > kMaxDynSmemBytes)
+        return fail(GLLS_ERR_INVALID, "coarsest level too large for the dense coarse solver");
+
+    const LevelHost& F = H.back();
+    P->N = F.N;
+    P->N0 = H[0].N;
+    const long long N = P->N;
+    CK(P->upload(&P->mass, F.mass));
+    double** vecs[] = {&P->f, &P->g, &P->v, &P->f0, &P->xk, &P->rk, &P->pk, &P->qk, &P->zk, &P->yk};
+    for (double** vp : vecs) {
+        CK(P->alloc(vp, N));
+        CK(cudaMemset(*vp, 0, sizeof(double) * N));
+    }
+    CK(P->alloc(&P->S, S_COUNT));
+    CK(P->alloc(&P->part, 2 * kDotBlocks));
+    CK(P->alloc(&P->r32, N));
+    CK(P->alloc(&P->z32, N));
+    CK(cudaMallocHost(&P->hostS, sizeof(double) * S_COUNT));
+    CK(cudaStreamCreateWithFlags(&P->capture_stream, cudaStreamNonBlocking));
+    CK(cudaDeviceSynchronize());
+    P->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = P.release();
+    return GLLS_OK;
+}
+
+void glls_problem_destroy(glls_problem* P) {
+    if (!P) return;
+    cudaSetDevice(P->device);
+    if (P->iter_exec) cudaGraphExecDestroy(P->iter_exec);
+    if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
+    for (void* a : P->allocs) cudaFree(a);
+    if (P->hostS) cudaFreeHost(P->hostS);
+    delete P;
+}
+
+glls_status glls_problem_info(const glls_problem* P, glls_info* out) {
+    if (!P || !out) return fail(GLLS_ERR_INVALID, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    out->dim = P->dim;
+    out->levels = (int)P->L64.size();
+    for (size_t l = 0; l < P->L64.size() && l < 8; ++l) {
+        out->order[l] = P->L64[l].dev.p;
+        for (int a = 0; a < 3; ++a) out->nodes[l][a] = P->L64[l].dev.n[a];
+        out->ndof[l] = P->L64[l].dev.N;
+    }
+    out->coarse_unknowns = P->C64.n;
+    out->device_bytes = P->bytes;
+    return GLLS_OK;
+}
+
+glls_status glls_set_dirichlet(glls_problem* P, const double* g, int on_device, void* stream) {
+    if (!P || !g) return fail(GLLS_ERR_INVALID, "null argument");
+    CK(cudaSetDevice(P->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(P->g, g, sizeof(double) * P->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    P->has_dirichlet = true;
+    return GLLS_OK;
+}
+
+glls_status glls_set_rhs(glls_problem* P, const double* f, int on_device, void* stream) {
+    if (!P || !f) return fail(GLLS_ERR_INVALID, "null argument");
+    CK(cudaSetDevice(P->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(P->f, f, sizeof(double) * P->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    P->has_rhs = true;
+    return GLLS_OK;
+}
+
+glls_status glls_lift_f64(glls_problem* P, const double* f, const double* g, double* f0, void* stream) {
+    if (!P || !f || !g || !f0) return fail(GLLS_ERR_INVALID, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int L = (int)P->L64.size() - 1;
+    const DevLevel<double>& F = P->L64[L].dev;
+    launch_boundary_only(g, P->v, F.n, F.dim, st);
+    launch_apply<double>(F, P->v, P->yk, false, st);
+    launch_lift_rhs(P->mass, f, P->yk, f0, F.n, F.dim, st);
+    CK(cudaGetLastError());
+    return GLLS_OK;
+}
+
+glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int on_device, void* stream,
+                       glls_stats* stats) {
+    if (!P || !u) return fail(GLLS_ERR_INVALID, "null argument");
+    glls_status s0 = check_opts(o);
+    if (s0 != GLLS_OK) return s0;
+    if (!P->has_rhs) return fail(GLLS_ERR_INVALID, "right-hand side not set");
+    CK(cudaSetDevice(P->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    const long long N = P->N;
+    const int L = (int)P->L64.size() - 1;
+    if (!P->has_dirichlet) CK(cudaMemsetAsync(P->g, 0, sizeof(double) * N, st));
+    // lifting: f0 = M f - A v
+    glls_status ls = glls_lift_f64(P, P->f, P->g, P->f0, stream);
+    if (ls != GLLS_OK) return ls;
+    // x = 0, r = f0, p = q = 0; S: rz = 1, alpha = 0 so that the first direction is p = z
+    CK(cudaMemsetAsync(P->xk, 0, sizeof(double) * N, st));
+    CK(cudaMemsetAsync(P->pk, 0, sizeof(double) * N, st));
+    CK(cudaMemsetAsync(P->qk, 0, sizeof(double) * N, st));
+    CK(cudaMemcpyAsync(P->rk, P->f0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    double init[S_COUNT] = {0};
+    init[S_RZ] = 1.0;
+    std::memcpy(P->hostS, init, sizeof(init));
+    CK(cudaMemcpyAsync(P->S, P->hostS, sizeof(init), cudaMemcpyHostToDevice, st));
+    launch_dots(P->rk, P->rk, nullptr, nullptr, 1, N, P->part, P->S, S_RR0, S_RR0, st);
+    CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double rr0 = P->hostS[S_RR0];
+    int it = 0;
+    double rel = 0.0;
+    glls_status result = GLLS_OK;
+    if (!(rr0 >= 0.0) || !std::isfinite(rr0)) {
+        result = fail(GLLS_ERR_BREAKDOWN, "non-finite right-hand side");
+    } else if (rr0 > 0.0) {
+        const double tol2 = o->tol * o->tol * rr0;
+        if (o->use_graph) {
+            glls_status gs = get_iteration_graph(P, o);
+            if (gs != GLLS_OK) return gs;
+        }
+        const int every = o->check_every > 0 ? o->check_every : 1;
+        result = GLLS_ERR_NOT_CONVERGED;
+        while (it < o->max_iter) {
+            if (o->use_graph) CK(cudaGraphLaunch(P->iter_exec, st));
+            else outer_iteration(P, o, st);
+            ++it;
+            if (it % every == 0 || it == o->max_iter) {
+                CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (P->hostS[S_FLAG] != 0.0 || !std::isfinite(P->hostS[S_RR])) {
+                    result = fail(GLLS_ERR_BREAKDOWN, "breakdown in the outer iteration (p.Ap <= 0 or NaN)");
+                    break;
+                }
+                if (P->hostS[S_RR] <= tol2) {
+                    result = GLLS_OK;
+                    break;
+                }
+            }
+        }
+        rel = std::sqrt(P->hostS[S_RR] / rr0);
+    }
+    CK(cudaGetLastError());
+    // u = w + v
+    CK(cudaMemcpyAsync(P->yk, P->xk, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    launch_axpy(P->yk, P->v, 1.0, N, st);
+    CK(cudaMemcpyAsync(u, P->yk, sizeof(double) * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (!on_device || stats) CK(cudaStreamSynchronize(st));
+    if (stats) {
+        stats->iterations = it;
+        stats->rel_residual = rel;
+        stats->setup_ms = P->setup_ms;
+        stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        stats->status = result;
+    }
+    (void)L;
+    return result;
+}
+
+#define LEVEL_OPS(SUF, T)                                                                                      \
+    glls_status glls_apply_##SUF(glls_problem* P, int level, const T* x, T* y, void* stream) {                  \
+        glls_status s = check_level(P, level, false);                                                           \
+        if (s != GLLS_OK) return s;                                                                             \
+        if (!x || !y) return fail(GLLS_ERR_INVALID, "null vector");                                             \
+        launch_apply<T>(levels_of<T>(P)[level].dev, x, y, true, (cudaStream_t)stream);                          \
+        CK(cudaGetLastError());                                                                                 \
+        return GLLS_OK;                                                                                         \
+    }                                                                                                           \
+    glls_status glls_line_solve_##SUF(glls_problem* P, int level, int axis, const T* g, T* x, void* stream) {   \
+        glls_status s = check_level(P, level, false);                                                           \
+        if (s != GLLS_OK) return s;                                                                             \
+        if (axis < 0 || axis >= P->dim) return fail(GLLS_ERR_INVALID, "axis out of range");                     \
+        if (!g || !x) return fail(GLLS_ERR_INVALID, "null vector");                                             \
+        launch_line_solve<T>(levels_of<T>(P)[level].dev, axis, 0, g, nullptr, nullptr, x, T(1),                 \
+                             (cudaStream_t)stream);                                                             \
+        CK(cudaGetLastError());                                                                                 \
+        return GLLS_OK;                                                                                         \
+    }                                                                                                           \
+    glls_status glls_smooth_##SUF(glls_problem* P, int level, int axis, T alpha, const T* r, T* x,              \
+                                  void* stream) {                                                               \
+        glls_status s = check_level(P, level, false);                                                           \
+        if (s != GLLS_OK) return s;                                                                             \
+        if (axis < 0 || axis >= P->dim) return fail(GLLS_ERR_INVALID, "axis out of range");                     \
+        if (!r || !x) return fail(GLLS_ERR_INVALID, "null vector");                                             \
+        smooth<T>(P, level, axis, alpha, r, x, false, (cudaStream_t)stream);                                    \
+        CK(cudaGetLastError());                                                                                 \
+        return GLLS_OK;                                                                                         \
+    }                                                                                                           \
+    glls_status glls_restrict_##SUF(glls_problem* P, int level, const T* r, const T* x, T* rc, void* stream) {  \
+        glls_status s = check_level(P, level, true);                                                            \
+        if (s != GLLS_OK) return s;                                                                             \
+        if (!r || !x || !rc) return fail(GLLS_ERR_INVALID, "null vector");                                      \
+        auto& Ls = levels_of<T>(P);                                                                             \
+        launch_apply<T>(Ls[level].dev, x, Ls[level].y, true, (cudaStream_t)stream);                             \
+        restrict_residual<T>(P, level, r, Ls[level].y, rc, (cudaStream_t)stream);                               \
+        CK(cudaGetLastError());                                                                                 \
+        return GLLS_OK;                                                                                         \
+    }                                                                                                           \
+    glls_status glls_prolong_add_##SUF(glls_problem* P, int level, const T* e, T* x, void* stream) {            \
+        glls_status s = check_level(P, level, true);                                                            \
+        if (s != GLLS_OK) return s;                                                                             \
+        if (!e || !x) return fail(GLLS_ERR_INVALID, "null vector");                                             \
+        prolong_add<T>(P, level, e, x, (cudaStream_t)stream);                                                   \
+        CK(cudaGetLastError());                                                                                 \
+        return GLLS_OK;                                                                                         \
+    }                                                                                                           \
+    glls_status glls_coarse_solve_##SUF(glls_problem* P, const T* r, T* e, void* stream) {                      \
+        if (!P || !r || !e) return fail(GLLS_ERR_INVALID, "null argument");                                    \
+        launch_coarse<T>(coarse_of<T>(P), levels_of<T>(P)[0].dev.N, r, e, (cudaStream_t)stream);                \
+        CK(cudaGetLastError());                                                                                 \
+        return GLLS_OK;                                                                                         \
+    }                                                                                                           \
+    glls_status glls_precondition_##SUF(glls_problem* P, const glls_solve_opts* o, const T* r, T* z,            \
+                                        void* stream) {                                                         \
+        if (!P || !r || !z) return fail(GLLS_ERR_INVALID, "null argument");                                     \
+        glls_status s = check_opts(o);                                                                          \
+        if (s != GLLS_OK) return s;                                                                             \
+        cycle<T>(P, (int)P->L64.size() - 1, r, z, o->gamma, o->m, (T)o->alpha, (cudaStream_t)stream);           \
+        CK(cudaGetLastError());                                                                                 \
+        return GLLS_OK;                                                                                         \
+    }
+
+LEVEL_OPS(f64, double)
+LEVEL_OPS(f32, float)
+
+}  // extern "C"

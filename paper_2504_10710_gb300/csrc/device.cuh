@@ -1,0 +1,101 @@
+// Device-side data layout of the GLL p-multigrid solver and the host
+// launchers of its kernels (kernels.cu).
+//
+// Layout in HBM, per level and precision T (double or float):
+//   nodal vectors   : global grid, x fastest, N = n0*n1*n2 entries
+//   G               : [ncomp][E * nloc] geometry factors, element-major, local
+//                     node index q = (k*(p+1) + j)*(p+1) + i
+//   diag, off[s]    : band-1 line-system coefficients on the global grid;
+//                     off[s][node] couples node and node + e_s
+//   D               : (p+1)^2 derivative matrix, D[i*(p+1)+j] = pi_j'(xi_i)
+//   P[a], R[a]      : fixed-width row bands of the 1-D transfer matrices
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace glls {
+
+template <typename T>
+struct DevBand {
+    int rows = 0, cols = 0, width = 0;
+    const int* start = nullptr;
+    const T* coef = nullptr;
+};
+
+template <typename T>
+struct DevLevel {
+    int dim = 2, p = 1, n1 = 2, nloc = 4, ncomp = 3;
+    int ne[3] = {1, 1, 1};
+    int n[3] = {1, 1, 1};
+    long long N = 0, E = 0;
+    const T* G = nullptr;
+    const T* D = nullptr;
+    const T* diag = nullptr;
+    const T* off[3] = {nullptr, nullptr, nullptr};
+    DevBand<T> P[3], R[3];
+};
+
+template <typename T>
+struct DevCoarse {
+    long long n = 0;
+    const long long* index = nullptr;   // interior node of each unknown
+    const T* inv = nullptr;             // dense n x n inverse, row-major
+};
+
+// Opt every kernel into up to 200 KB of dynamic shared memory (call once per
+// device, outside stream capture).
+bool init_kernel_attributes();
+constexpr size_t kMaxDynSmemBytes = 200 * 1024;
+
+// ---- launchers (all asynchronous on `st`) ---------------------------------
+// y = A x (y zeroed first); mask: zero boundary rows.
+template <typename T>
+void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st);
+
+// Line solves along axis s.  mode 0: x = B_s^-1 g (interior entries written);
+// mode 1: x += alpha B_s^-1 (r - y).
+template <typename T>
+void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, const T* y,
+                       T* x, T alpha, cudaStream_t st);
+
+// One tensor-product factor of a transfer: out = M in (or in - in2) along
+// axis a; grids nin/nout differ only along a.  add: out += ...; mask: zero
+// the output's boundary nodes.
+template <typename T>
+void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nout[3], const T* in,
+                     const T* in2, T* out, bool add, bool mask, cudaStream_t st);
+
+// e = A_0^-1 r on the coarsest level (e zeroed on the boundary).
+template <typename T>
+void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, cudaStream_t st);
+
+// ---- vector kernels -------------------------------------------------------
+template <typename Ti, typename To>
+void launch_cast(const Ti* in, To* out, long long n, cudaStream_t st);
+template <typename T>
+void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st);
+
+// Deterministic dot products: partial sums per block into `part`
+// (ndots * nblocks), then a one-block finaliser writes S[slot[k]].
+constexpr int kDotBlocks = 304;   // 2 x 152 SMs
+void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots,
+                 long long n, double* part, double* S, int slot0, int slot1, cudaStream_t st);
+
+// Krylov scalar slots in the device array S.
+enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZNEW, S_ZQ, S_RR0, S_ALPHA, S_FLAG, S_TOL2, S_ITER, S_COUNT };
+
+// q-independent update: alpha = S_RZ / S_PQ; x += alpha p; r -= alpha q;
+// then rr = r.r into S_RR (via part); flags breakdown in S_FLAG.
+void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, double* part,
+                       double* S, cudaStream_t st);
+// p = z + beta p with beta = -alpha S_ZQ / S_RZ (flexible) or S_RZNEW / S_RZ.
+void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, cudaStream_t st);
+// S_RZ <- S_RZNEW (after the direction update has consumed S_RZ)
+void launch_fcg_rotate(double* S, cudaStream_t st);
+// f0 = M f - y on interior nodes (0 on the boundary); v = g on the boundary, 0 inside.
+void launch_lift_rhs(const double* mass, const double* f, const double* y, double* f0, const int n[3], int dim,
+                     cudaStream_t st);
+void launch_boundary_only(const double* g, double* v, const int n[3], int dim, cudaStream_t st);
+void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st);   // y += a x
+
+}  // namespace glls

@@ -1,0 +1,533 @@
+// sm_103a kernels of the GLL p-multigrid gamma-cycle solver.
+//
+//   apply_kernel     y = A_l x, eq. (discreteBilinear): per element, x is staged
+//                    in shared memory, reference gradients by sum factorisation
+//                    (one 1-D contraction with D per axis), the pointwise
+//                    geometric factors G, then the transposed contractions;
+//                    element-interior nodes are stored, shared nodes summed
+//                    with atomics (direct stiffness summation).
+//   line_kernel      B_s^-1 on every interior grid line along axis s: the band-1
+//                    line system (Def. 3.1/3.2) staged in shared memory and
+//                    solved in place by cyclic reduction written as the direct
+//                    multigrid of Algorithm 1 / Thm. 3.8 / Cor. 3.9.
+//   transfer_kernel  one axis of the tensor-product transfers P_l, R_l (Sec. 3.3).
+//   coarse_kernel    M_0^-1 = A_0^-1 as a dense matrix-vector product.
+//   dots / fcg_*     FP64 outer-Krylov vector operations with scalars kept in
+//                    device memory, deterministic two-stage reductions.
+#include "device.cuh"
+
+#include <cstdio>
+
+namespace glls {
+
+namespace {
+
+__device__ __forceinline__ bool on_boundary(long long g, const int n[3], int dim) {
+    long long I = g % n[0];
+    long long J = (g / n[0]) % n[1];
+    if (I == 0 || I == n[0] - 1 || J == 0 || J == n[1] - 1) return true;
+    if (dim == 3) {
+        long long K = g / ((long long)n[0] * n[1]);
+        if (K == 0 || K == n[2] - 1) return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// stiffness apply
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) apply_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
+                                                    int mask, int epc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sD = reinterpret_cast<T*>(smem_raw);
+    const int n1 = L.n1, nloc = L.nloc, p = L.p;
+    T* sx = sD + n1 * n1;
+    T* sw = sx + epc * nloc;
+    for (int t = threadIdx.x; t < n1 * n1; t += blockDim.x) sD[t] = L.D[t];
+    const long long e0 = (long long)blockIdx.x * epc;
+    const int ecount = (int)min((long long)epc, L.E - e0);
+    const int total = ecount * nloc;
+    const long long EN = L.E * nloc;
+
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int el = t / nloc, q = t - el * nloc;
+        const long long e = e0 + el;
+        const int i = q % n1, j = (q / n1) % n1, k = DIM == 3 ? q / (n1 * n1) : 0;
+        const long long ex = e % L.ne[0], ey = (e / L.ne[0]) % L.ne[1], ez = DIM == 3 ? e / ((long long)L.ne[0] * L.ne[1]) : 0;
+        const long long g = ((ez * p + k) * L.n[1] + (ey * p + j)) * L.n[0] + (ex * p + i);
+        sx[t] = x[g];
+    }
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int el = t / nloc, q = t - el * nloc;
+        const int i = q % n1, j = (q / n1) % n1, k = DIM == 3 ? q / (n1 * n1) : 0;
+        const T* xe = sx + el * nloc;
+        T gr[3] = {T(0), T(0), T(0)};
+        // reference gradient: contraction with D along each axis
+        for (int m = 0; m < n1; ++m) {
+            gr[0] += sD[i * n1 + m] * xe[(k * n1 + j) * n1 + m];
+            gr[1] += sD[j * n1 + m] * xe[(k * n1 + m) * n1 + i];
+            if (DIM == 3) gr[2] += sD[k * n1 + m] * xe[(m * n1 + j) * n1 + i];
+        }
+        const long long gq = (e0 + el) * nloc + q;
+        if (DIM == 2) {
+            const T g00 = L.G[gq], g01 = L.G[EN + gq], g11 = L.G[2 * EN + gq];
+            sw[t] = g00 * gr[0] + g01 * gr[1];
+            sw[epc * nloc + t] = g01 * gr[0] + g11 * gr[1];
+        } else {
+            const T g00 = L.G[gq], g01 = L.G[EN + gq], g02 = L.G[2 * EN + gq];
+            const T g11 = L.G[3 * EN + gq], g12 = L.G[4 * EN + gq], g22 = L.G[5 * EN + gq];
+            sw[t] = g00 * gr[0] + g01 * gr[1] + g02 * gr[2];
+            sw[epc * nloc + t] = g01 * gr[0] + g11 * gr[1] + g12 * gr[2];
+            sw[2 * epc * nloc + t] = g02 * gr[0] + g12 * gr[1] + g22 * gr[2];
+        }
+    }
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int el = t / nloc, q = t - el * nloc;
+        const long long e = e0 + el;
+        const int i = q % n1, j = (q / n1) % n1, k = DIM == 3 ? q / (n1 * n1) : 0;
+        const T* w0 = sw + el * nloc;
+        const T* w1 = sw + epc * nloc + el * nloc;
+        const T* w2 = sw + 2 * epc * nloc + el * nloc;
+        T v = T(0);
+        for (int m = 0; m < n1; ++m) {
+            v += sD[m * n1 + i] * w0[(k * n1 + j) * n1 + m];
+            v += sD[m * n1 + j] * w1[(k * n1 + m) * n1 + i];
+            if (DIM == 3) v += sD[m * n1 + k] * w2[(m * n1 + j) * n1 + i];
+        }
+        const long long ex = e % L.ne[0], ey = (e / L.ne[0]) % L.ne[1], ez = DIM == 3 ? e / ((long long)L.ne[0] * L.ne[1]) : 0;
+        const long long g = ((ez * p + k) * L.n[1] + (ey * p + j)) * L.n[0] + (ex * p + i);
+        const bool inner = i > 0 && i < p && j > 0 && j < p && (DIM == 2 || (k > 0 && k < p));
+        if (inner) {
+            y[g] = v;
+        } else {
+            if (mask && on_boundary(g, L.n, DIM)) continue;
+            atomicAdd(&y[g], v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// line solves by cyclic reduction
+// ---------------------------------------------------------------------------
+template <typename T>
+struct LineArgs {
+    int n;              // unknowns per line
+    long long nlines;
+    int W;              // lines per CTA
+    long long stride;   // node stride along the line
+    int m1;             // interior extent of the faster other axis
+    long long st1, st2; // node strides of the two other axes
+    int contiguous;
+    int mode;
+    T alpha;
+    const T* diag;
+    const T* off;
+    const T* g;
+    const T* r;
+    const T* y;
+    T* x;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) line_kernel(LineArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = A.n;
+    const long long l0 = (long long)blockIdx.x * A.W;
+    const int Wc = (int)min((long long)A.W, A.nlines - l0);
+    T* sa = reinterpret_cast<T*>(smem_raw);
+    T* sl = sa + A.W * n;
+    T* su = sl + A.W * n;
+    T* sg = su + A.W * n;
+    const int total = Wc * n;
+
+    auto node_of = [&](int w, int kk) -> long long {
+        const long long li = l0 + w;
+        const long long c1 = li % A.m1 + 1, c2 = li / A.m1 + 1;
+        return c1 * A.st1 + c2 * A.st2 + (long long)(kk + 1) * A.stride;
+    };
+
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int w, kk;
+        if (A.contiguous) { w = t / n; kk = t - w * n; } else { kk = t / Wc; w = t - kk * Wc; }
+        const long long g = node_of(w, kk);
+        const int s = w * n + kk;
+        sa[s] = A.diag[g];
+        su[s] = kk < n - 1 ? A.off[g] : T(0);
+        sl[s] = kk > 0 ? A.off[g - A.stride] : T(0);
+        sg[s] = A.mode == 0 ? A.g[g] : (A.y ? A.r[g] - A.y[g] : A.r[g]);
+    }
+    __syncthreads();
+
+    // forward reduction: eliminate the odd multiples of h into the even ones
+    int h = 1;
+    while (n / h > 1) {
+        const int cnt = n / (2 * h);
+        for (int t = threadIdx.x; t < Wc * cnt; t += blockDim.x) {
+            const int w = t / cnt, c = t - w * cnt;
+            const int i = (c + 1) * 2 * h - 1;   // 0-based position of 1-based (c+1)*2h
+            const int il = w * n + i - h, ic = w * n + i, ir = w * n + i + h;
+            const T al = -sl[ic] / sa[il];
+            T be = T(0), ur = T(0), lr = T(0), gr = T(0);
+            if (i + h < n) { be = -su[ic] / sa[ir]; ur = su[ir]; lr = sl[ir]; gr = sg[ir]; }
+            sa[ic] = sa[ic] + al * su[il] + be * lr;
+            sg[ic] = sg[ic] + al * sg[il] + be * gr;
+            sl[ic] = al * sl[il];
+            su[ic] = be * ur;
+        }
+        __syncthreads();
+        h *= 2;
+    }
+    for (int w = threadIdx.x; w < Wc; w += blockDim.x) sg[w * n + h - 1] = sg[w * n + h - 1] / sa[w * n + h - 1];
+    __syncthreads();
+    // back substitution: odd multiples of h from their solved neighbours
+    for (h /= 2; h >= 1; h /= 2) {
+        const int cnt = (n / h + 1) / 2;
+        for (int t = threadIdx.x; t < Wc * cnt; t += blockDim.x) {
+            const int w = t / cnt, c = t - w * cnt;
+            const int i = (2 * c + 1) * h - 1;
+            const int ic = w * n + i;
+            const T xl = i - h >= 0 ? sg[ic - h] : T(0);
+            const T xr = i + h < n ? sg[ic + h] : T(0);
+            sg[ic] = (sg[ic] - sl[ic] * xl - su[ic] * xr) / sa[ic];
+        }
+        __syncthreads();
+    }
+
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int w, kk;
+        if (A.contiguous) { w = t / n; kk = t - w * n; } else { kk = t / Wc; w = t - kk * Wc; }
+        const long long g = node_of(w, kk);
+        const T v = sg[w * n + kk];
+        if (A.mode == 0) A.x[g] = v; else A.x[g] += A.alpha * v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// transfers
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void transfer_kernel(DevBand<T> M, int a, int3 nin, int3 nout, const T* __restrict__ in,
+                                const T* __restrict__ in2, T* __restrict__ out, int add, int mask, int dim) {
+    const long long total = (long long)nout.x * nout.y * nout.z;
+    const long long sin_a = a == 0 ? 1 : (a == 1 ? (long long)nin.x : (long long)nin.x * nin.y);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long c0 = idx % nout.x, c1 = (idx / nout.x) % nout.y, c2 = idx / ((long long)nout.x * nout.y);
+        if (mask) {
+            bool bnd = c0 == 0 || c0 == nout.x - 1 || c1 == 0 || c1 == nout.y - 1 ||
+                       (dim == 3 && (c2 == 0 || c2 == nout.z - 1));
+            if (bnd) { if (!add) out[idx] = T(0); continue; }
+        }
+        const long long K = a == 0 ? c0 : (a == 1 ? c1 : c2);
+        long long b0 = c0, b1 = c1, b2 = c2;
+        if (a == 0) b0 = 0; else if (a == 1) b1 = 0; else b2 = 0;
+        const long long base = (b2 * nin.y + b1) * nin.x + b0 + (long long)M.start[K] * sin_a;
+        const T* cf = M.coef + K * M.width;
+        T v = T(0);
+        if (in2) {
+            for (int k = 0; k < M.width; ++k) v += cf[k] * (in[base + k * sin_a] - in2[base + k * sin_a]);
+        } else {
+            for (int k = 0; k < M.width; ++k) v += cf[k] * in[base + k * sin_a];
+        }
+        out[idx] = add ? out[idx] + v : v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// coarsest solve: dense inverse times vector, one warp per row
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) coarse_kernel(long long n, const long long* __restrict__ index,
+                                                     const T* __restrict__ inv, const T* __restrict__ r,
+                                                     T* __restrict__ e) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* rs = reinterpret_cast<T*>(smem_raw);
+    for (long long t = threadIdx.x; t < n; t += blockDim.x) rs[t] = r[index[t]];
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const long long row = (long long)blockIdx.x * (blockDim.x / 32) + warp;
+    if (row >= n) return;
+    const T* a = inv + row * n;
+    T s = T(0);
+    for (long long j = lane; j < n; j += 32) s += a[j] * rs[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) e[index[row]] = s;
+}
+
+// ---------------------------------------------------------------------------
+// vector kernels
+// ---------------------------------------------------------------------------
+template <typename Ti, typename To>
+__global__ void cast_kernel(const Ti* __restrict__ in, To* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = static_cast<To>(in[i]);
+}
+
+template <typename T>
+__global__ void zero_boundary_kernel(T* v, int3 n, int dim) {
+    const long long total = (long long)n.x * n.y * n.z;
+    const int nn[3] = {n.x, n.y, n.z};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+        if (on_boundary(i, nn, dim)) v[i] = T(0);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
+    return s;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0, const double* __restrict__ b0,
+                                                   const double* __restrict__ a1, const double* __restrict__ b1,
+                                                   int ndots, long long n, double* part) {
+    __shared__ double red[32];
+    double s0 = 0.0, s1 = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        s0 += a0[i] * b0[i];
+        if (ndots > 1) s1 += a1[i] * b1[i];
+    }
+    double t0 = block_sum(s0, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t0;
+    if (ndots > 1) {
+        double t1 = block_sum(s1, red);
+        if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t1;
+    }
+}
+
+__global__ void __launch_bounds__(256) dots_finalize(const double* __restrict__ part, int ndots, int nblocks,
+                                                     double* S, int slot0, int slot1) {
+    __shared__ double red[32];
+    for (int d = 0; d < ndots; ++d) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += part[d * nblocks + i];
+        double t = block_sum(s, red);
+        if (threadIdx.x == 0) S[d == 0 ? slot0 : slot1] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x, double* __restrict__ r,
+                                                         const double* __restrict__ p, const double* __restrict__ q,
+                                                         long long n, double* part, double* S) {
+    __shared__ double red[32];
+    const double pq = S[S_PQ];
+    const double alpha = S[S_RZ] / pq;
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        s += ri * ri;
+    }
+    double t = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t;
+        if (blockIdx.x == 0) {
+            S[S_ALPHA] = alpha;
+            if (!(pq > 0.0) || !isfinite(alpha)) S[S_FLAG] = 1.0;
+        }
+    }
+}
+
+__global__ void fcg_direction_kernel(double* __restrict__ p, const double* __restrict__ z, long long n,
+                                     const double* __restrict__ S, int flexible) {
+    const double beta = flexible ? -S[S_ALPHA] * S[S_ZQ] / S[S_RZ] : S[S_RZNEW] / S[S_RZ];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+__global__ void fcg_rotate_kernel(double* S) {
+    if (threadIdx.x == 0) S[S_RZ] = S[S_RZNEW];
+}
+
+__global__ void lift_rhs_kernel(const double* __restrict__ mass, const double* __restrict__ f,
+                                const double* __restrict__ y, double* __restrict__ f0, int3 n, int dim) {
+    const long long total = (long long)n.x * n.y * n.z;
+    const int nn[3] = {n.x, n.y, n.z};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+        f0[i] = on_boundary(i, nn, dim) ? 0.0 : mass[i] * f[i] - y[i];
+}
+
+__global__ void boundary_only_kernel(const double* __restrict__ g, double* __restrict__ v, int3 n, int dim) {
+    const long long total = (long long)n.x * n.y * n.z;
+    const int nn[3] = {n.x, n.y, n.z};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+        v[i] = on_boundary(i, nn, dim) ? g[i] : 0.0;
+}
+
+__global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+
+inline int grid_for(long long n, int threads = 256) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 152LL * 16) b = 152LL * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// Dynamic shared memory above 48 KB needs an opt-in per kernel; it is set
+// once for every kernel at library initialisation (init_kernel_attributes),
+// never during stream capture.
+constexpr int kMaxDynSmem = 200 * 1024;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st) {
+    cudaMemsetAsync(y, 0, sizeof(T) * L.N, st);
+    int epc = 256 / L.nloc;
+    if (epc < 1) epc = 1;
+    const long long blocks = (L.E + epc - 1) / epc;
+    const size_t smem = sizeof(T) * (L.n1 * L.n1 + (size_t)epc * L.nloc * (1 + L.dim));
+    if (L.dim == 2) {
+        apply_kernel<T, 2><<<(unsigned)blocks, 256, smem, st>>>(L, x, y, mask ? 1 : 0, epc);
+    } else {
+        apply_kernel<T, 3><<<(unsigned)blocks, 256, smem, st>>>(L, x, y, mask ? 1 : 0, epc);
+    }
+}
+
+template <typename T>
+void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, const T* y, T* x, T alpha,
+                       cudaStream_t st) {
+    LineArgs<T> A;
+    A.n = L.n[s] - 2;
+    if (A.n <= 0) return;
+    int o1, o2;
+    if (s == 0) { o1 = 1; o2 = 2; } else if (s == 1) { o1 = 0; o2 = 2; } else { o1 = 0; o2 = 1; }
+    const long long strides[3] = {1, L.n[0], (long long)L.n[0] * L.n[1]};
+    A.m1 = L.n[o1] - 2;
+    const int m2 = L.dim == 3 ? L.n[o2] - 2 : 1;
+    A.nlines = (long long)A.m1 * m2;
+    if (A.nlines <= 0) return;
+    A.stride = strides[s];
+    A.st1 = strides[o1];
+    A.st2 = L.dim == 3 ? strides[o2] : 0;
+    if (L.dim == 2) A.st2 = 0;
+    A.contiguous = s == 0;
+    A.mode = mode;
+    A.alpha = alpha;
+    A.diag = L.diag;
+    A.off = L.off[s];
+    A.g = g;
+    A.r = r;
+    A.y = y;
+    A.x = x;
+    const size_t per_line = 4 * sizeof(T) * (size_t)A.n;
+    long long W = (96 * 1024) / (long long)per_line;
+    if (W > 32) W = 32;
+    if (W < 1) W = 1;
+    const long long wmin = A.contiguous ? 1 : (32 / (long long)sizeof(T));
+    while (W > wmin && (A.nlines + W - 1) / W < 2 * 152) W /= 2;
+    A.W = (int)W;
+    const size_t smem = per_line * W;
+    const long long blocks = (A.nlines + W - 1) / W;
+    line_kernel<T><<<(unsigned)blocks, 256, smem, st>>>(A);
+}
+
+template <typename T>
+void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nout[3], const T* in, const T* in2, T* out,
+                     bool add, bool mask, cudaStream_t st) {
+    const long long total = (long long)nout[0] * nout[1] * nout[2];
+    int dim = nout[2] > 1 ? 3 : 2;
+    transfer_kernel<T><<<grid_for(total), 256, 0, st>>>(M, a, make_int3(nin[0], nin[1], nin[2]),
+                                                         make_int3(nout[0], nout[1], nout[2]), in, in2, out,
+                                                         add ? 1 : 0, mask ? 1 : 0, dim);
+}
+
+template <typename T>
+void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, cudaStream_t st) {
+    cudaMemsetAsync(e, 0, sizeof(T) * N0, st);
+    const size_t smem = sizeof(T) * (size_t)C.n;
+    const long long blocks = (C.n + 7) / 8;
+    coarse_kernel<T><<<(unsigned)blocks, 256, smem, st>>>(C.n, C.index, C.inv, r, e);
+}
+
+template <typename Ti, typename To>
+void launch_cast(const Ti* in, To* out, long long n, cudaStream_t st) {
+    cast_kernel<Ti, To><<<grid_for(n), 256, 0, st>>>(in, out, n);
+}
+
+template <typename T>
+void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st) {
+    const long long total = (long long)n[0] * n[1] * n[2];
+    zero_boundary_kernel<T><<<grid_for(total), 256, 0, st>>>(v, make_int3(n[0], n[1], n[2]), dim);
+}
+
+void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots, long long n,
+                 double* part, double* S, int slot0, int slot1, cudaStream_t st) {
+    dots_kernel<<<kDotBlocks, 256, 0, st>>>(a0, b0, a1, b1, ndots, n, part);
+    dots_finalize<<<1, 256, 0, st>>>(part, ndots, kDotBlocks, S, slot0, slot1);
+}
+
+void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, double* part, double* S,
+                       cudaStream_t st) {
+    fcg_update_kernel<<<kDotBlocks, 256, 0, st>>>(x, r, p, q, n, part, S);
+    dots_finalize<<<1, 256, 0, st>>>(part, 1, kDotBlocks, S, S_RR, S_RR);
+}
+
+void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, cudaStream_t st) {
+    fcg_direction_kernel<<<grid_for(n), 256, 0, st>>>(p, z, n, S, flexible);
+}
+
+void launch_fcg_rotate(double* S, cudaStream_t st) { fcg_rotate_kernel<<<1, 32, 0, st>>>(S); }
+
+void launch_lift_rhs(const double* mass, const double* f, const double* y, double* f0, const int n[3], int dim,
+                     cudaStream_t st) {
+    const long long total = (long long)n[0] * n[1] * n[2];
+    lift_rhs_kernel<<<grid_for(total), 256, 0, st>>>(mass, f, y, f0, make_int3(n[0], n[1], n[2]), dim);
+}
+
+void launch_boundary_only(const double* g, double* v, const int n[3], int dim, cudaStream_t st) {
+    const long long total = (long long)n[0] * n[1] * n[2];
+    boundary_only_kernel<<<grid_for(total), 256, 0, st>>>(g, v, make_int3(n[0], n[1], n[2]), dim);
+}
+
+void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st) {
+    axpy_kernel<<<grid_for(n), 256, 0, st>>>(y, x, a, n);
+}
+
+bool init_kernel_attributes() {
+    const void* fns[] = {(const void*)apply_kernel<double, 2>, (const void*)apply_kernel<double, 3>,
+                         (const void*)apply_kernel<float, 2>,  (const void*)apply_kernel<float, 3>,
+                         (const void*)line_kernel<double>,     (const void*)line_kernel<float>,
+                         (const void*)coarse_kernel<double>,   (const void*)coarse_kernel<float>};
+    for (const void* f : fns)
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess)
+            return false;
+    return true;
+}
+
+// explicit instantiations
+template void launch_apply<double>(const DevLevel<double>&, const double*, double*, bool, cudaStream_t);
+template void launch_apply<float>(const DevLevel<float>&, const float*, float*, bool, cudaStream_t);
+template void launch_line_solve<double>(const DevLevel<double>&, int, int, const double*, const double*, const double*,
+                                        double*, double, cudaStream_t);
+template void launch_line_solve<float>(const DevLevel<float>&, int, int, const float*, const float*, const float*,
+                                       float*, float, cudaStream_t);
+template void launch_transfer<double>(const DevBand<double>&, int, const int*, const int*, const double*, const double*,
+                                      double*, bool, bool, cudaStream_t);
+template void launch_transfer<float>(const DevBand<float>&, int, const int*, const int*, const float*, const float*,
+                                     float*, bool, bool, cudaStream_t);
+template void launch_coarse<double>(const DevCoarse<double>&, long long, const double*, double*, cudaStream_t);
+template void launch_coarse<float>(const DevCoarse<float>&, long long, const float*, float*, cudaStream_t);
+template void launch_cast<double, float>(const double*, float*, long long, cudaStream_t);
+template void launch_cast<float, double>(const float*, double*, long long, cudaStream_t);
+template void launch_zero_boundary<double>(double*, const int*, int, cudaStream_t);
+template void launch_zero_boundary<float>(float*, const int*, int, cudaStream_t);
+
+}  // namespace glls

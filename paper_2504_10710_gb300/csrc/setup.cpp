@@ -1,0 +1,541 @@
+// Host-side FP64 construction of the solver's level data (runs once per
+// problem, before any solve).  See setup.h.
+#include "setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <sstream>
+
+namespace glls {
+
+namespace {
+
+// Legendre L_p and L_p' at x by the recurrences
+//   (n+1) L_{n+1} = (2n+1) x L_n - n L_{n-1},   L_{n+1}' = L_{n-1}' + (2n+1) L_n.
+void legendre(int p, double x, double* L, double* dL) {
+    double l0 = 1.0, l1 = x, d0 = 0.0, d1 = 1.0;
+    if (p == 0) { *L = 1.0; *dL = 0.0; return; }
+    for (int n = 1; n < p; ++n) {
+        double l2 = ((2 * n + 1) * x * l1 - n * l0) / (n + 1);
+        double d2 = d0 + (2 * n + 1) * l1;
+        l0 = l1; l1 = l2; d0 = d1; d1 = d2;
+    }
+    *L = l1;
+    *dL = d1;
+}
+
+int comp_index(int dim, int a, int b) {
+    if (a > b) std::swap(a, b);
+    if (dim == 2) return a == 0 ? b : 2;              // 00->0, 01->1, 11->2
+    static const int t[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    return t[a][b];
+}
+
+// dense (rows x cols) row-major -> banded rows
+Band1D to_band(const std::vector<double>& M, int rows, int cols) {
+    Band1D b;
+    b.rows = rows;
+    b.cols = cols;
+    b.start.assign(rows, 0);
+    int width = 1;
+    std::vector<int> lo(rows), hi(rows);
+    for (int r = 0; r < rows; ++r) {
+        int l = cols, h = -1;
+        for (int c = 0; c < cols; ++c)
+            if (M[(size_t)r * cols + c] != 0.0) { l = std::min(l, c); h = std::max(h, c); }
+        if (h < 0) { l = 0; h = 0; }
+        lo[r] = l; hi[r] = h;
+        width = std::max(width, h - l + 1);
+    }
+    b.width = width;
+    b.coef.assign((size_t)rows * width, 0.0);
+    for (int r = 0; r < rows; ++r) {
+        int s = std::min(lo[r], cols - width);
+        if (s < 0) s = 0;
+        b.start[r] = s;
+        for (int k = 0; k < width && s + k < cols; ++k) b.coef[(size_t)r * width + k] = M[(size_t)r * cols + s + k];
+    }
+    return b;
+}
+
+// 1-D global interpolation (ne*p_to + 1) x (ne*p_from + 1): a continuous
+// piecewise degree-p_from field sampled at the GLL(p_to) nodes of each element.
+std::vector<double> global_interp(int ne, int p_from, int p_to) {
+    std::vector<double> J = interpolation(p_from, p_to);
+    int rows = ne * p_to + 1, cols = ne * p_from + 1;
+    std::vector<double> M((size_t)rows * cols, 0.0);
+    for (int e = 0; e < ne; ++e)
+        for (int i = 0; i <= p_to; ++i)
+            for (int k = 0; k <= p_from; ++k)
+                M[(size_t)(e * p_to + i) * cols + e * p_from + k] = J[i * (p_from + 1) + k];
+    return M;
+}
+
+struct Geo {
+    int dim, p, n1, nloc;
+    const LevelHost* lv;
+    long long gnode(const int ec[3], const int lc[3]) const {
+        long long I = (long long)ec[0] * p + lc[0];
+        long long J = (long long)ec[1] * p + lc[1];
+        long long K = dim == 3 ? (long long)ec[2] * p + lc[2] : 0;
+        return (K * lv->n[1] + J) * lv->n[0] + I;
+    }
+};
+
+void element_coords(const LevelHost& lv, long long e, int ec[3]) {
+    ec[0] = (int)(e % lv.ne[0]);
+    ec[1] = (int)((e / lv.ne[0]) % lv.ne[1]);
+    ec[2] = (int)(e / ((long long)lv.ne[0] * lv.ne[1]));
+}
+
+void local_coords(int q, int n1, int dim, int lc[3]) {
+    lc[0] = q % n1;
+    lc[1] = (q / n1) % n1;
+    lc[2] = dim == 3 ? q / (n1 * n1) : 0;
+}
+
+int local_index(const int lc[3], int n1) { return (lc[2] * n1 + lc[1]) * n1 + lc[0]; }
+
+std::string geometry(LevelHost& lv) {
+    const int d = lv.dim, p = lv.p, n1 = p + 1, nloc = lv.nloc;
+    std::vector<double> w1;
+    gll_nodes(p, &w1);
+    lv.D = derivative_matrix(p);
+    lv.G.assign((size_t)lv.ncomp * lv.E * nloc, 0.0);
+    lv.mass.assign(lv.N, 0.0);
+    Geo geo{d, p, n1, nloc, &lv};
+    std::vector<double> X((size_t)d * nloc);
+    for (long long e = 0; e < lv.E; ++e) {
+        int ec[3];
+        element_coords(lv, e, ec);
+        for (int q = 0; q < nloc; ++q) {
+            int lc[3];
+            local_coords(q, n1, d, lc);
+            long long g = geo.gnode(ec, lc);
+            for (int b = 0; b < d; ++b) X[(size_t)b * nloc + q] = lv.coords[(size_t)b * lv.N + g];
+        }
+        for (int q = 0; q < nloc; ++q) {
+            int lc[3];
+            local_coords(q, n1, d, lc);
+            double Jm[3][3] = {{0}};   // Jm[b][a] = dx_b / dr_a
+            for (int a = 0; a < d; ++a) {
+                for (int m = 0; m < n1; ++m) {
+                    int mc[3] = {lc[0], lc[1], lc[2]};
+                    mc[a] = m;
+                    int qm = local_index(mc, n1);
+                    double dm = lv.D[lc[a] * n1 + m];
+                    for (int b = 0; b < d; ++b) Jm[b][a] += dm * X[(size_t)b * nloc + qm];
+                }
+            }
+            double det, inv[3][3];   // inv[a][c] = dr_a / dx_c
+            if (d == 2) {
+                det = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+                inv[0][0] = Jm[1][1] / det;  inv[0][1] = -Jm[0][1] / det;
+                inv[1][0] = -Jm[1][0] / det; inv[1][1] = Jm[0][0] / det;
+            } else {
+                double c00 = Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1];
+                double c01 = Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2];
+                double c02 = Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0];
+                det = Jm[0][0] * c00 + Jm[0][1] * c01 + Jm[0][2] * c02;
+                // inverse = adjugate / det; adj[a][c] = cofactor[c][a]
+                inv[0][0] = c00 / det;
+                inv[1][0] = c01 / det;
+                inv[2][0] = c02 / det;
+                inv[0][1] = (Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2]) / det;
+                inv[1][1] = (Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0]) / det;
+                inv[2][1] = (Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1]) / det;
+                inv[0][2] = (Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1]) / det;
+                inv[1][2] = (Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2]) / det;
+                inv[2][2] = (Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0]) / det;
+            }
+            if (!(det > 0.0)) {
+                std::ostringstream os;
+                os << "non-positive Jacobian " << det << " in element " << e << " (order " << p << ")";
+                return os.str();
+            }
+            double w = 1.0;
+            for (int a = 0; a < d; ++a) w *= w1[lc[a]];
+            for (int a = 0; a < d; ++a)
+                for (int b = a; b < d; ++b) {
+                    double s = 0.0;
+                    for (int c = 0; c < d; ++c) s += inv[a][c] * inv[b][c];
+                    lv.G[(size_t)comp_index(d, a, b) * lv.E * nloc + (size_t)e * nloc + q] = w * det * s;
+                }
+            lv.mass[geo.gnode(ec, lc)] += w * det;
+        }
+    }
+    return "";
+}
+
+inline double Gc(const LevelHost& lv, int a, int b, long long e, int q) {
+    return lv.G[(size_t)comp_index(lv.dim, a, b) * lv.E * lv.nloc + (size_t)e * lv.nloc + q];
+}
+
+// Band-1 entries of the assembled GLL stiffness (eq. discreteBilinear with
+// the nodal basis): diagonal and couplings to the next node along each axis.
+void gll_band(LevelHost& lv) {
+    const int d = lv.dim, p = lv.p, n1 = p + 1, nloc = lv.nloc;
+    const std::vector<double>& D = lv.D;
+    lv.diag.assign(lv.N, 0.0);
+    for (int s = 0; s < 3; ++s) lv.off[s].assign(lv.N, 0.0);
+    Geo geo{d, p, n1, nloc, &lv};
+    for (long long e = 0; e < lv.E; ++e) {
+        int ec[3];
+        element_coords(lv, e, ec);
+        for (int q = 0; q < nloc; ++q) {
+            int lc[3];
+            local_coords(q, n1, d, lc);
+            double v = 0.0;
+            for (int a = 0; a < d; ++a) {
+                for (int k = 0; k < n1; ++k) {       // sum over quadrature points along a
+                    int qc[3] = {lc[0], lc[1], lc[2]};
+                    qc[a] = k;
+                    double Dk = D[k * n1 + lc[a]];
+                    v += Gc(lv, a, a, e, local_index(qc, n1)) * Dk * Dk;
+                }
+                for (int b = 0; b < d; ++b)
+                    if (b != a) v += Gc(lv, a, b, e, q) * D[lc[a] * n1 + lc[a]] * D[lc[b] * n1 + lc[b]];
+            }
+            long long g = geo.gnode(ec, lc);
+            lv.diag[g] += v;
+            for (int s = 0; s < d; ++s) {
+                if (lc[s] == p) continue;
+                const int ms = lc[s];
+                double o = 0.0;
+                for (int k = 0; k < n1; ++k) {
+                    int qc[3] = {lc[0], lc[1], lc[2]};
+                    qc[s] = k;
+                    o += Gc(lv, s, s, e, local_index(qc, n1)) * D[k * n1 + ms] * D[k * n1 + ms + 1];
+                }
+                int up[3] = {lc[0], lc[1], lc[2]};
+                up[s] = ms + 1;
+                int qup = local_index(up, n1);
+                for (int b = 0; b < d; ++b) {
+                    if (b == s) continue;
+                    double Dbb = D[lc[b] * n1 + lc[b]];
+                    o += Gc(lv, s, b, e, qup) * D[(ms + 1) * n1 + ms] * Dbb;
+                    o += Gc(lv, b, s, e, q) * Dbb * D[ms * n1 + ms + 1];
+                }
+                lv.off[s][g] += o;
+            }
+        }
+    }
+}
+
+// Band-1 entries of the bilinear (trilinear) FEM matrix on the mesh of GLL
+// nodes, each cell a Q1 element on its physical vertices, 2-point Gauss rule.
+void fem_band(LevelHost& lv) {
+    const int d = lv.dim;
+    lv.diag.assign(lv.N, 0.0);
+    for (int s = 0; s < 3; ++s) lv.off[s].assign(lv.N, 0.0);
+    const int nc = 1 << d;
+    const double gp[2] = {-1.0 / std::sqrt(3.0), 1.0 / std::sqrt(3.0)};
+    int cn[3] = {lv.n[0] - 1, lv.n[1] - 1, d == 3 ? lv.n[2] - 1 : 1};
+    for (int ck = 0; ck < cn[2]; ++ck)
+        for (int cj = 0; cj < cn[1]; ++cj)
+            for (int ci = 0; ci < cn[0]; ++ci) {
+                long long node[8];
+                double X[3][8];
+                for (int c = 0; c < nc; ++c) {
+                    int o0 = c & 1, o1 = (c >> 1) & 1, o2 = (c >> 2) & 1;
+                    long long g = ((long long)(ck + o2) * lv.n[1] + (cj + o1)) * lv.n[0] + (ci + o0);
+                    node[c] = g;
+                    for (int b = 0; b < d; ++b) X[b][c] = lv.coords[(size_t)b * lv.N + g];
+                }
+                double K[8][8] = {{0}};
+                for (int qp = 0; qp < nc; ++qp) {
+                    double r[3] = {gp[qp & 1], gp[(qp >> 1) & 1], gp[(qp >> 2) & 1]};
+                    double dN[8][3];
+                    for (int c = 0; c < nc; ++c) {
+                        double sgn[3] = {(c & 1) ? 1.0 : -1.0, ((c >> 1) & 1) ? 1.0 : -1.0, ((c >> 2) & 1) ? 1.0 : -1.0};
+                        for (int t = 0; t < d; ++t) {
+                            double v = 0.5 * sgn[t];
+                            for (int t2 = 0; t2 < d; ++t2)
+                                if (t2 != t) v *= 0.5 * (1.0 + sgn[t2] * r[t2]);
+                            dN[c][t] = v;
+                        }
+                    }
+                    double Jm[3][3] = {{0}};
+                    for (int b = 0; b < d; ++b)
+                        for (int t = 0; t < d; ++t)
+                            for (int c = 0; c < nc; ++c) Jm[b][t] += X[b][c] * dN[c][t];
+                    double det, inv[3][3];
+                    if (d == 2) {
+                        det = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+                        inv[0][0] = Jm[1][1] / det;  inv[0][1] = -Jm[0][1] / det;
+                        inv[1][0] = -Jm[1][0] / det; inv[1][1] = Jm[0][0] / det;
+                    } else {
+                        double c00 = Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1];
+                        double c01 = Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2];
+                        double c02 = Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0];
+                        det = Jm[0][0] * c00 + Jm[0][1] * c01 + Jm[0][2] * c02;
+                        inv[0][0] = c00 / det; inv[1][0] = c01 / det; inv[2][0] = c02 / det;
+                        inv[0][1] = (Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2]) / det;
+                        inv[1][1] = (Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0]) / det;
+                        inv[2][1] = (Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1]) / det;
+                        inv[0][2] = (Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1]) / det;
+                        inv[1][2] = (Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2]) / det;
+                        inv[2][2] = (Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0]) / det;
+                    }
+                    double gx[8][3];
+                    for (int c = 0; c < nc; ++c)
+                        for (int b = 0; b < d; ++b) {
+                            double v = 0.0;
+                            for (int t = 0; t < d; ++t) v += dN[c][t] * inv[t][b];
+                            gx[c][b] = v;
+                        }
+                    for (int c = 0; c < nc; ++c)
+                        for (int c2 = 0; c2 < nc; ++c2) {
+                            double v = 0.0;
+                            for (int b = 0; b < d; ++b) v += gx[c][b] * gx[c2][b];
+                            K[c][c2] += v * std::fabs(det);
+                        }
+                }
+                for (int c = 0; c < nc; ++c) {
+                    lv.diag[node[c]] += K[c][c];
+                    for (int s = 0; s < d; ++s)
+                        if (!((c >> s) & 1)) lv.off[s][node[c]] += K[c][c | (1 << s)];
+                }
+            }
+}
+
+}  // namespace
+
+std::vector<double> gll_nodes(int p, std::vector<double>* weights) {
+    std::vector<double> xi(p + 1);
+    xi[0] = -1.0;
+    xi[p] = 1.0;
+    const double pi = 3.14159265358979323846;
+    for (int n = 1; n < p; ++n) {
+        double x = -std::cos(pi * n / p);
+        for (int it = 0; it < 100; ++it) {
+            double L, dL;
+            legendre(p, x, &L, &dL);
+            // Newton on L_p'(x); L_p'' from Legendre's equation
+            double d2L = (2.0 * x * dL - p * (p + 1.0) * L) / (1.0 - x * x);
+            double step = dL / d2L;
+            x -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        xi[n] = x;
+    }
+    if (weights) {
+        weights->assign(p + 1, 0.0);
+        for (int n = 0; n <= p; ++n) {
+            double L, dL;
+            legendre(p, xi[n], &L, &dL);
+            (*weights)[n] = 2.0 / (p * (p + 1.0) * L * L);
+        }
+    }
+    return xi;
+}
+
+// D[i][j] = pi_j'(xi_i) from the closed form in Legendre values:
+// L_p(xi_i) / (L_p(xi_j) (xi_i - xi_j)) off the diagonal, -+p(p+1)/4 at the ends.
+std::vector<double> derivative_matrix(int p) {
+    std::vector<double> xi = gll_nodes(p, nullptr);
+    std::vector<double> L(p + 1);
+    for (int i = 0; i <= p; ++i) {
+        double dl;
+        legendre(p, xi[i], &L[i], &dl);
+    }
+    std::vector<double> D((p + 1) * (p + 1), 0.0);
+    for (int i = 0; i <= p; ++i)
+        for (int j = 0; j <= p; ++j)
+            if (i != j) D[i * (p + 1) + j] = L[i] / (L[j] * (xi[i] - xi[j]));
+    D[0] = -p * (p + 1) / 4.0;
+    D[p * (p + 1) + p] = p * (p + 1) / 4.0;
+    return D;
+}
+
+std::vector<double> interpolation(int p_from, int p_to) {
+    std::vector<double> xf = gll_nodes(p_from, nullptr), xt = gll_nodes(p_to, nullptr);
+    std::vector<double> J((p_to + 1) * (p_from + 1));
+    for (int i = 0; i <= p_to; ++i)
+        for (int k = 0; k <= p_from; ++k) {
+            double v = 1.0;
+            for (int m = 0; m <= p_from; ++m)
+                if (m != k) v *= (xt[i] - xf[m]) / (xf[k] - xf[m]);
+            J[i * (p_from + 1) + k] = v;
+        }
+    return J;
+}
+
+std::vector<int> order_chain(int p_fine, bool multi) {
+    int p0 = multi ? 1 : 2;
+    std::vector<int> c{p_fine};
+    while (c.back() > p0) c.push_back(std::max(p0, c.back() / 2));
+    return c;
+}
+
+std::string build_levels(int dim, const int nelem[3], int p_fine, const double* coords,
+                         int smoother, int restriction, std::vector<LevelHost>& levels) {
+    bool multi = nelem[0] > 1 || nelem[1] > 1 || (dim == 3 && nelem[2] > 1);
+    std::vector<int> chain = order_chain(p_fine, multi);
+    levels.assign(chain.size(), LevelHost());
+    // fill from fine (back) to coarse (front)
+    for (size_t c = 0; c < chain.size(); ++c) {
+        LevelHost& lv = levels[chain.size() - 1 - c];
+        lv.dim = dim;
+        lv.p = chain[c];
+        lv.N = 1;
+        lv.E = 1;
+        for (int a = 0; a < 3; ++a) {
+            lv.ne[a] = a < dim ? nelem[a] : 1;
+            lv.n[a] = a < dim ? nelem[a] * lv.p + 1 : 1;
+            lv.N *= lv.n[a];
+            lv.E *= lv.ne[a];
+        }
+        lv.nloc = 1;
+        for (int a = 0; a < dim; ++a) lv.nloc *= lv.p + 1;
+        lv.ncomp = dim == 2 ? 3 : 6;
+        lv.coords.assign((size_t)dim * lv.N, 0.0);
+        if (c == 0) {
+            std::memcpy(lv.coords.data(), coords, sizeof(double) * dim * lv.N);
+        } else {
+            // coarse nodes: the finer element's coordinate polynomial at coarse GLL points
+            const LevelHost& f = levels[chain.size() - c];
+            const int pf = f.p, pc = lv.p, n1f = pf + 1, n1c = pc + 1;
+            std::vector<double> J = interpolation(pf, pc);   // [(pc+1) x (pf+1)]
+            for (long long e = 0; e < lv.E; ++e) {
+                int ec[3];
+                element_coords(lv, e, ec);
+                for (int qc = 0; qc < lv.nloc; ++qc) {
+                    int lc[3];
+                    local_coords(qc, n1c, dim, lc);
+                    long long gc = ((long long)(dim == 3 ? ec[2] * pc + lc[2] : 0) * lv.n[1] + ec[1] * pc + lc[1]) * lv.n[0] + ec[0] * pc + lc[0];
+                    for (int b = 0; b < dim; ++b) {
+                        double v = 0.0;
+                        for (int qf = 0; qf < f.nloc; ++qf) {
+                            int lf[3];
+                            local_coords(qf, n1f, dim, lf);
+                            double wgt = J[lc[0] * n1f + lf[0]] * J[lc[1] * n1f + lf[1]];
+                            if (dim == 3) wgt *= J[lc[2] * n1f + lf[2]];
+                            if (wgt == 0.0) continue;
+                            long long gf = ((long long)(dim == 3 ? ec[2] * pf + lf[2] : 0) * f.n[1] + ec[1] * pf + lf[1]) * f.n[0] + ec[0] * pf + lf[0];
+                            v += wgt * f.coords[(size_t)b * f.N + gf];
+                        }
+                        lv.coords[(size_t)b * lv.N + gc] = v;
+                    }
+                }
+            }
+        }
+        std::string err = geometry(lv);
+        if (!err.empty()) return err;
+        if (smoother == 0) gll_band(lv); else fem_band(lv);
+    }
+    // transfers between consecutive levels
+    for (size_t l = 1; l < levels.size(); ++l) {
+        LevelHost& f = levels[l];
+        const LevelHost& c = levels[l - 1];
+        for (int a = 0; a < dim; ++a) {
+            std::vector<double> P = global_interp(f.ne[a], c.p, f.p);     // n_f x n_c
+            int nf = f.n[a], ncn = c.n[a];
+            f.P[a] = to_band(P, nf, ncn);
+            std::vector<double> R((size_t)ncn * nf);
+            if (restriction == 0) {
+                for (int i = 0; i < nf; ++i)
+                    for (int k = 0; k < ncn; ++k) R[(size_t)k * nf + i] = P[(size_t)i * ncn + k];
+            } else {
+                R = global_interp(f.ne[a], f.p, c.p);                     // n_c x n_f
+            }
+            f.R[a] = to_band(R, ncn, nf);
+        }
+    }
+    return "";
+}
+
+// Dense inverse of the interior block of A_0 (assembled from element
+// matrices), via a banded Cholesky factorisation and one solve per column.
+std::string build_coarse(const LevelHost& lv, CoarseHost& out) {
+    const int d = lv.dim, p = lv.p, n1 = p + 1, nloc = lv.nloc;
+    std::vector<long long> id(lv.N, -1);
+    out.index.clear();
+    for (long long g = 0; g < lv.N; ++g) {
+        long long I = g % lv.n[0], J = (g / lv.n[0]) % lv.n[1], K = g / ((long long)lv.n[0] * lv.n[1]);
+        bool inner = I > 0 && I < lv.n[0] - 1 && J > 0 && J < lv.n[1] - 1 && (d == 2 || (K > 0 && K < lv.n[2] - 1));
+        if (inner) { id[g] = (long long)out.index.size(); out.index.push_back(g); }
+    }
+    const long long n = (long long)out.index.size();
+    out.n = n;
+    if (n == 0) return "coarsest level has no interior unknowns";
+    // half bandwidth in the interior numbering
+    long long bw = 0;
+    Geo geo{d, p, n1, nloc, &lv};
+    std::vector<double> A((size_t)n * n, 0.0);
+    const std::vector<double>& D = lv.D;
+    for (long long e = 0; e < lv.E; ++e) {
+        int ec[3];
+        element_coords(lv, e, ec);
+        for (int m = 0; m < nloc; ++m) {
+            int mc[3];
+            local_coords(m, n1, d, mc);
+            long long gm = id[geo.gnode(ec, mc)];
+            if (gm < 0) continue;
+            for (int m2 = 0; m2 < nloc; ++m2) {
+                int mc2[3];
+                local_coords(m2, n1, d, mc2);
+                long long gm2 = id[geo.gnode(ec, mc2)];
+                if (gm2 < 0) continue;
+                // A_e[m][m2] = sum_q sum_ab G_ab(q) B_a(q, m) B_b(q, m2)
+                double v = 0.0;
+                for (int q = 0; q < nloc; ++q) {
+                    int qc[3];
+                    local_coords(q, n1, d, qc);
+                    for (int a = 0; a < d; ++a) {
+                        bool oka = true;
+                        for (int c = 0; c < d; ++c) if (c != a && qc[c] != mc[c]) oka = false;
+                        if (!oka) continue;
+                        double Ba = D[qc[a] * n1 + mc[a]];
+                        for (int b = 0; b < d; ++b) {
+                            bool okb = true;
+                            for (int c = 0; c < d; ++c) if (c != b && qc[c] != mc2[c]) okb = false;
+                            if (!okb) continue;
+                            v += Gc(lv, a, b, e, q) * Ba * D[qc[b] * n1 + mc2[b]];
+                        }
+                    }
+                }
+                A[(size_t)gm * n + gm2] += v;
+                bw = std::max(bw, std::llabs(gm - gm2));
+            }
+        }
+    }
+    // banded Cholesky A = L L^T, L stored dense (lower band used)
+    std::vector<double> L((size_t)n * n, 0.0);
+    for (long long j = 0; j < n; ++j) {
+        long long k0 = std::max(0LL, j - bw);
+        double s = A[(size_t)j * n + j];
+        for (long long k = k0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        if (!(s > 0.0)) return "coarsest-level matrix is not positive definite";
+        double ljj = std::sqrt(s);
+        L[(size_t)j * n + j] = ljj;
+        for (long long i = j + 1; i <= std::min(n - 1, j + bw); ++i) {
+            double t = A[(size_t)i * n + j];
+            long long kk = std::max(k0, i - bw);
+            for (long long k = kk; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = t / ljj;
+        }
+    }
+    out.inv.assign((size_t)n * n, 0.0);
+    std::vector<double> y(n);
+    for (long long c = 0; c < n; ++c) {
+        // forward L y = e_c
+        std::fill(y.begin(), y.end(), 0.0);
+        for (long long i = c; i < n; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (long long k = std::max(c, i - bw); k < i; ++k) t -= L[(size_t)i * n + k] * y[k];
+            y[i] = t / L[(size_t)i * n + i];
+        }
+        // backward L^T x = y
+        for (long long i = n - 1; i >= 0; --i) {
+            double t = y[i];
+            for (long long k = i + 1; k <= std::min(n - 1, i + bw); ++k) t -= L[(size_t)k * n + i] * y[k];
+            y[i] = t / L[(size_t)i * n + i];
+        }
+        for (long long i = 0; i < n; ++i) out.inv[(size_t)i * n + c] = y[i];
+    }
+    return "";
+}
+
+}  // namespace glls

@@ -1,0 +1,52 @@
+// Host-side (FP64) construction of the level data of the GLL p-multigrid
+// solver: GLL tables, isoparametric geometry factors, band-1 line systems,
+// transfer operators and the coarsest-level factor.  Runs once per problem.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace glls {
+
+// Row-banded matrix: out[r] = sum_k coef[r*width + k] * in[start[r] + k].
+struct Band1D {
+    int rows = 0, cols = 0, width = 0;
+    std::vector<int> start;
+    std::vector<double> coef;
+};
+
+struct LevelHost {
+    int dim = 2, p = 1;
+    int ne[3] = {1, 1, 1};     // elements per axis
+    int n[3] = {1, 1, 1};      // nodes per axis (ne * p + 1)
+    long long N = 0;           // total nodes
+    long long E = 0;           // total elements
+    int nloc = 0;              // (p+1)^dim
+    int ncomp = 0;             // geometry components: 3 (2-D) or 6 (3-D)
+    std::vector<double> coords;   // [dim][N]
+    std::vector<double> G;        // [ncomp][E * nloc], element-major
+    std::vector<double> mass;     // [N] assembled diagonal mass
+    std::vector<double> diag;     // [N] line-system diagonal (A or A~)
+    std::vector<double> off[3];   // [N] line-system coupling node -> node + e_s
+    std::vector<double> D;        // (p+1)^2, D[i*(p+1)+j] = pi_j'(xi_i)
+    Band1D P[3];                  // prolongation (this level <- level-1), per axis
+    Band1D R[3];                  // restriction  (this level -> level-1), per axis
+};
+
+struct CoarseHost {
+    long long n = 0;                 // interior unknowns
+    std::vector<long long> index;    // interior node index (level-0 grid) per unknown
+    std::vector<double> inv;         // dense A_0^-1, n x n row-major
+};
+
+std::vector<double> gll_nodes(int p, std::vector<double>* weights);
+std::vector<double> derivative_matrix(int p);
+std::vector<double> interpolation(int p_from, int p_to);   // [(p_to+1) x (p_from+1)]
+std::vector<int> order_chain(int p_fine, bool multi_element);
+
+// Builds all levels (index 0 = coarsest).  Returns "" on success or an error message.
+std::string build_levels(int dim, const int nelem[3], int p_fine, const double* coords,
+                         int smoother, int restriction, std::vector<LevelHost>& levels);
+std::string build_coarse(const LevelHost& lv0, CoarseHost& out);
+
+}  // namespace glls

@@ -1,0 +1,236 @@
+"""Python binding of the C ABI in ``include/glls.h`` (ctypes; argument
+marshalling only).  Every step of the solver runs in ``libglls.so``; if the
+library is missing this module raises instead of falling back to anything.
+
+Device vectors are passed as torch CUDA tensors (their data pointers) and
+streams as ``torch.cuda.Stream`` objects or raw handles.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libglls.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 0, -1, -2, -3, -4, -5
+PREC_FP64, PREC_MIXED = 0, 1
+SMOOTHER_GLL, SMOOTHER_FEM = 0, 1
+RESTRICT_TRANSPOSE, RESTRICT_INTERP = 0, 1
+KRYLOV_FCG, KRYLOV_PCG = 0, 1
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nelem", C.c_int * 3), ("order", C.c_int),
+                ("coords", C.POINTER(C.c_double)), ("smoother", C.c_int), ("restriction", C.c_int),
+                ("device", C.c_int)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("gamma", C.c_int), ("m", C.c_int),
+                ("alpha", C.c_double), ("precision", C.c_int), ("krylov", C.c_int), ("use_graph", C.c_int),
+                ("check_every", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("setup_ms", C.c_double),
+                ("solve_ms", C.c_double), ("status", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("dim", C.c_int), ("levels", C.c_int), ("order", C.c_int * 8), ("nodes", (C.c_int * 3) * 8),
+                ("ndof", C.c_longlong * 8), ("coarse_unknowns", C.c_longlong), ("device_bytes", C.c_size_t)]
+
+
+class GllsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"glls status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                              "(the solver has no fallback path)")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        sig = {
+            "glls_gll": [i, C.POINTER(d), C.POINTER(d)],
+            "glls_problem_create": [C.POINTER(MeshDesc), C.POINTER(vp)],
+            "glls_problem_info": [vp, C.POINTER(Info)],
+            "glls_set_dirichlet": [vp, vp, i, vp],
+            "glls_set_rhs": [vp, vp, i, vp],
+            "glls_solve": [vp, C.POINTER(SolveOpts), vp, i, vp, C.POINTER(Stats)],
+            "glls_lift_f64": [vp, vp, vp, vp, vp],
+        }
+        for suf, real in (("f64", d), ("f32", C.c_float)):
+            sig[f"glls_apply_{suf}"] = [vp, i, vp, vp, vp]
+            sig[f"glls_line_solve_{suf}"] = [vp, i, i, vp, vp, vp]
+            sig[f"glls_smooth_{suf}"] = [vp, i, i, real, vp, vp, vp]
+            sig[f"glls_restrict_{suf}"] = [vp, i, vp, vp, vp, vp]
+            sig[f"glls_prolong_add_{suf}"] = [vp, i, vp, vp, vp]
+            sig[f"glls_coarse_solve_{suf}"] = [vp, vp, vp, vp]
+            sig[f"glls_precondition_{suf}"] = [vp, C.POINTER(SolveOpts), vp, vp, vp]
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.glls_problem_destroy.argtypes = [vp]
+        L.glls_problem_destroy.restype = None
+        L.glls_last_error.argtypes = []
+        L.glls_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        raise GllsError(status, lib().glls_last_error().decode())
+    return status
+
+
+def _ptr(t):
+    """Data pointer of a torch tensor (or None)."""
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def gll(p: int):
+    xi = (C.c_double * (p + 1))()
+    rho = (C.c_double * (p + 1))()
+    _check(lib().glls_gll(p, xi, rho))
+    return np.array(xi[:]), np.array(rho[:])
+
+
+def opts(tol=1e-10, max_iter=200, gamma=1, m=1, alpha=0.5, precision=PREC_MIXED, krylov=KRYLOV_FCG,
+         use_graph=1, check_every=1) -> SolveOpts:
+    return SolveOpts(tol, max_iter, gamma, m, alpha, precision, krylov, use_graph, check_every)
+
+
+class Problem:
+    """Owns a ``glls_problem``: mesh levels resident on the device."""
+
+    def __init__(self, dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE,
+                 device=0):
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        ne = (C.c_int * 3)(*(list(nelem) + [1] * (3 - len(nelem))))
+        self._coords = coords
+        desc = MeshDesc(dim, ne, order, coords.ctypes.data_as(C.POINTER(C.c_double)), smoother, restriction,
+                        device)
+        h = C.c_void_p()
+        _check(lib().glls_problem_create(C.byref(desc), C.byref(h)))
+        self.h = h
+        self.dim = dim
+        self.info = self._info()
+        self.N = int(self.info.ndof[self.info.levels - 1])
+
+    def _info(self):
+        inf = Info()
+        _check(lib().glls_problem_info(self.h, C.byref(inf)))
+        return inf
+
+    @property
+    def levels(self):
+        return self.info.levels
+
+    def level_shape(self, level):
+        n = self.info.nodes[level]
+        return tuple(n[a] for a in reversed(range(self.dim)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().glls_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- data ------------------------------------------------------------
+    def set_rhs(self, f, stream=None):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            _check(lib().glls_set_rhs(self.h, f.ctypes.data_as(C.c_void_p), 0, _stream(stream)))
+        else:
+            _check(lib().glls_set_rhs(self.h, _ptr(f), 1, _stream(stream)))
+
+    def set_dirichlet(self, g, stream=None):
+        if isinstance(g, np.ndarray):
+            g = np.ascontiguousarray(g, dtype=np.float64)
+            _check(lib().glls_set_dirichlet(self.h, g.ctypes.data_as(C.c_void_p), 0, _stream(stream)))
+        else:
+            _check(lib().glls_set_dirichlet(self.h, _ptr(g), 1, _stream(stream)))
+
+    def solve(self, out, o: SolveOpts, stream=None, raise_on_error=True):
+        """Solve into ``out`` (numpy float64 host array or torch CUDA float64
+        tensor).  Returns the Stats structure."""
+        st = Stats()
+        if isinstance(out, np.ndarray):
+            assert out.dtype == np.float64 and out.flags.c_contiguous
+            status = lib().glls_solve(self.h, C.byref(o), out.ctypes.data_as(C.c_void_p), 0, _stream(stream),
+                                      C.byref(st))
+        else:
+            status = lib().glls_solve(self.h, C.byref(o), _ptr(out), 1, _stream(stream), C.byref(st))
+        if raise_on_error:
+            _check(status)
+        return st
+
+    # ---- level operations (device tensors) -------------------------------
+    @staticmethod
+    def _suffix(t):
+        import torch
+        return "f64" if t.dtype == torch.float64 else "f32"
+
+    def apply(self, level, x, y, stream=None):
+        _check(getattr(lib(), f"glls_apply_{self._suffix(x)}")(self.h, level, _ptr(x), _ptr(y), _stream(stream)))
+
+    def line_solve(self, level, axis, g, x, stream=None):
+        _check(getattr(lib(), f"glls_line_solve_{self._suffix(g)}")(self.h, level, axis, _ptr(g), _ptr(x),
+                                                                       _stream(stream)))
+
+    def smooth(self, level, axis, alpha, r, x, stream=None):
+        _check(getattr(lib(), f"glls_smooth_{self._suffix(r)}")(self.h, level, axis, alpha, _ptr(r), _ptr(x),
+                                                                   _stream(stream)))
+
+    def restrict(self, level, r, x, rc, stream=None):
+        _check(getattr(lib(), f"glls_restrict_{self._suffix(r)}")(self.h, level, _ptr(r), _ptr(x), _ptr(rc),
+                                                                     _stream(stream)))
+
+    def prolong_add(self, level, e, x, stream=None):
+        _check(getattr(lib(), f"glls_prolong_add_{self._suffix(e)}")(self.h, level, _ptr(e), _ptr(x),
+                                                                        _stream(stream)))
+
+    def coarse_solve(self, r, e, stream=None):
+        _check(getattr(lib(), f"glls_coarse_solve_{self._suffix(r)}")(self.h, _ptr(r), _ptr(e), _stream(stream)))
+
+    def precondition(self, o: SolveOpts, r, z, stream=None):
+        _check(getattr(lib(), f"glls_precondition_{self._suffix(r)}")(self.h, C.byref(o), _ptr(r), _ptr(z),
+                                                                         _stream(stream)))
+
+    def lift(self, f, g, f0, stream=None):
+        _check(lib().glls_lift_f64(self.h, _ptr(f), _ptr(g), _ptr(f0), _stream(stream)))
+
+
+def problem_for(workload, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0):
+    """Problem of a workload description, with nodes placed at the library's
+    own GLL points."""
+    xi, _ = gll(workload.order)
+    coords = workload.coords(xi)
+    return Problem(workload.dim, workload.nelem, workload.order, coords, smoother, restriction, device), coords
