@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only the warm-up and timed mixed-precision solves (for an ncu launch list)")
     return ap.parse_args()
 
 
@@ -155,6 +157,9 @@ def run_ours(args, rank, world):
 
     clocks = ClockSampler(dev)
     ms_mixed, its_mixed, clk = timed(glls.PREC_MIXED, args.steps, args.warmup, clocks)
+    if args.profile:
+        print(json.dumps({"profile": True, "ms_per_step": ms_mixed, "iterations": its_mixed}))
+        sys.exit(0)
     ms_fp64, its_fp64, _ = timed(glls.PREC_FP64, max(3, args.steps // 2), 2)
     u_mixed = np.zeros(N)
     prob.solve(u_mixed, glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED))

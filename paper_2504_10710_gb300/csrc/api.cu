@@ -63,6 +63,7 @@ struct glls_problem {
     const double* mass = nullptr;
     double *xk = nullptr, *rk = nullptr, *pk = nullptr, *qk = nullptr, *zk = nullptr, *yk = nullptr;
     double *S = nullptr, *part = nullptr, *hostS = nullptr;
+    unsigned* ticket = nullptr;
     float *r32 = nullptr, *z32 = nullptr;
     std::vector<void*> allocs;
     size_t bytes = 0;
@@ -270,12 +271,11 @@ void outer_iteration(glls_problem* P, const glls_solve_opts* o, cudaStream_t st)
     const int L = (int)P->L64.size() - 1;
     const long long N = P->N;
     precondition_outer(P, o, P->rk, P->zk, st);
-    launch_dots(P->rk, P->zk, P->zk, P->qk, 2, N, P->part, P->S, S_RZNEW, S_ZQ, st);
-    launch_fcg_direction(P->pk, P->zk, N, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, st);
-    launch_fcg_rotate(P->S, st);
+    launch_dots(P->rk, P->zk, P->zk, P->qk, 2, N, P->part, P->S, S_RZNEW, S_ZQ, P->ticket, st);
+    launch_fcg_direction(P->pk, P->zk, N, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, P->ticket, st);
     launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st);
-    launch_dots(P->pk, P->qk, nullptr, nullptr, 1, N, P->part, P->S, S_PQ, S_PQ, st);
-    launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, P->part, P->S, st);
+    launch_dots(P->pk, P->qk, nullptr, nullptr, 1, N, P->part, P->S, S_PQ, S_PQ, P->ticket, st);
+    launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, P->part, P->S, P->ticket, st);
 }
 
 glls_status get_iteration_graph(glls_problem* P, const glls_solve_opts* o) {
@@ -352,6 +352,8 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
                                    desc->restriction, H);
     if (!err.empty()) return fail(GLLS_ERR_BREAKDOWN, err);
     for (auto& h : H) {
+        if (h.N > 2147483647LL || h.E * h.nloc * h.ncomp > 2147483647LL)
+            return fail(GLLS_ERR_INVALID, "problem too large for 32-bit node indexing");
         P->orders.push_back(h.p);
         for (long long i = 0; i < h.N; ++i) {
             // zero pivots would break cyclic reduction without pivoting
@@ -373,11 +375,21 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
     if (st != GLLS_OK) return st;
     P->C64.n = C.n;
     P->C32.n = C.n;
+    P->C64.ld = (C.n + 1) / 2 * 2;     // 16-byte rows for double2 loads
+    P->C32.ld = (C.n + 3) / 4 * 4;     // 16-byte rows for float4 loads
     CK(P->upload(&P->C64.index, C.index));
     P->C32.index = P->C64.index;
-    CK(P->upload(&P->C64.inv, C.inv));
-    CK(P->upload(&P->C32.inv, C.inv));
-    if ((size_t)C.n * sizeof(double) > kMaxDynSmemBytes)
+    {
+        std::vector<double> pad64((size_t)C.n * P->C64.ld, 0.0), pad32((size_t)C.n * P->C32.ld, 0.0);
+        for (long long i = 0; i < C.n; ++i)
+            for (long long j = 0; j < C.n; ++j) {
+                pad64[(size_t)i * P->C64.ld + j] = C.inv[(size_t)i * C.n + j];
+                pad32[(size_t)i * P->C32.ld + j] = C.inv[(size_t)i * C.n + j];
+            }
+        CK(P->upload(&P->C64.inv, pad64));
+        CK(P->upload(&P->C32.inv, pad32));
+    }
+    if ((size_t)P->C64.ld * sizeof(double) > kMaxDynSmemBytes)
         return fail(GLLS_ERR_INVALID, "coarsest level too large for the dense coarse solver");
 
     const LevelHost& F = H.back();
@@ -392,6 +404,8 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
     }
     CK(P->alloc(&P->S, S_COUNT));
     CK(P->alloc(&P->part, 2 * kDotBlocks));
+    CK(P->alloc(&P->ticket, 1));
+    CK(cudaMemset(P->ticket, 0, sizeof(unsigned)));
     CK(P->alloc(&P->r32, N));
     CK(P->alloc(&P->z32, N));
     CK(cudaMallocHost(&P->hostS, sizeof(double) * S_COUNT));
@@ -483,7 +497,7 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
     init[S_RZ] = 1.0;
     std::memcpy(P->hostS, init, sizeof(init));
     CK(cudaMemcpyAsync(P->S, P->hostS, sizeof(init), cudaMemcpyHostToDevice, st));
-    launch_dots(P->rk, P->rk, nullptr, nullptr, 1, N, P->part, P->S, S_RR0, S_RR0, st);
+    launch_dots(P->rk, P->rk, nullptr, nullptr, 1, N, P->part, P->S, S_RR0, S_RR0, P->ticket, st);
     CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const double rr0 = P->hostS[S_RR0];

@@ -1,0 +1,142 @@
+// Stiffness apply y = A_l x (eq. discreteBilinear) specialised on the GLL
+// order P, so that local index arithmetic and the sum-factorisation loops are
+// resolved at compile time.  Per CTA: EPB elements; x gathered into shared
+// memory, reference gradients by 1-D contractions with D, pointwise G, the
+// transposed contractions, then element-interior nodes stored and shared
+// nodes summed with atomics (direct stiffness summation).  32-bit indexing.
+#include "device.cuh"
+
+namespace glls {
+namespace {
+
+__device__ __forceinline__ bool on_boundary32(int I, int J, int K, const int n[3], int dim) {
+    return I == 0 || I == n[0] - 1 || J == 0 || J == n[1] - 1 || (dim == 3 && (K == 0 || K == n[2] - 1));
+}
+
+template <typename T, int DIM, int P>
+__global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
+                                                      int mask) {
+    constexpr int N1 = P + 1;
+    constexpr int NLOC = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
+    constexpr int EPB = NLOC >= 256 ? 1 : 256 / NLOC;
+    __shared__ T sD[N1 * N1];
+    __shared__ T sx[EPB * NLOC];
+    __shared__ T sw[DIM * EPB * NLOC];
+    const int E = (int)L.E;
+    const int ne0 = L.ne[0], ne1 = L.ne[1], n0 = L.n[0], n1 = L.n[1];
+    const int EN = E * NLOC;
+    for (int t = threadIdx.x; t < N1 * N1; t += blockDim.x) sD[t] = L.D[t];
+    const int e0 = blockIdx.x * EPB;
+    const int total = min(EPB, E - e0) * NLOC;
+
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int el = t / NLOC, q = t - el * NLOC;
+        const int e = e0 + el;
+        const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
+        const int ex = e % ne0, ey = (e / ne0) % ne1, ez = DIM == 3 ? e / (ne0 * ne1) : 0;
+        sx[t] = x[((ez * P + k) * n1 + ey * P + j) * n0 + ex * P + i];
+    }
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int el = t / NLOC, q = t - el * NLOC;
+        const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
+        const T* xe = sx + el * NLOC;
+        T Di[N1], Dj[N1], Dk[DIM == 3 ? N1 : 1];
+#pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            Di[m] = sD[i * N1 + m];
+            Dj[m] = sD[j * N1 + m];
+            if (DIM == 3) Dk[DIM == 3 ? m : 0] = sD[k * N1 + m];
+        }
+        T g0 = T(0), g1 = T(0), g2 = T(0);
+#pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            g0 += Di[m] * xe[(k * N1 + j) * N1 + m];
+            g1 += Dj[m] * xe[(k * N1 + m) * N1 + i];
+            if (DIM == 3) g2 += Dk[DIM == 3 ? m : 0] * xe[(m * N1 + j) * N1 + i];
+        }
+        const int gq = (e0 + el) * NLOC + q;
+        if (DIM == 2) {
+            const T a00 = L.G[gq], a01 = L.G[EN + gq], a11 = L.G[2 * EN + gq];
+            sw[t] = a00 * g0 + a01 * g1;
+            sw[EPB * NLOC + t] = a01 * g0 + a11 * g1;
+        } else {
+            const T a00 = L.G[gq], a01 = L.G[EN + gq], a02 = L.G[2 * EN + gq];
+            const T a11 = L.G[3 * EN + gq], a12 = L.G[4 * EN + gq], a22 = L.G[5 * EN + gq];
+            sw[t] = a00 * g0 + a01 * g1 + a02 * g2;
+            sw[EPB * NLOC + t] = a01 * g0 + a11 * g1 + a12 * g2;
+            sw[2 * EPB * NLOC + t] = a02 * g0 + a12 * g1 + a22 * g2;
+        }
+    }
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int el = t / NLOC, q = t - el * NLOC;
+        const int e = e0 + el;
+        const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
+        const T* w0 = sw + el * NLOC;
+        const T* w1 = sw + EPB * NLOC + el * NLOC;
+        T Ti[N1], Tj[N1], Tk[DIM == 3 ? N1 : 1];
+#pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            Ti[m] = sD[m * N1 + i];
+            Tj[m] = sD[m * N1 + j];
+            if (DIM == 3) Tk[DIM == 3 ? m : 0] = sD[m * N1 + k];
+        }
+        T v = T(0);
+#pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            v += Ti[m] * w0[(k * N1 + j) * N1 + m];
+            v += Tj[m] * w1[(k * N1 + m) * N1 + i];
+            if (DIM == 3) v += Tk[DIM == 3 ? m : 0] * sw[2 * EPB * NLOC + el * NLOC + (m * N1 + j) * N1 + i];
+        }
+        const int ex = e % ne0, ey = (e / ne0) % ne1, ez = DIM == 3 ? e / (ne0 * ne1) : 0;
+        const int I = ex * P + i, J = ey * P + j, K = ez * P + k;
+        const int g = (K * n1 + J) * n0 + I;
+        const bool inner = i > 0 && i < P && j > 0 && j < P && (DIM == 2 || (k > 0 && k < P));
+        if (inner) {
+            y[g] = v;
+        } else {
+            if (mask && on_boundary32(I, J, K, L.n, DIM)) continue;
+            atomicAdd(&y[g], v);
+        }
+    }
+}
+
+template <typename T, int DIM, int P>
+void launch_p(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st) {
+    constexpr int N1 = P + 1;
+    constexpr int NLOC = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
+    constexpr int EPB = NLOC >= 256 ? 1 : 256 / NLOC;
+    const int blocks = (int)((L.E + EPB - 1) / EPB);
+    apply_p_kernel<T, DIM, P><<<blocks, 256, 0, st>>>(L, x, y, mask ? 1 : 0);
+}
+
+template <typename T, int DIM, int P>
+bool dispatch(int p, const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st) {
+    if constexpr (P == 0) {
+        return false;
+    } else {
+        if (p == P) {
+            launch_p<T, DIM, P>(L, x, y, mask, st);
+            return true;
+        }
+        return dispatch<T, DIM, P - 1>(p, L, x, y, mask, st);
+    }
+}
+
+}  // namespace
+
+// Returns false when the order has no specialisation (the caller falls back).
+template <typename T>
+bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st) {
+    if (L.N > (1LL << 31) - 1 || L.E * L.nloc * (L.dim == 2 ? 3 : 6) > (1LL << 31) - 1) return false;
+    if (L.dim == 2) return dispatch<T, 2, 16>(L.p, L, x, y, mask, st);
+    return dispatch<T, 3, 8>(L.p, L, x, y, mask, st);
+}
+
+template bool launch_apply_fixed<float>(const DevLevel<float>&, const float*, float*, bool, cudaStream_t);
+template bool launch_apply_fixed<double>(const DevLevel<double>&, const double*, double*, bool, cudaStream_t);
+
+}  // namespace glls

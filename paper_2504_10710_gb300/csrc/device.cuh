@@ -38,14 +38,24 @@ struct DevLevel {
 template <typename T>
 struct DevCoarse {
     long long n = 0;
+    long long ld = 0;                   // padded row length (multiple of 16 bytes)
     const long long* index = nullptr;   // interior node of each unknown
-    const T* inv = nullptr;             // dense n x n inverse, row-major
+    const T* inv = nullptr;             // dense n x n inverse, row-major, leading dimension ld
 };
 
 // Opt every kernel into up to 200 KB of dynamic shared memory (call once per
 // device, outside stream capture).
 bool init_kernel_attributes();
 constexpr size_t kMaxDynSmemBytes = 200 * 1024;
+
+// Specialised fast paths (apply.cu, lines.cu); they return false when the
+// case is outside their compiled range and the generic kernels take over.
+template <typename T>
+bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st);
+template <typename T>
+bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, const T* y, T* x, T alpha,
+                      cudaStream_t st);
+bool init_line_warp_attributes();
 
 // ---- launchers (all asynchronous on `st`) ---------------------------------
 // y = A x (y zeroed first); mask: zero boundary rows.
@@ -75,11 +85,13 @@ void launch_cast(const Ti* in, To* out, long long n, cudaStream_t st);
 template <typename T>
 void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st);
 
-// Deterministic dot products: partial sums per block into `part`
-// (ndots * nblocks), then a one-block finaliser writes S[slot[k]].
+// Deterministic dot products in one launch: partial sums per block into
+// `part` (ndots * nblocks); the last block adds them in block order into
+// S[slot0] (and S[slot1]).  `ticket` is a zero-initialised counter that the
+// kernel resets.
 constexpr int kDotBlocks = 304;   // 2 x 152 SMs
 void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots,
-                 long long n, double* part, double* S, int slot0, int slot1, cudaStream_t st);
+                 long long n, double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st);
 
 // Krylov scalar slots in the device array S.
 enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZNEW, S_ZQ, S_RR0, S_ALPHA, S_FLAG, S_TOL2, S_ITER, S_COUNT };
@@ -87,11 +99,11 @@ enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZNEW, S_ZQ, S_RR0, S_ALPHA, S_FLAG, S_TOL2,
 // q-independent update: alpha = S_RZ / S_PQ; x += alpha p; r -= alpha q;
 // then rr = r.r into S_RR (via part); flags breakdown in S_FLAG.
 void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, double* part,
-                       double* S, cudaStream_t st);
-// p = z + beta p with beta = -alpha S_ZQ / S_RZ (flexible) or S_RZNEW / S_RZ.
-void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, cudaStream_t st);
-// S_RZ <- S_RZNEW (after the direction update has consumed S_RZ)
-void launch_fcg_rotate(double* S, cudaStream_t st);
+                       double* S, unsigned* ticket, cudaStream_t st);
+// p = z + beta p with beta = -alpha S_ZQ / S_RZ (flexible) or S_RZNEW / S_RZ;
+// afterwards S_RZ <- S_RZNEW.
+void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, unsigned* ticket,
+                          cudaStream_t st);
 // f0 = M f - y on interior nodes (0 on the boundary); v = g on the boundary, 0 inside.
 void launch_lift_rhs(const double* mass, const double* f, const double* y, double* f0, const int n[3], int dim,
                      cudaStream_t st);

@@ -17,6 +17,7 @@
 #include "device.cuh"
 
 #include <cstdio>
+#include <type_traits>
 
 namespace glls {
 
@@ -213,26 +214,25 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs<T> A) {
 template <typename T>
 __global__ void transfer_kernel(DevBand<T> M, int a, int3 nin, int3 nout, const T* __restrict__ in,
                                 const T* __restrict__ in2, T* __restrict__ out, int add, int mask, int dim) {
-    const long long total = (long long)nout.x * nout.y * nout.z;
-    const long long sin_a = a == 0 ? 1 : (a == 1 ? (long long)nin.x : (long long)nin.x * nin.y);
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long c0 = idx % nout.x, c1 = (idx / nout.x) % nout.y, c2 = idx / ((long long)nout.x * nout.y);
+    const int total = nout.x * nout.y * nout.z;
+    const int sin_a = a == 0 ? 1 : (a == 1 ? nin.x : nin.x * nin.y);
+    const int W = M.width;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int c0 = idx % nout.x, c1 = (idx / nout.x) % nout.y, c2 = idx / (nout.x * nout.y);
         if (mask) {
-            bool bnd = c0 == 0 || c0 == nout.x - 1 || c1 == 0 || c1 == nout.y - 1 ||
-                       (dim == 3 && (c2 == 0 || c2 == nout.z - 1));
+            const bool bnd = c0 == 0 || c0 == nout.x - 1 || c1 == 0 || c1 == nout.y - 1 ||
+                             (dim == 3 && (c2 == 0 || c2 == nout.z - 1));
             if (bnd) { if (!add) out[idx] = T(0); continue; }
         }
-        const long long K = a == 0 ? c0 : (a == 1 ? c1 : c2);
-        long long b0 = c0, b1 = c1, b2 = c2;
-        if (a == 0) b0 = 0; else if (a == 1) b1 = 0; else b2 = 0;
-        const long long base = (b2 * nin.y + b1) * nin.x + b0 + (long long)M.start[K] * sin_a;
-        const T* cf = M.coef + K * M.width;
+        const int K = a == 0 ? c0 : (a == 1 ? c1 : c2);
+        const int b0 = a == 0 ? 0 : c0, b1 = a == 1 ? 0 : c1, b2 = a == 2 ? 0 : c2;
+        const int base = (b2 * nin.y + b1) * nin.x + b0 + M.start[K] * sin_a;
+        const T* cf = M.coef + K * W;
         T v = T(0);
         if (in2) {
-            for (int k = 0; k < M.width; ++k) v += cf[k] * (in[base + k * sin_a] - in2[base + k * sin_a]);
+            for (int k = 0; k < W; ++k) v += cf[k] * (in[base + k * sin_a] - in2[base + k * sin_a]);
         } else {
-            for (int k = 0; k < M.width; ++k) v += cf[k] * in[base + k * sin_a];
+            for (int k = 0; k < W; ++k) v += cf[k] * in[base + k * sin_a];
         }
         out[idx] = add ? out[idx] + v : v;
     }
@@ -242,21 +242,29 @@ __global__ void transfer_kernel(DevBand<T> M, int a, int3 nin, int3 nout, const 
 // coarsest solve: dense inverse times vector, one warp per row
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) coarse_kernel(long long n, const long long* __restrict__ index,
+__global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, const long long* __restrict__ index,
                                                      const T* __restrict__ inv, const T* __restrict__ r,
                                                      T* __restrict__ e) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* rs = reinterpret_cast<T*>(smem_raw);
-    for (long long t = threadIdx.x; t < n; t += blockDim.x) rs[t] = r[index[t]];
+    for (long long t = threadIdx.x; t < ld; t += blockDim.x) rs[t] = t < n ? r[index[t]] : T(0);
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const long long row = (long long)blockIdx.x * (blockDim.x / 32) + warp;
-    if (row >= n) return;
-    const T* a = inv + row * n;
-    T s = T(0);
-    for (long long j = lane; j < n; j += 32) s += a[j] * rs[j];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) e[index[row]] = s;
+    const int wpb = blockDim.x / 32;
+    constexpr int V = 16 / sizeof(T);   // elements per 16-byte vector
+    using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    for (long long row = (long long)blockIdx.x * wpb + warp; row < n; row += (long long)gridDim.x * wpb) {
+        const Vec* a = reinterpret_cast<const Vec*>(inv + row * ld);
+        T s = T(0);
+        for (long long j = lane; j < ld / V; j += 32) {
+            const Vec v = a[j];
+            const T* vv = reinterpret_cast<const T*>(&v);
+#pragma unroll
+            for (int q = 0; q < V; ++q) s += vv[q] * rs[j * V + q];
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) e[index[row]] = s;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -288,9 +296,32 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;   // valid in thread 0
 }
 
+// Every block writes its partial sums; the last block to finish (atomic
+// ticket) adds the partials in block order, so the result does not depend on
+// scheduling, and resets the ticket for the next launch.
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    return is_last;
+}
+
+__device__ void finalize_partials(const double* part, int ndots, int nblocks, double* S, int slot0, int slot1,
+                                  double* red) {
+    for (int d = 0; d < ndots; ++d) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += __ldcg(part + d * nblocks + i);
+        double t = block_sum(s, red);
+        if (threadIdx.x == 0) S[d == 0 ? slot0 : slot1] = t;
+    }
+}
+
 __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0, const double* __restrict__ b0,
                                                    const double* __restrict__ a1, const double* __restrict__ b1,
-                                                   int ndots, long long n, double* part) {
+                                                   int ndots, long long n, double* part, double* S, int slot0,
+                                                   int slot1, unsigned* ticket, int rotate) {
     __shared__ double red[32];
     double s0 = 0.0, s1 = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -303,22 +334,18 @@ __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0
         double t1 = block_sum(s1, red);
         if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t1;
     }
-}
-
-__global__ void __launch_bounds__(256) dots_finalize(const double* __restrict__ part, int ndots, int nblocks,
-                                                     double* S, int slot0, int slot1) {
-    __shared__ double red[32];
-    for (int d = 0; d < ndots; ++d) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += part[d * nblocks + i];
-        double t = block_sum(s, red);
-        if (threadIdx.x == 0) S[d == 0 ? slot0 : slot1] = t;
+    if (last_block(ticket)) {
+        finalize_partials(part, ndots, gridDim.x, S, slot0, slot1, red);
+        if (threadIdx.x == 0) {
+            if (rotate) S[S_RZ] = S[S_RZNEW];
+            *ticket = 0u;
+        }
     }
 }
 
 __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x, double* __restrict__ r,
                                                          const double* __restrict__ p, const double* __restrict__ q,
-                                                         long long n, double* part, double* S) {
+                                                         long long n, double* part, double* S, unsigned* ticket) {
     __shared__ double red[32];
     const double pq = S[S_PQ];
     const double alpha = S[S_RZ] / pq;
@@ -330,24 +357,27 @@ __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x,
         s += ri * ri;
     }
     double t = block_sum(s, red);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = t;
-        if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (last_block(ticket)) {
+        finalize_partials(part, 1, gridDim.x, S, S_RR, S_RR, red);
+        if (threadIdx.x == 0) {
             S[S_ALPHA] = alpha;
             if (!(pq > 0.0) || !isfinite(alpha)) S[S_FLAG] = 1.0;
+            *ticket = 0u;
         }
     }
 }
 
 __global__ void fcg_direction_kernel(double* __restrict__ p, const double* __restrict__ z, long long n,
-                                     const double* __restrict__ S, int flexible) {
+                                     double* __restrict__ S, int flexible, unsigned* ticket) {
     const double beta = flexible ? -S[S_ALPHA] * S[S_ZQ] / S[S_RZ] : S[S_RZNEW] / S[S_RZ];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = z[i] + beta * p[i];
-}
-
-__global__ void fcg_rotate_kernel(double* S) {
-    if (threadIdx.x == 0) S[S_RZ] = S[S_RZNEW];
+    // every block has read S_RZ before taking its ticket: the last one rotates
+    if (last_block(ticket) && threadIdx.x == 0) {
+        S[S_RZ] = S[S_RZNEW];
+        *ticket = 0u;
+    }
 }
 
 __global__ void lift_rhs_kernel(const double* __restrict__ mass, const double* __restrict__ f,
@@ -390,6 +420,7 @@ constexpr int kMaxDynSmem = 200 * 1024;
 template <typename T>
 void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st) {
     cudaMemsetAsync(y, 0, sizeof(T) * L.N, st);
+    if (launch_apply_fixed<T>(L, x, y, mask, st)) return;
     int epc = 256 / L.nloc;
     if (epc < 1) epc = 1;
     const long long blocks = (L.E + epc - 1) / epc;
@@ -404,6 +435,7 @@ void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_
 template <typename T>
 void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, const T* y, T* x, T alpha,
                        cudaStream_t st) {
+    if (launch_line_warp<T>(L, s, mode, g, r, y, x, alpha, st)) return;
     LineArgs<T> A;
     A.n = L.n[s] - 2;
     if (A.n <= 0) return;
@@ -443,7 +475,7 @@ template <typename T>
 void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nout[3], const T* in, const T* in2, T* out,
                      bool add, bool mask, cudaStream_t st) {
     const long long total = (long long)nout[0] * nout[1] * nout[2];
-    int dim = nout[2] > 1 ? 3 : 2;
+    const int dim = nout[2] > 1 ? 3 : 2;
     transfer_kernel<T><<<grid_for(total), 256, 0, st>>>(M, a, make_int3(nin[0], nin[1], nin[2]),
                                                          make_int3(nout[0], nout[1], nout[2]), in, in2, out,
                                                          add ? 1 : 0, mask ? 1 : 0, dim);
@@ -452,9 +484,10 @@ void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nou
 template <typename T>
 void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, cudaStream_t st) {
     cudaMemsetAsync(e, 0, sizeof(T) * N0, st);
-    const size_t smem = sizeof(T) * (size_t)C.n;
-    const long long blocks = (C.n + 7) / 8;
-    coarse_kernel<T><<<(unsigned)blocks, 256, smem, st>>>(C.n, C.index, C.inv, r, e);
+    const size_t smem = sizeof(T) * (size_t)C.ld;
+    long long blocks = (C.n + 7) / 8;
+    if (blocks > 2 * 152) blocks = 2 * 152;
+    coarse_kernel<T><<<(unsigned)blocks, 256, smem, st>>>(C.n, C.ld, C.index, C.inv, r, e);
 }
 
 template <typename Ti, typename To>
@@ -469,22 +502,19 @@ void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st) {
 }
 
 void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots, long long n,
-                 double* part, double* S, int slot0, int slot1, cudaStream_t st) {
-    dots_kernel<<<kDotBlocks, 256, 0, st>>>(a0, b0, a1, b1, ndots, n, part);
-    dots_finalize<<<1, 256, 0, st>>>(part, ndots, kDotBlocks, S, slot0, slot1);
+                 double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st) {
+    dots_kernel<<<kDotBlocks, 256, 0, st>>>(a0, b0, a1, b1, ndots, n, part, S, slot0, slot1, ticket, 0);
 }
 
 void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, double* part, double* S,
-                       cudaStream_t st) {
-    fcg_update_kernel<<<kDotBlocks, 256, 0, st>>>(x, r, p, q, n, part, S);
-    dots_finalize<<<1, 256, 0, st>>>(part, 1, kDotBlocks, S, S_RR, S_RR);
+                       unsigned* ticket, cudaStream_t st) {
+    fcg_update_kernel<<<kDotBlocks, 256, 0, st>>>(x, r, p, q, n, part, S, ticket);
 }
 
-void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, cudaStream_t st) {
-    fcg_direction_kernel<<<grid_for(n), 256, 0, st>>>(p, z, n, S, flexible);
+void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, unsigned* ticket,
+                          cudaStream_t st) {
+    fcg_direction_kernel<<<grid_for(n), 256, 0, st>>>(p, z, n, S, flexible, ticket);
 }
-
-void launch_fcg_rotate(double* S, cudaStream_t st) { fcg_rotate_kernel<<<1, 32, 0, st>>>(S); }
 
 void launch_lift_rhs(const double* mass, const double* f, const double* y, double* f0, const int n[3], int dim,
                      cudaStream_t st) {
@@ -509,7 +539,7 @@ bool init_kernel_attributes() {
     for (const void* f : fns)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess)
             return false;
-    return true;
+    return init_line_warp_attributes();
 }
 
 // explicit instantiations

@@ -1,0 +1,282 @@
+// Line solves by cyclic reduction with one warp per grid line.
+//
+// The band-1 system of a line (Def. 3.1/3.2) is staged through shared memory
+// with coalesced loads (adjacent lines of a CTA are adjacent in memory for
+// strided directions), then each lane holds a contiguous chunk of C unknowns
+// in registers.  Cyclic reduction keeps the odd-even order of Algorithm 1 /
+// Thm. 3.8 / Cor. 3.9: at level h the odd multiples of h are eliminated into
+// the even ones with the Prop. 3.7 coefficients,
+//   a' = a - l u_{i-h}/a_{i-h} - u l_{i+h}/a_{i+h},  l' = -l l_{i-h}/a_{i-h},
+//   u' = -u u_{i+h}/a_{i+h},  g' = g - l g_{i-h}/a_{i-h} - u g_{i+h}/a_{i+h},
+// and the back substitution restores x_i = (g_i - l_i x_{i-h} - u_i x_{i+h})/a_i.
+// Each eliminated unknown's pivot is inverted once (1/a_i, reused by both
+// neighbours and by the back substitution).
+// Levels h < C run inside a lane (one shuffle brings the next lane's
+// neighbour), levels h >= C run across lanes with shuffles at distance
+// h / C.  A line of n unknowns is padded to 32 C with decoupled identity
+// rows (a = 1, l = u = g = 0), which leaves every real unknown's arithmetic
+// unchanged.
+#include "device.cuh"
+
+namespace glls {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+struct WarpLineArgs {
+    int n, nlines, stride, m1, st1, st2, contiguous, mode;
+    T alpha;
+    const T* diag;
+    const T* off;
+    const T* g;
+    const T* r;
+    const T* y;
+    T* x;
+};
+
+// shared-memory index with one pad word per 32: lane-chunk reads are conflict free
+__device__ __forceinline__ int padi(int k) { return k + (k >> 5); }
+
+// MODE 0: g = A.g; MODE 1: g = A.r - A.y; MODE 2: g = A.r.  Output: MODE 0
+// stores x = B^-1 g, MODE 1/2 add alpha B^-1 g to x.
+template <typename T, int C, int LPB, int MODE>
+__global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) {
+    constexpr int SPAN = 32 * C + C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sd = reinterpret_cast<T*>(smem_raw);
+    T* so = sd + LPB * SPAN;
+    T* sg = so + LPB * SPAN;
+    __shared__ int sbase[LPB];
+    const int n = A.n;
+    const int l0 = blockIdx.x * LPB;
+    const int Wc = min(LPB, A.nlines - l0);
+    const int tid = threadIdx.x;
+    if (tid < LPB) {
+        const int li = l0 + tid;
+        sbase[tid] = (li % A.m1 + 1) * A.st1 + (li / A.m1 + 1) * A.st2;
+    }
+    __syncthreads();
+    // staged loads: every thread has at most C elements per array, all issued
+    // back to back.  x-lines: warp w reads line w; strided lines: the LPB
+    // threads of a row group read LPB adjacent lines.
+    const bool contig = A.contiguous != 0;
+    const int lw = contig ? (tid >> 5) : (tid & (LPB - 1));
+    const int lk = contig ? (tid & 31) : (tid / LPB);
+    const int lnode = lw < Wc ? sbase[lw] : 0;
+    T vd[C], vo[C], vg[C];
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        const int k = lk + 32 * m;
+        vd[m] = T(1); vo[m] = T(0); vg[m] = T(0);
+        if (lw < Wc && k < n) {
+            const int node = lnode + (k + 1) * A.stride;
+            vd[m] = __ldg(A.diag + node);
+            vo[m] = k < n - 1 ? __ldg(A.off + node) : T(0);
+            if (MODE == 0) vg[m] = A.g[node];
+            else if (MODE == 1) vg[m] = A.r[node] - A.y[node];
+            else vg[m] = A.r[node];
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        const int k = lk + 32 * m;
+        if (lw < Wc && k < n) {
+            const int sidx = lw * SPAN + padi(k);
+            sd[sidx] = vd[m];
+            so[sidx] = vo[m];
+            sg[sidx] = vg[m];
+        }
+    }
+    __syncthreads();
+
+    const int w = tid >> 5, lane = tid & 31;
+    if (w < Wc) {
+        T a[C], l[C], u[C], g[C];
+        const int base = w * SPAN;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const int k = C * lane + j;
+            if (k < n) {
+                a[j] = sd[base + padi(k)];
+                u[j] = so[base + padi(k)];
+                g[j] = sg[base + padi(k)];
+                l[j] = k > 0 ? so[base + padi(k - 1)] : T(0);
+            } else {
+                a[j] = T(1); u[j] = T(0); l[j] = T(0); g[j] = T(0);
+            }
+        }
+        // ---- forward reduction inside the lane: h = 1, 2, ..., C/2
+#pragma unroll
+        for (int h = 1; h < C; h *= 2) {
+            // the odd points of this level are eliminated: keep 1/a from here on
+#pragma unroll
+            for (int j = h - 1; j < C; j += 2 * h) a[j] = T(1) / a[j];
+            T ar = __shfl_down_sync(kFull, a[h - 1], 1);
+            T lr = __shfl_down_sync(kFull, l[h - 1], 1);
+            T ur = __shfl_down_sync(kFull, u[h - 1], 1);
+            T gr = __shfl_down_sync(kFull, g[h - 1], 1);
+            if (lane == 31) { ar = T(1); lr = T(0); ur = T(0); gr = T(0); }
+#pragma unroll
+            for (int j = 2 * h - 1; j < C; j += 2 * h) {
+                const int jl = j - h, jr = j + h;
+                const T iaR = jr < C ? a[jr < C ? jr : 0] : ar;   // reciprocal of the right odd point
+                const T lR = jr < C ? l[jr < C ? jr : 0] : lr;
+                const T uR = jr < C ? u[jr < C ? jr : 0] : ur;
+                const T gR = jr < C ? g[jr < C ? jr : 0] : gr;
+                const T al = -l[j] * a[jl];
+                const T be = -u[j] * iaR;
+                a[j] = a[j] + al * u[jl] + be * lR;
+                g[j] = g[j] + al * g[jl] + be * gR;
+                l[j] = al * l[jl];
+                u[j] = be * uR;
+            }
+        }
+        // ---- forward reduction across lanes on each lane's top unknown (position C (lane+1))
+        T At = a[C - 1], Lt = l[C - 1], Ut = u[C - 1], Gt = g[C - 1];
+#pragma unroll
+        for (int d = 1; d < 32; d *= 2) {
+            if (((lane + 1) & (2 * d - 1)) == d) At = T(1) / At;     // odd at this level
+            const T aL = __shfl_up_sync(kFull, At, d), lL = __shfl_up_sync(kFull, Lt, d);
+            const T uL = __shfl_up_sync(kFull, Ut, d), gL = __shfl_up_sync(kFull, Gt, d);
+            T aR = __shfl_down_sync(kFull, At, d), lR = __shfl_down_sync(kFull, Lt, d);
+            T uR = __shfl_down_sync(kFull, Ut, d), gR = __shfl_down_sync(kFull, Gt, d);
+            if (lane + d > 31) { aR = T(1); lR = T(0); uR = T(0); gR = T(0); }
+            if (((lane + 1) & (2 * d - 1)) == 0) {
+                const T al = -Lt * aL;
+                const T be = -Ut * aR;
+                At = At + al * uL + be * lR;
+                Gt = Gt + al * gL + be * gR;
+                Lt = al * lL;
+                Ut = be * uR;
+            }
+        }
+        // ---- top equation (position 32 C) and back substitution across lanes
+        T X = lane == 31 ? Gt / At : T(0);
+#pragma unroll
+        for (int d = 16; d >= 1; d /= 2) {
+            T xl = __shfl_up_sync(kFull, X, d);
+            T xr = __shfl_down_sync(kFull, X, d);
+            if (lane - d < 0) xl = T(0);
+            if (lane + d > 31) xr = T(0);
+            if (((lane + 1) & (2 * d - 1)) == d) X = (Gt - Lt * xl - Ut * xr) * At;
+        }
+        // ---- back substitution inside the lane
+        g[C - 1] = X;
+        T xprev = __shfl_up_sync(kFull, X, 1);
+        if (lane == 0) xprev = T(0);
+#pragma unroll
+        for (int h = C / 2; h >= 1; h /= 2) {
+#pragma unroll
+            for (int j = h - 1; j < C; j += 2 * h) {
+                const T xl = j - h >= 0 ? g[j - h >= 0 ? j - h : 0] : xprev;
+                const T xr = g[j + h < C ? j + h : C - 1];
+                g[j] = (g[j] - l[j] * xl - u[j] * xr) * a[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const int k = C * lane + j;
+            if (k < n) sg[base + padi(k)] = g[j];
+        }
+    }
+    __syncthreads();
+    T out[C];
+    if (MODE != 0) {
+#pragma unroll
+        for (int m = 0; m < C; ++m) {
+            const int k = lk + 32 * m;
+            out[m] = T(0);
+            if (lw < Wc && k < n) out[m] = A.x[lnode + (k + 1) * A.stride];
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        const int k = lk + 32 * m;
+        if (lw < Wc && k < n) {
+            const T v = sg[lw * SPAN + padi(k)];
+            A.x[lnode + (k + 1) * A.stride] = MODE == 0 ? v : out[m] + A.alpha * v;
+        }
+    }
+}
+
+constexpr int kLPB = 4;
+
+template <typename T, int C>
+void launch_c(const WarpLineArgs<T>& A, cudaStream_t st) {
+    const size_t smem = sizeof(T) * 3 * kLPB * (32 * C + C);
+    const int blocks = (A.nlines + kLPB - 1) / kLPB;
+    if (A.mode == 0) line_warp_kernel<T, C, kLPB, 0><<<blocks, 32 * kLPB, smem, st>>>(A);
+    else if (A.y) line_warp_kernel<T, C, kLPB, 1><<<blocks, 32 * kLPB, smem, st>>>(A);
+    else line_warp_kernel<T, C, kLPB, 2><<<blocks, 32 * kLPB, smem, st>>>(A);
+}
+
+template <typename T, int C>
+bool set_attr() {
+    const int lim = 160 * 1024;
+    return cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, kLPB, 0>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess &&
+           cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, kLPB, 1>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess &&
+           cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, kLPB, 2>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+}
+
+}  // namespace
+
+bool init_line_warp_attributes() {
+    bool ok = set_attr<float, 1>() && set_attr<float, 2>() && set_attr<float, 4>() && set_attr<float, 8>() &&
+              set_attr<float, 16>() && set_attr<float, 32>();
+    ok = ok && set_attr<double, 1>() && set_attr<double, 2>() && set_attr<double, 4>() && set_attr<double, 8>() &&
+         set_attr<double, 16>();
+    return ok;
+}
+
+template <typename T>
+bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, const T* y, T* x, T alpha,
+                      cudaStream_t st) {
+    WarpLineArgs<T> A;
+    A.n = L.n[s] - 2;
+    const int cmax = sizeof(T) == 4 ? 32 : 16;
+    if (A.n > 32 * cmax || L.N > (1LL << 31) - 1) return false;
+    if (A.n <= 0) return true;
+    int o1, o2;
+    if (s == 0) { o1 = 1; o2 = 2; } else if (s == 1) { o1 = 0; o2 = 2; } else { o1 = 0; o2 = 1; }
+    const int strides[3] = {1, L.n[0], L.n[0] * L.n[1]};
+    A.m1 = L.n[o1] - 2;
+    const int m2 = L.dim == 3 ? L.n[o2] - 2 : 1;
+    A.nlines = A.m1 * m2;
+    if (A.nlines <= 0) return true;
+    A.stride = strides[s];
+    A.st1 = strides[o1];
+    A.st2 = L.dim == 3 ? strides[o2] : 0;
+    A.contiguous = s == 0;
+    A.mode = mode;
+    A.alpha = alpha;
+    A.diag = L.diag;
+    A.off = L.off[s];
+    A.g = g;
+    A.r = r;
+    A.y = y;
+    A.x = x;
+    int C = 1;
+    while (32 * C < A.n) C *= 2;
+    switch (C) {
+        case 1: launch_c<T, 1>(A, st); break;
+        case 2: launch_c<T, 2>(A, st); break;
+        case 4: launch_c<T, 4>(A, st); break;
+        case 8: launch_c<T, 8>(A, st); break;
+        case 16: launch_c<T, 16>(A, st); break;
+        default:
+            if constexpr (sizeof(T) == 4) { launch_c<T, 32>(A, st); break; }
+            return false;
+    }
+    return true;
+}
+
+template bool launch_line_warp<float>(const DevLevel<float>&, int, int, const float*, const float*, const float*,
+                                      float*, float, cudaStream_t);
+template bool launch_line_warp<double>(const DevLevel<double>&, int, int, const double*, const double*,
+                                       const double*, double*, double, cudaStream_t);
+
+}  // namespace glls
