@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -138,6 +139,7 @@ glls_status upload_levels(glls_problem* P, const std::vector<LevelHost>& H, std:
         CK(P->alloc(&s.t2, h.N));
         CK(cudaMemset(s.r, 0, sizeof(T) * h.N));
         CK(cudaMemset(s.x, 0, sizeof(T) * h.N));
+        CK(cudaMemset(s.y, 0, sizeof(T) * h.N));
     }
     return GLLS_OK;
 }
@@ -176,9 +178,9 @@ void restrict_residual(glls_problem* P, int l, const T* r, const T* y, T* rc, cu
     }
 }
 
-// x += P_l e
+// x += P_l e; clear (optional, level-l sized) is reset to 0 by the last pass
 template <typename T>
-void prolong_add(glls_problem* P, int l, const T* e, T* x, cudaStream_t st) {
+void prolong_add(glls_problem* P, int l, const T* e, T* x, cudaStream_t st, T* clear = nullptr) {
     auto& Ls = levels_of<T>(P);
     const DevLevel<T>& F = Ls[l].dev;
     const DevLevel<T>& C = Ls[l - 1].dev;
@@ -189,20 +191,22 @@ void prolong_add(glls_problem* P, int l, const T* e, T* x, cudaStream_t st) {
         nxt[a] = F.n[a];
         const bool last = a == F.dim - 1;
         T* out = last ? x : (a % 2 == 0 ? Ls[l].t1 : Ls[l].t2);
-        launch_transfer<T>(F.P[a], a, cur, nxt, in, nullptr, out, last, false, st);
+        launch_transfer<T>(F.P[a], a, cur, nxt, in, nullptr, out, last, false, st, last ? clear : nullptr);
         in = out;
         for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
     }
 }
 
-// x <- x + alpha B_s^-1 (r - A x); x_is_zero skips the apply
+// x <- x + alpha B_s^-1 (r - A x).  x_is_zero: x = alpha B_s^-1 r without
+// the apply.  The level scratch y is zero on entry and on exit: the apply
+// accumulates into it and the line solve resets what it reads.
 template <typename T>
 void smooth(glls_problem* P, int l, int s, T alpha, const T* r, T* x, bool x_is_zero, cudaStream_t st) {
     auto& Ls = levels_of<T>(P);
     if (x_is_zero) {
-        launch_line_solve<T>(Ls[l].dev, s, 1, nullptr, r, nullptr, x, alpha, st);
+        launch_line_solve<T>(Ls[l].dev, s, 3, nullptr, r, nullptr, x, alpha, st);
     } else {
-        launch_apply<T>(Ls[l].dev, x, Ls[l].y, true, st);
+        launch_apply<T>(Ls[l].dev, x, Ls[l].y, true, st, true);
         launch_line_solve<T>(Ls[l].dev, s, 1, nullptr, r, Ls[l].y, x, alpha, st);
     }
 }
@@ -211,12 +215,12 @@ void smooth(glls_problem* P, int l, int s, T alpha, const T* r, T* x, bool x_is_
 template <typename T>
 void cycle(glls_problem* P, int l, const T* r, T* x, int gamma, int m, T alpha, cudaStream_t st) {
     auto& Ls = levels_of<T>(P);
+    // x: boundary entries are zero and stay zero (only interior entries are written)
     if (l == 0) {
-        launch_coarse<T>(coarse_of<T>(P), Ls[0].dev.N, r, x, st);
+        launch_coarse<T>(coarse_of<T>(P), Ls[0].dev.N, r, x, st, true);
         return;
     }
     const int d = Ls[l].dev.dim;
-    cudaMemsetAsync(x, 0, sizeof(T) * Ls[l].dev.N, st);
     bool zero = true;
     for (int s = 0; s < d; ++s)
         for (int k = 0; k < m; ++k) {
@@ -224,10 +228,10 @@ void cycle(glls_problem* P, int l, const T* r, T* x, int gamma, int m, T alpha, 
             zero = false;
         }
     for (int g = 0; g < gamma; ++g) {
-        launch_apply<T>(Ls[l].dev, x, Ls[l].y, true, st);
+        launch_apply<T>(Ls[l].dev, x, Ls[l].y, true, st, true);
         restrict_residual<T>(P, l, r, Ls[l].y, Ls[l - 1].r, st);
         cycle<T>(P, l - 1, Ls[l - 1].r, Ls[l - 1].x, gamma, m, alpha, st);
-        prolong_add<T>(P, l, Ls[l - 1].x, x, st);
+        prolong_add<T>(P, l, Ls[l - 1].x, x, st, Ls[l].y);
         for (int s = d - 1; s >= 0; --s)
             for (int k = 0; k < m; ++k) smooth<T>(P, l, s, alpha, r, x, false, st);
     }
@@ -253,29 +257,22 @@ glls_status check_opts(const glls_solve_opts* o) {
     return GLLS_OK;
 }
 
-// z = M^-1 r for the outer iteration (FP64 in, FP64 out)
-void precondition_outer(glls_problem* P, const glls_solve_opts* o, const double* r, double* z, cudaStream_t st) {
-    const int L = (int)P->L64.size() - 1;
-    if (o->precision == GLLS_PREC_MIXED) {
-        launch_cast<double, float>(r, P->r32, P->N, st);
-        cycle<float>(P, L, P->r32, P->z32, o->gamma, o->m, (float)o->alpha, st);
-        launch_cast<float, double>(P->z32, z, P->N, st);
-    } else {
-        cycle<double>(P, L, r, z, o->gamma, o->m, o->alpha, st);
-    }
-}
-
-// Body of one outer iteration, in the order
-//   z = M r; (r.z, z.q); p = z + beta p; rz <- rz_new; q = A p; p.q; x, r update; r.r
+// Body of one outer iteration (4 launches besides the gamma-cycle):
+//   z = M r                      (FP32 cycle on r32 = float(r) in mixed precision)
+//   S_RZNEW = r.z, S_ZQ = z.q    (z = double(z32); q reset to 0 after reading)
+//   p = z + beta p; S_RZ <- S_RZNEW
+//   q = A p, S_PQ = p.q          (the dot accumulated per element in the apply)
+//   alpha; x += alpha p; r -= alpha q; S_RR = r.r; r32 = float(r)
 void outer_iteration(glls_problem* P, const glls_solve_opts* o, cudaStream_t st) {
     const int L = (int)P->L64.size() - 1;
     const long long N = P->N;
-    precondition_outer(P, o, P->rk, P->zk, st);
-    launch_dots(P->rk, P->zk, P->zk, P->qk, 2, N, P->part, P->S, S_RZNEW, S_ZQ, P->ticket, st);
+    const bool mixed = o->precision == GLLS_PREC_MIXED;
+    if (mixed) cycle<float>(P, L, P->r32, P->z32, o->gamma, o->m, (float)o->alpha, st);
+    else cycle<double>(P, L, P->rk, P->zk, o->gamma, o->m, o->alpha, st);
+    launch_dots_rz_zq(P->rk, P->zk, mixed ? P->z32 : nullptr, P->qk, N, P->part, P->S, P->ticket, st);
     launch_fcg_direction(P->pk, P->zk, N, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, P->ticket, st);
-    launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st);
-    launch_dots(P->pk, P->qk, nullptr, nullptr, 1, N, P->part, P->S, S_PQ, S_PQ, P->ticket, st);
-    launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, P->part, P->S, P->ticket, st);
+    launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st, true, P->S + S_PQ, P->part, P->ticket);
+    launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, P->part, P->S, P->ticket, mixed ? P->r32 : nullptr, st);
 }
 
 glls_status get_iteration_graph(glls_problem* P, const glls_solve_opts* o) {
@@ -403,11 +400,13 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
         CK(cudaMemset(*vp, 0, sizeof(double) * N));
     }
     CK(P->alloc(&P->S, S_COUNT));
-    CK(P->alloc(&P->part, 2 * kDotBlocks));
+    CK(P->alloc(&P->part, std::max<long long>(2 * kDotBlocks, H.back().E + 1)));
     CK(P->alloc(&P->ticket, 1));
     CK(cudaMemset(P->ticket, 0, sizeof(unsigned)));
     CK(P->alloc(&P->r32, N));
     CK(P->alloc(&P->z32, N));
+    CK(cudaMemset(P->r32, 0, sizeof(float) * N));
+    CK(cudaMemset(P->z32, 0, sizeof(float) * N));
     CK(cudaMallocHost(&P->hostS, sizeof(double) * S_COUNT));
     CK(cudaStreamCreateWithFlags(&P->capture_stream, cudaStreamNonBlocking));
     CK(cudaDeviceSynchronize());
@@ -498,6 +497,7 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
     std::memcpy(P->hostS, init, sizeof(init));
     CK(cudaMemcpyAsync(P->S, P->hostS, sizeof(init), cudaMemcpyHostToDevice, st));
     launch_dots(P->rk, P->rk, nullptr, nullptr, 1, N, P->part, P->S, S_RR0, S_RR0, P->ticket, st);
+    if (o->precision == GLLS_PREC_MIXED) launch_cast<double, float>(P->rk, P->r32, N, st);
     CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const double rr0 = P->hostS[S_RR0];
@@ -584,8 +584,9 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
         if (s != GLLS_OK) return s;                                                                             \
         if (!r || !x || !rc) return fail(GLLS_ERR_INVALID, "null vector");                                      \
         auto& Ls = levels_of<T>(P);                                                                             \
-        launch_apply<T>(Ls[level].dev, x, Ls[level].y, true, (cudaStream_t)stream);                             \
+        launch_apply<T>(Ls[level].dev, x, Ls[level].y, true, (cudaStream_t)stream, true);                       \
         restrict_residual<T>(P, level, r, Ls[level].y, rc, (cudaStream_t)stream);                               \
+        CK(cudaMemsetAsync(Ls[level].y, 0, sizeof(T) * Ls[level].dev.N, (cudaStream_t)stream));                 \
         CK(cudaGetLastError());                                                                                 \
         return GLLS_OK;                                                                                         \
     }                                                                                                           \
@@ -608,6 +609,7 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
         if (!P || !r || !z) return fail(GLLS_ERR_INVALID, "null argument");                                     \
         glls_status s = check_opts(o);                                                                          \
         if (s != GLLS_OK) return s;                                                                             \
+        CK(cudaMemsetAsync(z, 0, sizeof(T) * levels_of<T>(P).back().dev.N, (cudaStream_t)stream));               \
         cycle<T>(P, (int)P->L64.size() - 1, r, z, o->gamma, o->m, (T)o->alpha, (cudaStream_t)stream);           \
         CK(cudaGetLastError());                                                                                 \
         return GLLS_OK;                                                                                         \

@@ -5,6 +5,7 @@
 // transposed contractions, then element-interior nodes stored and shared
 // nodes summed with atomics (direct stiffness summation).  32-bit indexing.
 #include "device.cuh"
+#include "reduce.cuh"
 
 namespace glls {
 namespace {
@@ -13,9 +14,10 @@ __device__ __forceinline__ bool on_boundary32(int I, int J, int K, const int n[3
     return I == 0 || I == n[0] - 1 || J == 0 || J == n[1] - 1 || (dim == 3 && (K == 0 || K == n[2] - 1));
 }
 
-template <typename T, int DIM, int P>
+// DOT: also sum_e x_e^T (A_e x_e) over all elements into *dot (last block).
+template <typename T, int DIM, int P, bool DOT>
 __global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
-                                                      int mask) {
+                                                      int mask, double* dot, double* part, unsigned* ticket) {
     constexpr int N1 = P + 1;
     constexpr int NLOC = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
     constexpr int EPB = NLOC >= 256 ? 1 : 256 / NLOC;
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __
     }
     __syncthreads();
 
+    double local = 0.0;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int el = t / NLOC, q = t - el * NLOC;
         const int e = e0 + el;
@@ -94,6 +97,7 @@ __global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __
         const int ex = e % ne0, ey = (e / ne0) % ne1, ez = DIM == 3 ? e / (ne0 * ne1) : 0;
         const int I = ex * P + i, J = ey * P + j, K = ez * P + k;
         const int g = (K * n1 + J) * n0 + I;
+        if (DOT) local += (double)sx[t] * (double)v;
         const bool inner = i > 0 && i < P && j > 0 && j < P && (DIM == 2 || (k > 0 && k < P));
         if (inner) {
             y[g] = v;
@@ -102,27 +106,40 @@ __global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __
             atomicAdd(&y[g], v);
         }
     }
+    if (DOT) {
+        __shared__ double red[32];
+        const double tsum = block_sum(local, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = tsum;
+        if (last_block(ticket)) {
+            finalize_partials(part, 1, gridDim.x, dot, 0, 0, red);
+            if (threadIdx.x == 0) *ticket = 0u;
+        }
+    }
 }
 
 template <typename T, int DIM, int P>
-void launch_p(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st) {
+bool launch_p(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part, unsigned* ticket,
+              cudaStream_t st) {
     constexpr int N1 = P + 1;
     constexpr int NLOC = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
     constexpr int EPB = NLOC >= 256 ? 1 : 256 / NLOC;
     const int blocks = (int)((L.E + EPB - 1) / EPB);
-    apply_p_kernel<T, DIM, P><<<blocks, 256, 0, st>>>(L, x, y, mask ? 1 : 0);
+    if (dot) {
+        apply_p_kernel<T, DIM, P, true><<<blocks, 256, 0, st>>>(L, x, y, mask ? 1 : 0, dot, part, ticket);
+    } else {
+        apply_p_kernel<T, DIM, P, false><<<blocks, 256, 0, st>>>(L, x, y, mask ? 1 : 0, nullptr, nullptr, nullptr);
+    }
+    return true;
 }
 
 template <typename T, int DIM, int P>
-bool dispatch(int p, const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st) {
+bool dispatch(int p, const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part, unsigned* ticket,
+              cudaStream_t st) {
     if constexpr (P == 0) {
         return false;
     } else {
-        if (p == P) {
-            launch_p<T, DIM, P>(L, x, y, mask, st);
-            return true;
-        }
-        return dispatch<T, DIM, P - 1>(p, L, x, y, mask, st);
+        if (p == P) return launch_p<T, DIM, P>(L, x, y, mask, dot, part, ticket, st);
+        return dispatch<T, DIM, P - 1>(p, L, x, y, mask, dot, part, ticket, st);
     }
 }
 
@@ -130,13 +147,16 @@ bool dispatch(int p, const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStre
 
 // Returns false when the order has no specialisation (the caller falls back).
 template <typename T>
-bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st) {
+bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part,
+                        unsigned* ticket, cudaStream_t st) {
     if (L.N > (1LL << 31) - 1 || L.E * L.nloc * (L.dim == 2 ? 3 : 6) > (1LL << 31) - 1) return false;
-    if (L.dim == 2) return dispatch<T, 2, 16>(L.p, L, x, y, mask, st);
-    return dispatch<T, 3, 8>(L.p, L, x, y, mask, st);
+    if (L.dim == 2) return dispatch<T, 2, 16>(L.p, L, x, y, mask, dot, part, ticket, st);
+    return dispatch<T, 3, 8>(L.p, L, x, y, mask, dot, part, ticket, st);
 }
 
-template bool launch_apply_fixed<float>(const DevLevel<float>&, const float*, float*, bool, cudaStream_t);
-template bool launch_apply_fixed<double>(const DevLevel<double>&, const double*, double*, bool, cudaStream_t);
+template bool launch_apply_fixed<float>(const DevLevel<float>&, const float*, float*, bool, double*, double*,
+                                        unsigned*, cudaStream_t);
+template bool launch_apply_fixed<double>(const DevLevel<double>&, const double*, double*, bool, double*, double*,
+                                         unsigned*, cudaStream_t);
 
 }  // namespace glls

@@ -50,34 +50,44 @@ constexpr size_t kMaxDynSmemBytes = 200 * 1024;
 
 // Specialised fast paths (apply.cu, lines.cu); they return false when the
 // case is outside their compiled range and the generic kernels take over.
+// dot: if non-null, also accumulate sum_e x_e^T (A_e x_e) = x.(A x) for x
+// zero on the boundary; the last block writes it to dot[0] using `part` and
+// `ticket` (see launch_dots).
 template <typename T>
-bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st);
+bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part,
+                        unsigned* ticket, cudaStream_t st);
 template <typename T>
-bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, const T* y, T* x, T alpha,
+bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
                       cudaStream_t st);
 bool init_line_warp_attributes();
 
 // ---- launchers (all asynchronous on `st`) ---------------------------------
-// y = A x (y zeroed first); mask: zero boundary rows.
+// y = A x; mask: boundary rows of y are not written.  y_is_zero: the caller
+// guarantees y == 0 on entry (otherwise it is zeroed first).  dot, part,
+// ticket: optional x.(A x) into dot[0] (FP64 only).
 template <typename T>
-void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st);
+void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st, bool y_is_zero = false,
+                  double* dot = nullptr, double* part = nullptr, unsigned* ticket = nullptr);
 
-// Line solves along axis s.  mode 0: x = B_s^-1 g (interior entries written);
-// mode 1: x += alpha B_s^-1 (r - y).
+// Line solves along axis s.  mode 0: x = B_s^-1 g; mode 1: x += alpha
+// B_s^-1 (r - y) and y is reset to 0 where read; mode 2: x += alpha B_s^-1 r;
+// mode 3: x = alpha B_s^-1 r.  Only interior entries of x are written.
 template <typename T>
-void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, const T* y,
+void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y,
                        T* x, T alpha, cudaStream_t st);
 
 // One tensor-product factor of a transfer: out = M in (or in - in2) along
 // axis a; grids nin/nout differ only along a.  add: out += ...; mask: zero
-// the output's boundary nodes.
+// the output's boundary nodes; clear (optional, output-grid sized): set to 0.
 template <typename T>
 void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nout[3], const T* in,
-                     const T* in2, T* out, bool add, bool mask, cudaStream_t st);
+                     const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear = nullptr);
 
-// e = A_0^-1 r on the coarsest level (e zeroed on the boundary).
+// e = A_0^-1 r on the interior of the coarsest level; e's boundary entries
+// are zeroed first unless e_boundary_zero.
 template <typename T>
-void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, cudaStream_t st);
+void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, cudaStream_t st,
+                   bool e_boundary_zero = false);
 
 // ---- vector kernels -------------------------------------------------------
 template <typename Ti, typename To>
@@ -92,14 +102,19 @@ void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st);
 constexpr int kDotBlocks = 304;   // 2 x 152 SMs
 void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots,
                  long long n, double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st);
+// Outer-iteration dots S_RZNEW = r.z, S_ZQ = z.q; z is first taken from z32
+// when given (z = double(z32)); q is reset to 0 after it is read.
+void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* part,
+                       double* S, unsigned* ticket, cudaStream_t st);
 
 // Krylov scalar slots in the device array S.
 enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZNEW, S_ZQ, S_RR0, S_ALPHA, S_FLAG, S_TOL2, S_ITER, S_COUNT };
 
 // q-independent update: alpha = S_RZ / S_PQ; x += alpha p; r -= alpha q;
 // then rr = r.r into S_RR (via part); flags breakdown in S_FLAG.
+// r32 (optional): also r32 = float(r) for the FP32 gamma-cycle.
 void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, double* part,
-                       double* S, unsigned* ticket, cudaStream_t st);
+                       double* S, unsigned* ticket, float* r32, cudaStream_t st);
 // p = z + beta p with beta = -alpha S_ZQ / S_RZ (flexible) or S_RZNEW / S_RZ;
 // afterwards S_RZ <- S_RZNEW.
 void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, unsigned* ticket,

@@ -15,6 +15,7 @@
 //   dots / fcg_*     FP64 outer-Krylov vector operations with scalars kept in
 //                    device memory, deterministic two-stage reductions.
 #include "device.cuh"
+#include "reduce.cuh"
 
 #include <cstdio>
 #include <type_traits>
@@ -130,7 +131,7 @@ struct LineArgs {
     const T* off;
     const T* g;
     const T* r;
-    const T* y;
+    T* y;
     T* x;
 };
 
@@ -160,7 +161,14 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs<T> A) {
         sa[s] = A.diag[g];
         su[s] = kk < n - 1 ? A.off[g] : T(0);
         sl[s] = kk > 0 ? A.off[g - A.stride] : T(0);
-        sg[s] = A.mode == 0 ? A.g[g] : (A.y ? A.r[g] - A.y[g] : A.r[g]);
+        if (A.mode == 0) {
+            sg[s] = A.g[g];
+        } else if (A.mode == 1) {
+            sg[s] = A.r[g] - A.y[g];
+            A.y[g] = T(0);
+        } else {
+            sg[s] = A.r[g];
+        }
     }
     __syncthreads();
 
@@ -204,20 +212,26 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs<T> A) {
         if (A.contiguous) { w = t / n; kk = t - w * n; } else { kk = t / Wc; w = t - kk * Wc; }
         const long long g = node_of(w, kk);
         const T v = sg[w * n + kk];
-        if (A.mode == 0) A.x[g] = v; else A.x[g] += A.alpha * v;
+        if (A.mode == 0) A.x[g] = v;
+        else if (A.mode == 3) A.x[g] = A.alpha * v;
+        else A.x[g] += A.alpha * v;
     }
 }
 
 // ---------------------------------------------------------------------------
 // transfers
 // ---------------------------------------------------------------------------
-template <typename T>
+// WB: compile-time bound on the band width, so that all loads of a row are
+// issued back to back (WB = 0: runtime loop for very wide bands).
+template <typename T, int WB>
 __global__ void transfer_kernel(DevBand<T> M, int a, int3 nin, int3 nout, const T* __restrict__ in,
-                                const T* __restrict__ in2, T* __restrict__ out, int add, int mask, int dim) {
+                                const T* __restrict__ in2, T* __restrict__ out, int add, int mask, int dim,
+                                T* __restrict__ clear) {
     const int total = nout.x * nout.y * nout.z;
     const int sin_a = a == 0 ? 1 : (a == 1 ? nin.x : nin.x * nin.y);
     const int W = M.width;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        if (clear) clear[idx] = T(0);
         const int c0 = idx % nout.x, c1 = (idx / nout.x) % nout.y, c2 = idx / (nout.x * nout.y);
         if (mask) {
             const bool bnd = c0 == 0 || c0 == nout.x - 1 || c1 == 0 || c1 == nout.y - 1 ||
@@ -229,10 +243,22 @@ __global__ void transfer_kernel(DevBand<T> M, int a, int3 nin, int3 nout, const 
         const int base = (b2 * nin.y + b1) * nin.x + b0 + M.start[K] * sin_a;
         const T* cf = M.coef + K * W;
         T v = T(0);
-        if (in2) {
-            for (int k = 0; k < W; ++k) v += cf[k] * (in[base + k * sin_a] - in2[base + k * sin_a]);
+        if (WB > 0) {
+            T cv[WB > 0 ? WB : 1], iv[WB > 0 ? WB : 1];
+#pragma unroll
+            for (int k = 0; k < (WB > 0 ? WB : 1); ++k) {
+                cv[k] = T(0);
+                iv[k] = T(0);
+                if (k < W) {
+                    cv[k] = cf[k];
+                    iv[k] = in2 ? in[base + k * sin_a] - in2[base + k * sin_a] : in[base + k * sin_a];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < (WB > 0 ? WB : 1); ++k) v += cv[k] * iv[k];
         } else {
-            for (int k = 0; k < W; ++k) v += cf[k] * in[base + k * sin_a];
+            for (int k = 0; k < W; ++k)
+                v += cf[k] * (in2 ? in[base + k * sin_a] - in2[base + k * sin_a] : in[base + k * sin_a]);
         }
         out[idx] = add ? out[idx] + v : v;
     }
@@ -284,40 +310,6 @@ __global__ void zero_boundary_kernel(T* v, int3 n, int dim) {
         if (on_boundary(i, nn, dim)) v[i] = T(0);
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
-    return s;   // valid in thread 0
-}
-
-// Every block writes its partial sums; the last block to finish (atomic
-// ticket) adds the partials in block order, so the result does not depend on
-// scheduling, and resets the ticket for the next launch.
-__device__ __forceinline__ bool last_block(unsigned* ticket) {
-    __shared__ bool is_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    return is_last;
-}
-
-__device__ void finalize_partials(const double* part, int ndots, int nblocks, double* S, int slot0, int slot1,
-                                  double* red) {
-    for (int d = 0; d < ndots; ++d) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += __ldcg(part + d * nblocks + i);
-        double t = block_sum(s, red);
-        if (threadIdx.x == 0) S[d == 0 ? slot0 : slot1] = t;
-    }
-}
-
 __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0, const double* __restrict__ b0,
                                                    const double* __restrict__ a1, const double* __restrict__ b1,
                                                    int ndots, long long n, double* part, double* S, int slot0,
@@ -343,9 +335,37 @@ __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0
     }
 }
 
+__global__ void __launch_bounds__(256) dots_rz_zq_kernel(const double* __restrict__ r, double* __restrict__ z,
+                                                         const float* __restrict__ z32, double* __restrict__ q,
+                                                         long long n, double* part, double* S, unsigned* ticket) {
+    __shared__ double red[32];
+    double s0 = 0.0, s1 = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double zi;
+        if (z32) {
+            zi = (double)z32[i];
+            z[i] = zi;
+        } else {
+            zi = z[i];
+        }
+        s0 += r[i] * zi;
+        s1 += zi * q[i];
+        q[i] = 0.0;
+    }
+    double t0 = block_sum(s0, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t0;
+    double t1 = block_sum(s1, red);
+    if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t1;
+    if (last_block(ticket)) {
+        finalize_partials(part, 2, gridDim.x, S, S_RZNEW, S_ZQ, red);
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+}
+
 __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x, double* __restrict__ r,
                                                          const double* __restrict__ p, const double* __restrict__ q,
-                                                         long long n, double* part, double* S, unsigned* ticket) {
+                                                         long long n, double* part, double* S, unsigned* ticket,
+                                                         float* __restrict__ r32) {
     __shared__ double red[32];
     const double pq = S[S_PQ];
     const double alpha = S[S_RZ] / pq;
@@ -354,6 +374,7 @@ __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x,
         x[i] += alpha * p[i];
         const double ri = r[i] - alpha * q[i];
         r[i] = ri;
+        if (r32) r32[i] = (float)ri;
         s += ri * ri;
     }
     double t = block_sum(s, red);
@@ -418,9 +439,10 @@ constexpr int kMaxDynSmem = 200 * 1024;
 // launchers
 // ---------------------------------------------------------------------------
 template <typename T>
-void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st) {
-    cudaMemsetAsync(y, 0, sizeof(T) * L.N, st);
-    if (launch_apply_fixed<T>(L, x, y, mask, st)) return;
+void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st, bool y_is_zero, double* dot,
+                  double* part, unsigned* ticket) {
+    if (!y_is_zero) cudaMemsetAsync(y, 0, sizeof(T) * L.N, st);
+    if (launch_apply_fixed<T>(L, x, y, mask, dot, part, ticket, st)) return;
     int epc = 256 / L.nloc;
     if (epc < 1) epc = 1;
     const long long blocks = (L.E + epc - 1) / epc;
@@ -430,10 +452,16 @@ void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_
     } else {
         apply_kernel<T, 3><<<(unsigned)blocks, 256, smem, st>>>(L, x, y, mask ? 1 : 0, epc);
     }
+    // orders outside the specialised range: x.(A x) as a separate product
+    if (dot) {
+        if constexpr (sizeof(T) == 8)
+            launch_dots(reinterpret_cast<const double*>(x), reinterpret_cast<const double*>(y), nullptr, nullptr, 1,
+                        L.N, part, dot, 0, 0, ticket, st);
+    }
 }
 
 template <typename T>
-void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, const T* y, T* x, T alpha,
+void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
                        cudaStream_t st) {
     if (launch_line_warp<T>(L, s, mode, g, r, y, x, alpha, st)) return;
     LineArgs<T> A;
@@ -473,17 +501,22 @@ void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const 
 
 template <typename T>
 void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nout[3], const T* in, const T* in2, T* out,
-                     bool add, bool mask, cudaStream_t st) {
+                     bool add, bool mask, cudaStream_t st, T* clear) {
     const long long total = (long long)nout[0] * nout[1] * nout[2];
     const int dim = nout[2] > 1 ? 3 : 2;
-    transfer_kernel<T><<<grid_for(total), 256, 0, st>>>(M, a, make_int3(nin[0], nin[1], nin[2]),
-                                                         make_int3(nout[0], nout[1], nout[2]), in, in2, out,
-                                                         add ? 1 : 0, mask ? 1 : 0, dim);
+    const int3 ni = make_int3(nin[0], nin[1], nin[2]), no = make_int3(nout[0], nout[1], nout[2]);
+    const int g = grid_for(total);
+    const int ad = add ? 1 : 0, mk = mask ? 1 : 0;
+    if (M.width <= 4) transfer_kernel<T, 4><<<g, 256, 0, st>>>(M, a, ni, no, in, in2, out, ad, mk, dim, clear);
+    else if (M.width <= 8) transfer_kernel<T, 8><<<g, 256, 0, st>>>(M, a, ni, no, in, in2, out, ad, mk, dim, clear);
+    else if (M.width <= 16) transfer_kernel<T, 16><<<g, 256, 0, st>>>(M, a, ni, no, in, in2, out, ad, mk, dim, clear);
+    else if (M.width <= 32) transfer_kernel<T, 32><<<g, 256, 0, st>>>(M, a, ni, no, in, in2, out, ad, mk, dim, clear);
+    else transfer_kernel<T, 0><<<g, 256, 0, st>>>(M, a, ni, no, in, in2, out, ad, mk, dim, clear);
 }
 
 template <typename T>
-void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, cudaStream_t st) {
-    cudaMemsetAsync(e, 0, sizeof(T) * N0, st);
+void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, cudaStream_t st, bool e_boundary_zero) {
+    if (!e_boundary_zero) cudaMemsetAsync(e, 0, sizeof(T) * N0, st);
     const size_t smem = sizeof(T) * (size_t)C.ld;
     long long blocks = (C.n + 7) / 8;
     if (blocks > 2 * 152) blocks = 2 * 152;
@@ -507,8 +540,13 @@ void launch_dots(const double* a0, const double* b0, const double* a1, const dou
 }
 
 void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, double* part, double* S,
+                       unsigned* ticket, float* r32, cudaStream_t st) {
+    fcg_update_kernel<<<kDotBlocks, 256, 0, st>>>(x, r, p, q, n, part, S, ticket, r32);
+}
+
+void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* part, double* S,
                        unsigned* ticket, cudaStream_t st) {
-    fcg_update_kernel<<<kDotBlocks, 256, 0, st>>>(x, r, p, q, n, part, S, ticket);
+    dots_rz_zq_kernel<<<kDotBlocks, 256, 0, st>>>(r, z, z32, q, n, part, S, ticket);
 }
 
 void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, unsigned* ticket,
@@ -543,18 +581,20 @@ bool init_kernel_attributes() {
 }
 
 // explicit instantiations
-template void launch_apply<double>(const DevLevel<double>&, const double*, double*, bool, cudaStream_t);
-template void launch_apply<float>(const DevLevel<float>&, const float*, float*, bool, cudaStream_t);
-template void launch_line_solve<double>(const DevLevel<double>&, int, int, const double*, const double*, const double*,
+template void launch_apply<double>(const DevLevel<double>&, const double*, double*, bool, cudaStream_t, bool, double*,
+                                   double*, unsigned*);
+template void launch_apply<float>(const DevLevel<float>&, const float*, float*, bool, cudaStream_t, bool, double*,
+                                  double*, unsigned*);
+template void launch_line_solve<double>(const DevLevel<double>&, int, int, const double*, const double*, double*,
                                         double*, double, cudaStream_t);
-template void launch_line_solve<float>(const DevLevel<float>&, int, int, const float*, const float*, const float*,
+template void launch_line_solve<float>(const DevLevel<float>&, int, int, const float*, const float*, float*,
                                        float*, float, cudaStream_t);
 template void launch_transfer<double>(const DevBand<double>&, int, const int*, const int*, const double*, const double*,
-                                      double*, bool, bool, cudaStream_t);
+                                      double*, bool, bool, cudaStream_t, double*);
 template void launch_transfer<float>(const DevBand<float>&, int, const int*, const int*, const float*, const float*,
-                                     float*, bool, bool, cudaStream_t);
-template void launch_coarse<double>(const DevCoarse<double>&, long long, const double*, double*, cudaStream_t);
-template void launch_coarse<float>(const DevCoarse<float>&, long long, const float*, float*, cudaStream_t);
+                                     float*, bool, bool, cudaStream_t, float*);
+template void launch_coarse<double>(const DevCoarse<double>&, long long, const double*, double*, cudaStream_t, bool);
+template void launch_coarse<float>(const DevCoarse<float>&, long long, const float*, float*, cudaStream_t, bool);
 template void launch_cast<double, float>(const double*, float*, long long, cudaStream_t);
 template void launch_cast<float, double>(const float*, double*, long long, cudaStream_t);
 template void launch_zero_boundary<double>(double*, const int*, int, cudaStream_t);

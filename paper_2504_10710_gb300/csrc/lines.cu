@@ -31,15 +31,17 @@ struct WarpLineArgs {
     const T* off;
     const T* g;
     const T* r;
-    const T* y;
+    T* y;
     T* x;
 };
 
 // shared-memory index with one pad word per 32: lane-chunk reads are conflict free
 __device__ __forceinline__ int padi(int k) { return k + (k >> 5); }
 
-// MODE 0: g = A.g; MODE 1: g = A.r - A.y; MODE 2: g = A.r.  Output: MODE 0
-// stores x = B^-1 g, MODE 1/2 add alpha B^-1 g to x.
+// MODE 0: x = B^-1 g.  MODE 1: x += alpha B^-1 (r - y), and every y entry
+// read is reset to 0 (the apply that produced y accumulates into a zeroed
+// buffer, so its consumer restores that state).  MODE 2: x += alpha B^-1 r.
+// MODE 3: x = alpha B^-1 r (first smoothing step from x = 0).
 template <typename T, int C, int LPB, int MODE>
 __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) {
     constexpr int SPAN = 32 * C + C;
@@ -86,6 +88,7 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
             sd[sidx] = vd[m];
             so[sidx] = vo[m];
             sg[sidx] = vg[m];
+            if (MODE == 1) A.y[lnode + (k + 1) * A.stride] = T(0);
         }
     }
     __syncthreads();
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
     }
     __syncthreads();
     T out[C];
-    if (MODE != 0) {
+    if (MODE == 1 || MODE == 2) {
 #pragma unroll
         for (int m = 0; m < C; ++m) {
             const int k = lk + 32 * m;
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
         const int k = lk + 32 * m;
         if (lw < Wc && k < n) {
             const T v = sg[lw * SPAN + padi(k)];
-            A.x[lnode + (k + 1) * A.stride] = MODE == 0 ? v : out[m] + A.alpha * v;
+            A.x[lnode + (k + 1) * A.stride] = MODE == 0 ? v : (MODE == 3 ? A.alpha * v : out[m] + A.alpha * v);
         }
     }
 }
@@ -206,9 +209,12 @@ template <typename T, int C>
 void launch_c(const WarpLineArgs<T>& A, cudaStream_t st) {
     const size_t smem = sizeof(T) * 3 * kLPB * (32 * C + C);
     const int blocks = (A.nlines + kLPB - 1) / kLPB;
-    if (A.mode == 0) line_warp_kernel<T, C, kLPB, 0><<<blocks, 32 * kLPB, smem, st>>>(A);
-    else if (A.y) line_warp_kernel<T, C, kLPB, 1><<<blocks, 32 * kLPB, smem, st>>>(A);
-    else line_warp_kernel<T, C, kLPB, 2><<<blocks, 32 * kLPB, smem, st>>>(A);
+    switch (A.mode) {
+        case 0: line_warp_kernel<T, C, kLPB, 0><<<blocks, 32 * kLPB, smem, st>>>(A); break;
+        case 1: line_warp_kernel<T, C, kLPB, 1><<<blocks, 32 * kLPB, smem, st>>>(A); break;
+        case 2: line_warp_kernel<T, C, kLPB, 2><<<blocks, 32 * kLPB, smem, st>>>(A); break;
+        default: line_warp_kernel<T, C, kLPB, 3><<<blocks, 32 * kLPB, smem, st>>>(A); break;
+    }
 }
 
 template <typename T, int C>
@@ -219,6 +225,8 @@ bool set_attr() {
            cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, kLPB, 1>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess &&
            cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, kLPB, 2>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess &&
+           cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, kLPB, 3>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
 }
 
@@ -233,7 +241,7 @@ bool init_line_warp_attributes() {
 }
 
 template <typename T>
-bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, const T* y, T* x, T alpha,
+bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
                       cudaStream_t st) {
     WarpLineArgs<T> A;
     A.n = L.n[s] - 2;
@@ -274,9 +282,9 @@ bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T
     return true;
 }
 
-template bool launch_line_warp<float>(const DevLevel<float>&, int, int, const float*, const float*, const float*,
+template bool launch_line_warp<float>(const DevLevel<float>&, int, int, const float*, const float*, float*,
                                       float*, float, cudaStream_t);
 template bool launch_line_warp<double>(const DevLevel<double>&, int, int, const double*, const double*,
-                                       const double*, double*, double, cudaStream_t);
+                                       double*, double*, double, cudaStream_t);
 
 }  // namespace glls

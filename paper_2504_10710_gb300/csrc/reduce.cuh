@@ -1,0 +1,45 @@
+// Block-level FP64 reductions shared by the kernels: a warp-shuffle block
+// sum, the "last block" ticket, and the fixed-order sum of block partials
+// (results do not depend on block scheduling).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace glls {
+namespace {
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
+    return s;   // valid in thread 0
+}
+
+// Every block writes its partial sums; the last block to finish (atomic
+// ticket) adds the partials in block order, so the result does not depend on
+// scheduling, and resets the ticket for the next launch.
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    return is_last;
+}
+
+__device__ __forceinline__ void finalize_partials(const double* part, int ndots, int nblocks, double* S, int slot0, int slot1,
+                                  double* red) {
+    for (int d = 0; d < ndots; ++d) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += __ldcg(part + d * nblocks + i);
+        double t = block_sum(s, red);
+        if (threadIdx.x == 0) S[d == 0 ? slot0 : slot1] = t;
+    }
+}
+
+}  // namespace
+}  // namespace glls
