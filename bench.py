@@ -131,7 +131,7 @@ def run_ours(args, rank, world):
     prob.set_dirichlet(g_d, stream)
 
     def timed(precision, steps, warmup, clocks=None):
-        o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=precision, use_graph=1)
+        o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=precision, use_graph=2)
         its = []
         for _ in range(warmup):
             prob.solve(u_d, o, stream)

@@ -78,8 +78,11 @@ typedef struct {
     double alpha;    /* damping of the line smoothing step */
     int precision;   /* GLLS_PREC_FP64 or GLLS_PREC_MIXED */
     int krylov;      /* GLLS_KRYLOV_FCG (Polak-Ribiere beta) or _PCG (Fletcher-Reeves) */
-    int use_graph;   /* 1: replay the outer iteration as a captured CUDA graph */
-    int check_every; /* read the residual back every k iterations (>= 1) */
+    int use_graph;   /* 0: host loop, kernels launched per iteration;
+                        1: host loop, each outer iteration replayed as a captured CUDA graph;
+                        2: the whole solve as one captured graph whose outer loop is a
+                           device-side conditional WHILE node (one host synchronisation) */
+    int check_every; /* host loops (use_graph 0/1): read the residual back every k iterations */
 } glls_solve_opts;
 
 typedef struct {

@@ -69,11 +69,14 @@ struct glls_problem {
     std::vector<void*> allocs;
     size_t bytes = 0;
     double setup_ms = 0.0;
-    cudaStream_t capture_stream = nullptr;
-    // cached graph of one outer iteration
+    cudaStream_t capture_stream = nullptr, capture_stream2 = nullptr;
+    // cached graph of one outer iteration (host-driven loop) and of the whole
+    // solve (device-driven loop)
     cudaGraphExec_t iter_exec = nullptr;
     int g_gamma = -1, g_m = -1, g_prec = -1, g_krylov = -1;
     double g_alpha = 0.0;
+    cudaGraphExec_t solve_exec = nullptr;
+    glls_solve_opts solve_key{};
     bool has_rhs = false, has_dirichlet = false;
 
     template <typename T>
@@ -275,6 +278,84 @@ void outer_iteration(glls_problem* P, const glls_solve_opts* o, cudaStream_t st)
     launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, P->part, P->S, P->ticket, mixed ? P->r32 : nullptr, st);
 }
 
+// Lifting and Krylov initialisation (x = p = q = 0, r = f0, S_RR0 = r.r).
+void solve_prologue(glls_problem* P, const glls_solve_opts* o, cudaStream_t st) {
+    const long long N = P->N;
+    const int L = (int)P->L64.size() - 1;
+    const DevLevel<double>& F = P->L64[L].dev;
+    launch_boundary_only(P->g, P->v, F.n, F.dim, st);
+    launch_apply<double>(F, P->v, P->yk, false, st);
+    launch_lift_rhs(P->mass, P->f, P->yk, P->f0, F.n, F.dim, st);
+    cudaMemsetAsync(P->xk, 0, sizeof(double) * N, st);
+    cudaMemsetAsync(P->pk, 0, sizeof(double) * N, st);
+    cudaMemsetAsync(P->qk, 0, sizeof(double) * N, st);
+    cudaMemcpyAsync(P->rk, P->f0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    launch_dots(P->rk, P->rk, nullptr, nullptr, 1, N, P->part, P->S, S_RR0, S_RR0, P->ticket, st);
+    if (o->precision == GLLS_PREC_MIXED) launch_cast<double, float>(P->rk, P->r32, N, st);
+}
+
+bool same_solve_key(const glls_solve_opts& a, const glls_solve_opts& b) {
+    return a.tol == b.tol && a.max_iter == b.max_iter && a.gamma == b.gamma && a.m == b.m && a.alpha == b.alpha &&
+           a.precision == b.precision && a.krylov == b.krylov;
+}
+
+// The whole solve as one graph: prologue, a conditional WHILE node whose body
+// is one outer iteration followed by the loop-control kernel, then y = x + v.
+glls_status get_solve_graph(glls_problem* P, const glls_solve_opts* o) {
+    if (P->solve_exec && same_solve_key(P->solve_key, *o)) return GLLS_OK;
+    if (P->solve_exec) {
+        cudaGraphExecDestroy(P->solve_exec);
+        P->solve_exec = nullptr;
+    }
+    cudaStream_t cs = P->capture_stream, cs2 = P->capture_stream2;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaStreamCaptureStatus stt;
+    cudaGraph_t capg = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &capg, nullptr, nullptr, nullptr);
+    cudaGraphConditionalHandle handle = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, capg, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraph_t junk;
+        cudaStreamEndCapture(cs, &junk);
+        if (junk) cudaGraphDestroy(junk);
+        CK(e);
+    }
+    solve_prologue(P, o, cs);
+    launch_solve_init(P->S, handle, o->tol, o->max_iter, cs);
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &capg, &deps, nullptr, &ndeps);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, capg, deps, nullptr, ndeps, &cp);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            outer_iteration(P, o, cs2);
+            launch_solve_cond(P->S, handle, o->max_iter, cs2);
+            e = cudaStreamEndCapture(cs2, &body);
+        }
+    }
+    if (e == cudaSuccess) {
+        cudaMemcpyAsync(P->yk, P->xk, sizeof(double) * P->N, cudaMemcpyDeviceToDevice, cs);
+        launch_axpy(P->yk, P->v, 1.0, P->N, cs);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->solve_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    CK(e);
+    P->solve_key = *o;
+    return GLLS_OK;
+}
+
 glls_status get_iteration_graph(glls_problem* P, const glls_solve_opts* o) {
     if (P->iter_exec && P->g_gamma == o->gamma && P->g_m == o->m && P->g_prec == o->precision &&
         P->g_krylov == o->krylov && P->g_alpha == o->alpha)
@@ -400,7 +481,7 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
         CK(cudaMemset(*vp, 0, sizeof(double) * N));
     }
     CK(P->alloc(&P->S, S_COUNT));
-    CK(P->alloc(&P->part, std::max<long long>(2 * kDotBlocks, H.back().E + 1)));
+    CK(P->alloc(&P->part, std::max<long long>(2 * kMaxReduceBlocks, H.back().E + 1)));
     CK(P->alloc(&P->ticket, 1));
     CK(cudaMemset(P->ticket, 0, sizeof(unsigned)));
     CK(P->alloc(&P->r32, N));
@@ -409,6 +490,7 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
     CK(cudaMemset(P->z32, 0, sizeof(float) * N));
     CK(cudaMallocHost(&P->hostS, sizeof(double) * S_COUNT));
     CK(cudaStreamCreateWithFlags(&P->capture_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&P->capture_stream2, cudaStreamNonBlocking));
     CK(cudaDeviceSynchronize());
     P->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = P.release();
@@ -419,7 +501,9 @@ void glls_problem_destroy(glls_problem* P) {
     if (!P) return;
     cudaSetDevice(P->device);
     if (P->iter_exec) cudaGraphExecDestroy(P->iter_exec);
+    if (P->solve_exec) cudaGraphExecDestroy(P->solve_exec);
     if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
+    if (P->capture_stream2) cudaStreamDestroy(P->capture_stream2);
     for (void* a : P->allocs) cudaFree(a);
     if (P->hostS) cudaFreeHost(P->hostS);
     delete P;
@@ -482,28 +566,47 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
     cudaStream_t st = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     const long long N = P->N;
-    const int L = (int)P->L64.size() - 1;
     if (!P->has_dirichlet) CK(cudaMemsetAsync(P->g, 0, sizeof(double) * N, st));
-    // lifting: f0 = M f - A v
-    glls_status ls = glls_lift_f64(P, P->f, P->g, P->f0, stream);
-    if (ls != GLLS_OK) return ls;
-    // x = 0, r = f0, p = q = 0; S: rz = 1, alpha = 0 so that the first direction is p = z
-    CK(cudaMemsetAsync(P->xk, 0, sizeof(double) * N, st));
-    CK(cudaMemsetAsync(P->pk, 0, sizeof(double) * N, st));
-    CK(cudaMemsetAsync(P->qk, 0, sizeof(double) * N, st));
-    CK(cudaMemcpyAsync(P->rk, P->f0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-    double init[S_COUNT] = {0};
-    init[S_RZ] = 1.0;
-    std::memcpy(P->hostS, init, sizeof(init));
-    CK(cudaMemcpyAsync(P->S, P->hostS, sizeof(init), cudaMemcpyHostToDevice, st));
-    launch_dots(P->rk, P->rk, nullptr, nullptr, 1, N, P->part, P->S, S_RR0, S_RR0, P->ticket, st);
-    if (o->precision == GLLS_PREC_MIXED) launch_cast<double, float>(P->rk, P->r32, N, st);
-    CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    const double rr0 = P->hostS[S_RR0];
     int it = 0;
     double rel = 0.0;
     glls_status result = GLLS_OK;
+    if (o->use_graph == 2) {
+        // whole solve on the device: one graph launch, one synchronisation
+        glls_status gs = get_solve_graph(P, o);
+        if (gs != GLLS_OK) return gs;
+        CK(cudaGraphLaunch(P->solve_exec, st));
+        CK(cudaMemcpyAsync(u, P->yk, sizeof(double) * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           st));
+        CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const double* h = P->hostS;
+        it = (int)h[S_ITER];
+        if (h[S_FLAG] != 0.0) {
+            result = fail(GLLS_ERR_BREAKDOWN, "breakdown in the outer iteration (p.Ap <= 0 or NaN)");
+        } else if (h[S_RR0] > 0.0) {
+            rel = std::sqrt(h[S_RR] / h[S_RR0]);
+            result = h[S_RR] <= h[S_TOL2] ? GLLS_OK : fail(GLLS_ERR_NOT_CONVERGED, "max_iter reached");
+        }
+        CK(cudaGetLastError());
+        if (stats) {
+            stats->iterations = it;
+            stats->rel_residual = rel;
+            stats->setup_ms = P->setup_ms;
+            stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            stats->status = result;
+        }
+        return result;
+    }
+    // host-driven loop: prologue, then one outer iteration per launch
+    solve_prologue(P, o, st);
+    double init[S_COUNT] = {0};
+    CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double rr0 = P->hostS[S_RR0];
+    init[S_RZ] = 1.0;
+    init[S_RR0] = rr0;
+    std::memcpy(P->hostS, init, sizeof(init));
+    CK(cudaMemcpyAsync(P->S, P->hostS, sizeof(init), cudaMemcpyHostToDevice, st));
     if (!(rr0 >= 0.0) || !std::isfinite(rr0)) {
         result = fail(GLLS_ERR_BREAKDOWN, "non-finite right-hand side");
     } else if (rr0 > 0.0) {
@@ -531,6 +634,7 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
                 }
             }
         }
+        if (result == GLLS_ERR_NOT_CONVERGED) fail(GLLS_ERR_NOT_CONVERGED, "max_iter reached");
         rel = std::sqrt(P->hostS[S_RR] / rr0);
     }
     CK(cudaGetLastError());
@@ -546,7 +650,6 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
         stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         stats->status = result;
     }
-    (void)L;
     return result;
 }
 

@@ -100,6 +100,7 @@ void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st);
 // S[slot0] (and S[slot1]).  `ticket` is a zero-initialised counter that the
 // kernel resets.
 constexpr int kDotBlocks = 304;   // 2 x 152 SMs
+constexpr int kMaxReduceBlocks = 8192;
 void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots,
                  long long n, double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st);
 // Outer-iteration dots S_RZNEW = r.z, S_ZQ = z.q; z is first taken from z32
@@ -124,5 +125,10 @@ void launch_lift_rhs(const double* mass, const double* f, const double* y, doubl
                      cudaStream_t st);
 void launch_boundary_only(const double* g, double* v, const int n[3], int dim, cudaStream_t st);
 void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st);   // y += a x
+// Device-side solve loop: after S_RR0 is computed, initialise S and set the
+// WHILE handle (r0 != 0); at the end of each iteration count it and set the
+// handle to (r.r > tol^2 r0.r0, it < maxit, no breakdown).
+void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st);
+void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st);
 
 }  // namespace glls

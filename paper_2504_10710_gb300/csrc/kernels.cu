@@ -401,6 +401,36 @@ __global__ void fcg_direction_kernel(double* __restrict__ p, const double* __res
     }
 }
 
+// Device-side loop control for the captured solve graph (conditional WHILE
+// node): solve_init_kernel runs once after r0.r0 is known, solve_cond_kernel
+// ends every outer iteration.
+__global__ void solve_init_kernel(double* S, cudaGraphConditionalHandle h, double tol, int maxit) {
+    if (threadIdx.x != 0) return;
+    const double rr0 = S[S_RR0];
+    S[S_RR] = rr0;
+    S[S_TOL2] = tol * tol * rr0;
+    S[S_ITER] = 0.0;
+    S[S_RZ] = 1.0;
+    S[S_ALPHA] = 0.0;
+    S[S_FLAG] = 0.0;
+    S[S_ZQ] = 0.0;
+    S[S_PQ] = 0.0;
+    S[S_RZNEW] = 0.0;
+    const bool go = rr0 > 0.0 && isfinite(rr0) && maxit > 0;
+    if (!isfinite(rr0)) S[S_FLAG] = 1.0;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void solve_cond_kernel(double* S, cudaGraphConditionalHandle h, int maxit) {
+    if (threadIdx.x != 0) return;
+    const double it = S[S_ITER] + 1.0;
+    S[S_ITER] = it;
+    const double rr = S[S_RR];
+    const bool go = rr > S[S_TOL2] && it < (double)maxit && S[S_FLAG] == 0.0 && isfinite(rr);
+    if (!isfinite(rr)) S[S_FLAG] = 1.0;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 __global__ void lift_rhs_kernel(const double* __restrict__ mass, const double* __restrict__ f,
                                 const double* __restrict__ y, double* __restrict__ f0, int3 n, int dim) {
     const long long total = (long long)n.x * n.y * n.z;
@@ -419,6 +449,14 @@ __global__ void boundary_only_kernel(const double* __restrict__ g, double* __res
 __global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] += a * x[i];
+}
+
+// One element per thread (more loads in flight than a grid-stride loop);
+// the partial-sum buffer holds up to kMaxReduceBlocks entries per dot.
+inline int reduce_grid(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
+    return (int)(b < 1 ? 1 : b);
 }
 
 inline int grid_for(long long n, int threads = 256) {
@@ -546,7 +584,7 @@ void launch_fcg_update(double* x, double* r, const double* p, const double* q, l
 
 void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* part, double* S,
                        unsigned* ticket, cudaStream_t st) {
-    dots_rz_zq_kernel<<<kDotBlocks, 256, 0, st>>>(r, z, z32, q, n, part, S, ticket);
+    dots_rz_zq_kernel<<<reduce_grid(n), 256, 0, st>>>(r, z, z32, q, n, part, S, ticket);
 }
 
 void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, unsigned* ticket,
@@ -563,6 +601,14 @@ void launch_lift_rhs(const double* mass, const double* f, const double* y, doubl
 void launch_boundary_only(const double* g, double* v, const int n[3], int dim, cudaStream_t st) {
     const long long total = (long long)n[0] * n[1] * n[2];
     boundary_only_kernel<<<grid_for(total), 256, 0, st>>>(g, v, make_int3(n[0], n[1], n[2]), dim);
+}
+
+void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st) {
+    solve_init_kernel<<<1, 32, 0, st>>>(S, h, tol, maxit);
+}
+
+void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st) {
+    solve_cond_kernel<<<1, 32, 0, st>>>(S, h, maxit);
 }
 
 void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st) {

@@ -118,7 +118,7 @@ def gll(p: int):
 
 
 def opts(tol=1e-10, max_iter=200, gamma=1, m=1, alpha=0.5, precision=PREC_MIXED, krylov=KRYLOV_FCG,
-         use_graph=1, check_every=1) -> SolveOpts:
+         use_graph=2, check_every=1) -> SolveOpts:
     return SolveOpts(tol, max_iter, gamma, m, alpha, precision, krylov, use_graph, check_every)
 
 

@@ -186,7 +186,7 @@ SOLVE_CASES = [
 
 
 @pytest.mark.parametrize("name,mk,sm,rs,gamma,alpha", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
-@pytest.mark.parametrize("use_graph", [1, 0], ids=["graph", "stream"])
+@pytest.mark.parametrize("use_graph", [2, 1, 0], ids=["device_loop", "graph", "stream"])
 def test_solve_fp64_matches_oracle(name, mk, sm, rs, gamma, alpha, use_graph):
     wl = mk()
     prob, h, coords = make(wl, sm, rs)
