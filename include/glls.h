@@ -162,6 +162,25 @@ glls_status glls_precondition_f32(glls_problem* prob, const glls_solve_opts* opt
  * and 0 inside (Sec. 2.3); f, g, f0: fine-grid device vectors. */
 glls_status glls_lift_f64(glls_problem* prob, const double* f, const double* g, double* f0, void* stream);
 
+/* rc = R_l (r - A_l x), like glls_restrict_f32, for callers that cannot
+ * call cudaMalloc: code running while a stream is captured in global mode
+ * (where allocation calls are prohibited) or under an external allocator that
+ * owns all device memory.  This entry point allocates nothing and does not
+ * use the problem's own scratch: the apply result and the transfer
+ * temporaries live in one fixed library-wide device array of 3 x 262,144
+ * floats (3 MiB), which every GPU that loads the library holds until the
+ * process exits.  It has no counterpart in the paper.
+ *   - Level l must have at most 262,144 nodes; larger levels return
+ *     GLLS_ERR_INVALID with the limit in the message.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call shares the array and leaves its contents behind; each call
+ *     clears what must start at zero.  Calls that overlap on the GPU (other
+ *     streams, concurrent graphs) race on the array and must be serialised.
+ * Arguments as glls_restrict_f32 (device vectors, asynchronous on stream). */
+glls_status glls_restrict_noalloc_f32(glls_problem* prob, int level, const float* r, const float* x, float* rc,
+                                      void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* glls_last_error(void);
 

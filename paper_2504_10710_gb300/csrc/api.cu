@@ -722,3 +722,76 @@ LEVEL_OPS(f64, double)
 LEVEL_OPS(f32, float)
 
 }  // extern "C"
+
+// ===========================================================================
+// Restriction without any device allocation
+// ===========================================================================
+// Scratch for glls_restrict_noalloc_f32: the apply output y and two transfer
+// temporaries, each kNoAllocMaxNodes floats (3 MiB in total).  Being a
+// file-scope __device__ array it exists once on every device that loads the
+// library, for the life of the process, and every call shares it.
+namespace {
+
+constexpr long long kNoAllocMaxNodes = 1LL << 18;
+static __device__ __align__(256) float g_noalloc_scratch[3 * kNoAllocMaxNodes];
+
+std::mutex g_noalloc_mutex;
+float* g_noalloc_addr[128] = {nullptr};   // device address of the array, per device ordinal
+
+// Host code must not use g_noalloc_scratch as a pointer: its host-side symbol
+// is a stand-in, not a device address.  The device address is looked up once
+// per device, with that device current.
+glls_status noalloc_scratch(int device, float** out) {
+    if (device < 0 || device >= 128) return fail(GLLS_ERR_INVALID, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return fail(GLLS_ERR_CUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+        g_noalloc_addr[device] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return GLLS_OK;
+}
+
+}  // namespace
+
+extern "C" glls_status glls_restrict_noalloc_f32(glls_problem* P, int level, const float* r, const float* x,
+                                                 float* rc, void* stream) {
+    glls_status s = check_level(P, level, true);
+    if (s != GLLS_OK) return s;
+    if (!r || !x || !rc) return fail(GLLS_ERR_INVALID, "null vector");
+    const DevLevel<float>& F = P->L32[level].dev;
+    const DevLevel<float>& C = P->L32[level - 1].dev;
+    if (F.N > kNoAllocMaxNodes)
+        return fail(GLLS_ERR_INVALID, "glls_restrict_noalloc_f32: level has " + std::to_string(F.N) +
+                                          " nodes, more than the fixed scratch limit of " +
+                                          std::to_string(kNoAllocMaxNodes));
+    int cur_dev = -1;
+    CK(cudaGetDevice(&cur_dev));
+    if (cur_dev != P->device) CK(cudaSetDevice(P->device));
+    float* base = nullptr;
+    s = noalloc_scratch(P->device, &base);
+    if (s != GLLS_OK) return s;
+    float* y = base;
+    float* t[2] = {base + kNoAllocMaxNodes, base + 2 * kNoAllocMaxNodes};
+    cudaStream_t st = (cudaStream_t)stream;
+    // y must start at zero: the apply sums element contributions into it
+    launch_apply<float>(F, x, y, true, st, false);
+    int cur[3] = {F.n[0], F.n[1], F.n[2]};
+    const float* in = r;
+    const float* in2 = y;
+    for (int a = 0; a < F.dim; ++a) {
+        int nxt[3] = {cur[0], cur[1], cur[2]};
+        nxt[a] = C.n[a];
+        const bool last = a == F.dim - 1;
+        float* out = last ? rc : t[a % 2];
+        launch_transfer<float>(F.R[a], a, cur, nxt, in, in2, out, false, last, st);
+        in = out;
+        in2 = nullptr;
+        for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
+    }
+    CK(cudaGetLastError());
+    return GLLS_OK;
+}

@@ -70,6 +70,7 @@ def lib():
             "glls_set_rhs": [vp, vp, i, vp],
             "glls_solve": [vp, C.POINTER(SolveOpts), vp, i, vp, C.POINTER(Stats)],
             "glls_lift_f64": [vp, vp, vp, vp, vp],
+            "glls_restrict_noalloc_f32": [vp, i, vp, vp, vp, vp],
         }
         for suf, real in (("f64", d), ("f32", C.c_float)):
             sig[f"glls_apply_{suf}"] = [vp, i, vp, vp, vp]
