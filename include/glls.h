@@ -39,6 +39,7 @@ extern "C" {
 #endif
 
 typedef enum {
+    GLLS_NOT_READY = 1,           /* glls_poll: the request has not finished yet */
     GLLS_OK = 0,
     GLLS_ERR_INVALID = -1,        /* bad argument, size, level or axis */
     GLLS_ERR_OOM = -2,            /* device or host allocation failed */
@@ -123,6 +124,50 @@ glls_status glls_set_rhs(glls_problem* prob, const double* f, int on_device, voi
  * the last iterate) or GLLS_ERR_BREAKDOWN; stats may be NULL. */
 glls_status glls_solve(glls_problem* prob, const glls_solve_opts* opts, double* u, int on_device,
                        void* stream, glls_stats* stats);
+
+/* Solve several independent problems (any sizes, orders, dimensions, on one
+ * device) together: one graph launch whose parallel branches are the
+ * problems' whole solves, each with its own device-side loop; their kernels
+ * overlap on the GPU.  u[i]: N_i values per problem (device or host per
+ * on_device); stats: n entries or NULL.  The graph is cached per (problem
+ * list, options).  Returns GLLS_OK if every problem converged, else the
+ * first failure status (per-problem status in stats[i].status). */
+glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve_opts* opts, double* const* u,
+                             int on_device, void* stream, glls_stats* stats);
+
+/* Device bytes glls_problem_create would allocate for desc (estimate used for
+ * admission by an HBM budget; no allocation, no device work). */
+glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes);
+
+/* ---- serving: a request loop with admission by HBM budget ----------------
+ * A server owns `slots` worker threads, each with its own CUDA stream, and a
+ * cache of resident problems (meshes with their geometry factors, line data
+ * and Krylov state) keyed by the mesh.  Requests are admitted in arrival
+ * order as soon as a slot is free and the resident bytes plus the request's
+ * estimate fit the budget (idle cached meshes are evicted, least recently
+ * used first); admitted requests run concurrently on the device.  A request
+ * whose estimate exceeds the whole budget fails with GLLS_ERR_BUDGET. */
+typedef struct glls_server glls_server;
+typedef struct {
+    unsigned long long submitted, completed, failed, queued, running;
+    size_t resident_bytes, budget_bytes;
+    int cached_problems;
+} glls_server_info;
+
+glls_status glls_server_create(int device, size_t hbm_budget_bytes, int slots, glls_server** out);
+/* Waits for running requests, then frees every cached problem. */
+void glls_server_destroy(glls_server* server);
+/* Queue one solve.  mesh (with its coords), f and g (N host values each; g may
+ * be NULL for homogeneous data) are copied; u (N host values) is written when
+ * the request completes and must stay valid until then.  Returns a ticket. */
+glls_status glls_submit(glls_server* server, const glls_mesh_desc* mesh, const double* f, const double* g,
+                        const glls_solve_opts* opts, double* u, unsigned long long* ticket);
+/* GLLS_NOT_READY while queued or running (wait = 0), else the request's
+ * status with stats filled (queue + solve time in stats->solve_ms, set-up of a
+ * newly created problem in stats->setup_ms); wait = 1 blocks until done.  A
+ * finished ticket is released by the first poll that returns its result. */
+glls_status glls_poll(glls_server* server, unsigned long long ticket, int wait, glls_stats* stats);
+glls_status glls_server_info_get(glls_server* server, glls_server_info* out);
 
 /* ---- level operations on device vectors (parity tests, custom drivers) ----
  * Each exists as _f64 and _f32; the FP32 variant uses the FP32 copies of the

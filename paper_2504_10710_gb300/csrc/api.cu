@@ -299,27 +299,17 @@ bool same_solve_key(const glls_solve_opts& a, const glls_solve_opts& b) {
            a.precision == b.precision && a.krylov == b.krylov;
 }
 
-// The whole solve as one graph: prologue, a conditional WHILE node whose body
-// is one outer iteration followed by the loop-control kernel, then y = x + v.
-glls_status get_solve_graph(glls_problem* P, const glls_solve_opts* o) {
-    if (P->solve_exec && same_solve_key(P->solve_key, *o)) return GLLS_OK;
-    if (P->solve_exec) {
-        cudaGraphExecDestroy(P->solve_exec);
-        P->solve_exec = nullptr;
-    }
-    cudaStream_t cs = P->capture_stream, cs2 = P->capture_stream2;
-    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+// Adds the whole solve of P to the graph being captured on cs: prologue, a
+// conditional WHILE node whose body (captured on cs2) is one outer iteration
+// followed by the loop-control kernel, then y = x + v.  Returns the first
+// CUDA error; the caller ends the capture.
+cudaError_t capture_solve(glls_problem* P, const glls_solve_opts* o, cudaStream_t cs, cudaStream_t cs2) {
     cudaStreamCaptureStatus stt;
     cudaGraph_t capg = nullptr;
     cudaError_t e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &capg, nullptr, nullptr, nullptr);
     cudaGraphConditionalHandle handle = 0;
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, capg, 0, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) {
-        cudaGraph_t junk;
-        cudaStreamEndCapture(cs, &junk);
-        if (junk) cudaGraphDestroy(junk);
-        CK(e);
-    }
+    if (e != cudaSuccess) return e;
     solve_prologue(P, o, cs);
     launch_solve_init(P->S, handle, o->tol, o->max_iter, cs);
     const cudaGraphNode_t* deps = nullptr;
@@ -346,6 +336,19 @@ glls_status get_solve_graph(glls_problem* P, const glls_solve_opts* o) {
         cudaMemcpyAsync(P->yk, P->xk, sizeof(double) * P->N, cudaMemcpyDeviceToDevice, cs);
         launch_axpy(P->yk, P->v, 1.0, P->N, cs);
     }
+    return e;
+}
+
+// The whole solve as one cached graph (device-side loop).
+glls_status get_solve_graph(glls_problem* P, const glls_solve_opts* o) {
+    if (P->solve_exec && same_solve_key(P->solve_key, *o)) return GLLS_OK;
+    if (P->solve_exec) {
+        cudaGraphExecDestroy(P->solve_exec);
+        P->solve_exec = nullptr;
+    }
+    cudaStream_t cs = P->capture_stream, cs2 = P->capture_stream2;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = capture_solve(P, o, cs, cs2);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e2;
@@ -354,6 +357,53 @@ glls_status get_solve_graph(glls_problem* P, const glls_solve_opts* o) {
     CK(e);
     P->solve_key = *o;
     return GLLS_OK;
+}
+
+// Fills stats / status of a finished device-loop solve from the host copy of S.
+glls_status solve_result(glls_problem* P, const double* h, glls_stats* stats, double t_ms) {
+    glls_status result = GLLS_OK;
+    double rel = 0.0;
+    if (h[S_FLAG] != 0.0) {
+        result = GLLS_ERR_BREAKDOWN;
+    } else if (h[S_RR0] > 0.0) {
+        rel = std::sqrt(h[S_RR] / h[S_RR0]);
+        result = h[S_RR] <= h[S_TOL2] ? GLLS_OK : GLLS_ERR_NOT_CONVERGED;
+    }
+    if (stats) {
+        stats->iterations = (int)h[S_ITER];
+        stats->rel_residual = rel;
+        stats->setup_ms = P->setup_ms;
+        stats->solve_ms = t_ms;
+        stats->status = result;
+    }
+    return result;
+}
+
+// Batched solves: one graph whose parallel branches are the whole solves of
+// several problems (each with its own device-side loop), cached per
+// (problem list, options).
+struct BatchEntry {
+    std::vector<glls_problem*> probs;
+    glls_solve_opts key;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t master = nullptr;
+};
+std::mutex g_batch_mutex;
+std::vector<BatchEntry> g_batches;   // small LRU, newest last
+
+void forget_batches_of(glls_problem* P) {
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    for (size_t i = 0; i < g_batches.size();) {
+        bool hit = false;
+        for (auto* q : g_batches[i].probs) hit = hit || q == P;
+        if (hit) {
+            cudaGraphExecDestroy(g_batches[i].exec);
+            cudaStreamDestroy(g_batches[i].master);
+            g_batches.erase(g_batches.begin() + i);
+        } else {
+            ++i;
+        }
+    }
 }
 
 glls_status get_iteration_graph(glls_problem* P, const glls_solve_opts* o) {
@@ -499,6 +549,7 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
 
 void glls_problem_destroy(glls_problem* P) {
     if (!P) return;
+    forget_batches_of(P);
     cudaSetDevice(P->device);
     if (P->iter_exec) cudaGraphExecDestroy(P->iter_exec);
     if (P->solve_exec) cudaGraphExecDestroy(P->solve_exec);
@@ -579,22 +630,13 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
                            st));
         CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const double* h = P->hostS;
-        it = (int)h[S_ITER];
-        if (h[S_FLAG] != 0.0) {
-            result = fail(GLLS_ERR_BREAKDOWN, "breakdown in the outer iteration (p.Ap <= 0 or NaN)");
-        } else if (h[S_RR0] > 0.0) {
-            rel = std::sqrt(h[S_RR] / h[S_RR0]);
-            result = h[S_RR] <= h[S_TOL2] ? GLLS_OK : fail(GLLS_ERR_NOT_CONVERGED, "max_iter reached");
-        }
         CK(cudaGetLastError());
-        if (stats) {
-            stats->iterations = it;
-            stats->rel_residual = rel;
-            stats->setup_ms = P->setup_ms;
-            stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-            stats->status = result;
-        }
+        result = solve_result(P, P->hostS, stats,
+                              std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+        if (result == GLLS_ERR_BREAKDOWN) fail(result, "breakdown in the outer iteration (p.Ap <= 0 or NaN)");
+        if (result == GLLS_ERR_NOT_CONVERGED) fail(result, "max_iter reached");
+        (void)it;
+        (void)rel;
         return result;
     }
     // host-driven loop: prologue, then one outer iteration per launch
@@ -651,6 +693,136 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
         stats->status = result;
     }
     return result;
+}
+
+glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
+    if (!desc || !bytes) return fail(GLLS_ERR_INVALID, "null argument");
+    if (desc->dim != 2 && desc->dim != 3) return fail(GLLS_ERR_INVALID, "dim must be 2 or 3");
+    if (desc->order < 1 || desc->order > 24) return fail(GLLS_ERR_INVALID, "order must be in 1..24");
+    const int d = desc->dim;
+    long long ne[3] = {1, 1, 1}, E = 1;
+    for (int a = 0; a < d; ++a) {
+        if (desc->nelem[a] < 1) return fail(GLLS_ERR_INVALID, "nelem must be >= 1");
+        ne[a] = desc->nelem[a];
+        E *= ne[a];
+    }
+    const bool multi = E > 1;
+    std::vector<int> chain = order_chain(desc->order, multi);
+    const int ncomp = d == 2 ? 3 : 6;
+    double total = 0.0;
+    long long Nfine = 0, Ncoarse = 0, n0 = 1;
+    for (size_t c = 0; c < chain.size(); ++c) {
+        const int p = chain[c];
+        long long N = 1, nloc = 1, inner = 1;
+        for (int a = 0; a < d; ++a) {
+            N *= ne[a] * p + 1;
+            nloc *= p + 1;
+            inner *= ne[a] * p - 1;
+        }
+        if (c == 0) Nfine = N;
+        if (c + 1 == chain.size()) { Ncoarse = N; n0 = inner; }
+        // G, diag, off, D in FP64 + FP32; five level vectors in each precision; transfer bands
+        total += 12.0 * ((double)ncomp * E * nloc + (1 + d) * (double)N + (p + 1) * (p + 1)) + 12.0 * 5 * N;
+        total += 2.0 * d * (12.0 * (2 * p + 2) * (double)(ne[0] * p + 1) + 4.0 * (ne[0] * p + 1));
+    }
+    const double ld64 = (double)((n0 + 1) / 2 * 2), ld32 = (double)((n0 + 3) / 4 * 4);
+    total += 8.0 * n0 + (double)n0 * (8.0 * ld64 + 4.0 * ld32);       // coarse index + dense inverses
+    total += 8.0 * (11.0 * Nfine) + 8.0 * Nfine + 8.0 * std::max<double>(2 * kMaxReduceBlocks, E + 1) + 64.0;
+    total += 4.0 * 2.0 * Nfine;                                          // r32, z32
+    (void)Ncoarse;
+    *bytes = (size_t)total;
+    return GLLS_OK;
+}
+
+glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve_opts* o, double* const* u,
+                             int on_device, void* stream, glls_stats* stats) {
+    if (!probs || n < 1 || !u) return fail(GLLS_ERR_INVALID, "glls_solve_batch: need n >= 1 problems and outputs");
+    glls_status s0 = check_opts(o);
+    if (s0 != GLLS_OK) return s0;
+    const int dev = probs[0] ? probs[0]->device : 0;
+    for (int i = 0; i < n; ++i) {
+        if (!probs[i] || !u[i]) return fail(GLLS_ERR_INVALID, "glls_solve_batch: null problem or output");
+        if (probs[i]->device != dev) return fail(GLLS_ERR_INVALID, "glls_solve_batch: problems on different devices");
+        if (!probs[i]->has_rhs) return fail(GLLS_ERR_INVALID, "glls_solve_batch: right-hand side not set");
+        for (int j = 0; j < i; ++j)
+            if (probs[j] == probs[i]) return fail(GLLS_ERR_INVALID, "glls_solve_batch: a problem appears twice");
+    }
+    CK(cudaSetDevice(dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < n; ++i)
+        if (!probs[i]->has_dirichlet) CK(cudaMemsetAsync(probs[i]->g, 0, sizeof(double) * probs[i]->N, st));
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mutex);
+        std::vector<glls_problem*> key(probs, probs + n);
+        for (size_t i = 0; i < g_batches.size(); ++i)
+            if (g_batches[i].probs == key && same_solve_key(g_batches[i].key, *o)) {
+                BatchEntry hit = g_batches[i];
+                g_batches.erase(g_batches.begin() + i);
+                g_batches.push_back(hit);
+                exec = hit.exec;
+                break;
+            }
+        if (!exec) {
+            BatchEntry be;
+            be.probs = key;
+            be.key = *o;
+            CK(cudaStreamCreateWithFlags(&be.master, cudaStreamNonBlocking));
+            cudaEvent_t fork = nullptr;
+            std::vector<cudaEvent_t> joins(n, nullptr);
+            cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+            for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(be.master, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                e = cudaEventRecord(fork, be.master);
+                for (int i = 0; i < n && e == cudaSuccess; ++i) {
+                    glls_problem* P = probs[i];
+                    e = cudaStreamWaitEvent(P->capture_stream, fork, 0);
+                    if (e == cudaSuccess) e = capture_solve(P, o, P->capture_stream, P->capture_stream2);
+                    if (e == cudaSuccess) e = cudaEventRecord(joins[i], P->capture_stream);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(be.master, joins[i], 0);
+                }
+                cudaGraph_t graph = nullptr;
+                cudaError_t e2 = cudaStreamEndCapture(be.master, &graph);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&be.exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+            }
+            if (fork) cudaEventDestroy(fork);
+            for (auto ev : joins)
+                if (ev) cudaEventDestroy(ev);
+            if (e != cudaSuccess) {
+                cudaStreamDestroy(be.master);
+                CK(e);
+            }
+            exec = be.exec;
+            g_batches.push_back(be);
+            if (g_batches.size() > 8) {
+                cudaGraphExecDestroy(g_batches.front().exec);
+                cudaStreamDestroy(g_batches.front().master);
+                g_batches.erase(g_batches.begin());
+            }
+        }
+    }
+    CK(cudaGraphLaunch(exec, st));
+    for (int i = 0; i < n; ++i) {
+        glls_problem* P = probs[i];
+        CK(cudaMemcpyAsync(u[i], P->yk, sizeof(double) * P->N,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    const double t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    glls_status worst = GLLS_OK;
+    for (int i = 0; i < n; ++i) {
+        glls_status r = solve_result(probs[i], probs[i]->hostS, stats ? &stats[i] : nullptr, t_ms);
+        if (r != GLLS_OK && worst == GLLS_OK) worst = r;
+    }
+    if (worst == GLLS_ERR_BREAKDOWN) fail(worst, "breakdown in at least one problem of the batch");
+    if (worst == GLLS_ERR_NOT_CONVERGED) fail(worst, "at least one problem of the batch reached max_iter");
+    return worst;
 }
 
 #define LEVEL_OPS(SUF, T)                                                                                      \

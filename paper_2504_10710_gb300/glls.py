@@ -15,7 +15,8 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libglls.so")
 
-OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 0, -1, -2, -3, -4, -5
+NOT_READY, OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 1, 0, -1, -2, -3, -4, -5
+ERR_TIMEOUT, ERR_BUDGET = -6, -7
 PREC_FP64, PREC_MIXED = 0, 1
 SMOOTHER_GLL, SMOOTHER_FEM = 0, 1
 RESTRICT_TRANSPOSE, RESTRICT_INTERP = 0, 1
@@ -42,6 +43,12 @@ class Stats(C.Structure):
 class Info(C.Structure):
     _fields_ = [("dim", C.c_int), ("levels", C.c_int), ("order", C.c_int * 8), ("nodes", (C.c_int * 3) * 8),
                 ("ndof", C.c_longlong * 8), ("coarse_unknowns", C.c_longlong), ("device_bytes", C.c_size_t)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("submitted", C.c_ulonglong), ("completed", C.c_ulonglong), ("failed", C.c_ulonglong),
+                ("queued", C.c_ulonglong), ("running", C.c_ulonglong), ("resident_bytes", C.c_size_t),
+                ("budget_bytes", C.c_size_t), ("cached_problems", C.c_int)]
 
 
 class GllsError(RuntimeError):
@@ -71,6 +78,12 @@ def lib():
             "glls_solve": [vp, C.POINTER(SolveOpts), vp, i, vp, C.POINTER(Stats)],
             "glls_lift_f64": [vp, vp, vp, vp, vp],
             "glls_restrict_noalloc_f32": [vp, i, vp, vp, vp, vp],
+            "glls_solve_batch": [C.POINTER(vp), i, C.POINTER(SolveOpts), C.POINTER(vp), i, vp, C.POINTER(Stats)],
+            "glls_estimate_bytes": [C.POINTER(MeshDesc), C.POINTER(C.c_size_t)],
+            "glls_server_create": [i, C.c_size_t, i, C.POINTER(vp)],
+            "glls_submit": [vp, C.POINTER(MeshDesc), vp, vp, C.POINTER(SolveOpts), vp, C.POINTER(C.c_ulonglong)],
+            "glls_poll": [vp, C.c_ulonglong, i, C.POINTER(Stats)],
+            "glls_server_info_get": [vp, C.POINTER(ServerInfo)],
         }
         for suf, real in (("f64", d), ("f32", C.c_float)):
             sig[f"glls_apply_{suf}"] = [vp, i, vp, vp, vp]
@@ -86,6 +99,8 @@ def lib():
             fn.restype = C.c_int
         L.glls_problem_destroy.argtypes = [vp]
         L.glls_problem_destroy.restype = None
+        L.glls_server_destroy.argtypes = [vp]
+        L.glls_server_destroy.restype = None
         L.glls_last_error.argtypes = []
         L.glls_last_error.restype = C.c_char_p
         _lib = L
@@ -227,6 +242,82 @@ class Problem:
 
     def lift(self, f, g, f0, stream=None):
         _check(lib().glls_lift_f64(self.h, _ptr(f), _ptr(g), _ptr(f0), _stream(stream)))
+
+
+def solve_batch(problems, outs, o: SolveOpts, stream=None, raise_on_error=True):
+    """Solve several problems in one graph launch; outs: numpy host arrays
+    (or torch CUDA float64 tensors), one per problem.  Returns the stats."""
+    n = len(problems)
+    hs = (C.c_void_p * n)(*[p.h.value for p in problems])
+    on_device = 0 if isinstance(outs[0], np.ndarray) else 1
+    ptrs = (C.c_void_p * n)(*[(o_.ctypes.data if on_device == 0 else o_.data_ptr()) for o_ in outs])
+    st = (Stats * n)()
+    status = lib().glls_solve_batch(hs, n, C.byref(o), ptrs, on_device, _stream(stream), st)
+    if raise_on_error:
+        _check(status)
+    return list(st)
+
+
+def mesh_desc(dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0):
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    ne = (C.c_int * 3)(*(list(nelem) + [1] * (3 - len(nelem))))
+    return MeshDesc(dim, ne, order, coords.ctypes.data_as(C.POINTER(C.c_double)), smoother, restriction,
+                    device), coords
+
+
+def estimate_bytes(dim, nelem, order, coords):
+    desc, _keep = mesh_desc(dim, nelem, order, coords)
+    out = C.c_size_t()
+    _check(lib().glls_estimate_bytes(C.byref(desc), C.byref(out)))
+    return out.value
+
+
+class Server:
+    """Request loop with admission by HBM budget (native, see glls_submit)."""
+
+    def __init__(self, budget_bytes, slots=4, device=0):
+        h = C.c_void_p()
+        _check(lib().glls_server_create(device, budget_bytes, slots, C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, dim, nelem, order, coords, f, g, o: SolveOpts, out, smoother=SMOOTHER_GLL,
+               restriction=RESTRICT_TRANSPOSE):
+        desc, coords = mesh_desc(dim, nelem, order, coords, smoother, restriction)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+        assert out.dtype == np.float64 and out.flags.c_contiguous
+        t = C.c_ulonglong()
+        _check(lib().glls_submit(self.h, C.byref(desc), f.ctypes.data_as(C.c_void_p),
+                                 None if g is None else g.ctypes.data_as(C.c_void_p), C.byref(o),
+                                 out.ctypes.data_as(C.c_void_p), C.byref(t)))
+        self._keep[t.value] = out          # the output buffer must outlive the request
+        return t.value
+
+    def poll(self, ticket, wait=False):
+        """(status, stats) or (NOT_READY, None)."""
+        st = Stats()
+        status = lib().glls_poll(self.h, ticket, 1 if wait else 0, C.byref(st))
+        if status == NOT_READY:
+            return status, None
+        self._keep.pop(ticket, None)
+        return status, st
+
+    def info(self):
+        inf = ServerInfo()
+        _check(lib().glls_server_info_get(self.h, C.byref(inf)))
+        return inf
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().glls_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def problem_for(workload, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0):

@@ -1,0 +1,148 @@
+"""Batched solves of uneven problems in one graph launch, and the serving loop
+(admission by HBM budget, concurrent requests): results equal those of single
+solves, alone or in the mix."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2504_10710_gb300 import glls, inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+# uneven grids, orders and dimensions; all converge in 12-17 FCG iterations
+MIX = [inputs.random2d((9, 7), 6, amp=0.1, seed=21), inputs.random2d((16, 16), 8, amp=0.1, seed=22),
+       inputs.random2d((4, 5), 7, amp=0.05, seed=23), inputs.random3d((3, 3, 2), 4, amp=0.1, seed=24),
+       inputs.random2d((10, 6), 4, amp=0.1, seed=25), inputs.random2d((6, 8), 5, amp=0.1, seed=26)]
+
+
+def _setup(wl):
+    prob, coords = glls.problem_for(wl)
+    f = wl.sample_rhs(coords)[0]
+    g = wl.sample_dirichlet(coords)
+    prob.set_rhs(f)
+    prob.set_dirichlet(g)
+    return prob, coords, f, g
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("prec", [glls.PREC_FP64, glls.PREC_MIXED], ids=["fp64", "mixed"])
+def test_solve_batch_equals_single_solves(prec):
+    o = glls.opts(tol=1e-10, gamma=1, alpha=0.5, precision=prec, max_iter=300)
+    probs = [_setup(wl)[0] for wl in MIX]
+    single, its = [], []
+    for p in probs:
+        u = np.zeros(p.N)
+        its.append(p.solve(u, o).iterations)
+        single.append(u)
+    for _ in range(2):          # second launch reuses the cached batch graph
+        outs = [np.zeros(p.N) for p in probs]
+        stats = glls.solve_batch(probs, outs, o)
+        for u, ub, st, k in zip(single, outs, stats, its):
+            assert _rel(ub, u) < 1e-10
+            assert abs(st.iterations - k) <= 1
+            assert st.status == glls.OK and st.rel_residual <= 1e-10
+    for p in probs:
+        p.close()
+
+
+def test_estimate_bytes_tracks_allocation():
+    for wl in MIX:
+        prob, coords, _, _ = _setup(wl)
+        est = glls.estimate_bytes(wl.dim, wl.nelem, wl.order, coords)
+        actual = prob.info.device_bytes
+        assert 0.8 * actual <= est <= 1.25 * actual, (wl.name, est, actual)
+        prob.close()
+
+
+def _request(wl):
+    xi, _ = glls.gll(wl.order)
+    coords = wl.coords(xi)
+    return coords, wl.sample_rhs(coords)[0], wl.sample_dirichlet(coords)
+
+
+def test_server_results_same_alone_and_in_the_mix():
+    o = glls.opts(tol=1e-10, gamma=1, alpha=0.5, precision=glls.PREC_MIXED)
+    srv = glls.Server(budget_bytes=8 << 30, slots=4)
+    reqs = [(wl,) + _request(wl) for wl in MIX]
+    alone = []
+    for wl, coords, f, g in reqs:                    # one at a time
+        out = np.zeros(f.size)
+        t = srv.submit(wl.dim, wl.nelem, wl.order, coords, f, g, o, out)
+        st, stats = srv.poll(t, wait=True)
+        assert st == glls.OK
+        alone.append(out)
+    outs, tickets = [], []
+    for rep in range(3):                             # all at once, three times
+        for wl, coords, f, g in reqs:
+            out = np.zeros(f.size)
+            outs.append(out)
+            tickets.append(srv.submit(wl.dim, wl.nelem, wl.order, coords, f, g, o, out))
+    for t in tickets:
+        st, stats = srv.poll(t, wait=True)
+        assert st == glls.OK and stats.rel_residual <= 1e-10
+    for k, out in enumerate(outs):
+        assert _rel(out, alone[k % len(reqs)]) < 1e-10
+    inf = srv.info()
+    assert inf.completed == len(reqs) * 4 and inf.failed == 0
+    assert inf.cached_problems >= len(reqs)        # meshes stay resident
+    srv.close()
+
+
+def test_server_admission_by_budget_and_eviction():
+    o = glls.opts(tol=1e-10, gamma=1, alpha=0.5)
+    a, b = MIX[1], MIX[2]
+    ra, rb = _request(a), _request(b)
+    ea = glls.estimate_bytes(a.dim, a.nelem, a.order, ra[0])
+    eb = glls.estimate_bytes(b.dim, b.nelem, b.order, rb[0])
+    # room for either mesh but not both: alternating requests force eviction
+    srv = glls.Server(budget_bytes=int(1.05 * max(ea, eb)) + (ea + eb) // 10, slots=2)
+    tickets, outs = [], []
+    for k in range(6):
+        wl, (coords, f, g) = (a, ra) if k % 2 == 0 else (b, rb)
+        out = np.zeros(f.size)
+        outs.append((k % 2, out))
+        tickets.append(srv.submit(wl.dim, wl.nelem, wl.order, coords, f, g, o, out))
+    for t in tickets:
+        st, _ = srv.poll(t, wait=True)
+        assert st == glls.OK
+    assert srv.info().resident_bytes <= srv.info().budget_bytes
+    ref = {0: outs[0][1], 1: outs[1][1]}
+    for which, out in outs:
+        assert _rel(out, ref[which]) < 1e-10
+    # a request larger than the whole budget fails with GLLS_ERR_BUDGET
+    small = glls.Server(budget_bytes=max(eb // 4, 1), slots=1)
+    coords, f, g = rb
+    out = np.zeros(f.size)
+    t = small.submit(b.dim, b.nelem, b.order, coords, f, g, o, out)
+    st, _ = small.poll(t, wait=True)
+    assert st == glls.ERR_BUDGET
+    small.close()
+    srv.close()
+
+
+def test_server_poll_without_waiting():
+    o = glls.opts()
+    wl = MIX[1]
+    coords, f, g = _request(wl)
+    srv = glls.Server(budget_bytes=4 << 30, slots=1)
+    out = np.zeros(f.size)
+    t = srv.submit(wl.dim, wl.nelem, wl.order, coords, f, g, o, out)
+    st, stats = srv.poll(t, wait=False)
+    deadline = time.time() + 60
+    while st == glls.NOT_READY and time.time() < deadline:
+        time.sleep(0.005)
+        st, stats = srv.poll(t, wait=False)
+    assert st == glls.OK and stats.iterations > 0
+    srv.close()
