@@ -45,17 +45,18 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed mixed-precision solves (for an ncu launch list)")
     return ap.parse_args()
 
 
 def dist_init(n):
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
+    from paper_2504_10710_gb300 import replicas
+    rank, world = replicas.rank_world()
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("gloo")
+        dist.init_process_group("gloo")     # barrier and max-over-ranks only: no data-path collective
     return rank, world
 
 
@@ -114,7 +115,7 @@ def run_ours(args, rank, world):
     import torch
 
     import __graft_entry__
-    from paper_2504_10710_gb300 import glls, inputs
+    from paper_2504_10710_gb300 import glls, inputs, replicas
 
     __graft_entry__.build()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
@@ -129,16 +130,17 @@ def run_ours(args, rank, world):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     prob.set_rhs(f_d, stream)
     prob.set_dirichlet(g_d, stream)
+    tiles = prob.autotune()          # line-solve tiles per level / precision / direction (set-up, untimed)
+    kernels = [0]
 
     def timed(precision, steps, warmup, clocks=None):
         o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=precision, use_graph=2)
         its = []
+        kernels[0] = 0
         for _ in range(warmup):
             prob.solve(u_d, o, stream)
         torch.cuda.synchronize()
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        replicas.barrier(world)
         if clocks:
             clocks.start()
         ms = 0.0
@@ -151,12 +153,15 @@ def run_ours(args, rank, world):
             b.synchronize()
             ms += a.elapsed_time(b)
             its.append(st.iterations)
+            kernels[0] += st.kernels
         torch.cuda.synchronize()
+        replicas.barrier(world)
         clk = clocks.stop() if clocks else None
         return ms / steps, its, clk
 
     clocks = ClockSampler(dev)
     ms_mixed, its_mixed, clk = timed(glls.PREC_MIXED, args.steps, args.warmup, clocks)
+    launches = kernels[0]
     if args.profile:
         print(json.dumps({"profile": True, "ms_per_step": ms_mixed, "iterations": its_mixed}))
         sys.exit(0)
@@ -172,7 +177,7 @@ def run_ours(args, rank, world):
     u_h = torch.zeros(N, dtype=torch.float64).pin_memory()
     o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED)
     e2e = []
-    for k in range(args.warmup + max(3, args.steps // 2)):
+    for k in range(args.warmup + max(50, args.steps)):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -183,19 +188,16 @@ def run_ours(args, rank, world):
         if k >= args.warmup:
             e2e.append(t1 - t0)
     e2e_s = float(np.mean(e2e))
+    lat = np.array(e2e) * 1e3
 
     # dominant kernel: the fine-level FP32 line-smoothing step (apply + CR
     # line solve), timed alone with CUDA events over repeated launches
     roof = kernel_roofline(prob, glls, torch, stream, N)
+    serving = serving_run(glls, inputs) if not args.no_serving else None
 
-    # max over ranks
-    ms_step = ms_mixed
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * N / (ms_step / 1e3)
+    # whole-job throughput: all ranks' DOF over the slowest rank's time
+    ms_step = replicas.max_over_ranks(ms_mixed, world)
+    value = replicas.aggregate_throughput(N, ms_mixed / 1e3, world)
     res = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -207,9 +209,13 @@ def run_ours(args, rank, world):
         "fp64_plain": {"value": world * N / (ms_fp64 / 1e3), "ms_per_step": ms_fp64, "iterations": int(np.median(its_fp64))},
         "mixed_over_fp64": ms_fp64 / ms_mixed,
         "e2e": {"value": world * N / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": 2 * 8 * N, "d2h_bytes_per_step": 8 * N},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)), "n": int(lat.size),
+                       "what": "end to end through glls_set_rhs/set_dirichlet/solve with host buffers"},
         "clocks": clk,
         "roofline": roof,
-        "gpu_launches": None,
+        "gpu_launches": int(launches),
+        "line_tiles": {f"l{l}_{pn}_ax{a}": c for (l, pn, a), (c, _us) in sorted(tiles.items()) if pn == "f32"},
+        "serving": serving,
     }
     return res, (u_mixed, u_fp64, wl)
 
@@ -230,15 +236,22 @@ def kernel_roofline(prob, glls, torch, stream, N):
     r[:, 0] = 0
     r[:, -1] = 0
     r = r.reshape(-1).contiguous()
-    for _ in range(3):
-        prob.smooth(L, 0, 0.5, r, x, stream)
-    reps = 50
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            prob.smooth(L, 0, 0.5, r, x, s)
     torch.cuda.synchronize()
-    a.record(stream)
-    for _ in range(reps):
-        prob.smooth(L, 0, 0.5, r, x, stream)
-    b.record(stream)
+    reps = 50
+    g = torch.cuda.CUDAGraph()          # the step as the solve runs it: inside a graph
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(reps):
+            prob.smooth(L, 0, 0.5, r, x, s)
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    g.replay()
+    b.record()
     b.synchronize()
     ms = a.elapsed_time(b) / reps
     # algorithmic bytes of one fine-level FP32 smoothing step (apply + line solve):
@@ -251,7 +264,54 @@ def kernel_roofline(prob, glls, torch, stream, N):
             "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
             "ms_per_launch": ms, "algorithmic_bytes": bytes_alg,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s",
-            "note": "working set (~12 MB) is L2-resident; timed standalone with CUDA events"}
+            "note": "working set (~12 MB) is L2-resident; 50 launches replayed from a CUDA graph, CUDA events"}
+
+
+def serving_run(glls, inputs, nreq=120, rate=200.0, seed=5):
+    """Native serving loop under Poisson arrivals (mean `rate` per second):
+    requests drawn from a pool of 8 resident 2-D meshes (16..40 elements per
+    side, p 4..8, amplitude 0..0.1), each a mixed-precision solve to 1e-10.
+    Reports achieved DOF/s and p50/p99 latency (submit -> result in host
+    memory) of warm requests (mesh resident) and of all requests."""
+    rng = np.random.default_rng(seed)
+    pool = []
+    for k in range(8):
+        n = int(rng.integers(16, 41))
+        wl = inputs.random2d((n, n), int(rng.integers(4, 9)), amp=float(rng.uniform(0.0, 0.1)), seed=100 + k)
+        xi, _ = glls.gll(wl.order)
+        coords = wl.coords(xi)
+        pool.append((wl, coords, wl.sample_rhs(coords)[0], wl.sample_dirichlet(coords)))
+    srv = glls.Server(budget_bytes=16 << 30, slots=4)
+    o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED)
+    # warm the mesh cache (set-up) so that the stream measures serving, not set-up
+    for wl, coords, f, g in pool:
+        out = np.zeros(f.size)
+        srv.poll(srv.submit(wl.dim, wl.nelem, wl.order, coords, f, g, o, out), wait=True)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    choice = rng.integers(0, len(pool), nreq)
+    tickets, dofs = [], 0
+    t0 = time.perf_counter()
+    for k in range(nreq):
+        delay = t0 + arrivals[k] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        wl, coords, f, g = pool[choice[k]]
+        out = np.zeros(f.size)
+        tickets.append((srv.submit(wl.dim, wl.nelem, wl.order, coords, f, g, o, out), out))
+        dofs += f.size
+    lat, fails = [], 0
+    for t, _out in tickets:
+        st, stats = srv.poll(t, wait=True)
+        if st != glls.OK:
+            fails += 1
+        else:
+            lat.append(stats.solve_ms)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": nreq, "offered_per_s": rate, "achieved_per_s": nreq / wall, "dof_per_s": dofs / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)), "failed": fails,
+            "slots": 4, "pool": [p[0].name for p in pool]}
 
 
 def oracle_baseline(wl, u_ref_gpu=None):

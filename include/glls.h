@@ -92,6 +92,7 @@ typedef struct {
     double setup_ms;
     double solve_ms;
     int status;
+    long long kernels;   /* kernels this solve launched (graph kernel nodes x loop trips) */
 } glls_stats;
 
 typedef struct {
@@ -135,6 +136,14 @@ glls_status glls_solve(glls_problem* prob, const glls_solve_opts* opts, double* 
 glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve_opts* opts, double* const* u,
                              int on_device, void* stream, glls_stats* stats);
 
+/* Autotuner: for every level >= 1, precision and direction, time the line
+ * solve with 2, 4 and 8 lines per CTA on the problem's own data and keep the
+ * fastest.  chosen / best_us (optional): levels x 2 (FP32, FP64) x 3 entries,
+ * index (level * 2 + precision) * 3 + axis, the chosen tile and its time in
+ * microseconds per launch.  Cached graphs are rebuilt on the next solve.
+ * Synchronous. */
+glls_status glls_autotune(glls_problem* prob, int* chosen, float* best_us);
+
 /* Device bytes glls_problem_create would allocate for desc (estimate used for
  * admission by an HBM budget; no allocation, no device work). */
 glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes);
@@ -145,8 +154,10 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes);
  * and Krylov state) keyed by the mesh.  Requests are admitted in arrival
  * order as soon as a slot is free and the resident bytes plus the request's
  * estimate fit the budget (idle cached meshes are evicted, least recently
- * used first); admitted requests run concurrently on the device.  A request
- * whose estimate exceeds the whole budget fails with GLLS_ERR_BUDGET. */
+ * used first); a request whose mesh is resident but busy waits for it while
+ * later requests for other meshes go ahead.  Admitted requests run
+ * concurrently on the device.  A request whose estimate exceeds the whole
+ * budget fails with GLLS_ERR_BUDGET. */
 typedef struct glls_server glls_server;
 typedef struct {
     unsigned long long submitted, completed, failed, queued, running;

@@ -77,6 +77,7 @@ struct glls_problem {
     double g_alpha = 0.0;
     cudaGraphExec_t solve_exec = nullptr;
     glls_solve_opts solve_key{};
+    long long kern_fixed = 0, kern_iter = 0;   // kernel nodes of the solve graph (outside / inside the loop)
     bool has_rhs = false, has_dirichlet = false;
 
     template <typename T>
@@ -299,6 +300,19 @@ bool same_solve_key(const glls_solve_opts& a, const glls_solve_opts& b) {
            a.precision == b.precision && a.krylov == b.krylov;
 }
 
+long long count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    long long k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
 // Adds the whole solve of P to the graph being captured on cs: prologue, a
 // conditional WHILE node whose body (captured on cs2) is one outer iteration
 // followed by the loop-control kernel, then y = x + v.  Returns the first
@@ -330,6 +344,7 @@ cudaError_t capture_solve(glls_problem* P, const glls_solve_opts* o, cudaStream_
             outer_iteration(P, o, cs2);
             launch_solve_cond(P->S, handle, o->max_iter, cs2);
             e = cudaStreamEndCapture(cs2, &body);
+            if (e == cudaSuccess) P->kern_iter = count_kernel_nodes(body);
         }
     }
     if (e == cudaSuccess) {
@@ -352,6 +367,7 @@ glls_status get_solve_graph(glls_problem* P, const glls_solve_opts* o) {
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) P->kern_fixed = count_kernel_nodes(graph);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&P->solve_exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     CK(e);
@@ -375,6 +391,7 @@ glls_status solve_result(glls_problem* P, const double* h, glls_stats* stats, do
         stats->setup_ms = P->setup_ms;
         stats->solve_ms = t_ms;
         stats->status = result;
+        stats->kernels = P->kern_fixed + P->kern_iter * (long long)h[S_ITER];
     }
     return result;
 }
@@ -429,6 +446,43 @@ glls_status get_iteration_graph(glls_problem* P, const glls_solve_opts* o) {
     return GLLS_OK;
 }
 
+}  // namespace
+
+namespace {
+template <typename T>
+glls_status tune_levels(glls_problem* P, std::vector<LevelStore<T>>& Ls, int prec, int* chosen, float* best_us) {
+    cudaStream_t st = P->capture_stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    const int cand[3] = {2, 4, 8};
+    for (size_t l = 1; l < Ls.size(); ++l)
+        for (int s = 0; s < Ls[l].dev.dim; ++s) {
+            float best = 1e30f;
+            int pick = 4;
+            for (int c : cand) {
+                Ls[l].dev.lpb[s] = c;
+                for (int w = 0; w < 3; ++w)
+                    launch_line_solve<T>(Ls[l].dev, s, 0, Ls[l].r, nullptr, nullptr, Ls[l].t2, T(1), st);
+                CK(cudaEventRecord(a, st));
+                for (int w = 0; w < 10; ++w)
+                    launch_line_solve<T>(Ls[l].dev, s, 0, Ls[l].r, nullptr, nullptr, Ls[l].t2, T(1), st);
+                CK(cudaEventRecord(b, st));
+                CK(cudaEventSynchronize(b));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, a, b));
+                if (ms < best) { best = ms; pick = c; }
+            }
+            Ls[l].dev.lpb[s] = pick;
+            const size_t k = (l * 2 + prec) * 3 + s;
+            if (chosen) chosen[k] = pick;
+            if (best_us) best_us[k] = best * 100.f;   // 10 launches: ms * 1000 / 10
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    CK(cudaGetLastError());
+    return GLLS_OK;
+}
 }  // namespace
 
 // ===========================================================================
@@ -823,6 +877,21 @@ glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve
     if (worst == GLLS_ERR_BREAKDOWN) fail(worst, "breakdown in at least one problem of the batch");
     if (worst == GLLS_ERR_NOT_CONVERGED) fail(worst, "at least one problem of the batch reached max_iter");
     return worst;
+}
+
+glls_status glls_autotune(glls_problem* P, int* chosen, float* best_us) {
+    if (!P) return fail(GLLS_ERR_INVALID, "null problem");
+    CK(cudaSetDevice(P->device));
+    const size_t cells = P->L64.size() * 2 * 3;
+    if (chosen) std::fill(chosen, chosen + cells, 0);
+    if (best_us) std::fill(best_us, best_us + cells, 0.f);
+    glls_status s = tune_levels<float>(P, P->L32, 0, chosen, best_us);
+    if (s == GLLS_OK) s = tune_levels<double>(P, P->L64, 1, chosen, best_us);
+    // captured graphs hold the previous tiles
+    if (P->iter_exec) { cudaGraphExecDestroy(P->iter_exec); P->iter_exec = nullptr; }
+    if (P->solve_exec) { cudaGraphExecDestroy(P->solve_exec); P->solve_exec = nullptr; }
+    forget_batches_of(P);
+    return s;
 }
 
 #define LEVEL_OPS(SUF, T)                                                                                      \

@@ -33,6 +33,7 @@ struct DevLevel {
     const T* diag = nullptr;
     const T* off[3] = {nullptr, nullptr, nullptr};
     DevBand<T> P[3], R[3];
+    int lpb[3] = {4, 4, 4};   // line-solve tile (lines per CTA) per direction, set by the autotuner
 };
 
 template <typename T>

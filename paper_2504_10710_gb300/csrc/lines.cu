@@ -203,31 +203,42 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
     }
 }
 
-constexpr int kLPB = 4;
-
-template <typename T, int C>
-void launch_c(const WarpLineArgs<T>& A, cudaStream_t st) {
-    const size_t smem = sizeof(T) * 3 * kLPB * (32 * C + C);
-    const int blocks = (A.nlines + kLPB - 1) / kLPB;
+// Lines per CTA (the tile the autotuner chooses among): 2, 4 or 8.
+template <typename T, int C, int LPB>
+void launch_lpb(const WarpLineArgs<T>& A, cudaStream_t st) {
+    const size_t smem = sizeof(T) * 3 * LPB * (32 * C + C);
+    const int blocks = (A.nlines + LPB - 1) / LPB;
     switch (A.mode) {
-        case 0: line_warp_kernel<T, C, kLPB, 0><<<blocks, 32 * kLPB, smem, st>>>(A); break;
-        case 1: line_warp_kernel<T, C, kLPB, 1><<<blocks, 32 * kLPB, smem, st>>>(A); break;
-        case 2: line_warp_kernel<T, C, kLPB, 2><<<blocks, 32 * kLPB, smem, st>>>(A); break;
-        default: line_warp_kernel<T, C, kLPB, 3><<<blocks, 32 * kLPB, smem, st>>>(A); break;
+        case 0: line_warp_kernel<T, C, LPB, 0><<<blocks, 32 * LPB, smem, st>>>(A); break;
+        case 1: line_warp_kernel<T, C, LPB, 1><<<blocks, 32 * LPB, smem, st>>>(A); break;
+        case 2: line_warp_kernel<T, C, LPB, 2><<<blocks, 32 * LPB, smem, st>>>(A); break;
+        default: line_warp_kernel<T, C, LPB, 3><<<blocks, 32 * LPB, smem, st>>>(A); break;
     }
 }
 
 template <typename T, int C>
-bool set_attr() {
+void launch_c(const WarpLineArgs<T>& A, int lpb, cudaStream_t st) {
+    if (lpb == 2) launch_lpb<T, C, 2>(A, st);
+    else if (lpb == 8) launch_lpb<T, C, 8>(A, st);
+    else launch_lpb<T, C, 4>(A, st);
+}
+
+template <typename T, int C, int LPB>
+bool set_attr_lpb() {
     const int lim = 160 * 1024;
-    return cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, kLPB, 0>,
+    return cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, LPB, 0>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess &&
-           cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, kLPB, 1>,
+           cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, LPB, 1>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess &&
-           cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, kLPB, 2>,
+           cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, LPB, 2>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess &&
-           cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, kLPB, 3>,
+           cudaFuncSetAttribute((const void*)line_warp_kernel<T, C, LPB, 3>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+}
+
+template <typename T, int C>
+bool set_attr() {
+    return set_attr_lpb<T, C, 2>() && set_attr_lpb<T, C, 4>() && set_attr_lpb<T, C, 8>();
 }
 
 }  // namespace
@@ -269,14 +280,15 @@ bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T
     A.x = x;
     int C = 1;
     while (32 * C < A.n) C *= 2;
+    const int lpb = L.lpb[s];
     switch (C) {
-        case 1: launch_c<T, 1>(A, st); break;
-        case 2: launch_c<T, 2>(A, st); break;
-        case 4: launch_c<T, 4>(A, st); break;
-        case 8: launch_c<T, 8>(A, st); break;
-        case 16: launch_c<T, 16>(A, st); break;
+        case 1: launch_c<T, 1>(A, lpb, st); break;
+        case 2: launch_c<T, 2>(A, lpb, st); break;
+        case 4: launch_c<T, 4>(A, lpb, st); break;
+        case 8: launch_c<T, 8>(A, lpb, st); break;
+        case 16: launch_c<T, 16>(A, lpb, st); break;
         default:
-            if constexpr (sizeof(T) == 4) { launch_c<T, 32>(A, st); break; }
+            if constexpr (sizeof(T) == 4) { launch_c<T, 32>(A, lpb, st); break; }
             return false;
     }
     return true;

@@ -83,21 +83,36 @@ struct glls_server {
     unsigned long long next_id = 1, submitted = 0, completed = 0, failed = 0, running = 0;
     bool stop = false;
     std::vector<std::thread> workers;
+    std::vector<MeshKey> creating;   // meshes whose set-up is in progress
+
+    bool pending_key(const MeshKey& k) const {
+        for (const auto& c : creating)
+            if (c == k) return true;
+        return false;
+    }
 
     // Under the lock: choose the first queued request that can run now.
     // Returns it with `slot` set to a cached problem index, or -1 with
-    // `reserve` bytes reserved for a new problem.
+    // `reserve` bytes reserved for a new problem.  A request whose mesh is
+    // resident but busy waits for that instance (no duplicate set-up) while
+    // later requests for other meshes may proceed.
     Request* admit(int* slot, size_t* reserve) {
         for (auto it = queue.begin(); it != queue.end(); ++it) {
             Request* r = *it;
+            bool resident_busy = false;
             for (size_t i = 0; i < cache.size(); ++i)
-                if (!cache[i].busy && cache[i].key == r->key) {
+                if (cache[i].key == r->key) {
+                    if (cache[i].busy) {
+                        resident_busy = true;
+                        continue;
+                    }
                     cache[i].busy = true;
                     *slot = (int)i;
                     *reserve = 0;
                     queue.erase(it);
                     return r;
                 }
+            if (resident_busy || pending_key(r->key)) continue;
             if (r->estimate > budget) {       // can never fit: fail it here
                 r->status = GLLS_ERR_BUDGET;
                 r->state = 2;
@@ -122,6 +137,7 @@ struct glls_server {
                 resident += r->estimate;
                 *slot = -1;
                 *reserve = r->estimate;
+                creating.push_back(r->key);
                 queue.erase(it);
                 return r;
             }
@@ -159,6 +175,11 @@ struct glls_server {
                 setup_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
                 std::lock_guard<std::mutex> lock(m);
                 resident -= reserve;
+                for (size_t i = 0; i < creating.size(); ++i)
+                    if (creating[i] == r->key) {
+                        creating.erase(creating.begin() + i);
+                        break;
+                    }
                 if (st == GLLS_OK) {
                     glls_info inf;
                     glls_problem_info(prob, &inf);

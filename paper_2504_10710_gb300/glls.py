@@ -37,7 +37,7 @@ class SolveOpts(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("setup_ms", C.c_double),
-                ("solve_ms", C.c_double), ("status", C.c_int)]
+                ("solve_ms", C.c_double), ("status", C.c_int), ("kernels", C.c_longlong)]
 
 
 class Info(C.Structure):
@@ -80,6 +80,7 @@ def lib():
             "glls_restrict_noalloc_f32": [vp, i, vp, vp, vp, vp],
             "glls_solve_batch": [C.POINTER(vp), i, C.POINTER(SolveOpts), C.POINTER(vp), i, vp, C.POINTER(Stats)],
             "glls_estimate_bytes": [C.POINTER(MeshDesc), C.POINTER(C.c_size_t)],
+            "glls_autotune": [vp, C.POINTER(C.c_int), C.POINTER(C.c_float)],
             "glls_server_create": [i, C.c_size_t, i, C.POINTER(vp)],
             "glls_submit": [vp, C.POINTER(MeshDesc), vp, vp, C.POINTER(SolveOpts), vp, C.POINTER(C.c_ulonglong)],
             "glls_poll": [vp, C.c_ulonglong, i, C.POINTER(Stats)],
@@ -207,6 +208,21 @@ class Problem:
         if raise_on_error:
             _check(status)
         return st
+
+    def autotune(self):
+        """Pick the line-solve tile per level/precision/direction by timing;
+        returns {(level, 'f32'|'f64', axis): (lines_per_cta, us_per_launch)}."""
+        n = self.levels * 2 * 3
+        ch = (C.c_int * n)()
+        us = (C.c_float * n)()
+        _check(lib().glls_autotune(self.h, ch, us))
+        out = {}
+        for l in range(1, self.levels):
+            for pi, pn in enumerate(("f32", "f64")):
+                for a in range(self.dim):
+                    k = (l * 2 + pi) * 3 + a
+                    out[(l, pn, a)] = (ch[k], us[k])
+        return out
 
     # ---- level operations (device tensors) -------------------------------
     @staticmethod

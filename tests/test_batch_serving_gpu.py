@@ -146,3 +146,18 @@ def test_server_poll_without_waiting():
         st, stats = srv.poll(t, wait=False)
     assert st == glls.OK and stats.iterations > 0
     srv.close()
+
+
+def test_autotune_picks_valid_tiles_and_keeps_results():
+    wl = MIX[1]
+    prob, coords, f, g = _setup(wl)
+    o = glls.opts(tol=1e-10, gamma=1, alpha=0.5)
+    before = np.zeros(prob.N)
+    st0 = prob.solve(before, o)
+    tiles = prob.autotune()
+    assert tiles and all(c in (2, 4, 8) and us > 0 for c, us in tiles.values())
+    after = np.zeros(prob.N)
+    st1 = prob.solve(after, o)            # graphs are re-captured with the chosen tiles
+    assert _rel(after, before) < 1e-10 and abs(st1.iterations - st0.iterations) <= 1
+    assert st1.kernels > st1.iterations * 10
+    prob.close()
