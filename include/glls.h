@@ -53,7 +53,7 @@ typedef enum {
 enum { GLLS_PREC_FP64 = 0, GLLS_PREC_MIXED = 1 };          /* gamma-cycle in FP64, or FP32 */
 enum { GLLS_SMOOTHER_GLL = 0, GLLS_SMOOTHER_FEM = 1 };     /* line systems from A_p or A~_p */
 enum { GLLS_RESTRICT_TRANSPOSE = 0, GLLS_RESTRICT_INTERP = 1 };
-enum { GLLS_KRYLOV_FCG = 0, GLLS_KRYLOV_PCG = 1 };
+enum { GLLS_KRYLOV_FCG = 0, GLLS_KRYLOV_PCG = 1, GLLS_KRYLOV_GMRES = 2 };
 
 typedef struct glls_problem glls_problem;   /* opaque, library-owned */
 
@@ -78,7 +78,10 @@ typedef struct {
     int m;           /* smoothing steps per direction, >= 1 */
     double alpha;    /* damping of the line smoothing step */
     int precision;   /* GLLS_PREC_FP64 or GLLS_PREC_MIXED */
-    int krylov;      /* GLLS_KRYLOV_FCG (Polak-Ribiere beta) or _PCG (Fletcher-Reeves) */
+    int krylov;      /* GLLS_KRYLOV_FCG (Polak-Ribiere beta), _PCG (Fletcher-Reeves), or _GMRES:
+                        right-preconditioned flexible GMRES without restart, the paper's outer
+                        solver (Sec. 3), at most min(max_iter, 400) steps, host-driven loop;
+                        its residual test is the Arnoldi least-squares estimate */
     int use_graph;   /* 0: host loop, kernels launched per iteration;
                         1: host loop, each outer iteration replayed as a captured CUDA graph;
                         2: the whole solve as one captured graph whose outer loop is a

@@ -78,6 +78,10 @@ struct glls_problem {
     cudaGraphExec_t solve_exec = nullptr;
     glls_solve_opts solve_key{};
     long long kern_fixed = 0, kern_iter = 0;   // kernel nodes of the solve graph (outside / inside the loop)
+    // GMRES workspace (allocated on first use): Krylov basis V, preconditioned
+    // basis Z, Hessenberg column halves, partial sums
+    double *gV = nullptr, *gZ = nullptr, *gh = nullptr, *gpart = nullptr;
+    int gm = 0;
     bool has_rhs = false, has_dirichlet = false;
 
     template <typename T>
@@ -255,7 +259,8 @@ glls_status check_opts(const glls_solve_opts* o) {
     if (!(o->alpha > 0.0)) return fail(GLLS_ERR_INVALID, "alpha must be > 0");
     if (o->precision != GLLS_PREC_FP64 && o->precision != GLLS_PREC_MIXED)
         return fail(GLLS_ERR_INVALID, "bad precision");
-    if (o->krylov != GLLS_KRYLOV_FCG && o->krylov != GLLS_KRYLOV_PCG) return fail(GLLS_ERR_INVALID, "bad krylov");
+    if (o->krylov != GLLS_KRYLOV_FCG && o->krylov != GLLS_KRYLOV_PCG && o->krylov != GLLS_KRYLOV_GMRES)
+        return fail(GLLS_ERR_INVALID, "bad krylov");
     if (o->max_iter < 1) return fail(GLLS_ERR_INVALID, "max_iter must be >= 1");
     if (!(o->tol > 0.0)) return fail(GLLS_ERR_INVALID, "tol must be > 0");
     return GLLS_OK;
@@ -485,6 +490,106 @@ glls_status tune_levels(glls_problem* P, std::vector<LevelStore<T>>& Ls, int pre
 }
 }  // namespace
 
+// Right-preconditioned flexible GMRES without restart (the paper's outer
+// solver, Sec. 3): Arnoldi with classical Gram-Schmidt applied twice, the
+// preconditioned directions z_j kept (the FP32 cycle is not exactly linear),
+// Givens rotations on the host, x = sum_j y_j z_j.  Host-driven loop.
+glls_status gmres_solve(glls_problem* P, const glls_solve_opts* o, cudaStream_t st, int* it_out, double* rel_out) {
+    const long long N = P->N;
+    const int L = (int)P->L64.size() - 1;
+    const DevLevel<double>& F = P->L64[L].dev;
+    const int m = std::min(o->max_iter, 400);
+    if (P->gm < m) {
+        for (double* q : {P->gV, P->gZ, P->gh, P->gpart})
+            if (q) {
+                cudaFree(q);
+                P->allocs.erase(std::remove(P->allocs.begin(), P->allocs.end(), (void*)q), P->allocs.end());
+            }
+        CK(P->alloc(&P->gV, (size_t)(m + 1) * N));
+        CK(P->alloc(&P->gZ, (size_t)m * N));
+        CK(P->alloc(&P->gh, 2 * (size_t)(m + 1)));
+        CK(P->alloc(&P->gpart, 64 * (size_t)(m + 1)));
+        CK(cudaMemset(P->gZ, 0, sizeof(double) * (size_t)m * N));   // boundary entries stay zero
+        P->gm = m;
+    }
+    const bool mixed = o->precision == GLLS_PREC_MIXED;
+    solve_prologue(P, o, st);
+    std::vector<double> hS(S_COUNT);
+    CK(cudaMemcpyAsync(hS.data(), P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double rr0 = hS[S_RR0];
+    *it_out = 0;
+    *rel_out = 0.0;
+    if (!std::isfinite(rr0)) return fail(GLLS_ERR_BREAKDOWN, "non-finite right-hand side");
+    if (rr0 == 0.0) return GLLS_OK;
+    const double beta = std::sqrt(rr0);
+    launch_scale_by_norm(P->gV, P->rk, P->S + S_RR0, N, st);
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0), hv(2 * (m + 1));
+    auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+    g[0] = beta;
+    int kdone = m;
+    double rel = 1.0;
+    glls_status result = GLLS_ERR_NOT_CONVERGED;
+    for (int k = 0; k < m; ++k) {
+        double* vk = P->gV + (size_t)k * N;
+        double* zk = P->gZ + (size_t)k * N;
+        double* w = P->gV + (size_t)(k + 1) * N;
+        if (mixed) {
+            launch_cast<double, float>(vk, P->r32, N, st);
+            cycle<float>(P, L, P->r32, P->z32, o->gamma, o->m, (float)o->alpha, st);
+            launch_cast<float, double>(P->z32, zk, N, st);
+        } else {
+            cycle<double>(P, L, vk, zk, o->gamma, o->m, o->alpha, st);
+        }
+        launch_apply<double>(F, zk, w, true, st);
+        for (int pass = 0; pass < 2; ++pass) {
+            launch_multidot(P->gV, N, k + 1, w, N, P->gpart, P->gh + pass * (m + 1), P->ticket, st);
+            launch_gs_update(w, P->gV, N, k + 1, P->gh + pass * (m + 1), N, -1.0, st);
+        }
+        launch_dots(w, w, nullptr, nullptr, 1, N, P->part, P->S, S_RR, S_RR, P->ticket, st);
+        CK(cudaMemcpyAsync(hv.data(), P->gh, sizeof(double) * 2 * (m + 1), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hS.data(), P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int i = 0; i <= k; ++i) Hat(i, k) = hv[i] + hv[(m + 1) + i];
+        const double hk1 = std::sqrt(hS[S_RR]);
+        if (!std::isfinite(hk1)) return fail(GLLS_ERR_BREAKDOWN, "non-finite Arnoldi vector");
+        Hat(k + 1, k) = hk1;
+        if (hk1 > 0.0) launch_scale_by_norm(w, w, P->S + S_RR, N, st);
+        for (int i = 0; i < k; ++i) {   // previous rotations
+            const double t = cs[i] * Hat(i, k) + sn[i] * Hat(i + 1, k);
+            Hat(i + 1, k) = -sn[i] * Hat(i, k) + cs[i] * Hat(i + 1, k);
+            Hat(i, k) = t;
+        }
+        const double rr = std::hypot(Hat(k, k), Hat(k + 1, k));
+        cs[k] = Hat(k, k) / rr;
+        sn[k] = Hat(k + 1, k) / rr;
+        Hat(k, k) = rr;
+        Hat(k + 1, k) = 0.0;
+        g[k + 1] = -sn[k] * g[k];
+        g[k] = cs[k] * g[k];
+        rel = std::fabs(g[k + 1]) / beta;
+        if (rel <= o->tol || hk1 == 0.0) {
+            kdone = k + 1;
+            result = GLLS_OK;
+            break;
+        }
+    }
+    // y = H^-1 g (upper triangular), x = sum_j y_j z_j
+    std::vector<double> y(kdone, 0.0);
+    for (int i = kdone - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int j = i + 1; j < kdone; ++j) t -= Hat(i, j) * y[j];
+        y[i] = t / Hat(i, i);
+    }
+    CK(cudaMemcpyAsync(P->gh, y.data(), sizeof(double) * kdone, cudaMemcpyHostToDevice, st));
+    launch_gs_update(P->xk, P->gZ, N, kdone, P->gh, N, +1.0, st);
+    CK(cudaStreamSynchronize(st));
+    *it_out = kdone;
+    *rel_out = rel;
+    if (result == GLLS_ERR_NOT_CONVERGED) fail(result, "max_iter reached");
+    return result;
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -675,6 +780,25 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
     int it = 0;
     double rel = 0.0;
     glls_status result = GLLS_OK;
+    if (o->krylov == GLLS_KRYLOV_GMRES) {
+        result = gmres_solve(P, o, st, &it, &rel);
+        if (result != GLLS_OK && result != GLLS_ERR_NOT_CONVERGED) return result;
+        CK(cudaMemcpyAsync(P->yk, P->xk, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        launch_axpy(P->yk, P->v, 1.0, N, st);
+        CK(cudaMemcpyAsync(u, P->yk, sizeof(double) * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        if (stats) {
+            stats->iterations = it;
+            stats->rel_residual = rel;
+            stats->setup_ms = P->setup_ms;
+            stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            stats->status = result;
+            stats->kernels = 0;
+        }
+        return result;
+    }
     if (o->use_graph == 2) {
         // whole solve on the device: one graph launch, one synchronisation
         glls_status gs = get_solve_graph(P, o);

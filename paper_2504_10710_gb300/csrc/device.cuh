@@ -126,6 +126,14 @@ void launch_lift_rhs(const double* mass, const double* f, const double* y, doubl
                      cudaStream_t st);
 void launch_boundary_only(const double* g, double* v, const int n[3], int dim, cudaStream_t st);
 void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st);   // y += a x
+// GMRES: h[j] = V_j . w (j < k1, deterministic, part holds 64 k1 partials);
+// w += sign sum_j h[j] V_j; out = in / sqrt(nrm2[0]).
+void launch_multidot(const double* V, long long ld, int k1, const double* w, long long n, double* part, double* h,
+                     unsigned* ticket, cudaStream_t st);
+void launch_gs_update(double* w, const double* V, long long ld, int k1, const double* h, long long n, double sign,
+                      cudaStream_t st);
+void launch_scale_by_norm(double* out, const double* in, const double* nrm2, long long n, cudaStream_t st);
+
 // Device-side solve loop: after S_RR0 is computed, initialise S and set the
 // WHILE handle (r0 != 0); at the end of each iteration count it and set the
 // handle to (r.r > tol^2 r0.r0, it < maxit, no breakdown).

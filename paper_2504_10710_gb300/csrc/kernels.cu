@@ -401,6 +401,48 @@ __global__ void fcg_direction_kernel(double* __restrict__ p, const double* __res
     }
 }
 
+// ---- GMRES helpers (Arnoldi with classical Gram-Schmidt, twice) ----------
+// h[j] = V_j . w for j < k1; V rows of length n with leading dimension ld.
+__global__ void __launch_bounds__(256) multidot_kernel(const double* __restrict__ V, long long ld, int k1,
+                                                       const double* __restrict__ w, long long n,
+                                                       double* part, double* h, unsigned* ticket) {
+    __shared__ double red[32];
+    const int j = blockIdx.y;
+    const double* v = V + (long long)j * ld;
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += v[i] * w[i];
+    const double t = block_sum(s, red);
+    if (threadIdx.x == 0) part[j * gridDim.x + blockIdx.x] = t;
+    if (last_block_of(ticket, gridDim.x * gridDim.y)) {
+        for (int jj = 0; jj < k1; ++jj) {
+            double a = 0.0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a += __ldcg(part + jj * gridDim.x + b);
+            const double tt = block_sum(a, red);
+            if (threadIdx.x == 0) h[jj] = tt;
+        }
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+}
+
+// w -= sum_{j < k1} h[j] V_j ;  x += sum_{j < k1} h[j] V_j when sign > 0
+__global__ void gs_update_kernel(double* __restrict__ w, const double* __restrict__ V, long long ld, int k1,
+                                 const double* __restrict__ h, long long n, double sign) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int j = 0; j < k1; ++j) a += h[j] * V[(long long)j * ld + i];
+        w[i] += sign * a;
+    }
+}
+
+// out = in / sqrt(nrm2[0])
+__global__ void scale_by_norm_kernel(double* __restrict__ out, const double* __restrict__ in,
+                                     const double* __restrict__ nrm2, long long n) {
+    const double s = 1.0 / sqrt(nrm2[0]);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = in[i] * s;
+}
+
 // Device-side loop control for the captured solve graph (conditional WHILE
 // node): solve_init_kernel runs once after r0.r0 is known, solve_cond_kernel
 // ends every outer iteration.
@@ -601,6 +643,22 @@ void launch_lift_rhs(const double* mass, const double* f, const double* y, doubl
 void launch_boundary_only(const double* g, double* v, const int n[3], int dim, cudaStream_t st) {
     const long long total = (long long)n[0] * n[1] * n[2];
     boundary_only_kernel<<<grid_for(total), 256, 0, st>>>(g, v, make_int3(n[0], n[1], n[2]), dim);
+}
+
+void launch_multidot(const double* V, long long ld, int k1, const double* w, long long n, double* part, double* h,
+                     unsigned* ticket, cudaStream_t st) {
+    long long nb = (n + 255) / 256;
+    if (nb > 64) nb = 64;
+    multidot_kernel<<<dim3((unsigned)nb, (unsigned)k1), 256, 0, st>>>(V, ld, k1, w, n, part, h, ticket);
+}
+
+void launch_gs_update(double* w, const double* V, long long ld, int k1, const double* h, long long n, double sign,
+                      cudaStream_t st) {
+    gs_update_kernel<<<grid_for(n), 256, 0, st>>>(w, V, ld, k1, h, n, sign);
+}
+
+void launch_scale_by_norm(double* out, const double* in, const double* nrm2, long long n, cudaStream_t st) {
+    scale_by_norm_kernel<<<grid_for(n), 256, 0, st>>>(out, in, nrm2, n);
 }
 
 void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st) {

@@ -31,6 +31,16 @@ __device__ __forceinline__ bool last_block(unsigned* ticket) {
     return is_last;
 }
 
+// As last_block, for a launch of `total` blocks (multi-dimensional grids).
+__device__ __forceinline__ bool last_block_of(unsigned* ticket, unsigned total) {
+    __shared__ bool is_last_n;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last_n = atomicAdd(ticket, 1u) == total - 1;
+    __syncthreads();
+    return is_last_n;
+}
+
 __device__ __forceinline__ void finalize_partials(const double* part, int ndots, int nblocks, double* S, int slot0, int slot1,
                                   double* red) {
     for (int d = 0; d < ndots; ++d) {

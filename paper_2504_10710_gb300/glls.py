@@ -20,7 +20,7 @@ ERR_TIMEOUT, ERR_BUDGET = -6, -7
 PREC_FP64, PREC_MIXED = 0, 1
 SMOOTHER_GLL, SMOOTHER_FEM = 0, 1
 RESTRICT_TRANSPOSE, RESTRICT_INTERP = 0, 1
-KRYLOV_FCG, KRYLOV_PCG = 0, 1
+KRYLOV_FCG, KRYLOV_PCG, KRYLOV_GMRES = 0, 1, 2
 
 
 class MeshDesc(C.Structure):
