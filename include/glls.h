@@ -113,6 +113,13 @@ glls_status glls_gll(int p, double* xi, double* rho);
 /* Build every level: geometry factors, line bands, CR-ready data, transfers and
  * the coarsest-level factor, and upload them to the device.  Synchronous. */
 glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out);
+/* A second problem on the same mesh: it shares every read-only device array of
+ * prob (geometry factors, line bands, transfers, coarsest inverse, mass; held
+ * until the last of them is destroyed) and owns its own right-hand side,
+ * Dirichlet data and Krylov state.  Several right-hand sides of one mesh are
+ * solved together as clones in one glls_solve_batch.  Autotuned tiles are
+ * copied.  Synchronous. */
+glls_status glls_problem_clone(const glls_problem* prob, glls_problem** out);
 void glls_problem_destroy(glls_problem* prob);
 glls_status glls_problem_info(const glls_problem* prob, glls_info* out);
 

@@ -46,8 +46,21 @@ struct LevelStore {
 
 }  // namespace
 
+// Read-only mesh data (geometry factors, line bands, transfers, coarse
+// inverse, mass), shared by a problem and its clones; freed with the last one.
+struct SharedData {
+    int device = 0;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    ~SharedData() {
+        cudaSetDevice(device);
+        for (void* a : allocs) cudaFree(a);
+    }
+};
+
 struct glls_problem {
     int device = 0;
+    std::shared_ptr<SharedData> shared;
     int dim = 2;
     int nelem[3] = {1, 1, 1};
     int p = 1;
@@ -94,11 +107,17 @@ struct glls_problem {
         *ptr = static_cast<T*>(p_);
         return cudaSuccess;
     }
+    // read-only data: allocated into the shared block
     template <typename T, typename S>
     cudaError_t upload(const T** dst, const std::vector<S>& src) {
         T* d = nullptr;
-        cudaError_t e = alloc(&d, src.size());
+        void* p_ = nullptr;
+        const size_t count = src.size() ? src.size() : 1;
+        cudaError_t e = cudaMalloc(&p_, sizeof(T) * count);
         if (e != cudaSuccess) return e;
+        shared->allocs.push_back(p_);
+        shared->bytes += sizeof(T) * count;
+        d = static_cast<T*>(p_);
         std::vector<T> tmp(src.begin(), src.end());
         e = cudaMemcpy(d, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice);
         *dst = d;
@@ -107,6 +126,45 @@ struct glls_problem {
 };
 
 namespace {
+
+// Per-instance work vectors of every level (zeroed: boundary entries stay zero).
+template <typename T>
+glls_status alloc_level_vectors(glls_problem* P, std::vector<LevelStore<T>>& Ls) {
+    for (auto& s : Ls) {
+        const long long n = s.dev.N;
+        CK(P->alloc(&s.r, n));
+        CK(P->alloc(&s.x, n));
+        CK(P->alloc(&s.y, n));
+        CK(P->alloc(&s.t1, n));
+        CK(P->alloc(&s.t2, n));
+        CK(cudaMemset(s.r, 0, sizeof(T) * n));
+        CK(cudaMemset(s.x, 0, sizeof(T) * n));
+        CK(cudaMemset(s.y, 0, sizeof(T) * n));
+    }
+    return GLLS_OK;
+}
+
+// Per-instance Krylov state, scalars, streams.
+glls_status alloc_instance(glls_problem* P) {
+    const long long N = P->N;
+    double** vecs[] = {&P->f, &P->g, &P->v, &P->f0, &P->xk, &P->rk, &P->pk, &P->qk, &P->zk, &P->yk};
+    for (double** vp : vecs) {
+        CK(P->alloc(vp, N));
+        CK(cudaMemset(*vp, 0, sizeof(double) * N));
+    }
+    CK(P->alloc(&P->S, S_COUNT));
+    CK(P->alloc(&P->part, std::max<long long>(2 * kMaxReduceBlocks, P->L64.back().dev.E + 1)));
+    CK(P->alloc(&P->ticket, 1));
+    CK(cudaMemset(P->ticket, 0, sizeof(unsigned)));
+    CK(P->alloc(&P->r32, N));
+    CK(P->alloc(&P->z32, N));
+    CK(cudaMemset(P->r32, 0, sizeof(float) * N));
+    CK(cudaMemset(P->z32, 0, sizeof(float) * N));
+    CK(cudaMallocHost(&P->hostS, sizeof(double) * S_COUNT));
+    CK(cudaStreamCreateWithFlags(&P->capture_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&P->capture_stream2, cudaStreamNonBlocking));
+    return GLLS_OK;
+}
 
 template <typename T>
 glls_status upload_levels(glls_problem* P, const std::vector<LevelHost>& H, std::vector<LevelStore<T>>& out) {
@@ -140,16 +198,8 @@ glls_status upload_levels(glls_problem* P, const std::vector<LevelHost>& H, std:
                 }
             }
         }
-        CK(P->alloc(&s.r, h.N));
-        CK(P->alloc(&s.x, h.N));
-        CK(P->alloc(&s.y, h.N));
-        CK(P->alloc(&s.t1, h.N));
-        CK(P->alloc(&s.t2, h.N));
-        CK(cudaMemset(s.r, 0, sizeof(T) * h.N));
-        CK(cudaMemset(s.x, 0, sizeof(T) * h.N));
-        CK(cudaMemset(s.y, 0, sizeof(T) * h.N));
     }
-    return GLLS_OK;
+    return alloc_level_vectors<T>(P, out);
 }
 
 template <typename T>
@@ -628,6 +678,8 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
     if (!attrs_ok) return fail(GLLS_ERR_CUDA, "could not set kernel shared-memory attributes");
 
     std::unique_ptr<glls_problem> P(new glls_problem());
+    P->shared = std::make_shared<SharedData>();
+    P->shared->device = desc->device;
     P->device = desc->device;
     P->dim = desc->dim;
     P->p = desc->order;
@@ -682,26 +734,47 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
     const LevelHost& F = H.back();
     P->N = F.N;
     P->N0 = H[0].N;
-    const long long N = P->N;
     CK(P->upload(&P->mass, F.mass));
-    double** vecs[] = {&P->f, &P->g, &P->v, &P->f0, &P->xk, &P->rk, &P->pk, &P->qk, &P->zk, &P->yk};
-    for (double** vp : vecs) {
-        CK(P->alloc(vp, N));
-        CK(cudaMemset(*vp, 0, sizeof(double) * N));
-    }
-    CK(P->alloc(&P->S, S_COUNT));
-    CK(P->alloc(&P->part, std::max<long long>(2 * kMaxReduceBlocks, H.back().E + 1)));
-    CK(P->alloc(&P->ticket, 1));
-    CK(cudaMemset(P->ticket, 0, sizeof(unsigned)));
-    CK(P->alloc(&P->r32, N));
-    CK(P->alloc(&P->z32, N));
-    CK(cudaMemset(P->r32, 0, sizeof(float) * N));
-    CK(cudaMemset(P->z32, 0, sizeof(float) * N));
-    CK(cudaMallocHost(&P->hostS, sizeof(double) * S_COUNT));
-    CK(cudaStreamCreateWithFlags(&P->capture_stream, cudaStreamNonBlocking));
-    CK(cudaStreamCreateWithFlags(&P->capture_stream2, cudaStreamNonBlocking));
+    st = alloc_instance(P.get());
+    if (st != GLLS_OK) return st;
     CK(cudaDeviceSynchronize());
     P->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = P.release();
+    return GLLS_OK;
+}
+
+glls_status glls_problem_clone(const glls_problem* src, glls_problem** out) {
+    if (!src || !out) return fail(GLLS_ERR_INVALID, "null argument");
+    *out = nullptr;
+    CK(cudaSetDevice(src->device));
+    std::unique_ptr<glls_problem> P(new glls_problem());
+    P->shared = src->shared;
+    P->device = src->device;
+    P->dim = src->dim;
+    for (int a = 0; a < 3; ++a) P->nelem[a] = src->nelem[a];
+    P->p = src->p;
+    P->smoother = src->smoother;
+    P->restriction = src->restriction;
+    P->orders = src->orders;
+    P->C64 = src->C64;
+    P->C32 = src->C32;
+    P->N = src->N;
+    P->N0 = src->N0;
+    P->mass = src->mass;
+    P->L64.resize(src->L64.size());
+    P->L32.resize(src->L32.size());
+    for (size_t l = 0; l < src->L64.size(); ++l) {
+        P->L64[l].dev = src->L64[l].dev;
+        P->L32[l].dev = src->L32[l].dev;
+    }
+    glls_status st = alloc_level_vectors<double>(P.get(), P->L64);
+    if (st == GLLS_OK) st = alloc_level_vectors<float>(P.get(), P->L32);
+    if (st == GLLS_OK) st = alloc_instance(P.get());
+    if (st != GLLS_OK) {
+        for (void* a : P->allocs) cudaFree(a);
+        return st;
+    }
+    CK(cudaDeviceSynchronize());
     *out = P.release();
     return GLLS_OK;
 }
@@ -730,7 +803,7 @@ glls_status glls_problem_info(const glls_problem* P, glls_info* out) {
         out->ndof[l] = P->L64[l].dev.N;
     }
     out->coarse_unknowns = P->C64.n;
-    out->device_bytes = P->bytes;
+    out->device_bytes = P->bytes + (P->shared ? P->shared->bytes : 0);
     return GLLS_OK;
 }
 

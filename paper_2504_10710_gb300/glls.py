@@ -73,6 +73,7 @@ def lib():
             "glls_gll": [i, C.POINTER(d), C.POINTER(d)],
             "glls_problem_create": [C.POINTER(MeshDesc), C.POINTER(vp)],
             "glls_problem_info": [vp, C.POINTER(Info)],
+            "glls_problem_clone": [vp, C.POINTER(vp)],
             "glls_set_dirichlet": [vp, vp, i, vp],
             "glls_set_rhs": [vp, vp, i, vp],
             "glls_solve": [vp, C.POINTER(SolveOpts), vp, i, vp, C.POINTER(Stats)],
@@ -155,6 +156,16 @@ class Problem:
         self.dim = dim
         self.info = self._info()
         self.N = int(self.info.ndof[self.info.levels - 1])
+
+    def clone(self):
+        """A problem on the same mesh sharing its read-only device data."""
+        h = C.c_void_p()
+        _check(lib().glls_problem_clone(self.h, C.byref(h)))
+        c = Problem.__new__(Problem)
+        c.h, c.dim, c._coords = h, self.dim, self._coords
+        c.info = c._info()
+        c.N = self.N
+        return c
 
     def _info(self):
         inf = Info()
@@ -272,6 +283,23 @@ def solve_batch(problems, outs, o: SolveOpts, stream=None, raise_on_error=True):
     if raise_on_error:
         _check(status)
     return list(st)
+
+
+def solve_multi(problem, F, g, o: SolveOpts, clones=None):
+    """Several right-hand sides on one mesh: F has shape (nrhs, N); g is the
+    Dirichlet data (shared).  The RHS are solved together, as clones of
+    `problem` sharing its mesh data, in one glls_solve_batch launch.
+    Returns (U of shape (nrhs, N), stats, clones) - pass the clones back to
+    reuse them (and the cached batch graph)."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    nrhs = F.shape[0]
+    probs = [problem] + (clones if clones is not None else [problem.clone() for _ in range(nrhs - 1)])
+    for p, f in zip(probs, F):
+        p.set_rhs(f)
+        p.set_dirichlet(g)
+    U = np.zeros((nrhs, problem.N))
+    stats = solve_batch(probs, list(U), o)
+    return U, stats, probs[1:]
 
 
 def mesh_desc(dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0):
