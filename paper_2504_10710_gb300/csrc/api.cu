@@ -185,6 +185,22 @@ glls_status upload_levels(glls_problem* P, const std::vector<LevelHost>& H, std:
         CK(P->upload(&d.D, h.D));
         CK(P->upload(&d.diag, h.diag));
         for (int a = 0; a < h.dim; ++a) CK(P->upload(&d.off[a], h.off[a]));
+        for (int a = 0; a < h.dim; ++a) {
+            using V2 = typename Vec2Of<T>::type;
+            std::vector<V2> packed(h.N);
+            for (long long i = 0; i < h.N; ++i) {
+                packed[i].x = (T)h.diag[i];
+                packed[i].y = (T)h.off[a][i];
+            }
+            V2* dptr = nullptr;
+            void* p_ = nullptr;
+            CK(cudaMalloc(&p_, sizeof(V2) * packed.size()));
+            P->shared->allocs.push_back(p_);
+            P->shared->bytes += sizeof(V2) * packed.size();
+            dptr = static_cast<V2*>(p_);
+            CK(cudaMemcpy(dptr, packed.data(), sizeof(V2) * packed.size(), cudaMemcpyHostToDevice));
+            d.band[a] = dptr;
+        }
         if (l > 0) {
             for (int a = 0; a < h.dim; ++a) {
                 const Band1D* bs[2] = {&h.P[a], &h.R[a]};
@@ -972,8 +988,10 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
         }
         if (c == 0) Nfine = N;
         if (c + 1 == chain.size()) { Ncoarse = N; n0 = inner; }
-        // G, diag, off, D in FP64 + FP32; five level vectors in each precision; transfer bands
+        // G, diag, off, D in FP64 + FP32; packed (diag, off) pairs per direction; five level
+        // vectors in each precision; transfer bands
         total += 12.0 * ((double)ncomp * E * nloc + (1 + d) * (double)N + (p + 1) * (p + 1)) + 12.0 * 5 * N;
+        total += 24.0 * d * (double)N;
         total += 2.0 * d * (12.0 * (2 * p + 2) * (double)(ne[0] * p + 1) + 4.0 * (ne[0] * p + 1));
     }
     const double ld64 = (double)((n0 + 1) / 2 * 2), ld32 = (double)((n0 + 3) / 4 * 4);

@@ -23,6 +23,13 @@ struct DevBand {
 };
 
 template <typename T>
+struct Vec2Of;
+template <>
+struct Vec2Of<float> { using type = float2; };
+template <>
+struct Vec2Of<double> { using type = double2; };
+
+template <typename T>
 struct DevLevel {
     int dim = 2, p = 1, n1 = 2, nloc = 4, ncomp = 3;
     int ne[3] = {1, 1, 1};
@@ -32,6 +39,8 @@ struct DevLevel {
     const T* D = nullptr;
     const T* diag = nullptr;
     const T* off[3] = {nullptr, nullptr, nullptr};
+    // (diag, off[s]) interleaved per direction: one 8/16-byte load per node
+    const typename Vec2Of<T>::type* band[3] = {nullptr, nullptr, nullptr};
     DevBand<T> P[3], R[3];
     int lpb[3] = {4, 4, 4};   // line-solve tile (lines per CTA) per direction, set by the autotuner
 };

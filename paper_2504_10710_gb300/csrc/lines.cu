@@ -26,9 +26,9 @@ constexpr unsigned kFull = 0xffffffffu;
 template <typename T>
 struct WarpLineArgs {
     int n, nlines, stride, m1, st1, st2, contiguous, mode;
+    int p;              // element order: element-boundary nodes are multiples of p
     T alpha;
-    const T* diag;
-    const T* off;
+    const typename Vec2Of<T>::type* band;   // (diag, off) per node
     const T* g;
     const T* r;
     T* y;
@@ -38,9 +38,10 @@ struct WarpLineArgs {
 // shared-memory index with one pad word per 32: lane-chunk reads are conflict free
 __device__ __forceinline__ int padi(int k) { return k + (k >> 5); }
 
-// MODE 0: x = B^-1 g.  MODE 1: x += alpha B^-1 (r - y), and every y entry
-// read is reset to 0 (the apply that produced y accumulates into a zeroed
-// buffer, so its consumer restores that state).  MODE 2: x += alpha B^-1 r.
+// MODE 0: x = B^-1 g.  MODE 1: x += alpha B^-1 (r - y), and y is reset to 0
+// on element-boundary nodes (the apply that produced y plain-stores element-
+// interior nodes and adds into element-boundary ones, so its consumer
+// restores the zeros the next apply needs).  MODE 2: x += alpha B^-1 r.
 // MODE 3: x = alpha B^-1 r (first smoothing step from x = 0).
 template <typename T, int C, int LPB, int MODE>
 __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) {
@@ -50,13 +51,16 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
     T* so = sd + LPB * SPAN;
     T* sg = so + LPB * SPAN;
     __shared__ int sbase[LPB];
+    __shared__ int sseam[LPB];   // the whole line lies on element boundaries
     const int n = A.n;
     const int l0 = blockIdx.x * LPB;
     const int Wc = min(LPB, A.nlines - l0);
     const int tid = threadIdx.x;
     if (tid < LPB) {
         const int li = l0 + tid;
-        sbase[tid] = (li % A.m1 + 1) * A.st1 + (li / A.m1 + 1) * A.st2;
+        const int c1 = li % A.m1 + 1, c2 = li / A.m1 + 1;
+        sbase[tid] = c1 * A.st1 + c2 * A.st2;
+        sseam[tid] = (c1 % A.p == 0) || (A.st2 != 0 && c2 % A.p == 0);
     }
     __syncthreads();
     // staged loads: every thread has at most C elements per array, all issued
@@ -66,6 +70,7 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
     const int lw = contig ? (tid >> 5) : (tid & (LPB - 1));
     const int lk = contig ? (tid & 31) : (tid / LPB);
     const int lnode = lw < Wc ? sbase[lw] : 0;
+    const bool lseam = lw < Wc && sseam[lw] != 0;
     T vd[C], vo[C], vg[C];
 #pragma unroll
     for (int m = 0; m < C; ++m) {
@@ -73,8 +78,9 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
         vd[m] = T(1); vo[m] = T(0); vg[m] = T(0);
         if (lw < Wc && k < n) {
             const int node = lnode + (k + 1) * A.stride;
-            vd[m] = __ldg(A.diag + node);
-            vo[m] = k < n - 1 ? __ldg(A.off + node) : T(0);
+            const auto b = __ldg(A.band + node);
+            vd[m] = b.x;
+            vo[m] = k < n - 1 ? b.y : T(0);
             if (MODE == 0) vg[m] = A.g[node];
             else if (MODE == 1) vg[m] = A.r[node] - A.y[node];
             else vg[m] = A.r[node];
@@ -88,7 +94,6 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
             sd[sidx] = vd[m];
             so[sidx] = vo[m];
             sg[sidx] = vg[m];
-            if (MODE == 1) A.y[lnode + (k + 1) * A.stride] = T(0);
         }
     }
     __syncthreads();
@@ -199,6 +204,9 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
         if (lw < Wc && k < n) {
             const T v = sg[lw * SPAN + padi(k)];
             A.x[lnode + (k + 1) * A.stride] = MODE == 0 ? v : (MODE == 3 ? A.alpha * v : out[m] + A.alpha * v);
+            // the next apply stores element-interior nodes and adds into the
+            // element-boundary ones: only those must be reset
+            if (MODE == 1 && (lseam || (k + 1) % A.p == 0)) A.y[lnode + (k + 1) * A.stride] = T(0);
         }
     }
 }
@@ -271,9 +279,9 @@ bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T
     A.st2 = L.dim == 3 ? strides[o2] : 0;
     A.contiguous = s == 0;
     A.mode = mode;
+    A.p = L.p;
     A.alpha = alpha;
-    A.diag = L.diag;
-    A.off = L.off[s];
+    A.band = L.band[s];
     A.g = g;
     A.r = r;
     A.y = y;
