@@ -41,11 +41,14 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--graph", type=int, default=2, choices=[0, 1, 2],
+                    help="solve launch mode: 2 = one graph with a device-side loop (default), 1 = one graph "
+                         "per iteration (profilers can see its kernels), 0 = plain stream launches")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed mixed-precision solves (for an ncu launch list)")
     return ap.parse_args()
@@ -134,7 +137,7 @@ def run_ours(args, rank, world):
     kernels = [0]
 
     def timed(precision, steps, warmup, clocks=None):
-        o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=precision, use_graph=2)
+        o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=precision, use_graph=args.graph)
         its = []
         kernels[0] = 0
         for _ in range(warmup):

@@ -15,84 +15,93 @@ __device__ __forceinline__ bool on_boundary32(int I, int J, int K, const int n[3
 }
 
 // DOT: also sum_e x_e^T (A_e x_e) over all elements into *dot (last block).
+// Each thread owns ITEMS local nodes (t = threadIdx.x + 256 * it); its
+// geometry factors are loaded into registers before the x gather, so the two
+// global-memory latencies overlap.
 template <typename T, int DIM, int P, bool DOT>
 __global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
                                                       int mask, double* dot, double* part, unsigned* ticket) {
+    grid_dep_sync();
     constexpr int N1 = P + 1;
     constexpr int NLOC = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
     constexpr int EPB = NLOC >= 256 ? 1 : 256 / NLOC;
+    constexpr int ITEMS = (EPB * NLOC + 255) / 256;
+    constexpr int NC = DIM == 2 ? 3 : 6;
     __shared__ T sD[N1 * N1];
     __shared__ T sx[EPB * NLOC];
     __shared__ T sw[DIM * EPB * NLOC];
     const int E = (int)L.E;
     const int ne0 = L.ne[0], ne1 = L.ne[1], n0 = L.n[0], n1 = L.n[1];
     const int EN = E * NLOC;
-    for (int t = threadIdx.x; t < N1 * N1; t += blockDim.x) sD[t] = L.D[t];
     const int e0 = blockIdx.x * EPB;
     const int total = min(EPB, E - e0) * NLOC;
 
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int el = t / NLOC, q = t - el * NLOC;
-        const int e = e0 + el;
-        const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
-        const int ex = e % ne0, ey = (e / ne0) % ne1, ez = DIM == 3 ? e / (ne0 * ne1) : 0;
-        sx[t] = x[((ez * P + k) * n1 + ey * P + j) * n0 + ex * P + i];
+    T gk[ITEMS][NC];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const int t = threadIdx.x + 256 * it;
+        if (t < total) {
+            const int gq = e0 * NLOC + t;          // = (e0 + el) * NLOC + q
+#pragma unroll
+            for (int c = 0; c < NC; ++c) gk[it][c] = __ldg(L.G + c * EN + gq);
+        }
+    }
+    for (int t = threadIdx.x; t < N1 * N1; t += 256) sD[t] = L.D[t];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const int t = threadIdx.x + 256 * it;
+        if (t < total) {
+            const int el = t / NLOC, q = t - el * NLOC;
+            const int e = e0 + el;
+            const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
+            const int ex = e % ne0, ey = (e / ne0) % ne1, ez = DIM == 3 ? e / (ne0 * ne1) : 0;
+            sx[t] = x[((ez * P + k) * n1 + ey * P + j) * n0 + ex * P + i];
+        }
     }
     __syncthreads();
 
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const int t = threadIdx.x + 256 * it;
+        if (t >= total) break;
         const int el = t / NLOC, q = t - el * NLOC;
         const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
         const T* xe = sx + el * NLOC;
-        T Di[N1], Dj[N1], Dk[DIM == 3 ? N1 : 1];
-#pragma unroll
-        for (int m = 0; m < N1; ++m) {
-            Di[m] = sD[i * N1 + m];
-            Dj[m] = sD[j * N1 + m];
-            if (DIM == 3) Dk[DIM == 3 ? m : 0] = sD[k * N1 + m];
-        }
         T g0 = T(0), g1 = T(0), g2 = T(0);
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
-            g0 += Di[m] * xe[(k * N1 + j) * N1 + m];
-            g1 += Dj[m] * xe[(k * N1 + m) * N1 + i];
-            if (DIM == 3) g2 += Dk[DIM == 3 ? m : 0] * xe[(m * N1 + j) * N1 + i];
+            g0 += sD[i * N1 + m] * xe[(k * N1 + j) * N1 + m];
+            g1 += sD[j * N1 + m] * xe[(k * N1 + m) * N1 + i];
+            if (DIM == 3) g2 += sD[k * N1 + m] * xe[(m * N1 + j) * N1 + i];
         }
-        const int gq = (e0 + el) * NLOC + q;
+        const T* a = gk[it];
         if (DIM == 2) {
-            const T a00 = L.G[gq], a01 = L.G[EN + gq], a11 = L.G[2 * EN + gq];
-            sw[t] = a00 * g0 + a01 * g1;
-            sw[EPB * NLOC + t] = a01 * g0 + a11 * g1;
+            sw[t] = a[0] * g0 + a[1] * g1;
+            sw[EPB * NLOC + t] = a[1] * g0 + a[2] * g1;
         } else {
-            const T a00 = L.G[gq], a01 = L.G[EN + gq], a02 = L.G[2 * EN + gq];
-            const T a11 = L.G[3 * EN + gq], a12 = L.G[4 * EN + gq], a22 = L.G[5 * EN + gq];
-            sw[t] = a00 * g0 + a01 * g1 + a02 * g2;
-            sw[EPB * NLOC + t] = a01 * g0 + a11 * g1 + a12 * g2;
-            sw[2 * EPB * NLOC + t] = a02 * g0 + a12 * g1 + a22 * g2;
+            sw[t] = a[0] * g0 + a[1] * g1 + a[2] * g2;
+            sw[EPB * NLOC + t] = a[1] * g0 + a[3 % NC] * g1 + a[4 % NC] * g2;
+            sw[2 * EPB * NLOC + t] = a[2] * g0 + a[4 % NC] * g1 + a[5 % NC] * g2;
         }
     }
     __syncthreads();
 
     double local = 0.0;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const int t = threadIdx.x + 256 * it;
+        if (t >= total) break;
         const int el = t / NLOC, q = t - el * NLOC;
         const int e = e0 + el;
         const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
         const T* w0 = sw + el * NLOC;
         const T* w1 = sw + EPB * NLOC + el * NLOC;
-        T Ti[N1], Tj[N1], Tk[DIM == 3 ? N1 : 1];
-#pragma unroll
-        for (int m = 0; m < N1; ++m) {
-            Ti[m] = sD[m * N1 + i];
-            Tj[m] = sD[m * N1 + j];
-            if (DIM == 3) Tk[DIM == 3 ? m : 0] = sD[m * N1 + k];
-        }
         T v = T(0);
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
-            v += Ti[m] * w0[(k * N1 + j) * N1 + m];
-            v += Tj[m] * w1[(k * N1 + m) * N1 + i];
-            if (DIM == 3) v += Tk[DIM == 3 ? m : 0] * sw[2 * EPB * NLOC + el * NLOC + (m * N1 + j) * N1 + i];
+            v += sD[m * N1 + i] * w0[(k * N1 + j) * N1 + m];
+            v += sD[m * N1 + j] * w1[(k * N1 + m) * N1 + i];
+            if (DIM == 3) v += sD[m * N1 + k] * sw[2 * EPB * NLOC + el * NLOC + (m * N1 + j) * N1 + i];
         }
         const int ex = e % ne0, ey = (e / ne0) % ne1, ez = DIM == 3 ? e / (ne0 * ne1) : 0;
         const int I = ex * P + i, J = ey * P + j, K = ez * P + k;
@@ -125,9 +134,9 @@ bool launch_p(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, do
     constexpr int EPB = NLOC >= 256 ? 1 : 256 / NLOC;
     const int blocks = (int)((L.E + EPB - 1) / EPB);
     if (dot) {
-        apply_p_kernel<T, DIM, P, true><<<blocks, 256, 0, st>>>(L, x, y, mask ? 1 : 0, dot, part, ticket);
+        launch_k(apply_p_kernel<T, DIM, P, true>, blocks, 256, 0, st, L, x, y, mask ? 1 : 0, dot, part, ticket);
     } else {
-        apply_p_kernel<T, DIM, P, false><<<blocks, 256, 0, st>>>(L, x, y, mask ? 1 : 0, nullptr, nullptr, nullptr);
+        launch_k(apply_p_kernel<T, DIM, P, false>, blocks, 256, 0, st, L, x, y, mask ? 1 : 0, nullptr, nullptr, nullptr);
     }
     return true;
 }

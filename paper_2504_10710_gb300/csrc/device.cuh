@@ -12,8 +12,39 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <utility>
 
 namespace glls {
+
+// Programmatic dependent launch.  Kernels are launched with programmatic
+// stream serialisation, so the CTAs of the next kernel in a stream (or graph)
+// may be scheduled while the previous kernel drains.  Every kernel therefore
+// starts with grid_dep_sync(): it waits until the preceding kernel has
+// completed and its writes are visible, then lets the following kernel begin
+// launching.  Because each kernel waits before it touches memory, ordering is
+// transitive along the stream exactly as without the attribute.
+__device__ __forceinline__ void grid_dep_sync() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// False when GLLS_PDL=0 is set in the environment (plain stream order).
+bool pdl_enabled();
+
+template <typename... K, typename... A>
+inline cudaError_t launch_k(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 template <typename T>
 struct DevBand {

@@ -18,6 +18,7 @@
 #include "reduce.cuh"
 
 #include <cstdio>
+#include <cstdlib>
 #include <type_traits>
 
 namespace glls {
@@ -41,6 +42,7 @@ __device__ __forceinline__ bool on_boundary(long long g, const int n[3], int dim
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) apply_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
                                                     int mask, int epc) {
+    grid_dep_sync();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sD = reinterpret_cast<T*>(smem_raw);
     const int n1 = L.n1, nloc = L.nloc, p = L.p;
@@ -137,6 +139,7 @@ struct LineArgs {
 
 template <typename T>
 __global__ void __launch_bounds__(256) line_kernel(LineArgs<T> A) {
+    grid_dep_sync();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.n;
     const long long l0 = (long long)blockIdx.x * A.W;
@@ -227,6 +230,7 @@ template <typename T, int WB>
 __global__ void transfer_kernel(DevBand<T> M, int a, int3 nin, int3 nout, const T* __restrict__ in,
                                 const T* __restrict__ in2, T* __restrict__ out, int add, int mask, int dim,
                                 T* __restrict__ clear) {
+    grid_dep_sync();
     const int total = nout.x * nout.y * nout.z;
     const int sin_a = a == 0 ? 1 : (a == 1 ? nin.x : nin.x * nin.y);
     const int W = M.width;
@@ -271,6 +275,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, const long long* __restrict__ index,
                                                      const T* __restrict__ inv, const T* __restrict__ r,
                                                      T* __restrict__ e) {
+    grid_dep_sync();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* rs = reinterpret_cast<T*>(smem_raw);
     for (long long t = threadIdx.x; t < ld; t += blockDim.x) rs[t] = t < n ? r[index[t]] : T(0);
@@ -298,12 +303,14 @@ __global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, 
 // ---------------------------------------------------------------------------
 template <typename Ti, typename To>
 __global__ void cast_kernel(const Ti* __restrict__ in, To* __restrict__ out, long long n) {
+    grid_dep_sync();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = static_cast<To>(in[i]);
 }
 
 template <typename T>
 __global__ void zero_boundary_kernel(T* v, int3 n, int dim) {
+    grid_dep_sync();
     const long long total = (long long)n.x * n.y * n.z;
     const int nn[3] = {n.x, n.y, n.z};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
@@ -314,6 +321,7 @@ __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0
                                                    const double* __restrict__ a1, const double* __restrict__ b1,
                                                    int ndots, long long n, double* part, double* S, int slot0,
                                                    int slot1, unsigned* ticket, int rotate) {
+    grid_dep_sync();
     __shared__ double red[32];
     double s0 = 0.0, s1 = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -338,6 +346,7 @@ __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0
 __global__ void __launch_bounds__(256) dots_rz_zq_kernel(const double* __restrict__ r, double* __restrict__ z,
                                                          const float* __restrict__ z32, double* __restrict__ q,
                                                          long long n, double* part, double* S, unsigned* ticket) {
+    grid_dep_sync();
     __shared__ double red[32];
     double s0 = 0.0, s1 = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -366,9 +375,13 @@ __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x,
                                                          const double* __restrict__ p, const double* __restrict__ q,
                                                          long long n, double* part, double* S, unsigned* ticket,
                                                          float* __restrict__ r32) {
+    grid_dep_sync();
     __shared__ double red[32];
+    __shared__ double sh_alpha;
     const double pq = S[S_PQ];
-    const double alpha = S[S_RZ] / pq;
+    if (threadIdx.x == 0) sh_alpha = S[S_RZ] / pq;   // FP64 division once per block
+    __syncthreads();
+    const double alpha = sh_alpha;
     double s = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         x[i] += alpha * p[i];
@@ -391,7 +404,11 @@ __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x,
 
 __global__ void fcg_direction_kernel(double* __restrict__ p, const double* __restrict__ z, long long n,
                                      double* __restrict__ S, int flexible, unsigned* ticket) {
-    const double beta = flexible ? -S[S_ALPHA] * S[S_ZQ] / S[S_RZ] : S[S_RZNEW] / S[S_RZ];
+    grid_dep_sync();
+    __shared__ double sh_beta;
+    if (threadIdx.x == 0) sh_beta = flexible ? -S[S_ALPHA] * S[S_ZQ] / S[S_RZ] : S[S_RZNEW] / S[S_RZ];
+    __syncthreads();
+    const double beta = sh_beta;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = z[i] + beta * p[i];
     // every block has read S_RZ before taking its ticket: the last one rotates
@@ -406,6 +423,7 @@ __global__ void fcg_direction_kernel(double* __restrict__ p, const double* __res
 __global__ void __launch_bounds__(256) multidot_kernel(const double* __restrict__ V, long long ld, int k1,
                                                        const double* __restrict__ w, long long n,
                                                        double* part, double* h, unsigned* ticket) {
+    grid_dep_sync();
     __shared__ double red[32];
     const int j = blockIdx.y;
     const double* v = V + (long long)j * ld;
@@ -428,6 +446,7 @@ __global__ void __launch_bounds__(256) multidot_kernel(const double* __restrict_
 // w -= sum_{j < k1} h[j] V_j ;  x += sum_{j < k1} h[j] V_j when sign > 0
 __global__ void gs_update_kernel(double* __restrict__ w, const double* __restrict__ V, long long ld, int k1,
                                  const double* __restrict__ h, long long n, double sign) {
+    grid_dep_sync();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         double a = 0.0;
         for (int j = 0; j < k1; ++j) a += h[j] * V[(long long)j * ld + i];
@@ -438,7 +457,11 @@ __global__ void gs_update_kernel(double* __restrict__ w, const double* __restric
 // out = in / sqrt(nrm2[0])
 __global__ void scale_by_norm_kernel(double* __restrict__ out, const double* __restrict__ in,
                                      const double* __restrict__ nrm2, long long n) {
-    const double s = 1.0 / sqrt(nrm2[0]);
+    grid_dep_sync();
+    __shared__ double sh_s;
+    if (threadIdx.x == 0) sh_s = 1.0 / sqrt(nrm2[0]);
+    __syncthreads();
+    const double s = sh_s;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = in[i] * s;
 }
@@ -447,6 +470,7 @@ __global__ void scale_by_norm_kernel(double* __restrict__ out, const double* __r
 // node): solve_init_kernel runs once after r0.r0 is known, solve_cond_kernel
 // ends every outer iteration.
 __global__ void solve_init_kernel(double* S, cudaGraphConditionalHandle h, double tol, int maxit) {
+    grid_dep_sync();
     if (threadIdx.x != 0) return;
     const double rr0 = S[S_RR0];
     S[S_RR] = rr0;
@@ -464,6 +488,7 @@ __global__ void solve_init_kernel(double* S, cudaGraphConditionalHandle h, doubl
 }
 
 __global__ void solve_cond_kernel(double* S, cudaGraphConditionalHandle h, int maxit) {
+    grid_dep_sync();
     if (threadIdx.x != 0) return;
     const double it = S[S_ITER] + 1.0;
     S[S_ITER] = it;
@@ -475,6 +500,7 @@ __global__ void solve_cond_kernel(double* S, cudaGraphConditionalHandle h, int m
 
 __global__ void lift_rhs_kernel(const double* __restrict__ mass, const double* __restrict__ f,
                                 const double* __restrict__ y, double* __restrict__ f0, int3 n, int dim) {
+    grid_dep_sync();
     const long long total = (long long)n.x * n.y * n.z;
     const int nn[3] = {n.x, n.y, n.z};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
@@ -482,6 +508,7 @@ __global__ void lift_rhs_kernel(const double* __restrict__ mass, const double* _
 }
 
 __global__ void boundary_only_kernel(const double* __restrict__ g, double* __restrict__ v, int3 n, int dim) {
+    grid_dep_sync();
     const long long total = (long long)n.x * n.y * n.z;
     const int nn[3] = {n.x, n.y, n.z};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
@@ -489,6 +516,7 @@ __global__ void boundary_only_kernel(const double* __restrict__ g, double* __res
 }
 
 __global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a, long long n) {
+    grid_dep_sync();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] += a * x[i];
 }
@@ -528,9 +556,9 @@ void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_
     const long long blocks = (L.E + epc - 1) / epc;
     const size_t smem = sizeof(T) * (L.n1 * L.n1 + (size_t)epc * L.nloc * (1 + L.dim));
     if (L.dim == 2) {
-        apply_kernel<T, 2><<<(unsigned)blocks, 256, smem, st>>>(L, x, y, mask ? 1 : 0, epc);
+        launch_k(apply_kernel<T, 2>, (unsigned)blocks, 256, smem, st, L, x, y, mask ? 1 : 0, epc);
     } else {
-        apply_kernel<T, 3><<<(unsigned)blocks, 256, smem, st>>>(L, x, y, mask ? 1 : 0, epc);
+        launch_k(apply_kernel<T, 3>, (unsigned)blocks, 256, smem, st, L, x, y, mask ? 1 : 0, epc);
     }
     // orders outside the specialised range: x.(A x) as a separate product
     if (dot) {
@@ -576,7 +604,7 @@ void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const 
     A.W = (int)W;
     const size_t smem = per_line * W;
     const long long blocks = (A.nlines + W - 1) / W;
-    line_kernel<T><<<(unsigned)blocks, 256, smem, st>>>(A);
+    launch_k(line_kernel<T>, (unsigned)blocks, 256, smem, st, A);
 }
 
 template <typename T>
@@ -587,11 +615,11 @@ void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nou
     const int3 ni = make_int3(nin[0], nin[1], nin[2]), no = make_int3(nout[0], nout[1], nout[2]);
     const int g = grid_for(total);
     const int ad = add ? 1 : 0, mk = mask ? 1 : 0;
-    if (M.width <= 4) transfer_kernel<T, 4><<<g, 256, 0, st>>>(M, a, ni, no, in, in2, out, ad, mk, dim, clear);
-    else if (M.width <= 8) transfer_kernel<T, 8><<<g, 256, 0, st>>>(M, a, ni, no, in, in2, out, ad, mk, dim, clear);
-    else if (M.width <= 16) transfer_kernel<T, 16><<<g, 256, 0, st>>>(M, a, ni, no, in, in2, out, ad, mk, dim, clear);
-    else if (M.width <= 32) transfer_kernel<T, 32><<<g, 256, 0, st>>>(M, a, ni, no, in, in2, out, ad, mk, dim, clear);
-    else transfer_kernel<T, 0><<<g, 256, 0, st>>>(M, a, ni, no, in, in2, out, ad, mk, dim, clear);
+    if (M.width <= 4) launch_k(transfer_kernel<T, 4>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear);
+    else if (M.width <= 8) launch_k(transfer_kernel<T, 8>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear);
+    else if (M.width <= 16) launch_k(transfer_kernel<T, 16>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear);
+    else if (M.width <= 32) launch_k(transfer_kernel<T, 32>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear);
+    else launch_k(transfer_kernel<T, 0>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear);
 }
 
 template <typename T>
@@ -600,77 +628,85 @@ void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, cudaSt
     const size_t smem = sizeof(T) * (size_t)C.ld;
     long long blocks = (C.n + 7) / 8;
     if (blocks > 2 * 152) blocks = 2 * 152;
-    coarse_kernel<T><<<(unsigned)blocks, 256, smem, st>>>(C.n, C.ld, C.index, C.inv, r, e);
+    launch_k(coarse_kernel<T>, (unsigned)blocks, 256, smem, st, C.n, C.ld, C.index, C.inv, r, e);
 }
 
 template <typename Ti, typename To>
 void launch_cast(const Ti* in, To* out, long long n, cudaStream_t st) {
-    cast_kernel<Ti, To><<<grid_for(n), 256, 0, st>>>(in, out, n);
+    launch_k(cast_kernel<Ti, To>, grid_for(n), 256, 0, st, in, out, n);
 }
 
 template <typename T>
 void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st) {
     const long long total = (long long)n[0] * n[1] * n[2];
-    zero_boundary_kernel<T><<<grid_for(total), 256, 0, st>>>(v, make_int3(n[0], n[1], n[2]), dim);
+    launch_k(zero_boundary_kernel<T>, grid_for(total), 256, 0, st, v, make_int3(n[0], n[1], n[2]), dim);
 }
 
 void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots, long long n,
                  double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st) {
-    dots_kernel<<<kDotBlocks, 256, 0, st>>>(a0, b0, a1, b1, ndots, n, part, S, slot0, slot1, ticket, 0);
+    launch_k(dots_kernel, kDotBlocks, 256, 0, st, a0, b0, a1, b1, ndots, n, part, S, slot0, slot1, ticket, 0);
 }
 
 void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, double* part, double* S,
                        unsigned* ticket, float* r32, cudaStream_t st) {
-    fcg_update_kernel<<<kDotBlocks, 256, 0, st>>>(x, r, p, q, n, part, S, ticket, r32);
+    launch_k(fcg_update_kernel, kDotBlocks, 256, 0, st, x, r, p, q, n, part, S, ticket, r32);
 }
 
 void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* part, double* S,
                        unsigned* ticket, cudaStream_t st) {
-    dots_rz_zq_kernel<<<reduce_grid(n), 256, 0, st>>>(r, z, z32, q, n, part, S, ticket);
+    launch_k(dots_rz_zq_kernel, reduce_grid(n), 256, 0, st, r, z, z32, q, n, part, S, ticket);
 }
 
 void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, unsigned* ticket,
                           cudaStream_t st) {
-    fcg_direction_kernel<<<grid_for(n), 256, 0, st>>>(p, z, n, S, flexible, ticket);
+    launch_k(fcg_direction_kernel, grid_for(n), 256, 0, st, p, z, n, S, flexible, ticket);
 }
 
 void launch_lift_rhs(const double* mass, const double* f, const double* y, double* f0, const int n[3], int dim,
                      cudaStream_t st) {
     const long long total = (long long)n[0] * n[1] * n[2];
-    lift_rhs_kernel<<<grid_for(total), 256, 0, st>>>(mass, f, y, f0, make_int3(n[0], n[1], n[2]), dim);
+    launch_k(lift_rhs_kernel, grid_for(total), 256, 0, st, mass, f, y, f0, make_int3(n[0], n[1], n[2]), dim);
 }
 
 void launch_boundary_only(const double* g, double* v, const int n[3], int dim, cudaStream_t st) {
     const long long total = (long long)n[0] * n[1] * n[2];
-    boundary_only_kernel<<<grid_for(total), 256, 0, st>>>(g, v, make_int3(n[0], n[1], n[2]), dim);
+    launch_k(boundary_only_kernel, grid_for(total), 256, 0, st, g, v, make_int3(n[0], n[1], n[2]), dim);
 }
 
 void launch_multidot(const double* V, long long ld, int k1, const double* w, long long n, double* part, double* h,
                      unsigned* ticket, cudaStream_t st) {
     long long nb = (n + 255) / 256;
     if (nb > 64) nb = 64;
-    multidot_kernel<<<dim3((unsigned)nb, (unsigned)k1), 256, 0, st>>>(V, ld, k1, w, n, part, h, ticket);
+    launch_k(multidot_kernel, dim3((unsigned)nb, (unsigned)k1), 256, 0, st, V, ld, k1, w, n, part, h, ticket);
 }
 
 void launch_gs_update(double* w, const double* V, long long ld, int k1, const double* h, long long n, double sign,
                       cudaStream_t st) {
-    gs_update_kernel<<<grid_for(n), 256, 0, st>>>(w, V, ld, k1, h, n, sign);
+    launch_k(gs_update_kernel, grid_for(n), 256, 0, st, w, V, ld, k1, h, n, sign);
 }
 
 void launch_scale_by_norm(double* out, const double* in, const double* nrm2, long long n, cudaStream_t st) {
-    scale_by_norm_kernel<<<grid_for(n), 256, 0, st>>>(out, in, nrm2, n);
+    launch_k(scale_by_norm_kernel, grid_for(n), 256, 0, st, out, in, nrm2, n);
 }
 
 void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st) {
-    solve_init_kernel<<<1, 32, 0, st>>>(S, h, tol, maxit);
+    launch_k(solve_init_kernel, 1, 32, 0, st, S, h, tol, maxit);
 }
 
 void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st) {
-    solve_cond_kernel<<<1, 32, 0, st>>>(S, h, maxit);
+    launch_k(solve_cond_kernel, 1, 32, 0, st, S, h, maxit);
 }
 
 void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st) {
-    axpy_kernel<<<grid_for(n), 256, 0, st>>>(y, x, a, n);
+    launch_k(axpy_kernel, grid_for(n), 256, 0, st, y, x, a, n);
+}
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("GLLS_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
 bool init_kernel_attributes() {

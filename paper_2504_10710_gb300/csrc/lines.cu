@@ -45,6 +45,7 @@ __device__ __forceinline__ int padi(int k) { return k + (k >> 5); }
 // MODE 3: x = alpha B^-1 r (first smoothing step from x = 0).
 template <typename T, int C, int LPB, int MODE>
 __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) {
+    grid_dep_sync();
     constexpr int SPAN = 32 * C + C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sd = reinterpret_cast<T*>(smem_raw);
@@ -217,10 +218,10 @@ void launch_lpb(const WarpLineArgs<T>& A, cudaStream_t st) {
     const size_t smem = sizeof(T) * 3 * LPB * (32 * C + C);
     const int blocks = (A.nlines + LPB - 1) / LPB;
     switch (A.mode) {
-        case 0: line_warp_kernel<T, C, LPB, 0><<<blocks, 32 * LPB, smem, st>>>(A); break;
-        case 1: line_warp_kernel<T, C, LPB, 1><<<blocks, 32 * LPB, smem, st>>>(A); break;
-        case 2: line_warp_kernel<T, C, LPB, 2><<<blocks, 32 * LPB, smem, st>>>(A); break;
-        default: line_warp_kernel<T, C, LPB, 3><<<blocks, 32 * LPB, smem, st>>>(A); break;
+        case 0: launch_k(line_warp_kernel<T, C, LPB, 0>, blocks, 32 * LPB, smem, st, A); break;
+        case 1: launch_k(line_warp_kernel<T, C, LPB, 1>, blocks, 32 * LPB, smem, st, A); break;
+        case 2: launch_k(line_warp_kernel<T, C, LPB, 2>, blocks, 32 * LPB, smem, st, A); break;
+        default: launch_k(line_warp_kernel<T, C, LPB, 3>, blocks, 32 * LPB, smem, st, A); break;
     }
 }
 
