@@ -30,11 +30,19 @@ __global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __
     __shared__ T sD[N1 * N1];
     __shared__ T sx[EPB * NLOC];
     __shared__ T sw[DIM * EPB * NLOC];
+    __shared__ int sbase[EPB];   // global index of each element's first node
+    __shared__ int sxyz[EPB];    // element coordinates packed 10:10:10 bits
     const int E = (int)L.E;
-    const int ne0 = L.ne[0], ne1 = L.ne[1], n0 = L.n[0], n1 = L.n[1];
+    const int n0 = L.n[0], n1 = L.n[1];
     const int EN = E * NLOC;
     const int e0 = blockIdx.x * EPB;
     const int total = min(EPB, E - e0) * NLOC;
+    if (threadIdx.x < EPB && e0 + (int)threadIdx.x < E) {
+        const int e = e0 + threadIdx.x, ne0 = L.ne[0], ne1 = L.ne[1];
+        const int ex = e % ne0, ey = (e / ne0) % ne1, ez = DIM == 3 ? e / (ne0 * ne1) : 0;
+        sbase[threadIdx.x] = ((ez * P) * n1 + ey * P) * n0 + ex * P;
+        sxyz[threadIdx.x] = ex | (ey << 10) | (ez << 20);
+    }
 
     T gk[ITEMS][NC];
 #pragma unroll
@@ -47,15 +55,14 @@ __global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __
         }
     }
     for (int t = threadIdx.x; t < N1 * N1; t += 256) sD[t] = L.D[t];
+    __syncthreads();
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
         const int t = threadIdx.x + 256 * it;
         if (t < total) {
             const int el = t / NLOC, q = t - el * NLOC;
-            const int e = e0 + el;
             const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
-            const int ex = e % ne0, ey = (e / ne0) % ne1, ez = DIM == 3 ? e / (ne0 * ne1) : 0;
-            sx[t] = x[((ez * P + k) * n1 + ey * P + j) * n0 + ex * P + i];
+            sx[t] = x[sbase[el] + (k * n1 + j) * n0 + i];
         }
     }
     __syncthreads();
@@ -92,7 +99,6 @@ __global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __
         const int t = threadIdx.x + 256 * it;
         if (t >= total) break;
         const int el = t / NLOC, q = t - el * NLOC;
-        const int e = e0 + el;
         const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
         const T* w0 = sw + el * NLOC;
         const T* w1 = sw + EPB * NLOC + el * NLOC;
@@ -103,9 +109,9 @@ __global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __
             v += sD[m * N1 + j] * w1[(k * N1 + m) * N1 + i];
             if (DIM == 3) v += sD[m * N1 + k] * sw[2 * EPB * NLOC + el * NLOC + (m * N1 + j) * N1 + i];
         }
-        const int ex = e % ne0, ey = (e / ne0) % ne1, ez = DIM == 3 ? e / (ne0 * ne1) : 0;
-        const int I = ex * P + i, J = ey * P + j, K = ez * P + k;
-        const int g = (K * n1 + J) * n0 + I;
+        const int exyz = sxyz[el];
+        const int I = (exyz & 1023) * P + i, J = ((exyz >> 10) & 1023) * P + j, K = (exyz >> 20) * P + k;
+        const int g = sbase[el] + (k * n1 + j) * n0 + i;
         if (DOT) local += (double)sx[t] * (double)v;
         const bool inner = i > 0 && i < P && j > 0 && j < P && (DIM == 2 || (k > 0 && k < P));
         if (inner) {
@@ -159,6 +165,8 @@ template <typename T>
 bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part,
                         unsigned* ticket, cudaStream_t st) {
     if (L.N > (1LL << 31) - 1 || L.E * L.nloc * (L.dim == 2 ? 3 : 6) > (1LL << 31) - 1) return false;
+    for (int a = 0; a < L.dim; ++a)
+        if (L.ne[a] >= 1024) return false;   // element coordinates are packed in 10 bits
     if (L.dim == 2) return dispatch<T, 2, 16>(L.p, L, x, y, mask, dot, part, ticket, st);
     return dispatch<T, 3, 8>(L.p, L, x, y, mask, dot, part, ticket, st);
 }

@@ -72,11 +72,13 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
     const int lk = contig ? (tid & 31) : (tid / LPB);
     const int lnode = lw < Wc ? sbase[lw] : 0;
     const bool lseam = lw < Wc && sseam[lw] != 0;
-    T vd[C], vo[C], vg[C];
+    // x (MODE 1, 2) is read here with the band and the right-hand side, so the
+    // update after the solve waits on no further global load
+    T vd[C], vo[C], vg[C], out[C];
 #pragma unroll
     for (int m = 0; m < C; ++m) {
         const int k = lk + 32 * m;
-        vd[m] = T(1); vo[m] = T(0); vg[m] = T(0);
+        vd[m] = T(1); vo[m] = T(0); vg[m] = T(0); out[m] = T(0);
         if (lw < Wc && k < n) {
             const int node = lnode + (k + 1) * A.stride;
             const auto b = __ldg(A.band + node);
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
             if (MODE == 0) vg[m] = A.g[node];
             else if (MODE == 1) vg[m] = A.r[node] - A.y[node];
             else vg[m] = A.r[node];
+            if (MODE == 1 || MODE == 2) out[m] = A.x[node];
         }
     }
 #pragma unroll
@@ -190,15 +193,9 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
         }
     }
     __syncthreads();
-    T out[C];
-    if (MODE == 1 || MODE == 2) {
-#pragma unroll
-        for (int m = 0; m < C; ++m) {
-            const int k = lk + 32 * m;
-            out[m] = T(0);
-            if (lw < Wc && k < n) out[m] = A.x[lnode + (k + 1) * A.stride];
-        }
-    }
+    // (k + 1) mod p along this thread's nodes k = lk + 32 m, stepped without division
+    const int p = A.p, step = 32 % p;
+    int rem = (lk + 1) % p;
 #pragma unroll
     for (int m = 0; m < C; ++m) {
         const int k = lk + 32 * m;
@@ -207,8 +204,10 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
             A.x[lnode + (k + 1) * A.stride] = MODE == 0 ? v : (MODE == 3 ? A.alpha * v : out[m] + A.alpha * v);
             // the next apply stores element-interior nodes and adds into the
             // element-boundary ones: only those must be reset
-            if (MODE == 1 && (lseam || (k + 1) % A.p == 0)) A.y[lnode + (k + 1) * A.stride] = T(0);
+            if (MODE == 1 && (lseam || rem == 0)) A.y[lnode + (k + 1) * A.stride] = T(0);
         }
+        rem += step;
+        if (rem >= p) rem -= p;
     }
 }
 

@@ -19,14 +19,23 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;   // valid in thread 0
 }
 
-// Every block writes its partial sums; the last block to finish (atomic
-// ticket) adds the partials in block order, so the result does not depend on
-// scheduling, and resets the ticket for the next launch.
+// Ticket increment with acquire-release semantics at GPU scope: the calling
+// thread's earlier writes (its block's partial sums) are visible to whichever
+// thread observes a later ticket value, and that thread sees all of them.
+__device__ __forceinline__ unsigned ticket_add_acq_rel(unsigned* ticket) {
+    unsigned prev;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(ticket) : "memory");
+    return prev;
+}
+
+// Every block writes its partial sums (thread 0 writes them); the last block
+// to finish (atomic ticket) adds the partials in block order, so the result
+// does not depend on scheduling, and resets the ticket for the next launch.
+// Only thread 0's writes need ordering, so no block-wide fence is issued.
 __device__ __forceinline__ bool last_block(unsigned* ticket) {
     __shared__ bool is_last;
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) is_last = ticket_add_acq_rel(ticket) == gridDim.x - 1;
     __syncthreads();
     return is_last;
 }
@@ -34,9 +43,8 @@ __device__ __forceinline__ bool last_block(unsigned* ticket) {
 // As last_block, for a launch of `total` blocks (multi-dimensional grids).
 __device__ __forceinline__ bool last_block_of(unsigned* ticket, unsigned total) {
     __shared__ bool is_last_n;
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last_n = atomicAdd(ticket, 1u) == total - 1;
+    if (threadIdx.x == 0) is_last_n = ticket_add_acq_rel(ticket) == total - 1;
     __syncthreads();
     return is_last_n;
 }
