@@ -10,6 +10,8 @@
  *   Algorithm 1, Prop. 3.7, Thm. 3.8,
  *   Cor. 3.9                            cyclic reduction as a direct multigrid
  *   Sec. 3.3, Def. 3.12, Algorithm 2    p-transfers, gamma-cycle, M_0^-1 = A_0^-1
+ *   Def. 3.5, Prop. 3.7, Thm. 3.8
+ *   (blocks m > 1), Cor. 3.9            block cyclic reduction of the coarsest level
  *
  * Conventions for every entry point:
  *   - Return value: GLLS_OK (0) or a negative glls_status.  The message of the
@@ -54,6 +56,16 @@ enum { GLLS_PREC_FP64 = 0, GLLS_PREC_MIXED = 1 };          /* gamma-cycle in FP6
 enum { GLLS_SMOOTHER_GLL = 0, GLLS_SMOOTHER_FEM = 1 };     /* line systems from A_p or A~_p */
 enum { GLLS_RESTRICT_TRANSPOSE = 0, GLLS_RESTRICT_INTERP = 1 };
 enum { GLLS_KRYLOV_FCG = 0, GLLS_KRYLOV_PCG = 1, GLLS_KRYLOV_GMRES = 2 };
+/* Exact solver of the coarsest level (A_0^-1 of Algorithm 2):
+ *   AUTO     block cyclic reduction over the blocks of the slowest grid axis
+ *            (lines in 2-D, planes in 3-D) to the depth a launch-and-bytes
+ *            cost model prefers, then the dense inverse of what is left
+ *            (depth 0 = the dense inverse of A_0);
+ *   DENSE    the dense inverse of A_0 (one matrix-vector product);
+ *   BLOCK_CR coarse_cr_levels levels of block CR (0 = the model's depth, at
+ *            least one), clamped to floor(log2(blocks)).
+ * Every choice gives A_0^-1 r up to rounding. */
+enum { GLLS_COARSE_AUTO = 0, GLLS_COARSE_DENSE = 1, GLLS_COARSE_BLOCK_CR = 2 };
 
 typedef struct glls_problem glls_problem;   /* opaque, library-owned */
 
@@ -69,6 +81,8 @@ typedef struct {
     int smoother;         /* GLLS_SMOOTHER_* */
     int restriction;      /* GLLS_RESTRICT_* */
     int device;           /* CUDA device ordinal */
+    int coarse_solver;    /* GLLS_COARSE_* (0 = AUTO) */
+    int coarse_cr_levels; /* block-CR levels for GLLS_COARSE_BLOCK_CR (0 = automatic) */
 } glls_mesh_desc;
 
 typedef struct {
@@ -105,6 +119,8 @@ typedef struct {
     long long ndof[8];          /* total nodes per level */
     long long coarse_unknowns;  /* interior unknowns of level 0 */
     size_t device_bytes;        /* device memory held by the problem */
+    int coarse_cr_levels;       /* block-CR levels of the coarsest solve (0 = dense inverse) */
+    long long coarse_dense_unknowns;   /* size of the densely inverted system */
 } glls_info;
 
 /* Reference GLL(p) nodes and weights (Def. 2.1); xi, rho: host arrays of p+1. */

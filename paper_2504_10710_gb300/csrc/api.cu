@@ -218,6 +218,39 @@ glls_status upload_levels(glls_problem* P, const std::vector<LevelHost>& H, std:
     return alloc_level_vectors<T>(P, out);
 }
 
+// Coarsest-level solver data in precision T: node index (FP64 copy only),
+// block-CR operators padded to 16-byte rows, the dense inverse of the system
+// left after block CR (16-byte rows for vector loads).
+template <typename T>
+glls_status upload_coarse(glls_problem* P, const CoarseHost& C, DevCoarse<T>& D) {
+    constexpr int V = 16 / sizeof(T);
+    D.n = C.n;
+    D.nr = C.nr;
+    D.ld = (C.nr + V - 1) / V * V;
+    D.nb = C.nb;
+    D.m = C.m;
+    D.ldm = (C.m + V - 1) / V * V;
+    D.cr_levels = C.cr_levels;
+    if ((size_t)D.ld * sizeof(T) > kMaxDynSmemBytes)
+        return fail(GLLS_ERR_INVALID, "coarsest level too large for the dense coarse solver "
+                                      "(use GLLS_COARSE_BLOCK_CR with more levels)");
+    if (sizeof(T) == sizeof(double)) CK(P->upload(&D.index, C.index));
+    auto pad = [&](const std::vector<double>& src, long long rows, long long cols, long long ld) {
+        std::vector<T> out((size_t)rows * ld, T(0));
+        for (long long i = 0; i < rows; ++i)
+            for (long long j = 0; j < cols; ++j) out[(size_t)i * ld + j] = (T)src[(size_t)i * cols + j];
+        return out;
+    };
+    const size_t mm = (size_t)C.m * C.m;
+    for (int l = 0; l < C.cr_levels; ++l) {
+        const long long nfh = (long long)(C.fh[l].size() / mm), nagk = (long long)(C.agk[l].size() / mm);
+        CK(P->upload(&D.fh[l], pad(C.fh[l], nfh * C.m, C.m, D.ldm)));
+        CK(P->upload(&D.agk[l], pad(C.agk[l], nagk * C.m, C.m, D.ldm)));
+    }
+    CK(P->upload(&D.inv, pad(C.inv, C.nr, C.nr, D.ld)));
+    return GLLS_OK;
+}
+
 template <typename T>
 std::vector<LevelStore<T>>& levels_of(glls_problem* P);
 template <>
@@ -291,7 +324,7 @@ void cycle(glls_problem* P, int l, const T* r, T* x, int gamma, int m, T alpha, 
     auto& Ls = levels_of<T>(P);
     // x: boundary entries are zero and stay zero (only interior entries are written)
     if (l == 0) {
-        launch_coarse<T>(coarse_of<T>(P), Ls[0].dev.N, r, x, st, true);
+        launch_coarse<T>(coarse_of<T>(P), Ls[0].dev.N, r, x, Ls[0].t1, st, true);
         return;
     }
     const int d = Ls[l].dev.dim;
@@ -720,32 +753,21 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
             if (inner && !(h.diag[i] > 0.0)) return fail(GLLS_ERR_BREAKDOWN, "non-positive line-system diagonal");
         }
     }
+    if (desc->coarse_solver < 0 || desc->coarse_solver > 2 || desc->coarse_cr_levels < 0)
+        return fail(GLLS_ERR_INVALID, "coarse_solver must be GLLS_COARSE_* and coarse_cr_levels >= 0");
     CoarseHost C;
-    err = build_coarse(H[0], C);
+    err = build_coarse(H[0], desc->coarse_solver, desc->coarse_cr_levels, C);
     if (!err.empty()) return fail(GLLS_ERR_BREAKDOWN, err);
+    if (C.cr_levels > kMaxCrLevels) return fail(GLLS_ERR_INVALID, "too many block-CR levels");
 
     glls_status st = upload_levels<double>(P.get(), H, P->L64);
     if (st != GLLS_OK) return st;
     st = upload_levels<float>(P.get(), H, P->L32);
     if (st != GLLS_OK) return st;
-    P->C64.n = C.n;
-    P->C32.n = C.n;
-    P->C64.ld = (C.n + 1) / 2 * 2;     // 16-byte rows for double2 loads
-    P->C32.ld = (C.n + 3) / 4 * 4;     // 16-byte rows for float4 loads
-    CK(P->upload(&P->C64.index, C.index));
+    st = upload_coarse<double>(P.get(), C, P->C64);
+    if (st == GLLS_OK) st = upload_coarse<float>(P.get(), C, P->C32);
+    if (st != GLLS_OK) return st;
     P->C32.index = P->C64.index;
-    {
-        std::vector<double> pad64((size_t)C.n * P->C64.ld, 0.0), pad32((size_t)C.n * P->C32.ld, 0.0);
-        for (long long i = 0; i < C.n; ++i)
-            for (long long j = 0; j < C.n; ++j) {
-                pad64[(size_t)i * P->C64.ld + j] = C.inv[(size_t)i * C.n + j];
-                pad32[(size_t)i * P->C32.ld + j] = C.inv[(size_t)i * C.n + j];
-            }
-        CK(P->upload(&P->C64.inv, pad64));
-        CK(P->upload(&P->C32.inv, pad32));
-    }
-    if ((size_t)P->C64.ld * sizeof(double) > kMaxDynSmemBytes)
-        return fail(GLLS_ERR_INVALID, "coarsest level too large for the dense coarse solver");
 
     const LevelHost& F = H.back();
     P->N = F.N;
@@ -819,6 +841,8 @@ glls_status glls_problem_info(const glls_problem* P, glls_info* out) {
         out->ndof[l] = P->L64[l].dev.N;
     }
     out->coarse_unknowns = P->C64.n;
+    out->coarse_cr_levels = P->C64.cr_levels;
+    out->coarse_dense_unknowns = P->C64.nr;
     out->device_bytes = P->bytes + (P->shared ? P->shared->bytes : 0);
     return GLLS_OK;
 }
@@ -994,8 +1018,23 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
         total += 24.0 * d * (double)N;
         total += 2.0 * d * (12.0 * (2 * p + 2) * (double)(ne[0] * p + 1) + 4.0 * (ne[0] * p + 1));
     }
-    const double ld64 = (double)((n0 + 1) / 2 * 2), ld32 = (double)((n0 + 3) / 4 * 4);
-    total += 8.0 * n0 + (double)n0 * (8.0 * ld64 + 4.0 * ld32);       // coarse index + dense inverses
+    // coarsest solve: block-CR operators (FP64 + FP32) and the dense inverse of what is left
+    const int p0 = chain.back();
+    const int nb = (int)(ne[d - 1] * p0 - 1), m = nb > 0 ? (int)(n0 / nb) : 1;
+    int k = 0;
+    if (desc->coarse_solver == 2)
+        k = std::min(desc->coarse_cr_levels > 0 ? desc->coarse_cr_levels : std::max(1, auto_cr_levels(nb, m)),
+                     max_cr_levels(nb));
+    else if (desc->coarse_solver == 0)
+        k = auto_cr_levels(nb, m);
+    const double ldm = (double)((m + 3) / 4 * 4);
+    for (int l = 0; l < k; ++l) {
+        const int a = nb >> l;
+        total += 12.0 * (2.0 * (a / 2) + 3.0 * ((a + 1) / 2)) * m * ldm;
+    }
+    const long long nr = (long long)(nb >> k) * m;
+    const double ld64 = (double)((nr + 1) / 2 * 2), ld32 = (double)((nr + 3) / 4 * 4);
+    total += 8.0 * n0 + (double)nr * (8.0 * ld64 + 4.0 * ld32);
     total += 8.0 * (11.0 * Nfine) + 8.0 * Nfine + 8.0 * std::max<double>(2 * kMaxReduceBlocks, E + 1) + 64.0;
     total += 4.0 * 2.0 * Nfine;                                          // r32, z32
     (void)Ncoarse;
@@ -1159,7 +1198,8 @@ glls_status glls_autotune(glls_problem* P, int* chosen, float* best_us) {
     }                                                                                                           \
     glls_status glls_coarse_solve_##SUF(glls_problem* P, const T* r, T* e, void* stream) {                      \
         if (!P || !r || !e) return fail(GLLS_ERR_INVALID, "null argument");                                    \
-        launch_coarse<T>(coarse_of<T>(P), levels_of<T>(P)[0].dev.N, r, e, (cudaStream_t)stream);                \
+        launch_coarse<T>(coarse_of<T>(P), levels_of<T>(P)[0].dev.N, r, e, levels_of<T>(P)[0].t1,               \
+                         (cudaStream_t)stream);                                                                        \
         CK(cudaGetLastError());                                                                                 \
         return GLLS_OK;                                                                                         \
     }                                                                                                           \

@@ -76,12 +76,24 @@ struct DevLevel {
     int lpb[3] = {4, 4, 4};   // line-solve tile (lines per CTA) per direction, set by the autotuner
 };
 
+// Exact coarsest solve: cr_levels levels of block cyclic reduction over the
+// blocks of the slowest grid axis (Thm. 3.8 with m > 1, Cor. 3.9), then the
+// dense inverse of the remaining system (cr_levels = 0: of the whole system).
+// Unknowns are numbered lexicographically, so block b (0-based) holds unknowns
+// b m .. b m + m - 1.  At level l (h = 2^l) the active blocks are
+// b = (t + 1) h - 1, t = 0 .. (nb >> l) - 1; even t are eliminated, odd t kept.
+constexpr int kMaxCrLevels = 16;
 template <typename T>
 struct DevCoarse {
-    long long n = 0;
-    long long ld = 0;                   // padded row length (multiple of 16 bytes)
+    long long n = 0;                    // interior unknowns
     const long long* index = nullptr;   // interior node of each unknown
-    const T* inv = nullptr;             // dense n x n inverse, row-major, leading dimension ld
+    long long nr = 0;                   // unknowns of the densely solved system
+    long long ld = 0;                   // padded row length of inv (multiple of 16 bytes)
+    const T* inv = nullptr;             // dense nr x nr inverse, row-major, leading dimension ld
+    int nb = 1, m = 0, ldm = 0;         // blocks, block size, padded row length of the m x m blocks
+    int cr_levels = 0;
+    const T* fh[kMaxCrLevels] = {};     // level l: [kept][2][m][ldm]: L_i A_{i-h}^-1, U_i A_{i+h}^-1
+    const T* agk[kMaxCrLevels] = {};    // level l: [elim][3][m][ldm]: A_j^-1, A_j^-1 L_j, A_j^-1 U_j
 };
 
 // Opt every kernel into up to 200 KB of dynamic shared memory (call once per
@@ -125,9 +137,10 @@ void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nou
                      const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear = nullptr);
 
 // e = A_0^-1 r on the interior of the coarsest level; e's boundary entries
-// are zeroed first unless e_boundary_zero.
+// are zeroed first unless e_boundary_zero.  w: scratch of C.n values (used
+// when C.cr_levels > 0; must not alias r or e).
 template <typename T>
-void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, cudaStream_t st,
+void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, T* w, cudaStream_t st,
                    bool e_boundary_zero = false);
 
 // ---- vector kernels -------------------------------------------------------

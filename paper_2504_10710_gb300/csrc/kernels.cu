@@ -11,7 +11,11 @@
 //                    solved in place by cyclic reduction written as the direct
 //                    multigrid of Algorithm 1 / Thm. 3.8 / Cor. 3.9.
 //   transfer_kernel  one axis of the tensor-product transfers P_l, R_l (Sec. 3.3).
-//   coarse_kernel    M_0^-1 = A_0^-1 as a dense matrix-vector product.
+//   coarse_kernel    dense inverse times vector: A_0^-1 r, or the inverse of the
+//                    system left after block cyclic reduction.
+//   bcr_*_kernel     block cyclic reduction of the coarsest level over grid
+//                    lines / planes (Thm. 3.8 with m > 1, Cor. 3.9): forward
+//                    elimination and back substitution, one launch per level.
 //   dots / fcg_*     FP64 outer-Krylov vector operations with scalars kept in
 //                    device memory, deterministic two-stage reductions.
 #include "device.cuh"
@@ -271,14 +275,32 @@ __global__ void transfer_kernel(DevBand<T> M, int a, int3 nin, int3 nout, const 
 // ---------------------------------------------------------------------------
 // coarsest solve: dense inverse times vector, one warp per row
 // ---------------------------------------------------------------------------
+// Position, in the block-ordered unknown numbering, of unknown t of the
+// system left after k block-CR levels (H = 2^k): block (t / m + 1) H - 1.
+__device__ __forceinline__ long long reduced_pos(long long t, int m, int H) {
+    const long long b = t / m;
+    return ((b + 1) * H - 1) * m + (t - b * m);
+}
+
+// Dense inverse times vector.  The input is gathered into shared memory:
+// src[src_index[pos(t)]] (nodal source) or src[pos(t)] (block-ordered
+// source); row i of the result goes to e[index[pos(i)]].
 template <typename T>
 __global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, const long long* __restrict__ index,
-                                                     const T* __restrict__ inv, const T* __restrict__ r,
+                                                     const T* __restrict__ inv, const T* __restrict__ src,
+                                                     const long long* __restrict__ src_index, int m, int H,
                                                      T* __restrict__ e) {
     grid_dep_sync();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* rs = reinterpret_cast<T*>(smem_raw);
-    for (long long t = threadIdx.x; t < ld; t += blockDim.x) rs[t] = t < n ? r[index[t]] : T(0);
+    for (long long t = threadIdx.x; t < ld; t += blockDim.x) {
+        T v = T(0);
+        if (t < n) {
+            const long long q = reduced_pos(t, m, H);
+            v = src_index ? src[src_index[q]] : src[q];
+        }
+        rs[t] = v;
+    }
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int wpb = blockDim.x / 32;
@@ -294,7 +316,99 @@ __global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, 
             for (int q = 0; q < V; ++q) s += vv[q] * rs[j * V + q];
         }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) e[index[row]] = s;
+        if (lane == 0) e[index[reduced_pos(row, m, H)]] = s;
+    }
+}
+
+// Block CR forward step at level l (h = 2^l), one CTA per (kept block, 32
+// rows): for kept block b = (2q + 2) h - 1,
+//   w_b = src_b - (L_b A_{b-h}^-1) w_{b-h} - (U_b A_{b+h}^-1) w_{b+h}
+// (the c = R (g - M x) step of Algorithm 1 with x = S^-1 g).  At level 0 the
+// source is the nodal right-hand side r gathered through index, and CTAs
+// past the kept blocks copy the eliminated blocks into w; deeper levels
+// update w in place (they read only blocks eliminated at this level).
+template <typename T>
+__global__ void __launch_bounds__(256) bcr_forward_kernel(const T* __restrict__ FH, int l, int nb, int m, int ldm,
+                                                          const long long* __restrict__ index,
+                                                          const T* __restrict__ r, T* w) {
+    grid_dep_sync();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xl = reinterpret_cast<T*>(smem_raw);
+    T* xr = xl + m;
+    const int h = 1 << l, nk = (nb >> l) / 2;
+    const int row0 = blockIdx.y * 32;
+    const bool lvl0 = l == 0;
+    const int q = blockIdx.x;
+    if (q >= nk) {                                   // level 0: copy eliminated block 2 (q - nk)
+        const long long b = 2LL * (q - nk);
+        for (int rr = threadIdx.x; rr < 32; rr += blockDim.x) {
+            const int row = row0 + rr;
+            if (row < m) w[b * m + row] = r[index[b * m + row]];
+        }
+        return;
+    }
+    const long long b = (2LL * q + 2) * h - 1, lb = b - h, rb = b + h;
+    const bool right = rb < nb;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        xl[c] = lvl0 ? r[index[lb * m + c]] : w[lb * m + c];
+        xr[c] = right ? (lvl0 ? r[index[rb * m + c]] : w[rb * m + c]) : T(0);
+    }
+    __syncthreads();
+    const T* F = FH + (size_t)q * 2 * m * ldm;
+    const T* Hm = F + (size_t)m * ldm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int rr = warp; rr < 32; rr += 8) {
+        const int row = row0 + rr;
+        if (row >= m) break;
+        T s = T(0);
+        for (int c = lane; c < m; c += 32) s += F[(size_t)row * ldm + c] * xl[c] + Hm[(size_t)row * ldm + c] * xr[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const long long o = b * m + row;
+            w[o] = (lvl0 ? r[index[o]] : w[o]) - s;
+        }
+    }
+}
+
+// Block CR back substitution at level l, one CTA per (eliminated block, 32
+// rows): for b = (2s + 1) h - 1,
+//   x_b = A_b^-1 w_b - (A_b^-1 L_b) x_{b-h} - (A_b^-1 U_b) x_{b+h}
+// (y = x + P e of Algorithm 1); the kept neighbours' values are already in
+// e (solved at deeper levels), read and written through index.
+template <typename T>
+__global__ void __launch_bounds__(256) bcr_backward_kernel(const T* __restrict__ AGK, int l, int nb, int m, int ldm,
+                                                           const long long* __restrict__ index,
+                                                           const T* __restrict__ w, T* e) {
+    grid_dep_sync();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xw = reinterpret_cast<T*>(smem_raw);
+    T* xl = xw + m;
+    T* xr = xl + m;
+    const int h = 1 << l;
+    const int row0 = blockIdx.y * 32;
+    const long long s_ = blockIdx.x;
+    const long long b = (2 * s_ + 1) * h - 1, lb = b - h, rb = b + h;
+    const bool left = lb >= 0, right = rb < nb;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        xw[c] = w[b * m + c];
+        xl[c] = left ? e[index[lb * m + c]] : T(0);
+        xr[c] = right ? e[index[rb * m + c]] : T(0);
+    }
+    __syncthreads();
+    const T* Ai = AGK + (size_t)s_ * 3 * m * ldm;
+    const T* G = Ai + (size_t)m * ldm;
+    const T* K = G + (size_t)m * ldm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int rr = warp; rr < 32; rr += 8) {
+        const int row = row0 + rr;
+        if (row >= m) break;
+        T v = T(0);
+        for (int c = lane; c < m; c += 32) {
+            const size_t o = (size_t)row * ldm + c;
+            v += Ai[o] * xw[c] - G[o] * xl[c] - K[o] * xr[c];
+        }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) e[index[b * m + row]] = v;
     }
 }
 
@@ -623,12 +737,28 @@ void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nou
 }
 
 template <typename T>
-void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, cudaStream_t st, bool e_boundary_zero) {
+void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, T* w, cudaStream_t st, bool e_boundary_zero) {
     if (!e_boundary_zero) cudaMemsetAsync(e, 0, sizeof(T) * N0, st);
+    const int k = C.cr_levels, m = C.m;
+    const unsigned rows = (unsigned)((m + 31) / 32);
+    for (int l = 0; l < k; ++l) {
+        const int a = C.nb >> l, nk = a / 2, ne = (a + 1) / 2;
+        const unsigned gx = (unsigned)(l == 0 ? nk + ne : nk);
+        launch_k(bcr_forward_kernel<T>, dim3(gx, rows), 256, 2 * sizeof(T) * (size_t)m, st, C.fh[l], l, C.nb, m,
+                 C.ldm, C.index, r, w);
+    }
     const size_t smem = sizeof(T) * (size_t)C.ld;
-    long long blocks = (C.n + 7) / 8;
+    long long blocks = (C.nr + 7) / 8;
     if (blocks > 2 * 152) blocks = 2 * 152;
-    launch_k(coarse_kernel<T>, (unsigned)blocks, 256, smem, st, C.n, C.ld, C.index, C.inv, r, e);
+    const T* src = k > 0 ? w : r;
+    const long long* src_index = k > 0 ? nullptr : C.index;
+    launch_k(coarse_kernel<T>, (unsigned)blocks, 256, smem, st, C.nr, C.ld, C.index, C.inv, src, src_index, m,
+             1 << k, e);
+    for (int l = k - 1; l >= 0; --l) {
+        const unsigned ne = (unsigned)(((C.nb >> l) + 1) / 2);
+        launch_k(bcr_backward_kernel<T>, dim3(ne, rows), 256, 3 * sizeof(T) * (size_t)m, st, C.agk[l], l, C.nb, m,
+                 C.ldm, C.index, (const T*)w, e);
+    }
 }
 
 template <typename Ti, typename To>
@@ -713,7 +843,9 @@ bool init_kernel_attributes() {
     const void* fns[] = {(const void*)apply_kernel<double, 2>, (const void*)apply_kernel<double, 3>,
                          (const void*)apply_kernel<float, 2>,  (const void*)apply_kernel<float, 3>,
                          (const void*)line_kernel<double>,     (const void*)line_kernel<float>,
-                         (const void*)coarse_kernel<double>,   (const void*)coarse_kernel<float>};
+                         (const void*)coarse_kernel<double>,   (const void*)coarse_kernel<float>,
+                         (const void*)bcr_forward_kernel<double>, (const void*)bcr_forward_kernel<float>,
+                         (const void*)bcr_backward_kernel<double>, (const void*)bcr_backward_kernel<float>};
     for (const void* f : fns)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess)
             return false;
@@ -733,8 +865,9 @@ template void launch_transfer<double>(const DevBand<double>&, int, const int*, c
                                       double*, bool, bool, cudaStream_t, double*);
 template void launch_transfer<float>(const DevBand<float>&, int, const int*, const int*, const float*, const float*,
                                      float*, bool, bool, cudaStream_t, float*);
-template void launch_coarse<double>(const DevCoarse<double>&, long long, const double*, double*, cudaStream_t, bool);
-template void launch_coarse<float>(const DevCoarse<float>&, long long, const float*, float*, cudaStream_t, bool);
+template void launch_coarse<double>(const DevCoarse<double>&, long long, const double*, double*, double*, cudaStream_t,
+                                    bool);
+template void launch_coarse<float>(const DevCoarse<float>&, long long, const float*, float*, float*, cudaStream_t, bool);
 template void launch_cast<double, float>(const double*, float*, long long, cudaStream_t);
 template void launch_cast<float, double>(const float*, double*, long long, cudaStream_t);
 template void launch_zero_boundary<double>(double*, const int*, int, cudaStream_t);

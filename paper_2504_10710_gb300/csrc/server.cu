@@ -25,11 +25,13 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 struct MeshKey {
-    int dim = 0, order = 0, smoother = 0, restriction = 0, nelem[3] = {1, 1, 1};
+    int dim = 0, order = 0, smoother = 0, restriction = 0, coarse_solver = 0, coarse_cr_levels = 0;
+    int nelem[3] = {1, 1, 1};
     size_t ncoords = 0;
     unsigned long long hash = 0;
     bool operator==(const MeshKey& o) const {
         return dim == o.dim && order == o.order && smoother == o.smoother && restriction == o.restriction &&
+               coarse_solver == o.coarse_solver && coarse_cr_levels == o.coarse_cr_levels &&
                nelem[0] == o.nelem[0] && nelem[1] == o.nelem[1] && nelem[2] == o.nelem[2] &&
                ncoords == o.ncoords && hash == o.hash;
     }
@@ -272,6 +274,8 @@ glls_status glls_submit(glls_server* S, const glls_mesh_desc* mesh, const double
     r->key.order = mesh->order;
     r->key.smoother = mesh->smoother;
     r->key.restriction = mesh->restriction;
+    r->key.coarse_solver = mesh->coarse_solver;
+    r->key.coarse_cr_levels = mesh->coarse_cr_levels;
     for (int a = 0; a < 3; ++a) r->key.nelem[a] = a < mesh->dim ? mesh->nelem[a] : 1;
     r->key.ncoords = r->coords.size();
     r->key.hash = fnv1a(r->coords.data(), sizeof(double) * r->coords.size());

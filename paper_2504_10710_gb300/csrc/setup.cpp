@@ -448,7 +448,168 @@ std::string build_levels(int dim, const int nelem[3], int p_fine, const double* 
 
 // Dense inverse of the interior block of A_0 (assembled from element
 // matrices), via a banded Cholesky factorisation and one solve per column.
-std::string build_coarse(const LevelHost& lv, CoarseHost& out) {
+// Inverse of an SPD matrix with half bandwidth bw (dense n x n row-major):
+// banded Cholesky A = L L^T, then L L^T x = e_c for every column c.
+std::string spd_band_inverse(const std::vector<double>& A, long long n, long long bw, std::vector<double>& inv) {
+    // banded Cholesky A = L L^T, L stored dense (lower band used)
+    std::vector<double> L((size_t)n * n, 0.0);
+    for (long long j = 0; j < n; ++j) {
+        long long k0 = std::max(0LL, j - bw);
+        double s = A[(size_t)j * n + j];
+        for (long long k = k0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        if (!(s > 0.0)) return "coarsest-level matrix is not positive definite";
+        double ljj = std::sqrt(s);
+        L[(size_t)j * n + j] = ljj;
+        for (long long i = j + 1; i <= std::min(n - 1, j + bw); ++i) {
+            double t = A[(size_t)i * n + j];
+            long long kk = std::max(k0, i - bw);
+            for (long long k = kk; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = t / ljj;
+        }
+    }
+    inv.assign((size_t)n * n, 0.0);
+    std::vector<double> y(n);
+    for (long long c = 0; c < n; ++c) {
+        // forward L y = e_c
+        std::fill(y.begin(), y.end(), 0.0);
+        for (long long i = c; i < n; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (long long k = std::max(c, i - bw); k < i; ++k) t -= L[(size_t)i * n + k] * y[k];
+            y[i] = t / L[(size_t)i * n + i];
+        }
+        // backward L^T x = y
+        for (long long i = n - 1; i >= 0; --i) {
+            double t = y[i];
+            for (long long k = i + 1; k <= std::min(n - 1, i + bw); ++k) t -= L[(size_t)k * n + i] * y[k];
+            y[i] = t / L[(size_t)i * n + i];
+        }
+        for (long long i = 0; i < n; ++i) inv[(size_t)i * n + c] = y[i];
+    }
+    return "";
+}
+
+namespace {
+
+using Mat = std::vector<double>;
+
+Mat matmul(const Mat& a, const Mat& b, int m) {
+    Mat c((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i)
+        for (int k = 0; k < m; ++k) {
+            const double aik = a[(size_t)i * m + k];
+            if (aik == 0.0) continue;
+            for (int j = 0; j < m; ++j) c[(size_t)i * m + j] += aik * b[(size_t)k * m + j];
+        }
+    return c;
+}
+
+void sub_into(Mat& a, const Mat& b) {
+    for (size_t i = 0; i < a.size(); ++i) a[i] -= b[i];
+}
+
+Mat negated(Mat a) {
+    for (double& v : a) v = -v;
+    return a;
+}
+
+}  // namespace
+
+int max_cr_levels(int nb) {
+    int k = 0;
+    while ((2 << k) <= nb) ++k;     // at least one block is left after k levels
+    return k;
+}
+
+// Depth of block CR before the dense solve that minimises a launch-plus-bytes
+// model of the GPU solve: each CR level costs a forward and a backward launch
+// (about 2 us each) and reads 2 m^2 values per kept block and 3 m^2 per
+// eliminated block; the dense solve reads (remaining unknowns)^2 values; FP32
+// bytes streamed at 5 TB/s.  0 means the dense inverse of the whole system.
+int auto_cr_levels(int nb, int m) {
+    const double mm = (double)m * m;
+    int best = 0;
+    double best_t = 2.0 + 4.0 * ((double)nb * m) * ((double)nb * m) / 5.0e6;
+    double level_bytes = 0.0;
+    for (int k = 1; k <= max_cr_levels(nb); ++k) {
+        const int a = nb >> (k - 1);                 // active blocks at level k - 1
+        level_bytes += 4.0 * mm * (2.0 * (a / 2) + 3.0 * ((a + 1) / 2));
+        const double nr = (double)(nb >> k) * m;
+        const double t = 2.0 * (2 * k + 1) + (level_bytes + 4.0 * nr * nr) / 5.0e6;
+        if (t < best_t) {
+            best_t = t;
+            best = k;
+        }
+    }
+    return best;
+}
+
+// Block cyclic reduction of the block-tridiagonal A (Def. 3.5 blocks of size
+// m, nb blocks) for k levels (Thm. 3.8 with m > 1, Prop. 3.7, Cor. 3.9), then
+// the dense inverse of the remaining coarse system.  At each level the odd
+// blocks (1-based) are eliminated: stored A_j^-1, A_j^-1 L_j, A_j^-1 U_j; the
+// even blocks are kept: stored L_i A_{i-1}^-1 and U_i A_{i+1}^-1, and their
+// coarse blocks follow Prop. 3.7.
+std::string build_block_cr(const std::vector<double>& A, long long n, int nb, int m, int k, CoarseHost& out) {
+    const Mat zero((size_t)m * m, 0.0);
+    auto block = [&](int bi, int bj) {
+        Mat B((size_t)m * m);
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < m; ++c) B[(size_t)r * m + c] = A[(size_t)((long long)bi * m + r) * n + (long long)bj * m + c];
+        return B;
+    };
+    std::vector<Mat> Ab(nb), Lb(nb), Ub(nb);
+    for (int i = 0; i < nb; ++i) {
+        Ab[i] = block(i, i);
+        Lb[i] = i > 0 ? block(i, i - 1) : zero;
+        Ub[i] = i + 1 < nb ? block(i, i + 1) : zero;
+    }
+    out.fh.assign(k, Mat());
+    out.agk.assign(k, Mat());
+    for (int l = 0; l < k; ++l) {
+        const int a = (int)Ab.size();
+        std::vector<Mat> Ainv(a);
+        for (int t = 0; t < a; t += 2) {             // eliminated (1-based odd)
+            std::string e = spd_band_inverse(Ab[t], m, m - 1, Ainv[t]);
+            if (!e.empty()) return e;
+            const Mat G = matmul(Ainv[t], Lb[t], m), K = matmul(Ainv[t], Ub[t], m);
+            out.agk[l].insert(out.agk[l].end(), Ainv[t].begin(), Ainv[t].end());
+            out.agk[l].insert(out.agk[l].end(), G.begin(), G.end());
+            out.agk[l].insert(out.agk[l].end(), K.begin(), K.end());
+        }
+        std::vector<Mat> A2, L2, U2;
+        for (int t = 1; t < a; t += 2) {             // kept (1-based even)
+            const bool right = t + 1 < a;
+            const Mat F = matmul(Lb[t], Ainv[t - 1], m);
+            const Mat H = right ? matmul(Ub[t], Ainv[t + 1], m) : zero;
+            out.fh[l].insert(out.fh[l].end(), F.begin(), F.end());
+            out.fh[l].insert(out.fh[l].end(), H.begin(), H.end());
+            Mat An = Ab[t];
+            sub_into(An, matmul(F, Ub[t - 1], m));
+            if (right) sub_into(An, matmul(H, Lb[t + 1], m));
+            A2.push_back(An);
+            L2.push_back(negated(matmul(F, Lb[t - 1], m)));
+            U2.push_back(right ? negated(matmul(H, Ub[t + 1], m)) : zero);
+        }
+        Ab.swap(A2);
+        Lb.swap(L2);
+        Ub.swap(U2);
+    }
+    const int a = (int)Ab.size();
+    const long long nr = (long long)a * m;
+    out.nr = nr;
+    std::vector<double> Ar((size_t)nr * nr, 0.0);
+    for (int t = 0; t < a; ++t)
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < m; ++c) {
+                const size_t row = (size_t)((long long)t * m + r) * nr;
+                Ar[row + (size_t)t * m + c] = Ab[t][(size_t)r * m + c];
+                if (t > 0) Ar[row + (size_t)(t - 1) * m + c] = Lb[t][(size_t)r * m + c];
+                if (t + 1 < a) Ar[row + (size_t)(t + 1) * m + c] = Ub[t][(size_t)r * m + c];
+            }
+    return spd_band_inverse(Ar, nr, std::min<long long>(nr - 1, 2LL * m - 1), out.inv);
+}
+
+std::string build_coarse(const LevelHost& lv, int coarse_solver, int cr_levels, CoarseHost& out) {
     const int d = lv.dim, p = lv.p, n1 = p + 1, nloc = lv.nloc;
     std::vector<long long> id(lv.N, -1);
     out.index.clear();
@@ -501,41 +662,20 @@ std::string build_coarse(const LevelHost& lv, CoarseHost& out) {
             }
         }
     }
-    // banded Cholesky A = L L^T, L stored dense (lower band used)
-    std::vector<double> L((size_t)n * n, 0.0);
-    for (long long j = 0; j < n; ++j) {
-        long long k0 = std::max(0LL, j - bw);
-        double s = A[(size_t)j * n + j];
-        for (long long k = k0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
-        if (!(s > 0.0)) return "coarsest-level matrix is not positive definite";
-        double ljj = std::sqrt(s);
-        L[(size_t)j * n + j] = ljj;
-        for (long long i = j + 1; i <= std::min(n - 1, j + bw); ++i) {
-            double t = A[(size_t)i * n + j];
-            long long kk = std::max(k0, i - bw);
-            for (long long k = kk; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
-            L[(size_t)i * n + j] = t / ljj;
-        }
+    // blocks: one per interior index of the slowest axis (grid lines in 2-D,
+    // planes in 3-D); the lexicographic numbering makes them contiguous
+    out.nb = lv.n[d - 1] - 2;
+    out.m = (int)(n / out.nb);
+    int k = 0;
+    if (coarse_solver == 2)
+        k = std::min(cr_levels > 0 ? cr_levels : std::max(1, auto_cr_levels(out.nb, out.m)), max_cr_levels(out.nb));
+    else if (coarse_solver == 0) k = auto_cr_levels(out.nb, out.m);
+    out.cr_levels = k;
+    if (k == 0) {       // dense A_0^-1
+        out.nr = n;
+        return spd_band_inverse(A, n, bw, out.inv);
     }
-    out.inv.assign((size_t)n * n, 0.0);
-    std::vector<double> y(n);
-    for (long long c = 0; c < n; ++c) {
-        // forward L y = e_c
-        std::fill(y.begin(), y.end(), 0.0);
-        for (long long i = c; i < n; ++i) {
-            double t = (i == c) ? 1.0 : 0.0;
-            for (long long k = std::max(c, i - bw); k < i; ++k) t -= L[(size_t)i * n + k] * y[k];
-            y[i] = t / L[(size_t)i * n + i];
-        }
-        // backward L^T x = y
-        for (long long i = n - 1; i >= 0; --i) {
-            double t = y[i];
-            for (long long k = i + 1; k <= std::min(n - 1, i + bw); ++k) t -= L[(size_t)k * n + i] * y[k];
-            y[i] = t / L[(size_t)i * n + i];
-        }
-        for (long long i = 0; i < n; ++i) out.inv[(size_t)i * n + c] = y[i];
-    }
-    return "";
+    return build_block_cr(A, n, out.nb, out.m, k, out);
 }
 
 }  // namespace glls

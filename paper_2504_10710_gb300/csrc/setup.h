@@ -33,10 +33,18 @@ struct LevelHost {
     Band1D R[3];                  // restriction  (this level -> level-1), per axis
 };
 
+// Exact solver of the coarsest level: k levels of block cyclic reduction over
+// the blocks of the slowest grid axis (k = 0: none), then the dense inverse of
+// the remaining system.
 struct CoarseHost {
     long long n = 0;                 // interior unknowns
     std::vector<long long> index;    // interior node index (level-0 grid) per unknown
-    std::vector<double> inv;         // dense A_0^-1, n x n row-major
+    int nb = 0, m = 0;               // blocks (slowest-axis interior indices) and block size
+    int cr_levels = 0;               // k
+    std::vector<std::vector<double>> fh;    // per level: [kept][2][m][m]  L_i A_{i-h}^-1, U_i A_{i+h}^-1
+    std::vector<std::vector<double>> agk;   // per level: [elim][3][m][m]  A_j^-1, A_j^-1 L_j, A_j^-1 U_j
+    long long nr = 0;                // unknowns of the densely solved system (n when k = 0)
+    std::vector<double> inv;         // its inverse, nr x nr row-major
 };
 
 std::vector<double> gll_nodes(int p, std::vector<double>* weights);
@@ -47,6 +55,11 @@ std::vector<int> order_chain(int p_fine, bool multi_element);
 // Builds all levels (index 0 = coarsest).  Returns "" on success or an error message.
 std::string build_levels(int dim, const int nelem[3], int p_fine, const double* coords,
                          int smoother, int restriction, std::vector<LevelHost>& levels);
-std::string build_coarse(const LevelHost& lv0, CoarseHost& out);
+// coarse_solver: 0 automatic (block-CR depth from a cost model, 0 levels =
+// dense), 1 dense A_0^-1, 2 block CR with cr_levels levels (clamped to what
+// the block count allows; 0 = the model's depth, at least one level).
+std::string build_coarse(const LevelHost& lv0, int coarse_solver, int cr_levels, CoarseHost& out);
+int max_cr_levels(int nb);
+int auto_cr_levels(int nb, int m);
 
 }  // namespace glls

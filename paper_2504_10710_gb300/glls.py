@@ -21,12 +21,13 @@ PREC_FP64, PREC_MIXED = 0, 1
 SMOOTHER_GLL, SMOOTHER_FEM = 0, 1
 RESTRICT_TRANSPOSE, RESTRICT_INTERP = 0, 1
 KRYLOV_FCG, KRYLOV_PCG, KRYLOV_GMRES = 0, 1, 2
+COARSE_AUTO, COARSE_DENSE, COARSE_BLOCK_CR = 0, 1, 2
 
 
 class MeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("nelem", C.c_int * 3), ("order", C.c_int),
                 ("coords", C.POINTER(C.c_double)), ("smoother", C.c_int), ("restriction", C.c_int),
-                ("device", C.c_int)]
+                ("device", C.c_int), ("coarse_solver", C.c_int), ("coarse_cr_levels", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -42,7 +43,8 @@ class Stats(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("dim", C.c_int), ("levels", C.c_int), ("order", C.c_int * 8), ("nodes", (C.c_int * 3) * 8),
-                ("ndof", C.c_longlong * 8), ("coarse_unknowns", C.c_longlong), ("device_bytes", C.c_size_t)]
+                ("ndof", C.c_longlong * 8), ("coarse_unknowns", C.c_longlong), ("device_bytes", C.c_size_t),
+                ("coarse_cr_levels", C.c_int), ("coarse_dense_unknowns", C.c_longlong)]
 
 
 class ServerInfo(C.Structure):
@@ -144,12 +146,10 @@ class Problem:
     """Owns a ``glls_problem``: mesh levels resident on the device."""
 
     def __init__(self, dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE,
-                 device=0):
-        coords = np.ascontiguousarray(coords, dtype=np.float64)
-        ne = (C.c_int * 3)(*(list(nelem) + [1] * (3 - len(nelem))))
+                 device=0, coarse_solver=COARSE_AUTO, coarse_cr_levels=0):
+        desc, coords = mesh_desc(dim, nelem, order, coords, smoother, restriction, device, coarse_solver,
+                                 coarse_cr_levels)
         self._coords = coords
-        desc = MeshDesc(dim, ne, order, coords.ctypes.data_as(C.POINTER(C.c_double)), smoother, restriction,
-                        device)
         h = C.c_void_p()
         _check(lib().glls_problem_create(C.byref(desc), C.byref(h)))
         self.h = h
@@ -302,15 +302,16 @@ def solve_multi(problem, F, g, o: SolveOpts, clones=None):
     return U, stats, probs[1:]
 
 
-def mesh_desc(dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0):
+def mesh_desc(dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0,
+              coarse_solver=COARSE_AUTO, coarse_cr_levels=0):
     coords = np.ascontiguousarray(coords, dtype=np.float64)
     ne = (C.c_int * 3)(*(list(nelem) + [1] * (3 - len(nelem))))
     return MeshDesc(dim, ne, order, coords.ctypes.data_as(C.POINTER(C.c_double)), smoother, restriction,
-                    device), coords
+                    device, coarse_solver, coarse_cr_levels), coords
 
 
-def estimate_bytes(dim, nelem, order, coords):
-    desc, _keep = mesh_desc(dim, nelem, order, coords)
+def estimate_bytes(dim, nelem, order, coords, coarse_solver=COARSE_AUTO, coarse_cr_levels=0):
+    desc, _keep = mesh_desc(dim, nelem, order, coords, coarse_solver=coarse_solver, coarse_cr_levels=coarse_cr_levels)
     out = C.c_size_t()
     _check(lib().glls_estimate_bytes(C.byref(desc), C.byref(out)))
     return out.value
@@ -364,9 +365,11 @@ class Server:
             pass
 
 
-def problem_for(workload, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0):
+def problem_for(workload, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0,
+                coarse_solver=COARSE_AUTO, coarse_cr_levels=0):
     """Problem of a workload description, with nodes placed at the library's
     own GLL points."""
     xi, _ = gll(workload.order)
     coords = workload.coords(xi)
-    return Problem(workload.dim, workload.nelem, workload.order, coords, smoother, restriction, device), coords
+    return Problem(workload.dim, workload.nelem, workload.order, coords, smoother, restriction, device,
+                   coarse_solver, coarse_cr_levels), coords
