@@ -166,6 +166,21 @@ glls_status alloc_instance(glls_problem* P) {
     return GLLS_OK;
 }
 
+// Largest input window (max(start) + width - min(start)) of `tile`
+// consecutive rows starting at multiples of `tile`.
+int band_span(const Band1D& b, int tile) {
+    int best = 0;
+    for (int r0 = 0; r0 < b.rows; r0 += tile) {
+        int lo = b.start[r0], hi = b.start[r0] + b.width;
+        for (int r = r0; r < std::min(b.rows, r0 + tile); ++r) {
+            lo = std::min(lo, b.start[r]);
+            hi = std::max(hi, b.start[r] + b.width);
+        }
+        best = std::max(best, hi - lo);
+    }
+    return best;
+}
+
 template <typename T>
 glls_status upload_levels(glls_problem* P, const std::vector<LevelHost>& H, std::vector<LevelStore<T>>& out) {
     out.assign(H.size(), LevelStore<T>());
@@ -209,6 +224,8 @@ glls_status upload_levels(glls_problem* P, const std::vector<LevelHost>& H, std:
                     ds[k]->rows = bs[k]->rows;
                     ds[k]->cols = bs[k]->cols;
                     ds[k]->width = bs[k]->width;
+                    ds[k]->span32 = band_span(*bs[k], 32);
+                    ds[k]->span8 = band_span(*bs[k], 8);
                     CK(P->upload(&ds[k]->start, bs[k]->start));
                     CK(P->upload(&ds[k]->coef, bs[k]->coef));
                 }
@@ -270,6 +287,13 @@ void restrict_residual(glls_problem* P, int l, const T* r, const T* y, T* rc, cu
     auto& Ls = levels_of<T>(P);
     const DevLevel<T>& F = Ls[l].dev;
     const DevLevel<T>& C = Ls[l - 1].dev;
+    // axes 0 and 1 in one fused launch (then axis 2 in 3-D)
+    const int mid[3] = {C.n[0], C.n[1], F.n[2]};
+    const bool only2 = F.dim == 2;
+    if (launch_transfer2<T>(F.R[0], F.R[1], F.n, mid, r, y, only2 ? rc : Ls[l].t1, false, only2, st)) {
+        if (!only2) launch_transfer<T>(F.R[2], 2, mid, C.n, Ls[l].t1, nullptr, rc, false, true, st);
+        return;
+    }
     int cur[3] = {F.n[0], F.n[1], F.n[2]};
     const T* in = r;
     const T* in2 = y;
@@ -291,6 +315,13 @@ void prolong_add(glls_problem* P, int l, const T* e, T* x, cudaStream_t st, T* c
     auto& Ls = levels_of<T>(P);
     const DevLevel<T>& F = Ls[l].dev;
     const DevLevel<T>& C = Ls[l - 1].dev;
+    const int mid[3] = {F.n[0], F.n[1], C.n[2]};
+    const bool only2 = F.dim == 2;
+    if (launch_transfer2<T>(F.P[0], F.P[1], C.n, mid, e, nullptr, only2 ? x : Ls[l].t1, only2, false, st,
+                            only2 ? clear : nullptr)) {
+        if (!only2) launch_transfer<T>(F.P[2], 2, mid, F.n, Ls[l].t1, nullptr, x, true, false, st, clear);
+        return;
+    }
     int cur[3] = {C.n[0], C.n[1], C.n[2]};
     const T* in = e;
     for (int a = 0; a < F.dim; ++a) {

@@ -51,6 +51,9 @@ struct DevBand {
     int rows = 0, cols = 0, width = 0;
     const int* start = nullptr;
     const T* coef = nullptr;
+    // largest input span (max start + width - min start) of 32 / 8
+    // consecutive rows: the shared-memory window of a fused transfer tile
+    int span32 = 0, span8 = 0;
 };
 
 template <typename T>
@@ -135,6 +138,16 @@ void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const 
 template <typename T>
 void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nout[3], const T* in,
                      const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear = nullptr);
+
+// The first two tensor-product factors of a transfer in one launch: out =
+// M1 (M0 (in - in2)) along axes 0 and 1, for every index of axis 2 (nin and
+// nout differ along axes 0 and 1 only).  add / mask / clear as for
+// launch_transfer (mask only when these are the last factors, i.e. in 2-D).
+// Returns false when the tile window does not fit in shared memory (the
+// caller then runs the two passes separately).
+template <typename T>
+bool launch_transfer2(const DevBand<T>& M0, const DevBand<T>& M1, const int nin[3], const int nout[3], const T* in,
+                      const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear = nullptr);
 
 // e = A_0^-1 r on the interior of the coarsest level; e's boundary entries
 // are zeroed first unless e_boundary_zero.  w: scratch of C.n values (used

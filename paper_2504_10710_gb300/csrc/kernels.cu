@@ -21,6 +21,7 @@
 #include "device.cuh"
 #include "reduce.cuh"
 
+#include <climits>
 #include <cstdio>
 #include <cstdlib>
 #include <type_traits>
@@ -306,15 +307,35 @@ __global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, 
     const int wpb = blockDim.x / 32;
     constexpr int V = 16 / sizeof(T);   // elements per 16-byte vector
     using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    // each lane keeps U row chunks in flight (independent loads and partial
+    // sums), so a row costs about one memory latency instead of one per chunk
+    constexpr int U = 8;
+    const long long nvec = ld / V;
     for (long long row = (long long)blockIdx.x * wpb + warp; row < n; row += (long long)gridDim.x * wpb) {
         const Vec* a = reinterpret_cast<const Vec*>(inv + row * ld);
-        T s = T(0);
-        for (long long j = lane; j < ld / V; j += 32) {
-            const Vec v = a[j];
-            const T* vv = reinterpret_cast<const T*>(&v);
+        T part[U];
 #pragma unroll
-            for (int q = 0; q < V; ++q) s += vv[q] * rs[j * V + q];
+        for (int u = 0; u < U; ++u) part[u] = T(0);
+        for (long long j0 = lane; j0 < nvec; j0 += 32 * U) {
+            Vec v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long j = j0 + 32LL * u;
+                if (j < nvec) v[u] = __ldg(a + j);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long j = j0 + 32LL * u;
+                if (j < nvec) {
+                    const T* vv = reinterpret_cast<const T*>(&v[u]);
+#pragma unroll
+                    for (int q = 0; q < V; ++q) part[u] += vv[q] * rs[j * V + q];
+                }
+            }
         }
+        T s = T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) s += part[u];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) e[index[reduced_pos(row, m, H)]] = s;
     }
@@ -409,6 +430,116 @@ __global__ void __launch_bounds__(256) bcr_backward_kernel(const T* __restrict__
         }
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) e[index[b * m + row]] = v;
+    }
+}
+
+// Fused two-factor transfer: a CTA of 32 x 8 threads computes a 32 x TY tile
+// of outputs (I, J) of one axis-2 plane.  Its input window (rows of axis 1 x
+// columns of axis 0 that the tile's bands touch) is staged in shared memory
+// as in - in2, contracted along axis 0 into t (window rows x 32), then along
+// axis 1:  out(I, J) = sum_k M1(J, k) sum_q M0(I, q) in(q, s1(J) + k).
+// Band rows are held in registers (width bucket WB >= both widths).
+template <typename T, int WB, int TY>
+__global__ void __launch_bounds__(256) transfer2_kernel(DevBand<T> M0, DevBand<T> M1, int3 nin, int3 nout,
+                                                        const T* __restrict__ in, const T* __restrict__ in2,
+                                                        T* __restrict__ out, int add, int mask, T* __restrict__ clear) {
+    grid_dep_sync();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int win[4];                       // column lo, column count, row lo, row count
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int I0 = blockIdx.x * 32, J0 = blockIdx.y * TY, z = blockIdx.z;
+    const int W0 = M0.width, W1 = M1.width;
+    const int I = I0 + tx;
+    const bool okI = I < nout.x;
+    const int s0 = okI ? M0.start[I] : 0;
+    T c0[WB];
+#pragma unroll
+    for (int k = 0; k < WB; ++k) c0[k] = okI && k < W0 ? M0.coef[(size_t)I * W0 + k] : T(0);
+    if (ty == 0) {
+        int lo = okI ? s0 : INT_MAX, hi = okI ? s0 + W0 : INT_MIN;
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        const int J = J0 + tx;
+        const bool okJ = tx < TY && J < nout.y;
+        const int s1 = okJ ? M1.start[J] : 0;
+        int rlo = okJ ? s1 : INT_MAX, rhi = okJ ? s1 + W1 : INT_MIN;
+        for (int o = 16; o > 0; o >>= 1) {
+            rlo = min(rlo, __shfl_xor_sync(0xffffffffu, rlo, o));
+            rhi = max(rhi, __shfl_xor_sync(0xffffffffu, rhi, o));
+        }
+        if (tx == 0) {
+            win[0] = lo;
+            win[1] = hi - lo;
+            win[2] = rlo;
+            win[3] = rhi - rlo;
+        }
+    }
+    __syncthreads();
+    const int clo = win[0], ncol = win[1], rlo = win[2], nrow = win[3];
+    T* sin = reinterpret_cast<T*>(smem_raw);      // nrow x ncol
+    T* st = sin + (size_t)M1.span8 * M0.span32;   // nrow x 32
+    const size_t pin = (size_t)nin.x * nin.y, pout = (size_t)nout.x * nout.y;
+    const T* inz = in + z * pin;
+    const T* in2z = in2 ? in2 + z * pin : nullptr;
+    // staged in rounds of U loads per thread, all issued before any is used
+    constexpr int U = 4;
+    const int total = nrow * ncol;
+    for (int base = threadIdx.x; base < total; base += 256 * U) {
+        T a[U], b[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + 256 * u;
+            a[u] = T(0);
+            b[u] = T(0);
+            if (idx < total) {
+                const int r = idx / ncol, c = idx - r * ncol;
+                const size_t g = (size_t)(rlo + r) * nin.x + clo + c;
+                a[u] = inz[g];
+                if (in2z) b[u] = in2z[g];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + 256 * u;
+            if (idx < total) sin[idx] = a[u] - b[u];
+        }
+    }
+    __syncthreads();
+    // lanes past the last output column read column 0 of the window (their
+    // coefficients are zero), never outside it
+    const int coff = okI ? s0 - clo : 0;
+    for (int r = ty; r < nrow; r += 8) {
+        const T* row = sin + (size_t)r * ncol + coff;
+        T v = T(0);
+#pragma unroll
+        for (int k = 0; k < WB; ++k)
+            if (k < W0) v += c0[k] * row[k];
+        st[r * 32 + tx] = v;
+    }
+    __syncthreads();
+    if (!okI) return;
+    for (int jj = ty; jj < TY; jj += 8) {
+        const int J = J0 + jj;
+        if (J >= nout.y) break;
+        const size_t o = z * pout + (size_t)J * nout.x + I;
+        if (clear) clear[o] = T(0);
+        if (mask && (I == 0 || I == nout.x - 1 || J == 0 || J == nout.y - 1)) {
+            if (!add) out[o] = T(0);
+            continue;
+        }
+        const int s1 = M1.start[J];
+        const T* c1 = M1.coef + (size_t)J * W1;
+        const T* col = st + (s1 - rlo) * 32 + tx;
+        T cv[WB];
+#pragma unroll
+        for (int k = 0; k < WB; ++k) cv[k] = k < W1 ? c1[k] : T(0);
+        T v = T(0);
+#pragma unroll
+        for (int k = 0; k < WB; ++k)
+            if (k < W1) v += cv[k] * col[k * 32];
+        out[o] = add ? out[o] + v : v;
     }
 }
 
@@ -737,6 +868,23 @@ void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nou
 }
 
 template <typename T>
+bool launch_transfer2(const DevBand<T>& M0, const DevBand<T>& M1, const int nin[3], const int nout[3], const T* in,
+                      const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear) {
+    constexpr int TY = 8;
+    const size_t smem = sizeof(T) * (size_t)M1.span8 * (M0.span32 + 32);
+    const int W = M0.width > M1.width ? M0.width : M1.width;
+    if (M0.span32 <= 0 || M1.span8 <= 0 || smem > kMaxDynSmem || W > 32) return false;
+    const dim3 grid((unsigned)((nout[0] + 31) / 32), (unsigned)((nout[1] + TY - 1) / TY), (unsigned)nout[2]);
+    const int3 ni = make_int3(nin[0], nin[1], nin[2]), no = make_int3(nout[0], nout[1], nout[2]);
+    const int ad = add ? 1 : 0, mk = mask ? 1 : 0;
+    if (W <= 4) launch_k(transfer2_kernel<T, 4, TY>, grid, 256, smem, st, M0, M1, ni, no, in, in2, out, ad, mk, clear);
+    else if (W <= 8) launch_k(transfer2_kernel<T, 8, TY>, grid, 256, smem, st, M0, M1, ni, no, in, in2, out, ad, mk, clear);
+    else if (W <= 16) launch_k(transfer2_kernel<T, 16, TY>, grid, 256, smem, st, M0, M1, ni, no, in, in2, out, ad, mk, clear);
+    else launch_k(transfer2_kernel<T, 32, TY>, grid, 256, smem, st, M0, M1, ni, no, in, in2, out, ad, mk, clear);
+    return true;
+}
+
+template <typename T>
 void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, T* w, cudaStream_t st, bool e_boundary_zero) {
     if (!e_boundary_zero) cudaMemsetAsync(e, 0, sizeof(T) * N0, st);
     const int k = C.cr_levels, m = C.m;
@@ -845,7 +993,11 @@ bool init_kernel_attributes() {
                          (const void*)line_kernel<double>,     (const void*)line_kernel<float>,
                          (const void*)coarse_kernel<double>,   (const void*)coarse_kernel<float>,
                          (const void*)bcr_forward_kernel<double>, (const void*)bcr_forward_kernel<float>,
-                         (const void*)bcr_backward_kernel<double>, (const void*)bcr_backward_kernel<float>};
+                         (const void*)bcr_backward_kernel<double>, (const void*)bcr_backward_kernel<float>,
+                         (const void*)transfer2_kernel<double, 4, 8>, (const void*)transfer2_kernel<float, 4, 8>,
+                         (const void*)transfer2_kernel<double, 8, 8>, (const void*)transfer2_kernel<float, 8, 8>,
+                         (const void*)transfer2_kernel<double, 16, 8>, (const void*)transfer2_kernel<float, 16, 8>,
+                         (const void*)transfer2_kernel<double, 32, 8>, (const void*)transfer2_kernel<float, 32, 8>};
     for (const void* f : fns)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess)
             return false;
@@ -868,6 +1020,10 @@ template void launch_transfer<float>(const DevBand<float>&, int, const int*, con
 template void launch_coarse<double>(const DevCoarse<double>&, long long, const double*, double*, double*, cudaStream_t,
                                     bool);
 template void launch_coarse<float>(const DevCoarse<float>&, long long, const float*, float*, float*, cudaStream_t, bool);
+template bool launch_transfer2<double>(const DevBand<double>&, const DevBand<double>&, const int*, const int*,
+                                       const double*, const double*, double*, bool, bool, cudaStream_t, double*);
+template bool launch_transfer2<float>(const DevBand<float>&, const DevBand<float>&, const int*, const int*,
+                                      const float*, const float*, float*, bool, bool, cudaStream_t, float*);
 template void launch_cast<double, float>(const double*, float*, long long, cudaStream_t);
 template void launch_cast<float, double>(const float*, double*, long long, cudaStream_t);
 template void launch_zero_boundary<double>(double*, const int*, int, cudaStream_t);
