@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--roofline-only", action="store_true",
+                    help="only the kernel roofline measurements (used for ncu captures of single kernels)")
+    ap.add_argument("--roofline-3d", action="store_true",
+                    help="only the 3-D fine-level FP32 kernel measurements (small ncu captures)")
     ap.add_argument("--graph", type=int, default=2, choices=[0, 1, 2],
                     help="solve launch mode: 2 = one graph with a device-side loop (default), 1 = one graph "
                          "per iteration (profilers can see its kernels), 0 = plain stream launches")
@@ -134,6 +138,10 @@ def run_ours(args, rank, world):
     prob.set_rhs(f_d, stream)
     prob.set_dirichlet(g_d, stream)
     tiles = prob.autotune()          # line-solve tiles per level / precision / direction (set-up, untimed)
+    if args.roofline_only:
+        print(json.dumps({"roofline": kernel_roofline(prob, glls, torch),
+                          "roofline_hbm": smoother_rooflines(prob, glls, torch, inputs, flush)}))
+        sys.exit(0)
     kernels = [0]
 
     def timed(precision, steps, warmup, clocks=None):
@@ -193,9 +201,10 @@ def run_ours(args, rank, world):
     e2e_s = float(np.mean(e2e))
     lat = np.array(e2e) * 1e3
 
-    # dominant kernel: the fine-level FP32 line-smoothing step (apply + CR
-    # line solve), timed alone with CUDA events over repeated launches
-    roof = kernel_roofline(prob, glls, torch, stream, N)
+    # the top kernel of the ncu launch list (FP64 apply), and the FP32
+    # smoother / operator kernels against HBM (bench workload and 3-D)
+    roof = kernel_roofline(prob, glls, torch)
+    roof_hbm = smoother_rooflines(prob, glls, torch, inputs, flush)
     serving = serving_run(glls, inputs) if not args.no_serving else None
 
     # whole-job throughput: all ranks' DOF over the slowest rank's time
@@ -216,6 +225,7 @@ def run_ours(args, rank, world):
                        "what": "end to end through glls_set_rhs/set_dirichlet/solve with host buffers"},
         "clocks": clk,
         "roofline": roof,
+        "roofline_hbm": roof_hbm,
         "gpu_launches": int(launches),
         "line_tiles": {f"l{l}_{pn}_ax{a}": c for (l, pn, a), (c, _us) in sorted(tiles.items()) if pn == "f32"},
         "serving": serving,
@@ -223,51 +233,157 @@ def run_ours(args, rank, world):
     return res, (u_mixed, u_fp64, wl)
 
 
-def kernel_roofline(prob, glls, torch, stream, N):
-    peaks = {}
+FP64_PEAK_GFLOPS = 1250.0     # nominal GB300 FP64 rate (no measured FP64 peak is available)
+
+
+def _peaks():
     try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "MEASURED_PEAKS.json hbm_gbs (of measured)"
     except (OSError, ValueError):
-        pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    L = prob.levels - 1
-    shape = prob.level_shape(L)
-    x = torch.zeros(N, dtype=torch.float32, device="cuda")
-    r = torch.randn(shape, dtype=torch.float32, device="cuda")
-    r[0, :] = 0
-    r[-1, :] = 0
-    r[:, 0] = 0
-    r[:, -1] = 0
-    r = r.reshape(-1).contiguous()
+        return {"hbm_gbs": 6800.0}, "fallback 6800 GB/s (of fallback)"
+
+
+def _traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary, or None when the kernel's source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        f = ln.split()
+        if len(f) == 5 and not ln.startswith("#") and f[0] == kernel and f[1] == workload:
+            src = os.path.join(ROOT, "paper_2504_10710_gb300", "csrc", f[3])
+            try:
+                sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+            except OSError:
+                return None
+            return float(f[2]) if sha == f[4] else None
+    return None
+
+
+def _time_graph(torch, fn, reps=50):
+    """Average time of fn(stream) replayed `reps` times from one CUDA graph
+    (as inside a solve: data stays in L2 between launches)."""
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         for _ in range(3):
-            prob.smooth(L, 0, 0.5, r, x, s)
+            fn(s)
     torch.cuda.synchronize()
-    reps = 50
-    g = torch.cuda.CUDAGraph()          # the step as the solve runs it: inside a graph
+    g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         for _ in range(reps):
-            prob.smooth(L, 0, 0.5, r, x, s)
+            fn(s)
     g.replay()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    g.replay()
-    b.record()
+    with torch.cuda.stream(s):          # replay() launches on the current stream
+        a.record()
+        g.replay()
+        b.record()
     b.synchronize()
-    ms = a.elapsed_time(b) / reps
-    # algorithmic bytes of one fine-level FP32 smoothing step (apply + line solve):
-    # apply reads x (4N) and G (3 * E * 81 * 4), writes y (4N); line solve reads
-    # r, y, diag, off (16N), reads and writes x (8N)
-    E = 64 * 64
-    bytes_alg = 4 * N + 3 * E * 81 * 4 + 4 * N + 16 * N + 8 * N
-    ach = bytes_alg / (ms / 1e3) / 1e9
-    return {"bound": "hbm", "kernel": "fine-level FP32 smoothing step (apply_kernel + line_kernel)",
-            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-            "ms_per_launch": ms, "algorithmic_bytes": bytes_alg,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s",
-            "note": "working set (~12 MB) is L2-resident; 50 launches replayed from a CUDA graph, CUDA events"}
+    return a.elapsed_time(b) / reps
+
+
+def _time_cold(torch, fn, flush, reps=10):
+    """Average time of single launches of fn(stream), L2 flushed before each
+    (data comes from HBM), CUDA events on the launching stream."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            fn(s)
+    tot = 0.0
+    for _ in range(reps):
+        with torch.cuda.stream(s):
+            # a read-only pass over a buffer twice the L2 evicts the kernel's
+            # data without leaving dirty lines to write back during the launch
+            flush.sum()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn(s)
+        b.record(s)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def _interior_random(torch, shape, dtype):
+    x = torch.randn(shape, dtype=dtype, device="cuda")
+    for ax in range(len(shape)):
+        x.narrow(ax, 0, 1).zero_()
+        x.narrow(ax, shape[ax] - 1, 1).zero_()
+    return x.reshape(-1).contiguous()
+
+
+def kernel_roofline(prob, glls, torch):
+    """The bench workload's top kernel in the ncu launch list: the FP64 fine-
+    level stiffness apply of the outer iteration, FP64-ALU bound.  FLOPs per
+    launch from the sum-factorised algorithm: per element 4 (p+1)^3 FMA for
+    the four 1-D contraction sweeps and 4 (p+1)^2 for the geometric factors,
+    2 FLOP per FMA."""
+    L = prob.levels - 1
+    shape = prob.level_shape(L)
+    p, E = 8, 64 * 64
+    x = _interior_random(torch, shape, torch.float64)
+    y = torch.zeros_like(x)
+    ms = _time_graph(torch, lambda s: prob.apply(L, x, y, s))
+    flops = 2.0 * E * (4 * (p + 1) ** 3 + 4 * (p + 1) ** 2)
+    ach = flops / (ms / 1e3) / 1e9
+    return {"bound": "alu", "kernel": "apply_p_kernel<double, 2, 8> (fine-level FP64 stiffness apply)",
+            "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
+            "traffic": _traffic("apply_p_kernel<double,2,8>", "terrain2d_64x64_p8"),
+            "ms_per_launch": ms, "algorithmic_flops": flops,
+            "peak_source": "nominal FP64 rate of the recipe (1.25 TFLOP/s; none measured)",
+            "note": "FMA counted as 2 FLOP; 50 launches replayed from a CUDA graph, CUDA events"}
+
+
+def smoother_rooflines(prob, glls, torch, inputs, flush):
+    """FP32 smoother and operator kernels against HBM: the bench workload's
+    fine level (L2-resident between launches, as inside a solve) and the 3-D
+    16^3 p = 7 fine level (1.44M nodes; L2 flushed before every launch).
+    Algorithmic bytes per launch: apply x + G + y (4 + 4 B per node plus
+    ncomp (p+1)^d 4 B per element); line solve (B^-1 g) band 8 B + g + x
+    4 B each per node; smoothing step (apply + damped line update, the K2
+    step of the scope table) x, r read, x written, band and G."""
+    peaks, src = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = []
+
+    def entry(kernel, work, ms, byts, cold, tkey):
+        ach = byts / (ms / 1e3) / 1e9
+        out.append({"kernel": kernel, "workload": work, "ms_per_launch": ms, "algorithmic_bytes": byts,
+                    "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": _traffic(tkey, work) if tkey else None,
+                    "l2": "flushed before each launch" if cold else "resident (graph replay)"})
+
+    cases = [("terrain2d_64x64_p8", prob, False)] if prob is not None else []
+    wl3 = inputs.terrain3d()
+    p3, _ = glls.problem_for(wl3)
+    cases.append(("terrain3d_16x16x16_p7", p3, True))
+    for work, pb, cold in cases:
+        L = pb.levels - 1
+        shape = pb.level_shape(L)
+        N = int(np.prod(shape))
+        d = len(shape)
+        p = pb.info.order[L]
+        E = int(np.prod([(n - 1) // p for n in shape]))
+        G = (3 if d == 2 else 6) * E * (p + 1) ** d * 4
+        x = _interior_random(torch, shape, torch.float32)
+        y = torch.zeros_like(x)
+        r = _interior_random(torch, shape, torch.float32)
+        tm = (lambda fn: _time_cold(torch, fn, flush)) if cold else (lambda fn: _time_graph(torch, fn))
+        entry(f"apply_p_kernel<float, {d}, {p}>", work, tm(lambda s: pb.apply(L, x, y, s)), 8 * N + G, cold,
+              f"apply_p_kernel<float,{d},{p}>")
+        for ax in range(d):
+            entry(f"line_warp_kernel<float> B^-1 g, axis {ax}", work, tm(lambda s: pb.line_solve(L, ax, r, x, s)),
+                  16 * N, cold, f"line_warp_kernel<float>_ax{ax}")
+            entry(f"smoothing step (apply + line_warp_kernel MODE 1), axis {ax}", work,
+                  tm(lambda s: pb.smooth(L, ax, 0.5, r, x, s)), 20 * N + G, cold, None)
+        if pb is not prob:
+            pb.close()
+    return {"peak_source": src, "kernels": out}
 
 
 def serving_run(glls, inputs, nreq=120, rate=200.0, seed=5):
@@ -341,27 +457,51 @@ def main():
         from paper_2504_10710_gb300 import inputs
         wl = inputs.terrain2d()
         from oracle import solve as osolve
+        from oracle.discretize import lift
         fine, h = osolve.build(wl, restriction="transpose")
+        # iterations of a full solve (untimed), then one bounded sample per
+        # step: one outer FCG iteration (gamma-cycle, FP64 apply, dots, updates)
+        its_full = osolve.solve(wl, gamma=GAMMA, alpha=ALPHA, tol=1e-10, maxit=200, hierarchy=h).iterations[0]
+        f0, _v = lift(fine, wl.sample_rhs(fine.coords)[0], wl.sample_dirichlet(fine.coords))
+        r = f0.copy()
+        z = h.precondition(r, GAMMA, ALPHA, 1)
+        pdir = z.copy()
+        rz = float(np.vdot(r, z))
         times = []
-        its = []
         for k in range(args.warmup + args.steps):
             t0 = time.perf_counter()
-            r = osolve.solve(wl, gamma=GAMMA, alpha=ALPHA, tol=1e-10, maxit=200, hierarchy=h)
+            q = fine.apply(pdir)
+            alpha = rz / float(np.vdot(pdir, q))
+            r_new = r - alpha * q
+            z_new = h.precondition(r_new, GAMMA, ALPHA, 1)
+            rz_new = float(np.vdot(r_new, z_new))
+            beta = (rz_new - float(np.vdot(r, z_new))) / rz
+            pdir = z_new + beta * pdir
+            r, rz = r_new, rz_new
             if k >= args.warmup:
                 times.append(time.perf_counter() - t0)
-                its.append(r.iterations[0])
-        ms = 1e3 * float(np.mean(times))
-        val = fine.N / (ms / 1e3)
+        step_s = float(np.mean(times))
+        val = fine.N / (its_full * step_s)
+        sample = (f"one outer FCG iteration of the FP64 oracle per step (gamma-cycle + FP64 apply + dots); "
+                  f"value = DOF / ({its_full} iterations x {1e3 * step_s:.0f} ms mean step)")
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": val, "unit": "DOF/s", "n_gpus": 0, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": {"workload": WORKLOAD, "dof": fine.N, "gamma": GAMMA, "alpha": ALPHA, "tol": 1e-10},
-            "iterations": int(np.median(its)),
-            "cpu_baseline": {"value": val, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-                             "sample": "one full FP64 oracle solve of the workload per step"},
+            "iterations": int(its_full),
+            "cpu_baseline": {"value": val, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
+        return
+    if args.roofline_3d:
+        import torch
+
+        import __graft_entry__
+        from paper_2504_10710_gb300 import glls, inputs
+        __graft_entry__.build()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps({"roofline_hbm": smoother_rooflines(None, glls, torch, inputs, flush)}))
         return
     res, (u_mixed, u_fp64, wl) = run_ours(args, rank, world)
     if rank == 0:
