@@ -153,7 +153,7 @@ glls_status alloc_instance(glls_problem* P) {
         CK(cudaMemset(*vp, 0, sizeof(double) * N));
     }
     CK(P->alloc(&P->S, S_COUNT));
-    CK(P->alloc(&P->part, std::max<long long>(2 * kMaxReduceBlocks, P->L64.back().dev.E + 1)));
+    CK(P->alloc(&P->part, std::max<long long>(2 * kMaxReduceBlocks, 3 * kDotBlocks + P->L64.back().dev.E + 1)));
     CK(P->alloc(&P->ticket, 1));
     CK(cudaMemset(P->ticket, 0, sizeof(unsigned)));
     CK(P->alloc(&P->r32, N));
@@ -398,20 +398,30 @@ glls_status check_opts(const glls_solve_opts* o) {
 
 // Body of one outer iteration (4 launches besides the gamma-cycle):
 //   z = M r                      (FP32 cycle on r32 = float(r) in mixed precision)
-//   S_RZNEW = r.z, S_ZQ = z.q    (z = double(z32); q reset to 0 after reading)
-//   p = z + beta p; S_RZ <- S_RZNEW
-//   q = A p, S_PQ = p.q          (the dot accumulated per element in the apply)
-//   alpha; x += alpha p; r -= alpha q; S_RR = r.r; r32 = float(r)
+//   partials of r.z and z.q      (z = double(z32); q reset to 0 after reading)
+//   p = z + beta p               (every block sums the r.z, z.q partials)
+//   q = A p, partials of p.q     (accumulated per element in the apply)
+//   alpha = r.z / p.q; x += alpha p; r -= alpha q; r32 = float(r);
+//   S_RR = r.r, S_RZ = r.z, S_ALPHA, S_PQ published by the last block
+// Producers write per-block partials and consumers sum them (the same fixed
+// order in every block): only the update ends with a grid-wide ticket.
 void outer_iteration(glls_problem* P, const glls_solve_opts* o, cudaStream_t st) {
     const int L = (int)P->L64.size() - 1;
     const long long N = P->N;
     const bool mixed = o->precision == GLLS_PREC_MIXED;
     if (mixed) cycle<float>(P, L, P->r32, P->z32, o->gamma, o->m, (float)o->alpha, st);
     else cycle<double>(P, L, P->rk, P->zk, o->gamma, o->m, o->alpha, st);
-    launch_dots_rz_zq(P->rk, P->zk, mixed ? P->z32 : nullptr, P->qk, N, P->part, P->S, P->ticket, st);
-    launch_fcg_direction(P->pk, P->zk, N, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, P->ticket, st);
-    launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st, true, P->S + S_PQ, P->part, P->ticket);
-    launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, P->part, P->S, P->ticket, mixed ? P->r32 : nullptr, st);
+    // partial sums: r.z and z.q (kDotBlocks each), r.r (kDotBlocks), p.q (one per apply CTA)
+    double* prz = P->part;
+    double* pzq = prz + kDotBlocks;
+    double* prr = pzq + kDotBlocks;
+    double* ppq = prr + kDotBlocks;
+    const int npq = apply_dot_partials<double>(P->L64[L].dev);
+    launch_dots_rz_zq(P->rk, P->zk, mixed ? P->z32 : nullptr, P->qk, N, prz, pzq, st);
+    launch_fcg_direction(P->pk, P->zk, N, prz, pzq, kDotBlocks, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, st);
+    launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st, true, P->S + S_PQ, ppq, nullptr);
+    launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, ppq, npq, prz, kDotBlocks, prr, P->S, P->ticket,
+                      mixed ? P->r32 : nullptr, st);
 }
 
 // Lifting and Krylov initialisation (x = p = q = 0, r = f0, S_RR0 = r.r).

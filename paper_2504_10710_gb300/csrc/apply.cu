@@ -18,8 +18,15 @@ __device__ __forceinline__ bool on_boundary32(int I, int J, int K, const int n[3
 // Each thread owns ITEMS local nodes (t = threadIdx.x + 256 * it); its
 // geometry factors are loaded into registers before the x gather, so the two
 // global-memory latencies overlap.
+// 3-D FP32: at most 51 registers so that five CTAs (1,280 threads) stay
+// resident per SM; more loads in flight on the HBM-bound large levels.
+template <typename T, int DIM>
+struct ApplyMinBlocks {
+    static constexpr int value = (DIM == 3 && sizeof(T) == 4) ? 5 : 1;
+};
+
 template <typename T, int DIM, int P, bool DOT>
-__global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
+__global__ void __launch_bounds__(256, ApplyMinBlocks<T, DIM>::value) apply_p_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
                                                       int mask, double* dot, double* part, unsigned* ticket) {
     grid_dep_sync();
     constexpr int N1 = P + 1;
@@ -122,14 +129,25 @@ __global__ void __launch_bounds__(256) apply_p_kernel(DevLevel<T> L, const T* __
         }
     }
     if (DOT) {
+        // per-block partial of x.(A x); with a ticket the last block also sums
+        // them into dot[0], without one the consumer sums the partials
         __shared__ double red[32];
         const double tsum = block_sum(local, red);
         if (threadIdx.x == 0) part[blockIdx.x] = tsum;
-        if (last_block(ticket)) {
+        if (ticket && last_block(ticket)) {
             finalize_partials(part, 1, gridDim.x, dot, 0, 0, red);
             if (threadIdx.x == 0) *ticket = 0u;
         }
     }
+}
+
+// Number of CTAs (= dot partials) the specialised apply launches for L.
+template <typename T, int DIM, int P>
+int apply_blocks(const DevLevel<T>& L) {
+    constexpr int N1 = P + 1;
+    constexpr int NLOC = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
+    constexpr int EPB = NLOC >= 256 ? 1 : 256 / NLOC;
+    return (int)((L.E + EPB - 1) / EPB);
 }
 
 template <typename T, int DIM, int P>
@@ -159,6 +177,22 @@ bool dispatch(int p, const DevLevel<T>& L, const T* x, T* y, bool mask, double* 
 }
 
 }  // namespace
+
+// Dot partials that launch_apply writes for L (one per CTA of the
+// specialised kernel, else one per block of the separate dot launch).
+template <typename T>
+int apply_dot_partials(const DevLevel<T>& L) {
+    bool fixed = L.N <= (1LL << 31) - 1 && L.E * L.nloc * (L.dim == 2 ? 3 : 6) <= (1LL << 31) - 1 && L.p >= 1 &&
+                 L.p <= (L.dim == 2 ? 16 : 8);
+    for (int a = 0; a < L.dim; ++a)
+        if (L.ne[a] >= 1024) fixed = false;
+    if (!fixed) return kDotBlocks;
+    long long nloc = 1;
+    for (int a = 0; a < L.dim; ++a) nloc *= L.p + 1;
+    const long long epb = nloc >= 256 ? 1 : 256 / nloc;
+    return (int)((L.E + epb - 1) / epb);
+}
+template int apply_dot_partials<double>(const DevLevel<double>&);
 
 // Returns false when the order has no specialisation (the caller falls back).
 template <typename T>

@@ -170,23 +170,30 @@ constexpr int kDotBlocks = 304;   // 2 x 152 SMs
 constexpr int kMaxReduceBlocks = 8192;
 void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots,
                  long long n, double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st);
-// Outer-iteration dots S_RZNEW = r.z, S_ZQ = z.q; z is first taken from z32
+// Outer-iteration dots without a grid-wide finish: kDotBlocks per-block
+// partials of r.z into prz and of z.q into pzq; z is first taken from z32
 // when given (z = double(z32)); q is reset to 0 after it is read.
-void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* part,
-                       double* S, unsigned* ticket, cudaStream_t st);
+void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* prz, double* pzq,
+                       cudaStream_t st);
 
 // Krylov scalar slots in the device array S.
 enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZNEW, S_ZQ, S_RR0, S_ALPHA, S_FLAG, S_TOL2, S_ITER, S_COUNT };
 
-// q-independent update: alpha = S_RZ / S_PQ; x += alpha p; r -= alpha q;
-// then rr = r.r into S_RR (via part); flags breakdown in S_FLAG.
-// r32 (optional): also r32 = float(r) for the FP32 gamma-cycle.
-void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, double* part,
-                       double* S, unsigned* ticket, float* r32, cudaStream_t st);
-// p = z + beta p with beta = -alpha S_ZQ / S_RZ (flexible) or S_RZNEW / S_RZ;
-// afterwards S_RZ <- S_RZNEW.
-void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, unsigned* ticket,
-                          cudaStream_t st);
+// q-independent update: p.q (npq partials from the apply) and r.z (nrz
+// partials) are summed in every block, alpha = r.z / p.q; x += alpha p;
+// r -= alpha q; r.r partials into prr; the last block writes S_RR, S_RZ,
+// S_ALPHA, S_PQ and flags breakdown in S_FLAG.  r32 (optional): also
+// r32 = float(r) for the FP32 gamma-cycle.
+void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, const double* ppq,
+                       int npq, const double* prz, int nrz, double* prr, double* S, unsigned* ticket, float* r32,
+                       cudaStream_t st);
+// p = z + beta p with beta = -S_ALPHA zq / S_RZ (flexible) or rz_new / S_RZ,
+// rz_new and zq summed from the nd partials of launch_dots_rz_zq.
+void launch_fcg_direction(double* p, const double* z, long long n, const double* prz, const double* pzq, int nd,
+                          const double* S, int flexible, cudaStream_t st);
+// Dot partials launch_apply writes for L when asked for x.(A x) without a ticket.
+template <typename T>
+int apply_dot_partials(const DevLevel<T>& L);
 // f0 = M f - y on interior nodes (0 on the boundary); v = g on the boundary, 0 inside.
 void launch_lift_rhs(const double* mass, const double* f, const double* y, double* f0, const int n[3], int dim,
                      cudaStream_t st);

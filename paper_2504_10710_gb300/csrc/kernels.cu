@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0
         double t1 = block_sum(s1, red);
         if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t1;
     }
-    if (last_block(ticket)) {
+    if (ticket && last_block(ticket)) {
         finalize_partials(part, ndots, gridDim.x, S, slot0, slot1, red);
         if (threadIdx.x == 0) {
             if (rotate) S[S_RZ] = S[S_RZNEW];
@@ -588,9 +588,21 @@ __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0
     }
 }
 
+// Sum of n partials in a fixed order (every block gets the same value);
+// valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double* part, int n, double* red) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(part + i);
+    return block_sum(s, red);
+}
+
+// Outer-iteration dots, grid-stride over kDotBlocks CTAs: per-block partials
+// of r.z into prz and of z.q into pzq (summed by the consumers); z is taken
+// from z32 when given (z = double(z32)); q is reset to 0 after it is read.
 __global__ void __launch_bounds__(256) dots_rz_zq_kernel(const double* __restrict__ r, double* __restrict__ z,
                                                          const float* __restrict__ z32, double* __restrict__ q,
-                                                         long long n, double* part, double* S, unsigned* ticket) {
+                                                         long long n, double* __restrict__ prz,
+                                                         double* __restrict__ pzq) {
     grid_dep_sync();
     __shared__ double red[32];
     double s0 = 0.0, s1 = 0.0;
@@ -606,27 +618,33 @@ __global__ void __launch_bounds__(256) dots_rz_zq_kernel(const double* __restric
         s1 += zi * q[i];
         q[i] = 0.0;
     }
-    double t0 = block_sum(s0, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = t0;
-    double t1 = block_sum(s1, red);
-    if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = t1;
-    if (last_block(ticket)) {
-        finalize_partials(part, 2, gridDim.x, S, S_RZNEW, S_ZQ, red);
-        if (threadIdx.x == 0) *ticket = 0u;
-    }
+    const double t0 = block_sum(s0, red);
+    if (threadIdx.x == 0) prz[blockIdx.x] = t0;
+    const double t1 = block_sum(s1, red);
+    if (threadIdx.x == 0) pzq[blockIdx.x] = t1;
 }
 
+// q-independent update: every block sums the partials of p.q (npq, from the
+// apply) and of r.z (nrz), alpha = r.z / p.q; x += alpha p; r -= alpha q;
+// partials of r.r into prr; the last block publishes S_RR, S_RZ (for the next
+// direction), S_ALPHA, S_PQ and the breakdown flag.
 __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x, double* __restrict__ r,
                                                          const double* __restrict__ p, const double* __restrict__ q,
-                                                         long long n, double* part, double* S, unsigned* ticket,
+                                                         long long n, const double* ppq, int npq, const double* prz,
+                                                         int nrz, double* prr, double* S, unsigned* ticket,
                                                          float* __restrict__ r32) {
     grid_dep_sync();
     __shared__ double red[32];
-    __shared__ double sh_alpha;
-    const double pq = S[S_PQ];
-    if (threadIdx.x == 0) sh_alpha = S[S_RZ] / pq;   // FP64 division once per block
+    __shared__ double sh[3];
+    const double pq = sum_partials(ppq, npq, red);
+    const double rz = sum_partials(prz, nrz, red);
+    if (threadIdx.x == 0) {
+        sh[0] = rz / pq;                    // FP64 division once per block
+        sh[1] = pq;
+        sh[2] = rz;
+    }
     __syncthreads();
-    const double alpha = sh_alpha;
+    const double alpha = sh[0];
     double s = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         x[i] += alpha * p[i];
@@ -635,32 +653,36 @@ __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x,
         if (r32) r32[i] = (float)ri;
         s += ri * ri;
     }
-    double t = block_sum(s, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    const double t = block_sum(s, red);
+    if (threadIdx.x == 0) prr[blockIdx.x] = t;
     if (last_block(ticket)) {
-        finalize_partials(part, 1, gridDim.x, S, S_RR, S_RR, red);
+        finalize_partials(prr, 1, gridDim.x, S, S_RR, S_RR, red);
         if (threadIdx.x == 0) {
             S[S_ALPHA] = alpha;
-            if (!(pq > 0.0) || !isfinite(alpha)) S[S_FLAG] = 1.0;
+            S[S_PQ] = sh[1];
+            S[S_RZ] = sh[2];
+            if (!(sh[1] > 0.0) || !isfinite(alpha)) S[S_FLAG] = 1.0;
             *ticket = 0u;
         }
     }
 }
 
-__global__ void fcg_direction_kernel(double* __restrict__ p, const double* __restrict__ z, long long n,
-                                     double* __restrict__ S, int flexible, unsigned* ticket) {
+// p = z + beta p, beta = -alpha zq / rz_old (flexible) or rz_new / rz_old
+// (Fletcher-Reeves), with rz_new and zq summed from the dots' partials in
+// every block and rz_old, alpha from the previous update.
+__global__ void __launch_bounds__(256) fcg_direction_kernel(double* __restrict__ p, const double* __restrict__ z,
+                                                            long long n, const double* prz, const double* pzq, int nd,
+                                                            const double* __restrict__ S, int flexible) {
     grid_dep_sync();
+    __shared__ double red[32];
     __shared__ double sh_beta;
-    if (threadIdx.x == 0) sh_beta = flexible ? -S[S_ALPHA] * S[S_ZQ] / S[S_RZ] : S[S_RZNEW] / S[S_RZ];
+    const double rz_new = sum_partials(prz, nd, red);
+    const double zq = sum_partials(pzq, nd, red);
+    if (threadIdx.x == 0) sh_beta = flexible ? -S[S_ALPHA] * zq / S[S_RZ] : rz_new / S[S_RZ];
     __syncthreads();
     const double beta = sh_beta;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = z[i] + beta * p[i];
-    // every block has read S_RZ before taking its ticket: the last one rotates
-    if (last_block(ticket) && threadIdx.x == 0) {
-        S[S_RZ] = S[S_RZNEW];
-        *ticket = 0u;
-    }
 }
 
 // ---- GMRES helpers (Arnoldi with classical Gram-Schmidt, twice) ----------
@@ -807,9 +829,15 @@ void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_
     }
     // orders outside the specialised range: x.(A x) as a separate product
     if (dot) {
-        if constexpr (sizeof(T) == 8)
-            launch_dots(reinterpret_cast<const double*>(x), reinterpret_cast<const double*>(y), nullptr, nullptr, 1,
-                        L.N, part, dot, 0, 0, ticket, st);
+        if constexpr (sizeof(T) == 8) {
+            if (ticket)
+                launch_dots(reinterpret_cast<const double*>(x), reinterpret_cast<const double*>(y), nullptr, nullptr,
+                            1, L.N, part, dot, 0, 0, ticket, st);
+            else   // kDotBlocks partials only
+                launch_k(dots_kernel, kDotBlocks, 256, 0, st, reinterpret_cast<const double*>(x),
+                         reinterpret_cast<const double*>(y), (const double*)nullptr, (const double*)nullptr, 1, L.N,
+                         part, dot, 0, 0, (unsigned*)nullptr, 0);
+        }
     }
 }
 
@@ -925,19 +953,20 @@ void launch_dots(const double* a0, const double* b0, const double* a1, const dou
     launch_k(dots_kernel, kDotBlocks, 256, 0, st, a0, b0, a1, b1, ndots, n, part, S, slot0, slot1, ticket, 0);
 }
 
-void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, double* part, double* S,
-                       unsigned* ticket, float* r32, cudaStream_t st) {
-    launch_k(fcg_update_kernel, kDotBlocks, 256, 0, st, x, r, p, q, n, part, S, ticket, r32);
+void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, const double* ppq,
+                       int npq, const double* prz, int nrz, double* prr, double* S, unsigned* ticket, float* r32,
+                       cudaStream_t st) {
+    launch_k(fcg_update_kernel, kDotBlocks, 256, 0, st, x, r, p, q, n, ppq, npq, prz, nrz, prr, S, ticket, r32);
 }
 
-void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* part, double* S,
-                       unsigned* ticket, cudaStream_t st) {
-    launch_k(dots_rz_zq_kernel, reduce_grid(n), 256, 0, st, r, z, z32, q, n, part, S, ticket);
+void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* prz, double* pzq,
+                       cudaStream_t st) {
+    launch_k(dots_rz_zq_kernel, kDotBlocks, 256, 0, st, r, z, z32, q, n, prz, pzq);
 }
 
-void launch_fcg_direction(double* p, const double* z, long long n, double* S, int flexible, unsigned* ticket,
-                          cudaStream_t st) {
-    launch_k(fcg_direction_kernel, grid_for(n), 256, 0, st, p, z, n, S, flexible, ticket);
+void launch_fcg_direction(double* p, const double* z, long long n, const double* prz, const double* pzq, int nd,
+                          const double* S, int flexible, cudaStream_t st) {
+    launch_k(fcg_direction_kernel, kDotBlocks, 256, 0, st, p, z, n, prz, pzq, nd, S, flexible);
 }
 
 void launch_lift_rhs(const double* mass, const double* f, const double* y, double* f0, const int n[3], int dim,
