@@ -163,8 +163,8 @@ glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve
                              int on_device, void* stream, glls_stats* stats);
 
 /* Autotuner: for every level >= 1, precision and direction, time the line
- * solve with 2, 4 and 8 lines per CTA on the problem's own data and keep the
- * fastest.  chosen / best_us (optional): levels x 2 (FP32, FP64) x 3 entries,
+ * solve with 2, 4, 8 and (FP32 only) 16 lines per CTA on the problem's own
+ * data and keep the fastest.  chosen / best_us (optional): levels x 2 (FP32, FP64) x 3 entries,
  * index (level * 2 + precision) * 3 + axis, the chosen tile and its time in
  * microseconds per launch.  Cached graphs are rebuilt on the next solve.
  * Synchronous. */

@@ -600,12 +600,15 @@ glls_status tune_levels(glls_problem* P, std::vector<LevelStore<T>>& Ls, int pre
     cudaEvent_t a = nullptr, b = nullptr;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
-    const int cand[3] = {2, 4, 8};
+    // lines per CTA: 16 only in FP32 (launch_line_warp falls back to 8 otherwise)
+    const int cand[4] = {2, 4, 8, 16};
+    const int ncand = sizeof(T) == 4 ? 4 : 3;
     for (size_t l = 1; l < Ls.size(); ++l)
         for (int s = 0; s < Ls[l].dev.dim; ++s) {
             float best = 1e30f;
             int pick = 4;
-            for (int c : cand) {
+            for (int ci = 0; ci < ncand; ++ci) {
+                const int c = cand[ci];
                 Ls[l].dev.lpb[s] = c;
                 for (int w = 0; w < 3; ++w)
                     launch_line_solve<T>(Ls[l].dev, s, 0, Ls[l].r, nullptr, nullptr, Ls[l].t2, T(1), st);

@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
     }
 }
 
-// Lines per CTA (the tile the autotuner chooses among): 2, 4 or 8.
+// Lines per CTA (the tile the autotuner chooses among): 2, 4, 8, or 16 (FP32).
 template <typename T, int C, int LPB>
 void launch_lpb(const WarpLineArgs<T>& A, cudaStream_t st) {
     const size_t smem = sizeof(T) * 3 * LPB * (32 * C + C);
@@ -226,6 +226,15 @@ void launch_lpb(const WarpLineArgs<T>& A, cudaStream_t st) {
 
 template <typename T, int C>
 void launch_c(const WarpLineArgs<T>& A, int lpb, cudaStream_t st) {
+    if (lpb == 16) {
+        // 16 lines per CTA (512 threads): FP32 with at most 16 unknowns per
+        // lane only (register and shared-memory budget); otherwise 8
+        if constexpr (sizeof(T) == 4 && C <= 16) {
+            launch_lpb<T, C, 16>(A, st);
+            return;
+        }
+        lpb = 8;
+    }
     if (lpb == 2) launch_lpb<T, C, 2>(A, st);
     else if (lpb == 8) launch_lpb<T, C, 8>(A, st);
     else launch_lpb<T, C, 4>(A, st);
@@ -246,7 +255,9 @@ bool set_attr_lpb() {
 
 template <typename T, int C>
 bool set_attr() {
-    return set_attr_lpb<T, C, 2>() && set_attr_lpb<T, C, 4>() && set_attr_lpb<T, C, 8>();
+    bool ok = set_attr_lpb<T, C, 2>() && set_attr_lpb<T, C, 4>() && set_attr_lpb<T, C, 8>();
+    if constexpr (sizeof(T) == 4 && C <= 16) ok = ok && set_attr_lpb<T, C, 16>();
+    return ok;
 }
 
 }  // namespace

@@ -155,7 +155,7 @@ def test_autotune_picks_valid_tiles_and_keeps_results():
     before = np.zeros(prob.N)
     st0 = prob.solve(before, o)
     tiles = prob.autotune()
-    assert tiles and all(c in (2, 4, 8) and us > 0 for c, us in tiles.values())
+    assert tiles and all(c in (2, 4, 8, 16) and us > 0 for c, us in tiles.values())
     after = np.zeros(prob.N)
     st1 = prob.solve(after, o)            # graphs are re-captured with the chosen tiles
     assert _rel(after, before) < 1e-10 and abs(st1.iterations - st0.iterations) <= 1
