@@ -24,6 +24,8 @@ Workloads (seeds are numpy.random.default_rng(2504_10710 + 1000*cfg + i)):
   * ``table1_problem1``  one element, -Laplace(u) = 1, u = 0 on the boundary.
   * ``table1_problem3``  one element, u = sin(8 pi / (x + y + pi/10)).
   * ``random2d/3d``      any element grid / order / amplitude, for parity tests.
+  * ``batch_uneven``     independent 2-D problems, n x n elements with n ~ U{4..64},
+                         p ~ U{4..12}, amplitude ~ U(0, 0.2), terrain2d generators.
 """
 from __future__ import annotations
 
@@ -252,6 +254,24 @@ def random3d(nelem: Sequence[int], order: int, amp: float = 0.15, seed: int = 0,
     ne = tuple(int(n) for n in nelem)
     return Workload(f"random3d_{'x'.join(map(str, ne))}_p{order}_s{seed}", 3, ne, order,
                     terrain3d_map(amp), fs, g, params=dict(amp=amp, seed=seed))
+
+
+def batch_uneven(count: int = 256) -> list[Workload]:
+    """Independent 2-D problems of uneven size for batched solves: problem i
+    draws n ~ U{4..64} (n x n elements), p ~ U{4..12} and an amplitude
+    A ~ U(0, 0.2) of the terrain2d map, then a right-hand side and Dirichlet
+    data from the terrain2d generators (seeds 2504_10710 + 3000 + i)."""
+    out = []
+    for i in range(count):
+        rng = rng_for(3, i)
+        n = int(rng.integers(4, 65))
+        p = int(rng.integers(4, 13))
+        amp = float(rng.uniform(0.0, 0.2))
+        f, fp = fourier_rhs_2d(rng)
+        g, gp = smooth_dirichlet_2d(rng)
+        out.append(Workload(f"batch{i}_{n}x{n}_p{p}_a{amp:.3f}", 2, (n, n), p, terrain2d_map(amp), [f], g,
+                            params=dict(amp=amp, f=fp, g=gp)))
+    return out
 
 
 def random_field(shape, seed: int) -> np.ndarray:

@@ -161,3 +161,30 @@ def test_autotune_picks_valid_tiles_and_keeps_results():
     assert _rel(after, before) < 1e-10 and abs(st1.iterations - st0.iterations) <= 1
     assert st1.kernels > st1.iterations * 10
     prob.close()
+
+
+def test_uneven_batch_sample_with_fem_smoother():
+    """A sample of the batched uneven workload (n x n elements, n in 4..64,
+    p in 4..12, amplitude up to 0.2), including its hardest draws (p = 12 and
+    amplitude near 0.2): with the FEM line smoother (alpha = 0.16) every
+    problem reaches 1e-10 in the batch, with the single solves' results."""
+    ws = inputs.batch_uneven()
+    pick = [w for w in ws if w.order == 12 and w.params["amp"] > 0.17][:2] + ws[:4]
+    o = glls.opts(tol=1e-10, gamma=1, alpha=0.16, precision=glls.PREC_MIXED, max_iter=300)
+    probs, single = [], []
+    for w in pick:
+        prob, coords = glls.problem_for(w, glls.SMOOTHER_FEM)
+        prob.set_rhs(w.sample_rhs(coords)[0])
+        prob.set_dirichlet(w.sample_dirichlet(coords))
+        u = np.zeros(prob.N)
+        st = prob.solve(u, o)
+        assert st.status == glls.OK and st.rel_residual <= 1e-10, w.name
+        probs.append(prob)
+        single.append((u, st.iterations))
+    outs = [np.zeros(p.N) for p in probs]
+    stats = glls.solve_batch(probs, outs, o)
+    for (u, k), ub, st in zip(single, outs, stats):
+        assert st.status == glls.OK and abs(st.iterations - k) <= 1
+        assert _rel(ub, u) < 1e-9
+    for p in probs:
+        p.close()
