@@ -130,43 +130,47 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
             // the odd points of this level are eliminated: keep 1/a from here on
 #pragma unroll
             for (int j = h - 1; j < C; j += 2 * h) a[j] = recip(a[j]);
-            T ar = __shfl_down_sync(kFull, a[h - 1], 1);
-            T lr = __shfl_down_sync(kFull, l[h - 1], 1);
-            T ur = __shfl_down_sync(kFull, u[h - 1], 1);
-            T gr = __shfl_down_sync(kFull, g[h - 1], 1);
-            if (lane == 31) { ar = T(1); lr = T(0); ur = T(0); gr = T(0); }
+            // the next lane's first odd point, premultiplied by its 1/a
+            T lr = __shfl_down_sync(kFull, a[h - 1] * l[h - 1], 1);
+            T ur = __shfl_down_sync(kFull, a[h - 1] * u[h - 1], 1);
+            T gr = __shfl_down_sync(kFull, a[h - 1] * g[h - 1], 1);
+            if (lane == 31) { lr = T(0); ur = T(0); gr = T(0); }
 #pragma unroll
             for (int j = 2 * h - 1; j < C; j += 2 * h) {
                 const int jl = j - h, jr = j + h;
-                const T iaR = jr < C ? a[jr < C ? jr : 0] : ar;   // reciprocal of the right odd point
-                const T lR = jr < C ? l[jr < C ? jr : 0] : lr;
-                const T uR = jr < C ? u[jr < C ? jr : 0] : ur;
-                const T gR = jr < C ? g[jr < C ? jr : 0] : gr;
+                const int jr0 = jr < C ? jr : 0;
+                // right odd point's couplings times its reciprocal
+                const T lR = jr < C ? a[jr0] * l[jr0] : lr;
+                const T uR = jr < C ? a[jr0] * u[jr0] : ur;
+                const T gR = jr < C ? a[jr0] * g[jr0] : gr;
                 const T al = -l[j] * a[jl];
-                const T be = -u[j] * iaR;
-                a[j] = a[j] + al * u[jl] + be * lR;
-                g[j] = g[j] + al * g[jl] + be * gR;
+                const T mu = -u[j];
+                a[j] = a[j] + al * u[jl] + mu * lR;
+                g[j] = g[j] + al * g[jl] + mu * gR;
                 l[j] = al * l[jl];
-                u[j] = be * uR;
+                u[j] = mu * uR;
             }
         }
         // ---- forward reduction across lanes on each lane's top unknown (position C (lane+1))
         T At = a[C - 1], Lt = l[C - 1], Ut = u[C - 1], Gt = g[C - 1];
 #pragma unroll
         for (int d = 1; d < 32; d *= 2) {
-            if (((lane + 1) & (2 * d - 1)) == d) At = recip(At);     // odd at this level
-            const T aL = __shfl_up_sync(kFull, At, d), lL = __shfl_up_sync(kFull, Lt, d);
-            const T uL = __shfl_up_sync(kFull, Ut, d), gL = __shfl_up_sync(kFull, Gt, d);
-            T aR = __shfl_down_sync(kFull, At, d), lR = __shfl_down_sync(kFull, Lt, d);
-            T uR = __shfl_down_sync(kFull, Ut, d), gR = __shfl_down_sync(kFull, Gt, d);
-            if (lane + d > 31) { aR = T(1); lR = T(0); uR = T(0); gR = T(0); }
+            // a lane eliminated at this level sends its couplings premultiplied
+            // by its reciprocal pivot: 3 values each way instead of 4
+            const bool odd = ((lane + 1) & (2 * d - 1)) == d;
+            if (odd) At = recip(At);
+            const T pl = At * Lt, pu = At * Ut, pg = At * Gt;
+            const T lL = __shfl_up_sync(kFull, pl, d), uL = __shfl_up_sync(kFull, pu, d);
+            const T gL = __shfl_up_sync(kFull, pg, d);
+            T lR = __shfl_down_sync(kFull, pl, d), uR = __shfl_down_sync(kFull, pu, d);
+            T gR = __shfl_down_sync(kFull, pg, d);
+            if (lane + d > 31) { lR = T(0); uR = T(0); gR = T(0); }
             if (((lane + 1) & (2 * d - 1)) == 0) {
-                const T al = -Lt * aL;
-                const T be = -Ut * aR;
-                At = At + al * uL + be * lR;
-                Gt = Gt + al * gL + be * gR;
-                Lt = al * lL;
-                Ut = be * uR;
+                const T ml = -Lt, mu = -Ut;
+                At = At + ml * uL + mu * lR;
+                Gt = Gt + ml * gL + mu * gR;
+                Lt = ml * lL;
+                Ut = mu * uR;
             }
         }
         // ---- top equation (position 32 C) and back substitution across lanes
