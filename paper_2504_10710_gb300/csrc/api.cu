@@ -799,6 +799,13 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
     }
     if (desc->coarse_solver < 0 || desc->coarse_solver > 2 || desc->coarse_cr_levels < 0)
         return fail(GLLS_ERR_INVALID, "coarse_solver must be GLLS_COARSE_* and coarse_cr_levels >= 0");
+    {
+        long long n0 = 1;
+        for (int a = 0; a < H[0].dim; ++a) n0 *= H[0].n[a] - 2;
+        if (n0 > 16384)
+            return fail(GLLS_ERR_INVALID, "coarsest level has more than 16384 interior unknowns (its matrix is "
+                                          "assembled densely on the host at set-up)");
+    }
     CoarseHost C;
     err = build_coarse(H[0], desc->coarse_solver, desc->coarse_cr_levels, C);
     if (!err.empty()) return fail(GLLS_ERR_BREAKDOWN, err);

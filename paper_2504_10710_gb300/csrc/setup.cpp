@@ -621,6 +621,11 @@ std::string build_coarse(const LevelHost& lv, int coarse_solver, int cr_levels, 
     const long long n = (long long)out.index.size();
     out.n = n;
     if (n == 0) return "coarsest level has no interior unknowns";
+    // The coarsest matrix is assembled densely on the host before its block
+    // factorisation; beyond this size that costs gigabytes and minutes.
+    constexpr long long kMaxCoarseUnknowns = 16384;
+    if (n > kMaxCoarseUnknowns)
+        return "coarsest level has more than 16384 interior unknowns (dense host assembly); use fewer elements";
     // half bandwidth in the interior numbering
     long long bw = 0;
     Geo geo{d, p, n1, nloc, &lv};

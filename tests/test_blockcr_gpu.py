@@ -143,3 +143,13 @@ def test_estimate_bytes_tracks_block_cr_allocation(k):
     actual = prob.info.device_bytes
     assert 0.8 * actual <= est <= 1.25 * actual, (est, actual)
     prob.close()
+
+
+def test_oversized_coarsest_level_is_refused():
+    """27^3 elements put 26^3 = 17,576 unknowns on the p = 1 level, above the
+    16,384 the dense host assembly accepts: GLLS_ERR_INVALID, no allocation."""
+    wl = inputs.random3d((27, 27, 27), 2, amp=0.1, seed=47)
+    xi, _ = glls.gll(wl.order)
+    with pytest.raises(glls.GllsError) as err:
+        glls.Problem(wl.dim, wl.nelem, wl.order, wl.coords(xi))
+    assert err.value.status == glls.ERR_INVALID
