@@ -18,6 +18,39 @@ __device__ __forceinline__ bool on_boundary32(int I, int J, int K, const int n[3
 // Each thread owns ITEMS local nodes (t = threadIdx.x + 256 * it); its
 // geometry factors are loaded into registers before the x gather, so the two
 // global-memory latencies overlap.
+// sum_m a[m] b[m] and sum_m a[m] b[m * stride] over N terms with a (and, in
+// the first form, b) contiguous and 16-byte aligned: float4 loads, the terms
+// added in m order.
+template <int N>
+__device__ __forceinline__ float dot_cc(const float* a, const float* b) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+        const float4 u = a4[q], v = b4[q];
+        s += u.x * v.x;
+        s += u.y * v.y;
+        s += u.z * v.z;
+        s += u.w * v.w;
+    }
+    return s;
+}
+template <int N, int STRIDE>
+__device__ __forceinline__ float dot_cs(const float* a, const float* b) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+        const float4 u = a4[q];
+        s += u.x * b[(4 * q) * STRIDE];
+        s += u.y * b[(4 * q + 1) * STRIDE];
+        s += u.z * b[(4 * q + 2) * STRIDE];
+        s += u.w * b[(4 * q + 3) * STRIDE];
+    }
+    return s;
+}
+
 // 3-D FP32: at most 51 registers so that five CTAs (1,280 threads) stay
 // resident per SM; more loads in flight on the HBM-bound large levels.
 template <typename T, int DIM>
@@ -34,9 +67,13 @@ __global__ void __launch_bounds__(256, ApplyMinBlocks<T, DIM>::value) apply_p_ke
     constexpr int EPB = NLOC >= 256 ? 1 : 256 / NLOC;
     constexpr int ITEMS = (EPB * NLOC + 255) / 256;
     constexpr int NC = DIM == 2 ? 3 : 6;
-    __shared__ T sD[N1 * N1];
-    __shared__ T sx[EPB * NLOC];
-    __shared__ T sw[DIM * EPB * NLOC];
+    // FP32 with N1 a multiple of 4: rows of D, D^T, x and w are 16-byte
+    // aligned, so the contractions read them with float4 loads
+    constexpr bool VEC = sizeof(T) == 4 && N1 % 4 == 0;
+    __shared__ __align__(16) T sD[N1 * N1];
+    __shared__ __align__(16) T sDT[VEC ? N1 * N1 : 1];
+    __shared__ __align__(16) T sx[EPB * NLOC];
+    __shared__ __align__(16) T sw[DIM * EPB * NLOC];
     __shared__ int sbase[EPB];   // global index of each element's first node
     __shared__ int sxyz[EPB];    // element coordinates packed 10:10:10 bits
     const int E = (int)L.E;
@@ -61,7 +98,10 @@ __global__ void __launch_bounds__(256, ApplyMinBlocks<T, DIM>::value) apply_p_ke
             for (int c = 0; c < NC; ++c) gk[it][c] = __ldg(L.G + c * EN + gq);
         }
     }
-    for (int t = threadIdx.x; t < N1 * N1; t += 256) sD[t] = L.D[t];
+    for (int t = threadIdx.x; t < N1 * N1; t += 256) {
+        sD[t] = L.D[t];
+        if constexpr (VEC) sDT[t] = L.D[(t % N1) * N1 + t / N1];
+    }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
@@ -82,11 +122,17 @@ __global__ void __launch_bounds__(256, ApplyMinBlocks<T, DIM>::value) apply_p_ke
         const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
         const T* xe = sx + el * NLOC;
         T g0 = T(0), g1 = T(0), g2 = T(0);
+        if constexpr (VEC) {
+            g0 = dot_cc<N1>(sD + i * N1, xe + (k * N1 + j) * N1);
+            g1 = dot_cs<N1, N1>(sD + j * N1, xe + k * N1 * N1 + i);
+            if (DIM == 3) g2 = dot_cs<N1, N1 * N1>(sD + k * N1, xe + j * N1 + i);
+        } else {
 #pragma unroll
-        for (int m = 0; m < N1; ++m) {
-            g0 += sD[i * N1 + m] * xe[(k * N1 + j) * N1 + m];
-            g1 += sD[j * N1 + m] * xe[(k * N1 + m) * N1 + i];
-            if (DIM == 3) g2 += sD[k * N1 + m] * xe[(m * N1 + j) * N1 + i];
+            for (int m = 0; m < N1; ++m) {
+                g0 += sD[i * N1 + m] * xe[(k * N1 + j) * N1 + m];
+                g1 += sD[j * N1 + m] * xe[(k * N1 + m) * N1 + i];
+                if (DIM == 3) g2 += sD[k * N1 + m] * xe[(m * N1 + j) * N1 + i];
+            }
         }
         const T* a = gk[it];
         if (DIM == 2) {
@@ -110,11 +156,16 @@ __global__ void __launch_bounds__(256, ApplyMinBlocks<T, DIM>::value) apply_p_ke
         const T* w0 = sw + el * NLOC;
         const T* w1 = sw + EPB * NLOC + el * NLOC;
         T v = T(0);
+        if constexpr (VEC) {
+            v = dot_cc<N1>(sDT + i * N1, w0 + (k * N1 + j) * N1) + dot_cs<N1, N1>(sDT + j * N1, w1 + k * N1 * N1 + i);
+            if (DIM == 3) v += dot_cs<N1, N1 * N1>(sDT + k * N1, sw + 2 * EPB * NLOC + el * NLOC + j * N1 + i);
+        } else {
 #pragma unroll
-        for (int m = 0; m < N1; ++m) {
-            v += sD[m * N1 + i] * w0[(k * N1 + j) * N1 + m];
-            v += sD[m * N1 + j] * w1[(k * N1 + m) * N1 + i];
-            if (DIM == 3) v += sD[m * N1 + k] * sw[2 * EPB * NLOC + el * NLOC + (m * N1 + j) * N1 + i];
+            for (int m = 0; m < N1; ++m) {
+                v += sD[m * N1 + i] * w0[(k * N1 + j) * N1 + m];
+                v += sD[m * N1 + j] * w1[(k * N1 + m) * N1 + i];
+                if (DIM == 3) v += sD[m * N1 + k] * sw[2 * EPB * NLOC + el * NLOC + (m * N1 + j) * N1 + i];
+            }
         }
         const int exyz = sxyz[el];
         const int I = (exyz & 1023) * P + i, J = ((exyz >> 10) & 1023) * P + j, K = (exyz >> 20) * P + k;
