@@ -51,11 +51,14 @@ __device__ __forceinline__ float dot_cs(const float* a, const float* b) {
     return s;
 }
 
-// 3-D FP32: at most 51 registers so that five CTAs (1,280 threads) stay
-// resident per SM; more loads in flight on the HBM-bound large levels.
+// Resident CTAs per SM the register allocation must allow: 3-D FP32 five
+// (at most 51 registers; more loads in flight on the HBM-bound large
+// levels); otherwise one.  (Eight for 2-D FP32 caps it at 32 registers;
+// measured inside the solve that is 0.5-1 % slower than the 48 registers
+// the compiler picks with one.)
 template <typename T, int DIM>
 struct ApplyMinBlocks {
-    static constexpr int value = (DIM == 3 && sizeof(T) == 4) ? 5 : 1;
+    static constexpr int value = (sizeof(T) == 4 && DIM == 3) ? 5 : 1;
 };
 
 template <typename T, int DIM, int P, bool DOT>
