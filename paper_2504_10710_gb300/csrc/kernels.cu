@@ -588,6 +588,9 @@ __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0
     }
 }
 
+// Elements per thread per trip of the FCG vector kernels' grid-stride loops.
+constexpr int kVecU = 4;
+
 // Sum of n partials in a fixed order (every block gets the same value);
 // valid in thread 0.
 __device__ __forceinline__ double sum_partials(const double* part, int n, double* red) {
@@ -606,17 +609,31 @@ __global__ void __launch_bounds__(256) dots_rz_zq_kernel(const double* __restric
     grid_dep_sync();
     __shared__ double red[32];
     double s0 = 0.0, s1 = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double zi;
-        if (z32) {
-            zi = (double)z32[i];
-            z[i] = zi;
-        } else {
-            zi = z[i];
+    // kVecU elements per thread per trip, all loads issued before use (same
+    // summation order as a plain grid-stride loop)
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += kVecU * stride) {
+        double rv[kVecU], zv[kVecU], qv[kVecU];
+#pragma unroll
+        for (int u = 0; u < kVecU; ++u) {
+            const long long i = i0 + u * stride;
+            rv[u] = zv[u] = qv[u] = 0.0;
+            if (i < n) {
+                rv[u] = r[i];
+                zv[u] = z32 ? (double)z32[i] : z[i];
+                qv[u] = q[i];
+            }
         }
-        s0 += r[i] * zi;
-        s1 += zi * q[i];
-        q[i] = 0.0;
+#pragma unroll
+        for (int u = 0; u < kVecU; ++u) {
+            const long long i = i0 + u * stride;
+            if (i < n) {
+                if (z32) z[i] = zv[u];
+                s0 += rv[u] * zv[u];
+                s1 += zv[u] * qv[u];
+                q[i] = 0.0;
+            }
+        }
     }
     const double t0 = block_sum(s0, red);
     if (threadIdx.x == 0) prz[blockIdx.x] = t0;
@@ -646,12 +663,31 @@ __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x,
     __syncthreads();
     const double alpha = sh[0];
     double s = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        x[i] += alpha * p[i];
-        const double ri = r[i] - alpha * q[i];
-        r[i] = ri;
-        if (r32) r32[i] = (float)ri;
-        s += ri * ri;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += kVecU * stride) {
+        double xv[kVecU], rv[kVecU], pv[kVecU], qv[kVecU];
+#pragma unroll
+        for (int u = 0; u < kVecU; ++u) {
+            const long long i = i0 + u * stride;
+            xv[u] = rv[u] = pv[u] = qv[u] = 0.0;
+            if (i < n) {
+                xv[u] = x[i];
+                rv[u] = r[i];
+                pv[u] = p[i];
+                qv[u] = q[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVecU; ++u) {
+            const long long i = i0 + u * stride;
+            if (i < n) {
+                x[i] = xv[u] + alpha * pv[u];
+                const double ri = rv[u] - alpha * qv[u];
+                r[i] = ri;
+                if (r32) r32[i] = (float)ri;
+                s += ri * ri;
+            }
+        }
     }
     const double t = block_sum(s, red);
     if (threadIdx.x == 0) prr[blockIdx.x] = t;
@@ -681,8 +717,24 @@ __global__ void __launch_bounds__(256) fcg_direction_kernel(double* __restrict__
     if (threadIdx.x == 0) sh_beta = flexible ? -S[S_ALPHA] * zq / S[S_RZ] : rz_new / S[S_RZ];
     __syncthreads();
     const double beta = sh_beta;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = z[i] + beta * p[i];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += kVecU * stride) {
+        double zv[kVecU], pv[kVecU];
+#pragma unroll
+        for (int u = 0; u < kVecU; ++u) {
+            const long long i = i0 + u * stride;
+            zv[u] = pv[u] = 0.0;
+            if (i < n) {
+                zv[u] = z[i];
+                pv[u] = p[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVecU; ++u) {
+            const long long i = i0 + u * stride;
+            if (i < n) p[i] = zv[u] + beta * pv[u];
+        }
+    }
 }
 
 // ---- GMRES helpers (Arnoldi with classical Gram-Schmidt, twice) ----------
