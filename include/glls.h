@@ -27,8 +27,8 @@
  *     caller owns every buffer it passes; the library copies what it keeps.
  *   - stream: a cudaStream_t (NULL = legacy default stream).  Device-pointer
  *     operations are asynchronous on that stream unless stated otherwise.
- *   - Levels are numbered 0 (coarsest, p = 1 on multi-element grids, p = 2 on
- *     a single element) to L (finest), with p_{l-1} = floor(p_l / 2).
+ *   - Levels are numbered 0 (coarsest: p = 1 when every axis has at least two
+ *     elements, else p = 2) to L (finest), with p_{l-1} = floor(p_l / 2).
  */
 #ifndef GLLS_H
 #define GLLS_H

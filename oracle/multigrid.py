@@ -3,8 +3,10 @@ Test infrastructure only.
 
 Readings taken where the paper is silent or ambiguous:
   * Order chain: p_{l-1} = floor(p_l / 2) (coarsening factor f = 2 of
-    Prop. 3.13).  A multi-element grid stops at p = 1 (the lowest order with
-    unknowns); a single element stops at p = 2 (p = 1 has no interior node).
+    Prop. 3.13).  The chain stops at the lowest order whose grid has interior
+    unknowns: p = 1 when every axis has at least two elements, p = 2
+    otherwise (one element along an axis has no interior node there at p = 1;
+    a single element is the paper's case).
   * Coarse geometry: coarse nodes are the fine element's coordinate polynomial
     evaluated at the coarse GLL points, and A_l is rediscretised on that mesh
     with eq. (discreteBilinear) (the paper rediscretises and notes that the
@@ -87,7 +89,7 @@ class Hierarchy:
     the exact coarsest solver M_0^-1 = A_0^-1."""
 
     def __init__(self, fine: Level, chain=None, smoother="gll", restriction="interp"):
-        multi = any(e > 1 for e in fine.nelem)
+        multi = all(e > 1 for e in fine.nelem)       # p = 1 has interior unknowns
         self.chain = chain or order_chain(fine.p, multi)
         self.levels = [fine]
         for p_c in self.chain[1:]:

@@ -1048,7 +1048,8 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
         ne[a] = desc->nelem[a];
         E *= ne[a];
     }
-    const bool multi = E > 1;
+    bool multi = true;                      // p = 1 has interior unknowns
+    for (int a = 0; a < d; ++a) multi = multi && ne[a] > 1;
     std::vector<int> chain = order_chain(desc->order, multi);
     const int ncomp = d == 2 ? 3 : 6;
     double total = 0.0;

@@ -371,7 +371,8 @@ std::vector<int> order_chain(int p_fine, bool multi) {
 
 std::string build_levels(int dim, const int nelem[3], int p_fine, const double* coords,
                          int smoother, int restriction, std::vector<LevelHost>& levels) {
-    bool multi = nelem[0] > 1 || nelem[1] > 1 || (dim == 3 && nelem[2] > 1);
+    // p = 1 has interior unknowns only with at least two elements along every axis
+    bool multi = nelem[0] > 1 && nelem[1] > 1 && (dim == 2 || nelem[2] > 1);
     std::vector<int> chain = order_chain(p_fine, multi);
     levels.assign(chain.size(), LevelHost());
     // fill from fine (back) to coarse (front)

@@ -20,6 +20,21 @@ def level_of(wl):
     return Level(wl.dim, wl.nelem, wl.order, wl.coords(xi))
 
 
+def test_one_element_row_stops_at_p2():
+    """One element along an axis: p = 1 has no interior node there, so the
+    hierarchy stops at p = 2, whose coarse matrix is the exact coarsest solve."""
+    from oracle.gll import gll
+    from paper_2504_10710_gb300 import inputs
+    for ne in [(9, 1), (1, 7)]:
+        wl = inputs.random2d(ne, 4, amp=0.1, seed=35)
+        h = Hierarchy(Level(2, ne, 4, wl.coords(gll(4)[0])), restriction="transpose")
+        assert h.chain == [4, 2]
+        assert h.levels[0].interior.sum() > 0
+    wl = inputs.random3d((3, 2, 1), 3, amp=0.1, seed=38)
+    h = Hierarchy(Level(3, (3, 2, 1), 3, wl.coords(gll(3)[0])), restriction="transpose")
+    assert h.chain == [3, 2] and h.levels[0].interior.sum() > 0
+
+
 def test_order_chains():
     assert order_chain(8, True) == [8, 4, 2, 1]
     assert order_chain(7, True) == [7, 3, 1]
