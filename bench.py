@@ -56,6 +56,8 @@ def parse():
                          "per iteration (profilers can see its kernels), 0 = plain stream launches")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed mixed-precision solves (for an ncu launch list)")
+    ap.add_argument("--profile3d", action="store_true",
+                    help="as --profile, on the 3-D 16^3 p = 7 workload with one right-hand side")
     return ap.parse_args()
 
 
@@ -128,7 +130,7 @@ def run_ours(args, rank, world):
     __graft_entry__.build()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
-    wl = inputs.terrain2d()
+    wl = inputs.terrain3d(nrhs=1) if args.profile3d else inputs.terrain2d()
     prob, f, g = make_problem(wl, glls)
     N = prob.N
     stream = torch.cuda.current_stream()
@@ -174,8 +176,8 @@ def run_ours(args, rank, world):
     clocks = ClockSampler(dev)
     ms_mixed, its_mixed, clk = timed(glls.PREC_MIXED, args.steps, args.warmup, clocks)
     launches = kernels[0]
-    if args.profile:
-        print(json.dumps({"profile": True, "ms_per_step": ms_mixed, "iterations": its_mixed}))
+    if args.profile or args.profile3d:
+        print(json.dumps({"profile": True, "workload": wl.name, "ms_per_step": ms_mixed, "iterations": its_mixed}))
         sys.exit(0)
     ms_fp64, its_fp64, _ = timed(glls.PREC_FP64, max(3, args.steps // 2), 2)
     u_mixed = np.zeros(N)
@@ -342,6 +344,16 @@ def kernel_roofline(prob, glls, torch):
             "note": "FMA counted as 2 FLOP; 50 launches replayed from a CUDA graph, CUDA events"}
 
 
+def _fp32_apply_kernel(d, p):
+    """Name and traffic key of the FP32 apply kernel the library launches for
+    a level of dimension d and order p (the dispatch in csrc/apply.cu)."""
+    if d == 3 and p >= 4:
+        return f"apply_eo3_kernel<float, {p}> (even-odd line apply)", f"apply_eo3_kernel<float,{p}>"
+    if d == 3:
+        return f"apply_col_kernel<{p}> (column apply)", f"apply_col_kernel<{p}>"
+    return f"apply_p_kernel<float, {d}, {p}>", f"apply_p_kernel<float,{d},{p}>"
+
+
 def smoother_rooflines(prob, glls, torch, inputs, flush):
     """FP32 smoother and operator kernels against HBM: the bench workload's
     fine level (L2-resident between launches, as inside a solve) and the 3-D
@@ -377,8 +389,8 @@ def smoother_rooflines(prob, glls, torch, inputs, flush):
         y = torch.zeros_like(x)
         r = _interior_random(torch, shape, torch.float32)
         tm = (lambda fn: _time_cold(torch, fn, flush)) if cold else (lambda fn: _time_graph(torch, fn))
-        entry(f"apply_p_kernel<float, {d}, {p}>", work, tm(lambda s: pb.apply(L, x, y, s)), 8 * N + G, cold,
-              f"apply_p_kernel<float,{d},{p}>")
+        kname, tkey = _fp32_apply_kernel(d, p)
+        entry(kname, work, tm(lambda s: pb.apply(L, x, y, s)), 8 * N + G, cold, tkey)
         for ax in range(d):
             entry(f"line_warp_kernel<float> B^-1 g, axis {ax}", work, tm(lambda s: pb.line_solve(L, ax, r, x, s)),
                   16 * N, cold, f"line_warp_kernel<float>_ax{ax}")

@@ -241,6 +241,7 @@ int apply_dot_partials(const DevLevel<T>& L) {
     for (int a = 0; a < L.dim; ++a)
         if (L.ne[a] >= 1024) fixed = false;
     if (!fixed) return kDotBlocks;
+    if (apply_eo_selected(L.dim, L.p, true)) return apply_eo_blocks(L.p, L.E);
     long long nloc = 1;
     for (int a = 0; a < L.dim; ++a) nloc *= L.p + 1;
     const long long epb = nloc >= 256 ? 1 : 256 / nloc;
@@ -255,6 +256,12 @@ bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, doubl
     if (L.N > (1LL << 31) - 1 || L.E * L.nloc * (L.dim == 2 ? 3 : 6) > (1LL << 31) - 1) return false;
     for (int a = 0; a < L.dim; ++a)
         if (L.ne[a] >= 1024) return false;   // element coordinates are packed in 10 bits
+    // 3-D: the even-odd line kernel where it was measured fastest, then the
+    // FP32 column kernel, else the node-per-thread kernel below
+    if (launch_apply_eo<T>(L, x, y, mask, dot, part, ticket, st)) return true;
+    if constexpr (sizeof(T) == 4) {
+        if (L.dim == 3 && !dot && launch_apply_col(L, x, y, mask, st)) return true;
+    }
     if (L.dim == 2) return dispatch<T, 2, 16>(L.p, L, x, y, mask, dot, part, ticket, st);
     return dispatch<T, 3, 8>(L.p, L, x, y, mask, dot, part, ticket, st);
 }

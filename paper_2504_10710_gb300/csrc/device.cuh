@@ -116,6 +116,20 @@ template <typename T>
 bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
                       cudaStream_t st);
 bool init_line_warp_attributes();
+// 3-D FP32 apply with one thread per element column (apply_col.cu), p <= 3
+// (the orders the even-odd kernel does not take); no x.(A x) product.
+// Returns false outside that range.
+bool launch_apply_col(const DevLevel<float>& L, const float* x, float* y, bool mask, cudaStream_t st);
+bool init_apply_col_attributes();
+// 3-D apply with one thread per element grid line and even-odd derivative
+// sweeps (apply_eo.cu), for the orders apply_eo_selected names, with the
+// optional x.(A x) partials (one per CTA, apply_eo_blocks of them).
+bool apply_eo_selected(int dim, int p, bool f64);
+template <typename T>
+bool launch_apply_eo(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part,
+                     unsigned* ticket, cudaStream_t st);
+int apply_eo_blocks(int p, long long E);
+bool init_apply_eo_attributes();
 
 // ---- launchers (all asynchronous on `st`) ---------------------------------
 // y = A x; mask: boundary rows of y are not written.  y_is_zero: the caller

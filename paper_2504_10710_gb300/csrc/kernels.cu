@@ -1082,7 +1082,7 @@ bool init_kernel_attributes() {
     for (const void* f : fns)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess)
             return false;
-    return init_line_warp_attributes();
+    return init_line_warp_attributes() && init_apply_col_attributes() && init_apply_eo_attributes();
 }
 
 // explicit instantiations

@@ -198,6 +198,7 @@ SOLVE_CASES = [
     ("2d_5x4_p7", lambda: inputs.random2d((5, 4), 7, amp=0.1, seed=10), "gll", "transpose", 1, 0.5),
     ("3d_3x3x2_p4", lambda: inputs.random3d((3, 3, 2), 4, amp=0.15, seed=11), "gll", "transpose", 1, 0.5),
     ("3d_2x2x2_p7_fem", lambda: inputs.random3d((2, 2, 2), 7, amp=0.15, seed=12), "fem", "transpose", 1, 0.16),
+    ("3d_2x2x3_p6", lambda: inputs.random3d((2, 2, 3), 6, amp=0.1, seed=16), "gll", "transpose", 1, 0.5),
     ("2d_66x66_p8_long_lines", lambda: inputs.random2d((66, 66), 8, amp=0.1, seed=13), "gll", "transpose", 1, 0.5),
 ]
 
