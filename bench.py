@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
-    ap.add_argument("--no-batch", action="store_true", help="skip the 256-problem batched measurement")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 256-problem batched and the 3-D 32-RHS measurements")
     ap.add_argument("--roofline-only", action="store_true",
                     help="only the kernel roofline measurements (used for ncu captures of single kernels)")
     ap.add_argument("--roofline-3d", action="store_true",
@@ -210,6 +211,7 @@ def run_ours(args, rank, world):
     roof_hbm = smoother_rooflines(prob, glls, torch, inputs, flush)
     serving = serving_run(glls, inputs) if not args.no_serving else None
     batch = batch_run(glls, inputs, torch) if not args.no_batch else None
+    multirhs = multirhs_run(glls, inputs, torch) if not args.no_batch else None
 
     # whole-job throughput: all ranks' DOF over the slowest rank's time
     ms_step = replicas.max_over_ranks(ms_mixed, world)
@@ -234,6 +236,7 @@ def run_ours(args, rank, world):
         "line_tiles": {f"l{l}_{pn}_ax{a}": c for (l, pn, a), (c, _us) in sorted(tiles.items()) if pn == "f32"},
         "serving": serving,
         "batch": batch,
+        "multirhs_3d": multirhs,
     }
     return res, (u_mixed, u_fp64, wl)
 
@@ -292,14 +295,14 @@ def _time_graph(torch, fn, reps=50):
     return a.elapsed_time(b) / reps
 
 
-def _time_cold(torch, fn, flush, reps=10):
-    """Average time of single launches of fn(stream), L2 flushed before each
+def _time_cold(torch, fn, flush, reps=30):
+    """Median time of single launches of fn(stream), L2 flushed before each
     (data comes from HBM), CUDA events on the launching stream."""
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         for _ in range(2):
             fn(s)
-    tot = 0.0
+    ts = []
     for _ in range(reps):
         with torch.cuda.stream(s):
             # a read-only pass over a buffer twice the L2 evicts the kernel's
@@ -310,8 +313,8 @@ def _time_cold(torch, fn, flush, reps=10):
         fn(s)
         b.record(s)
         b.synchronize()
-        tot += a.elapsed_time(b)
-    return tot / reps
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
 
 
 def _interior_random(torch, shape, dtype):
@@ -399,6 +402,45 @@ def smoother_rooflines(prob, glls, torch, inputs, flush):
         if pb is not prob:
             pb.close()
     return {"peak_source": src, "kernels": out}
+
+
+def multirhs_run(glls, inputs, torch, reps=3):
+    """The 3-D multi-RHS workload: 16^3 hexahedra, p = 7 (1,442,897 nodes),
+    32 seeded right-hand sides solved together (the problem and 31 clones
+    sharing its mesh data, one glls_solve_batch launch), FP32 gamma-cycle
+    inside FP64 flexible CG, to 1e-10.  Outputs on the device, CUDA events."""
+    wl = inputs.terrain3d()
+    t0 = time.perf_counter()
+    base, coords = glls.problem_for(wl, glls.SMOOTHER_GLL)
+    F = wl.sample_rhs(coords)
+    g = wl.sample_dirichlet(coords)
+    probs = [base] + [base.clone() for _ in range(len(F) - 1)]
+    for pr, f in zip(probs, F):
+        pr.set_rhs(f)
+        pr.set_dirichlet(g)
+    setup_s = time.perf_counter() - t0
+    outs = [torch.zeros(base.N, dtype=torch.float64, device="cuda") for _ in probs]
+    o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED, max_iter=300)
+    st = glls.solve_batch(probs, outs, o, raise_on_error=False)      # captures the batch graph
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = glls.solve_batch(probs, outs, o, stream, raise_on_error=False)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    its = np.array([x.iterations for x in st])
+    dof = base.N * len(probs)
+    res = {"workload": wl.name, "nrhs": len(probs), "dof": dof, "ms": float(np.median(ms)),
+           "dof_per_s": dof / (float(np.median(ms)) / 1e3),
+           "converged": int(sum(x.status == glls.OK for x in st)),
+           "iterations": {"median": float(np.median(its)), "max": int(its.max())}, "setup_s": setup_s}
+    for pr in probs[1:]:
+        pr.close()
+    base.close()
+    return res
 
 
 def batch_run(glls, inputs, torch, reps=3):

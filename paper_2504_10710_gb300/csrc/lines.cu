@@ -23,10 +23,14 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// 1 / a, correctly rounded: the reciprocal intrinsic in FP32 (fewer
-// instructions on the reduction's critical path than a division), a
-// division in FP64.
-__device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
+// 1 / a: in FP32 the hardware approximate reciprocal (one instruction on
+// the reduction's critical path, at most 1 ulp from the rounded quotient;
+// pivots are never subnormal), in FP64 a division.
+__device__ __forceinline__ float recip(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
 __device__ __forceinline__ double recip(double a) { return 1.0 / a; }
 
 template <typename T>
