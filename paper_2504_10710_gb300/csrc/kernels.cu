@@ -341,8 +341,12 @@ __global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, 
     }
 }
 
-// Block CR forward step at level l (h = 2^l), one CTA per (kept block, 32
-// rows): for kept block b = (2q + 2) h - 1,
+// Rows of a block per CTA in the block-CR kernels: one per warp, so that a
+// level with few blocks still spreads over many CTAs.
+constexpr int kBcrRows = 8;
+
+// Block CR forward step at level l (h = 2^l), one CTA per (kept block,
+// kBcrRows rows): for kept block b = (2q + 2) h - 1,
 //   w_b = src_b - (L_b A_{b-h}^-1) w_{b-h} - (U_b A_{b+h}^-1) w_{b+h}
 // (the c = R (g - M x) step of Algorithm 1 with x = S^-1 g).  At level 0 the
 // source is the nodal right-hand side r gathered through index, and CTAs
@@ -357,12 +361,12 @@ __global__ void __launch_bounds__(256) bcr_forward_kernel(const T* __restrict__ 
     T* xl = reinterpret_cast<T*>(smem_raw);
     T* xr = xl + m;
     const int h = 1 << l, nk = (nb >> l) / 2;
-    const int row0 = blockIdx.y * 32;
+    const int row0 = blockIdx.y * kBcrRows;
     const bool lvl0 = l == 0;
     const int q = blockIdx.x;
     if (q >= nk) {                                   // level 0: copy eliminated block 2 (q - nk)
         const long long b = 2LL * (q - nk);
-        for (int rr = threadIdx.x; rr < 32; rr += blockDim.x) {
+        for (int rr = threadIdx.x; rr < kBcrRows; rr += blockDim.x) {
             const int row = row0 + rr;
             if (row < m) w[b * m + row] = r[index[b * m + row]];
         }
@@ -378,7 +382,7 @@ __global__ void __launch_bounds__(256) bcr_forward_kernel(const T* __restrict__ 
     const T* F = FH + (size_t)q * 2 * m * ldm;
     const T* Hm = F + (size_t)m * ldm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int rr = warp; rr < 32; rr += 8) {
+    for (int rr = warp; rr < kBcrRows; rr += 8) {
         const int row = row0 + rr;
         if (row >= m) break;
         T s = T(0);
@@ -391,8 +395,8 @@ __global__ void __launch_bounds__(256) bcr_forward_kernel(const T* __restrict__ 
     }
 }
 
-// Block CR back substitution at level l, one CTA per (eliminated block, 32
-// rows): for b = (2s + 1) h - 1,
+// Block CR back substitution at level l, one CTA per (eliminated block,
+// kBcrRows rows): for b = (2s + 1) h - 1,
 //   x_b = A_b^-1 w_b - (A_b^-1 L_b) x_{b-h} - (A_b^-1 U_b) x_{b+h}
 // (y = x + P e of Algorithm 1); the kept neighbours' values are already in
 // e (solved at deeper levels), read and written through index.
@@ -406,7 +410,7 @@ __global__ void __launch_bounds__(256) bcr_backward_kernel(const T* __restrict__
     T* xl = xw + m;
     T* xr = xl + m;
     const int h = 1 << l;
-    const int row0 = blockIdx.y * 32;
+    const int row0 = blockIdx.y * kBcrRows;
     const long long s_ = blockIdx.x;
     const long long b = (2 * s_ + 1) * h - 1, lb = b - h, rb = b + h;
     const bool left = lb >= 0, right = rb < nb;
@@ -420,7 +424,7 @@ __global__ void __launch_bounds__(256) bcr_backward_kernel(const T* __restrict__
     const T* G = Ai + (size_t)m * ldm;
     const T* K = G + (size_t)m * ldm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int rr = warp; rr < 32; rr += 8) {
+    for (int rr = warp; rr < kBcrRows; rr += 8) {
         const int row = row0 + rr;
         if (row >= m) break;
         T v = T(0);
@@ -968,7 +972,7 @@ template <typename T>
 void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, T* w, cudaStream_t st, bool e_boundary_zero) {
     if (!e_boundary_zero) cudaMemsetAsync(e, 0, sizeof(T) * N0, st);
     const int k = C.cr_levels, m = C.m;
-    const unsigned rows = (unsigned)((m + 31) / 32);
+    const unsigned rows = (unsigned)((m + kBcrRows - 1) / kBcrRows);
     for (int l = 0; l < k; ++l) {
         const int a = C.nb >> l, nk = a / 2, ne = (a + 1) / 2;
         const unsigned gx = (unsigned)(l == 0 ? nk + ne : nk);
