@@ -51,19 +51,12 @@ __device__ __forceinline__ float dot_cs(const float* a, const float* b) {
     return s;
 }
 
-// Resident CTAs per SM the register allocation must allow: 3-D FP32 five
-// (at most 51 registers; more loads in flight on the HBM-bound large
-// levels); otherwise one.  (Eight for 2-D FP32 caps it at 32 registers;
-// measured inside the solve that is 0.5-1 % slower than the 48 registers
-// the compiler picks with one.)
-template <typename T, int DIM>
-struct ApplyMinBlocks {
-    static constexpr int value = (sizeof(T) == 4 && DIM == 3) ? 5 : 1;
-};
-
+// Launch bounds (256, 1): at least one resident CTA per SM.  (Eight for 2-D
+// FP32 would cap it at 32 registers; measured inside the solve that is
+// 0.5-1 % slower than the 48 registers the compiler picks with one.)
 template <typename T, int DIM, int P, bool DOT>
-__global__ void __launch_bounds__(256, ApplyMinBlocks<T, DIM>::value) apply_p_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
-                                                      int mask, double* dot, double* part, unsigned* ticket) {
+__global__ void __launch_bounds__(256, 1) apply_p_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
+                                                         int mask, double* dot, double* part, unsigned* ticket) {
     grid_dep_sync();
     constexpr int N1 = P + 1;
     constexpr int NLOC = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
@@ -263,7 +256,10 @@ bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, doubl
         if (L.dim == 3 && !dot && launch_apply_col(L, x, y, mask, st)) return true;
     }
     if (L.dim == 2) return dispatch<T, 2, 16>(L.p, L, x, y, mask, dot, part, ticket, st);
-    return dispatch<T, 3, 8>(L.p, L, x, y, mask, dot, part, ticket, st);
+    // 3-D FP32 is served by the even-odd and column kernels above at every
+    // order up to 8; this kernel keeps 3-D FP64
+    if constexpr (sizeof(T) == 8) return dispatch<T, 3, 8>(L.p, L, x, y, mask, dot, part, ticket, st);
+    return false;
 }
 
 template bool launch_apply_fixed<float>(const DevLevel<float>&, const float*, float*, bool, double*, double*,

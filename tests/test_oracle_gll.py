@@ -80,6 +80,33 @@ def test_derivative_matrix_matches_legendre_closed_form(p):
     np.testing.assert_allclose(gll.derivative_matrix(xi), ref, atol=1e-11 * p ** 2)
 
 
+@pytest.mark.parametrize("p", range(1, 17))
+def test_derivative_matrix_centro_antisymmetric(p):
+    """GLL nodes are symmetric about 0 (x_{p-i} = -x_i), so l_{p-j}(x) = l_j(-x)
+    and D_{p-i, p-j} = -D_ij; the 3-D apply's even-odd sweeps rely on it.
+    With the even and odd halves of u, D u is recovered from half-size
+    products: (Du)_i = A_i + B_i, (Du)_{p-i} = B_i - A_i."""
+    xi, _ = gll.gll(p)
+    np.testing.assert_allclose(xi[::-1], -xi, atol=1e-15)
+    D = gll.derivative_matrix(xi)
+    n, h = p + 1, (p + 1) // 2
+    np.testing.assert_allclose(D[::-1, ::-1], -D, atol=1e-12 * p * p)
+    u = np.random.default_rng(p).standard_normal(n)
+    for M in (D, D.T):
+        ue = u[:h] + u[::-1][:h]
+        uo = u[:h] - u[::-1][:h]
+        E = 0.5 * (M[:h, :h] + M[:h, ::-1][:, :h])
+        O = 0.5 * (M[:h, :h] - M[:h, ::-1][:, :h])
+        A = E @ ue + (M[:h, h] * u[h] if n % 2 else 0.0)
+        B = O @ uo
+        out = np.empty(n)
+        out[:h] = A + B
+        out[::-1][:h] = B - A
+        if n % 2:
+            out[h] = M[h, :h] @ uo
+        np.testing.assert_allclose(out, M @ u, atol=1e-12 * p * p * np.abs(u).max())
+
+
 @pytest.mark.parametrize("pc,pf", [(1, 2), (2, 4), (3, 7), (4, 8), (6, 12), (5, 11)])
 def test_interpolation_exact_up_to_coarse_degree(pc, pf):
     J = gll.interpolation_matrix(pc, pf)
