@@ -104,8 +104,9 @@ struct DevCoarse {
 bool init_kernel_attributes();
 constexpr size_t kMaxDynSmemBytes = 200 * 1024;
 
-// Specialised fast paths (apply.cu, lines.cu); they return false when the
-// case is outside their compiled range and the generic kernels take over.
+// Specialised fast paths (apply.cu with apply_eo.cu and apply_col.cu for
+// 3-D, lines.cu); they return false when the case is outside their compiled
+// range and the generic kernels take over.
 // dot: if non-null, also accumulate sum_e x_e^T (A_e x_e) = x.(A x) for x
 // zero on the boundary; the last block writes it to dot[0] using `part` and
 // `ticket` (see launch_dots).
