@@ -215,7 +215,9 @@ glls_status glls_apply_f64(glls_problem* prob, int level, const double* x, doubl
 glls_status glls_apply_f32(glls_problem* prob, int level, const float* x, float* y, void* stream);
 
 /* x = B_s^-1 g: every interior grid line along axis s solved by cyclic
- * reduction (Def. 3.2, Cor. 3.9); x is written on interior nodes only. */
+ * reduction (Def. 3.2, Cor. 3.9); x is written on interior nodes only.  The
+ * FP32 variant takes each pivot's reciprocal from the hardware approximation
+ * (at most 1 ulp from the rounded quotient). */
 glls_status glls_line_solve_f64(glls_problem* prob, int level, int axis, const double* g, double* x, void* stream);
 glls_status glls_line_solve_f32(glls_problem* prob, int level, int axis, const float* g, float* x, void* stream);
 
