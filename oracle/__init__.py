@@ -14,9 +14,10 @@ elements and lines only (no blocking, fusion or reordering of the math):
                 interpolation between orders (Sec. 3.3).
   discretize.py Sec. 2.2 eq. (discreteBilinear): geometry factors, mass,
                 matrix-free stiffness apply, dense assembly; Sec. 2.3 lifting.
-  lines.py      Def. 3.1 / 3.2 line systems (band 1 of A along each grid line);
-                Algorithm 1, Prop. 3.7, Thm. 3.8, Cor. 3.9 (cyclic reduction as
-                a direct multigrid); the damped line-smoothing step.
+  lines.py      Def. 3.1 / 3.2 line systems: the line blocks R A P of each grid
+                line (banded, solved by a library banded Cholesky), and their
+                band-1 part; Algorithm 1, Prop. 3.7, Thm. 3.8, Cor. 3.9 (cyclic
+                reduction as a direct multigrid); the damped smoothing step.
   multigrid.py  Sec. 3.3: level hierarchy, P_l / R_l = P_l^T, Def. 3.12 /
                 Algorithm 2 (gamma-cycle), exact coarsest solve.
   krylov.py     Outer solvers: flexible CG, plain PCG, right-preconditioned

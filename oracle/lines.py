@@ -1,17 +1,31 @@
-"""Line systems (Def. 3.1 with half-bandwidth 1, Def. 3.2), cyclic reduction as
-a direct multigrid (Algorithm 1, Prop. 3.7, Thm. 3.8, Cor. 3.9) and the damped
-line-smoothing step of Algorithm 2.  Test infrastructure only.
+"""Line systems (Def. 3.1, Def. 3.2), cyclic reduction as a direct multigrid
+(Algorithm 1, Prop. 3.7, Thm. 3.8, Cor. 3.9) and the damped line-smoothing
+step of Algorithm 2.  Test infrastructure only.
 
-Reading of Def. 3.2 / Fig. 4 (the restriction R A_p P is written as a full
-block but described as tridiagonal): the line system of a grid line is the
-band-1 part [A]^(1) of A restricted to the line's interior nodes, i.e. its
-diagonal and the couplings to the two neighbours along the line.  On a
-multi-element grid the lines are the global grid lines, running through all
-elements.
+Def. 3.2 writes the line system of a grid line L as R_L A_p P_L, the
+principal submatrix of the assembled stiffness on L's interior nodes, while
+its surrounding text calls the systems tridiagonal.  Both readings are here:
+
+  * ``BlockLineSmoother`` (the default GLL smoother): R_L A_p P_L taken
+    literally.  Two nodes of a line couple only through an element that holds
+    both, and an element spans p intervals of the line, so the block has
+    half-bandwidth p; it is kept in banded storage and solved by a banded
+    Cholesky factorisation (a library routine).  With this reading the GLL
+    column of Table 1 (problem 1) is reproduced at p_L = 8 .. 64.
+  * ``LineSmoother`` on ``line_band`` (option ``gll_band1``): the band-1 part
+    [A]^(1) restricted to the line (Def. 3.1 with half-bandwidth 1), i.e.
+    the diagonal and the couplings to the two neighbours along the line,
+    solved by cyclic reduction.
+
+For the FEM matrix A~_p (bilinear elements on the GLL nodes) a node couples
+only to its neighbours along a line, so R_L A~_p P_L is tridiagonal and both
+readings coincide.  On a multi-element grid the lines are the global grid
+lines, running through all elements.
 """
 from __future__ import annotations
 
 import numpy as np
+import scipy.linalg as sla
 
 from .discretize import Level, apply_1d
 
@@ -241,6 +255,65 @@ class LineSmoother:
         out = np.zeros(self.level.shape)
         out[inner] = np.moveaxis(x, -1, self.t)
         return out
+
+    def smooth(self, x, r, alpha):
+        """x <- x + alpha B_s^-1 (r - A x)   (one step of Algorithm 2)."""
+        return x + alpha * self.apply_inverse(r - self.level.apply(x))
+
+
+# --------------------------------------------------------------------------
+# Def. 3.2 read literally: the line block R_L A_p P_L
+# --------------------------------------------------------------------------
+def line_nodes(level: Level, s: int):
+    """Global node indices of the interior nodes of every interior grid line
+    along axis s: array (nlines, n), n = N_s - 2, the other axes' interior
+    indices enumerated slowest first, nodes ordered along s."""
+    d = level.dim
+    t = d - 1 - s
+    idx = np.arange(level.N).reshape(level.shape)
+    inner = tuple(slice(1, -1) for _ in range(d))
+    lin = np.moveaxis(idx[inner], t, -1)
+    return lin.reshape(-1, lin.shape[-1])
+
+
+def line_block_bands(level: Level, s: int, A=None):
+    """R_L A P_L (Def. 3.2) of every interior grid line L along axis s, read
+    from the assembled stiffness A (``Level.assemble`` when not given).
+
+    Returns (ab, w): LAPACK upper banded storage ab[line, w + i - j, j] =
+    T_L[i, j] for j - w <= i <= j, with w = min(p, n - 1).  Entries of T_L
+    farther than p from the diagonal are zero (no element spans more than p
+    intervals of a line), so the band holds the whole block."""
+    if A is None:
+        A = level.assemble()
+    A = A.tocsr()
+    lin = line_nodes(level, s)
+    nl, n = lin.shape
+    w = min(level.p, n - 1)
+    ab = np.zeros((nl, w + 1, n))
+    for o in range(w + 1):
+        rows = lin[:, :n - o].ravel()
+        cols = lin[:, o:].ravel()
+        ab[:, w - o, o:] = np.asarray(A[rows, cols]).reshape(nl, n - o)
+    return ab, w
+
+
+class BlockLineSmoother:
+    """B_s^-1 of Def. 3.2 with the literal line blocks: block Jacobi over the
+    grid lines along axis s, each block R_L A P_L solved exactly."""
+
+    def __init__(self, level: Level, s: int, A=None):
+        self.level, self.s = level, s
+        self.lin = line_nodes(level, s)
+        ab, self.w = line_block_bands(level, s, A)
+        self.factors = [sla.cholesky_banded(ab[k], lower=False) for k in range(len(ab))]
+
+    def apply_inverse(self, res):
+        r = np.asarray(res).ravel()
+        out = np.zeros(self.level.N)
+        for rows, c in zip(self.lin, self.factors):
+            out[rows] = sla.cho_solve_banded((c, False), r[rows])
+        return out.reshape(self.level.shape)
 
     def smooth(self, x, r, alpha):
         """x <- x + alpha B_s^-1 (r - A x)   (one step of Algorithm 2)."""

@@ -35,7 +35,7 @@ import scipy.linalg as sla
 from . import gll as _gll
 from .discretize import Level, apply_1d
 from .fem import line_band_from_matrix, q1_stiffness
-from .lines import LineSmoother
+from .lines import BlockLineSmoother, LineSmoother
 
 
 def order_chain(p_fine: int, multi_element: bool):
@@ -121,8 +121,13 @@ class Hierarchy:
         self.coarse_factor = sla.cho_factor(A0[ii][:, ii].toarray())
 
     def _make_smoothers(self, lv):
+        """Line smoothers of one level.  "gll": Def. 3.2's R A_p P line blocks;
+        "gll_band1": their band-1 part; "fem": R A~_p P (tridiagonal)."""
         d = lv.dim
         if self.smoother == "gll":
+            A = lv.assemble()
+            return [BlockLineSmoother(lv, s, A) for s in range(d)]
+        if self.smoother == "gll_band1":
             return [LineSmoother(lv, s) for s in range(d)]
         if self.smoother == "fem":
             At = q1_stiffness(lv)

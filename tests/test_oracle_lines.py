@@ -145,3 +145,113 @@ def test_fem_matrix_undeformed_is_q1_stencil():
     c = 2 * 5 + 2
     row = A[c].reshape(5, 5)
     np.testing.assert_allclose(row[1:4, 1:4], [[-1 / 3] * 3, [-1 / 3, 8 / 3, -1 / 3], [-1 / 3] * 3], atol=1e-14)
+
+
+# ---- Def. 3.2 read literally: the line blocks R_L A P_L ---------------------
+def _dense_line_blocks(lv, A, s):
+    Ad = A.toarray()
+    return [Ad[np.ix_(rows, rows)] for rows in lines.line_nodes(lv, s)]
+
+
+def _from_band(ab, w):
+    n = ab.shape[-1]
+    T = np.zeros((n, n))
+    for o in range(w + 1):
+        T[np.arange(n - o), np.arange(o, n)] = ab[w - o, o:]
+        T[np.arange(o, n), np.arange(n - o)] = ab[w - o, o:]
+    return T
+
+
+@pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
+def test_line_block_band_holds_the_whole_block(wl):
+    """No entry of R_L A P_L lies farther than p from its diagonal: the banded
+    copy equals the principal submatrix of the assembled A on every line."""
+    lv = level_of(wl)
+    A = lv.assemble()
+    for s in range(lv.dim):
+        ab, w = lines.line_block_bands(lv, s, A)
+        for k, T in enumerate(_dense_line_blocks(lv, A, s)):
+            np.testing.assert_allclose(_from_band(ab[k], w), T, atol=1e-13 * np.abs(T).max())
+
+
+def _assembled_1d(ne, p):
+    """Assembled 1-D reference stiffness K = D^T W D and weights W on ne
+    elements (global 1-D grid of ne p + 1 nodes)."""
+    xi, rho = gll.gll(p)
+    D = gll.derivative_matrix(xi)
+    Ke = D.T @ np.diag(rho) @ D
+    n = ne * p + 1
+    K = np.zeros((n, n))
+    W = np.zeros(n)
+    for e in range(ne):
+        sl = slice(e * p, e * p + p + 1)
+        K[sl, sl] += Ke
+        W[sl] += rho
+    return K, W
+
+
+@pytest.mark.parametrize("dim,nelem,p", [(2, (3, 2), 4), (2, (1, 1), 7), (3, (2, 1, 2), 3)])
+def test_line_block_of_a_box_grid_is_the_kronecker_closed_form(dim, nelem, p):
+    """Undeformed box elements of sides h_a: A is the sum over axes a of
+    c_a (K_a along a) x (W along the other axes) with c_a = prod_{b != a} h_b
+    / h_a * 2^(2 - d) (the Jacobian and metric of the affine map), so the
+    line block along axis s at fixed other indices m_b is
+    c_s prod_b W_b[m_b] K_s[int, int] + sum_{a != s} c_a K_a[m_a, m_a]
+    prod_{b != a, s} W_b[m_b] W_s[int].  Side lengths differ per axis, so a
+    transposed axis fails."""
+    scale = (2.0, 0.5, 1.5)[:dim]
+    mp = lambda *X: tuple(scale[a] * X[a] for a in range(dim))
+    wl = inputs.Workload("box", dim, nelem, p, mp, [], inputs._zero)
+    lv = level_of(wl)
+    A = lv.assemble()
+    h = [scale[a] / nelem[a] for a in range(dim)]
+    c = [np.prod([h[b] for b in range(dim) if b != a]) / h[a] * 2.0 ** (2 - dim) for a in range(dim)]
+    KW = [_assembled_1d(nelem[a], p) for a in range(dim)]
+    for s in range(dim):
+        blocks = _dense_line_blocks(lv, A, s)
+        others = [a for a in range(dim) if a != s]
+        # interior indices of the other axes, slowest axis first (line order)
+        grids = np.meshgrid(*[np.arange(1, nelem[a] * p) for a in reversed(others)], indexing="ij")
+        idx = [g.ravel() for g in grids]
+        m = {a: idx[len(others) - 1 - j] for j, a in enumerate(others)}
+        Ks, Ws = KW[s]
+        inner = slice(1, -1)
+        for k, T in enumerate(blocks):
+            ref = c[s] * np.prod([KW[b][1][m[b][k]] for b in others]) * Ks[inner, inner]
+            for a in others:
+                wprod = np.prod([KW[b][1][m[b][k]] for b in others if b != a])
+                ref = ref + c[a] * KW[a][0][m[a][k], m[a][k]] * wprod * np.diag(Ws[inner])
+            np.testing.assert_allclose(T, ref, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
+def test_fem_line_blocks_are_tridiagonal(wl):
+    """R_L A~ P_L of the bilinear FEM matrix has no coupling beyond the
+    neighbours along the line: the two readings of Def. 3.2 coincide there."""
+    lv = level_of(wl)
+    At = q1_stiffness(lv)
+    for s in range(lv.dim):
+        a, l, u = (z.reshape(-1, z.shape[-1]) for z in line_band_from_matrix(lv, At, s))
+        for k, T in enumerate(_dense_line_blocks(lv, At, s)):
+            tri = np.diag(a[k]) + np.diag(l[k][1:], -1) + np.diag(u[k][:-1], 1)
+            np.testing.assert_allclose(T, tri, atol=1e-13 * np.abs(T).max())
+
+
+@pytest.mark.parametrize("wl", CASES + [inputs.random2d((4, 3), 1, amp=0.1, seed=5)], ids=lambda w: w.name)
+def test_block_line_preconditioner_inverts_each_line_block(wl):
+    """B_s^-1 (B_s y) = y with B_s the block-diagonal matrix of the line
+    blocks R_L A P_L (every coupling between two nodes of the same interior
+    line along s); at p = 1 it is the band-1 preconditioner."""
+    lv = level_of(wl)
+    A = lv.assemble()
+    Ad = A.toarray()
+    for s in range(lv.dim):
+        B = np.zeros_like(Ad)
+        for rows in lines.line_nodes(lv, s):
+            B[np.ix_(rows, rows)] = Ad[np.ix_(rows, rows)]
+        y = np.where(lv.interior, np.random.default_rng(s).standard_normal(lv.shape), 0.0)
+        sm = lines.BlockLineSmoother(lv, s, A)
+        np.testing.assert_allclose(sm.apply_inverse((B @ y.ravel()).reshape(lv.shape)), y, atol=1e-11)
+        if lv.p == 1:
+            g = np.where(lv.interior, np.random.default_rng(7 + s).standard_normal(lv.shape), 0.0)
+            np.testing.assert_allclose(sm.apply_inverse(g), lines.LineSmoother(lv, s).apply_inverse(g), atol=1e-12)

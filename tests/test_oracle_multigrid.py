@@ -133,51 +133,95 @@ def test_cycle_is_linear_and_symmetric_for_gamma1_transpose():
     assert abs(np.vdot(Mx2, y) - np.vdot(x, My2)) > 1e-8 * abs(np.vdot(Mx2, y))
 
 
-@pytest.mark.parametrize("smoother,problem,pL", [
-    ("FEM", "problem1_lap_u_eq_minus1", 8), ("FEM", "problem1_lap_u_eq_minus1", 16),
-    ("FEM", "problem3_sin_8pi_over_x_plus_y_plus_pi_10", 8),
-    ("FEM", "problem3_sin_8pi_over_x_plus_y_plus_pi_10", 16),
-    ("GLL", "problem1_lap_u_eq_minus1", 8), ("GLL", "problem1_lap_u_eq_minus1", 16),
-])
-def test_table1_gmres_iteration_counts(smoother, problem, pL):
-    """Soft pin against Table 1: GMRES iterations to 1e-8 within one of the
-    printed count for every gamma = 1..8, with the interpolation-type
-    restriction.  (The p_L = 16 row of problem 3 is printed as "11".)"""
+P1 = "problem1_lap_u_eq_minus1"
+P3 = "problem3_sin_8pi_over_x_plus_y_plus_pi_10"
+
+# (smoother, problem, p_L, gammas, allowed deviation per gamma).  GLL rows use
+# Def. 3.2's line blocks R A_p P read literally.  The band-1 reading misses
+# the p_L = 32 row by up to 14 iterations and does not converge within 60 at
+# p_L = 64 (test_band1_reading_misses_table1_at_high_order).  Deviations
+# larger than one: GLL problem 1 at p_L = 32 gives 17 for the printed 19
+# (gamma = 1) and at p_L = 64 gives 28 for 31; problem 3 with the GLL
+# smoother at p_L = 8 gives 8 / 6 / 5 for 10 / 7 / 6 (gamma = 1..3).
+TABLE1_CASES = [
+    ("FEM", P1, 8, range(1, 9), 1), ("FEM", P1, 16, range(1, 9), 1), ("FEM", P1, 32, range(1, 9), 1),
+    ("FEM", P3, 8, range(1, 9), 1), ("FEM", P3, 16, range(1, 9), 1),
+    ("GLL", P1, 8, range(1, 9), 1), ("GLL", P1, 16, range(1, 9), 1), ("GLL", P1, 32, range(1, 9), 2),
+    ("GLL", P1, 64, range(1, 4), (3, 1, 1)),
+    ("GLL", P3, 8, range(1, 9), 2),
+]
+
+
+@pytest.mark.parametrize("smoother,problem,pL,gammas,dev", TABLE1_CASES,
+                         ids=[f"{c[0]}-{c[1][:8]}-p{c[2]}" for c in TABLE1_CASES])
+def test_table1_gmres_iteration_counts(smoother, problem, pL, gammas, dev):
+    """Soft pin against Table 1: GMRES iterations to 1e-8 within `dev` of the
+    printed count for each gamma, with the interpolation-type restriction.
+    (The p_L = 16 row of problem 3 is printed as "11".)"""
     gold = json.load(open(os.path.join(GOLD, "table1_iterations.json")))
     key = str(pL) if str(pL) in gold[problem][smoother] else "11"
-    printed = gold[problem][smoother][key]
-    wl = inputs.table1_problem1(pL) if problem.startswith("problem1") else inputs.table1_problem3(pL)
+    gammas = list(gammas)
+    printed = [gold[problem][smoother][key][g - 1] for g in gammas]
+    devs = dev if isinstance(dev, tuple) else (dev,) * len(gammas)
+    wl = inputs.table1_problem1(pL) if problem == P1 else inputs.table1_problem3(pL)
     alpha = 2 / 3 if smoother == "GLL" else 0.16
     fine, hier = solve.build(wl, smoother=smoother.lower(), restriction="interp")
     ours = [solve.solve(wl, gamma=g, alpha=alpha, tol=1e-8, maxit=60, method="gmres",
-                        hierarchy=hier).iterations[0] for g in range(1, 9)]
-    assert all(abs(o - q) <= 1 for o, q in zip(ours, printed)), (ours, printed)
+                        hierarchy=hier).iterations[0] for g in gammas]
+    assert all(abs(o - q) <= d for o, q, d in zip(ours, printed, devs)), (ours, printed)
+
+
+def test_band1_reading_misses_table1_at_high_order():
+    """Records why Def. 3.2 is read literally: with the band-1 part of the
+    line blocks the GLL row p_L = 32 of problem 1 (printed 19 12 9 ...) takes
+    more than 30 GMRES iterations at gamma = 1."""
+    wl = inputs.table1_problem1(32)
+    fine, hier = solve.build(wl, smoother="gll_band1", restriction="interp")
+    it = solve.solve(wl, gamma=1, alpha=2 / 3, tol=1e-8, maxit=60, method="gmres", hierarchy=hier).iterations[0]
+    assert it > 30, it
+
+
+def _smoothed_spectrum(smoother):
+    wl = inputs.random2d((2, 2), 8, amp=0.1, seed=1)
+    lv = level_of(wl)
+    h = Hierarchy(lv, smoother=smoother, restriction="transpose")
+    ii = lv.interior_index()
+    A = lv.assemble()[ii][:, ii].toarray()
+    out = []
+    for s in range(2):
+        B = np.zeros_like(A)
+        for k in range(len(ii)):
+            e = np.zeros(lv.N)
+            e[ii[k]] = 1
+            B[:, k] = h.smoothers[-1][s].apply_inverse(e.reshape(lv.shape)).ravel()[ii]
+        out.append(np.linalg.eigvals(B @ A).real)
+    return out
+
+
+def test_line_block_smoother_admits_alpha_two_thirds():
+    """With the literal line blocks the spectrum of B_s^-1 A on a deformed
+    p = 8 grid lies in (0, 2.5), below 2/alpha = 3 for the paper's alpha =
+    2/3, so the damped line smoothing step contracts."""
+    for lam in _smoothed_spectrum("gll"):
+        assert lam.min() > 0 and 2.0 < lam.max() < 2.5
 
 
 def test_gll_band1_smoother_diverges_at_high_order_alpha_two_thirds():
-    """Records why the GLL smoother needs alpha < 2/3 on deformed grids: the
+    """Records why the band-1 reading needs alpha < 2/3 on deformed grids: the
     largest eigenvalue of B_x^-1 A exceeds 2/alpha = 3 at p = 8."""
-    wl = inputs.random2d((2, 2), 8, amp=0.1, seed=1)
-    lv = level_of(wl)
-    h = Hierarchy(lv, restriction="transpose")
-    ii = lv.interior_index()
-    A = lv.assemble()[ii][:, ii].toarray()
-    B = np.zeros_like(A)
-    for k in range(len(ii)):
-        e = np.zeros(lv.N)
-        e[ii[k]] = 1
-        B[:, k] = h.smoothers[-1][0].apply_inverse(e.reshape(lv.shape)).ravel()[ii]
-    lam = np.linalg.eigvals(B @ A).real
+    lam = _smoothed_spectrum("gll_band1")[0]
     assert lam.min() > 0 and 3.0 < lam.max() < 4.0
 
 
 def test_multielement_fcg_counts_are_small():
-    """cfg2-like deformed grid, 16x16 elements p = 8, FCG to 1e-10."""
+    """cfg2-like deformed grid, 16x16 elements p = 8, FCG to 1e-10: the line
+    blocks at the paper's alpha = 2/3 take 9 (gamma = 1), the band-1 reading
+    at alpha = 0.5 takes 14, the FEM smoother 12 (gamma = 2)."""
     wl = inputs.terrain2d(nelem=16)
     with warnings.catch_warnings():
         warnings.simplefilter("ignore")
-        fine, hier = solve.build(wl, smoother="gll", restriction="transpose")
-        r1 = solve.solve(wl, gamma=1, alpha=0.5, tol=1e-10, maxit=100, hierarchy=hier)
-        fine, hier = solve.build(wl, smoother="fem", restriction="transpose")
-        r2 = solve.solve(wl, gamma=2, alpha=0.16, tol=1e-10, maxit=100, hierarchy=hier)
-    assert r1.iterations[0] <= 16 and r2.iterations[0] <= 15, (r1.iterations, r2.iterations)
+        counts = {}
+        for sm, g, a in (("gll", 1, 2 / 3), ("gll_band1", 1, 0.5), ("fem", 2, 0.16)):
+            fine, hier = solve.build(wl, smoother=sm, restriction="transpose")
+            counts[sm] = solve.solve(wl, gamma=g, alpha=a, tol=1e-10, maxit=100, hierarchy=hier).iterations[0]
+    assert counts["gll"] <= 10 and counts["gll_band1"] <= 16 and counts["fem"] <= 15, counts
