@@ -276,25 +276,54 @@ def line_nodes(level: Level, s: int):
     return lin.reshape(-1, lin.shape[-1])
 
 
-def line_block_bands(level: Level, s: int, A=None):
-    """R_L A P_L (Def. 3.2) of every interior grid line L along axis s, read
-    from the assembled stiffness A (``Level.assemble`` when not given).
+def line_block_bands(level: Level, s: int, A=None, Ae=None):
+    """R_L A P_L (Def. 3.2) of every interior grid line L along axis s.
 
     Returns (ab, w): LAPACK upper banded storage ab[line, w + i - j, j] =
     T_L[i, j] for j - w <= i <= j, with w = min(p, n - 1).  Entries of T_L
     farther than p from the diagonal are zero (no element spans more than p
-    intervals of a line), so the band holds the whole block."""
-    if A is None:
-        A = level.assemble()
-    A = A.tocsr()
+    intervals of a line), so the band holds the whole block.
+
+    With A (an assembled sparse stiffness) the entries are read from it.
+    Otherwise they are assembled from the element matrices (``Ae``, or
+    ``Level.element_matrices`` chunk by chunk): R_L A P_L = sum over the
+    elements e of R_L Q_e^T A_e Q_e P_L, i.e. every entry of A_e between two
+    local nodes that differ only in their s index, added at the two nodes'
+    positions on their global line when both are interior unknowns of an
+    interior line."""
     lin = line_nodes(level, s)
     nl, n = lin.shape
     w = min(level.p, n - 1)
     ab = np.zeros((nl, w + 1, n))
-    for o in range(w + 1):
-        rows = lin[:, :n - o].ravel()
-        cols = lin[:, o:].ravel()
-        ab[:, w - o, o:] = np.asarray(A[rows, cols]).reshape(nl, n - o)
+    if A is not None:
+        A = A.tocsr()
+        for o in range(w + 1):
+            rows = lin[:, :n - o].ravel()
+            cols = lin[:, o:].ravel()
+            ab[:, w - o, o:] = np.asarray(A[rows, cols]).reshape(nl, n - o)
+        return ab, w
+    d, n1 = level.dim, level.p + 1
+    n1d = n1 ** d
+    line_of = np.full(level.N, -1)
+    pos_of = np.full(level.N, -1)
+    line_of[lin.ravel()] = np.repeat(np.arange(nl), n)
+    pos_of[lin.ravel()] = np.tile(np.arange(n), nl)
+    # local lines along s: element-local flat indices, (n1^(d-1), n1)
+    loc = np.moveaxis(np.arange(n1d).reshape((n1,) * d), d - 1 - s, -1).reshape(-1, n1)
+    glin = level.lin.reshape(-1, n1d)
+    nE = glin.shape[0]
+    chunk = max(1, int(2e7 // (n1d * n1d)))
+    for e0 in range(0, nE, chunk):
+        e1 = min(nE, e0 + chunk)
+        Ablk = Ae[e0:e1] if Ae is not None else level.element_matrices(slice(e0, e1))
+        gnode = glin[e0:e1][:, loc]                 # (ne, nloc_lines, n1) global nodes
+        li = line_of[gnode]
+        po = pos_of[gnode]
+        for i in range(n1):
+            for i2 in range(i, min(n1, i + w + 1)):
+                vals = Ablk[:, loc[:, i], loc[:, i2]]   # (ne, nloc_lines)
+                ok = (li[:, :, i] >= 0) & (li[:, :, i2] >= 0)
+                np.add.at(ab, (li[:, :, i2][ok], w - (i2 - i), po[:, :, i2][ok]), vals[ok])
     return ab, w
 
 
@@ -302,10 +331,10 @@ class BlockLineSmoother:
     """B_s^-1 of Def. 3.2 with the literal line blocks: block Jacobi over the
     grid lines along axis s, each block R_L A P_L solved exactly."""
 
-    def __init__(self, level: Level, s: int, A=None):
+    def __init__(self, level: Level, s: int, A=None, Ae=None):
         self.level, self.s = level, s
         self.lin = line_nodes(level, s)
-        ab, self.w = line_block_bands(level, s, A)
+        ab, self.w = line_block_bands(level, s, A, Ae)
         self.factors = [sla.cholesky_banded(ab[k], lower=False) for k in range(len(ab))]
 
     def apply_inverse(self, res):

@@ -125,8 +125,9 @@ class Hierarchy:
         "gll_band1": their band-1 part; "fem": R A~_p P (tridiagonal)."""
         d = lv.dim
         if self.smoother == "gll":
-            A = lv.assemble()
-            return [BlockLineSmoother(lv, s, A) for s in range(d)]
+            n1d = (lv.p + 1) ** d
+            Ae = lv.element_matrices() if int(np.prod(lv.nelem)) * n1d * n1d <= 5e7 else None
+            return [BlockLineSmoother(lv, s, Ae=Ae) for s in range(d)]
         if self.smoother == "gll_band1":
             return [LineSmoother(lv, s) for s in range(d)]
         if self.smoother == "fem":

@@ -101,6 +101,7 @@ def test_cr_block_toeplitz_matches_bgn_reduced_system():
 
 CASES = [inputs.random2d((3, 2), 4, amp=0.1, seed=1), inputs.random2d((2, 3), 3, amp=0.15, seed=2),
          inputs.random3d((2, 2, 1), 3, amp=0.15, seed=3)]
+BLOCK_CASES = CASES + [inputs.random2d((1, 1), 6, amp=0.1, seed=6), inputs.random3d((2, 1, 3), 4, amp=0.1, seed=7)]
 
 
 @pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
@@ -162,16 +163,20 @@ def _from_band(ab, w):
     return T
 
 
-@pytest.mark.parametrize("wl", CASES, ids=lambda w: w.name)
+@pytest.mark.parametrize("wl", BLOCK_CASES, ids=lambda w: w.name)
 def test_line_block_band_holds_the_whole_block(wl):
     """No entry of R_L A P_L lies farther than p from its diagonal: the banded
-    copy equals the principal submatrix of the assembled A on every line."""
+    copies, read from the assembled A and summed from the element matrices,
+    both equal the principal submatrix of the assembled A on every line."""
     lv = level_of(wl)
     A = lv.assemble()
     for s in range(lv.dim):
         ab, w = lines.line_block_bands(lv, s, A)
+        ab2, w2 = lines.line_block_bands(lv, s)
+        assert w2 == w
         for k, T in enumerate(_dense_line_blocks(lv, A, s)):
             np.testing.assert_allclose(_from_band(ab[k], w), T, atol=1e-13 * np.abs(T).max())
+            np.testing.assert_allclose(_from_band(ab2[k], w), T, atol=1e-13 * np.abs(T).max())
 
 
 def _assembled_1d(ne, p):
