@@ -34,7 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solved DOF/s to 1e-10 rel. residual (FP32-gamma vs FP64 plain)"
 WORKLOAD = "terrain2d 64x64 quads p=8 (263,169 nodes), y'=y+0.1 sin(2 pi x)(1-y), 16 random Fourier modes"
-GAMMA, ALPHA = 1, 0.5
+GAMMA, ALPHA = 1, 2.0 / 3.0
+SMOOTHER = "GLL line blocks R A_p P (Def. 3.2), alpha 2/3"
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -220,7 +221,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 gamma-cycle / f64 outer", "data": "synthetic (seeded)",
-        "config": {"workload": WORKLOAD, "dof": N, "nrhs": 1, "gamma": GAMMA, "alpha": ALPHA, "smoother": "GLL band-1",
+        "config": {"workload": WORKLOAD, "dof": N, "nrhs": 1, "gamma": GAMMA, "alpha": ALPHA, "smoother": SMOOTHER,
                    "restriction": "P^T", "levels": [8, 4, 2, 1], "tol": 1e-10, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "iterations_mixed": int(np.median(its_mixed)),
@@ -239,9 +240,6 @@ def run_ours(args, rank, world):
         "multirhs_3d": multirhs,
     }
     return res, (u_mixed, u_fp64, wl)
-
-
-FP64_PEAK_GFLOPS = 1250.0     # nominal GB300 FP64 rate (no measured FP64 peak is available)
 
 
 def _peaks():
@@ -325,26 +323,42 @@ def _interior_random(torch, shape, dtype):
     return x.reshape(-1).contiguous()
 
 
+def _fp64_peak_gflops(torch):
+    """GB300's FP64 rate: 2 FP64 fused multiply-adds per clock per SM (the
+    nominal 1.25 TFLOP/s over 152 SMs at 2,070 MHz), times this device's SM
+    count and the maximum SM clock in MEASURED_PEAKS.json."""
+    peaks, _ = _peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return 4.0 * sms * mhz / 1e3, sms, mhz
+
+
 def kernel_roofline(prob, glls, torch):
-    """The bench workload's top kernel in the ncu launch list: the FP64 fine-
-    level stiffness apply of the outer iteration, FP64-ALU bound.  FLOPs per
-    launch from the sum-factorised algorithm: per element 4 (p+1)^3 FMA for
-    the four 1-D contraction sweeps and 4 (p+1)^2 for the geometric factors,
-    2 FLOP per FMA."""
+    """The FP64 fine-level stiffness apply of the outer iteration, in the
+    form the solve launches it: y = A p with the per-CTA partials of p.(A p)
+    fused (flexible CG's p.Ap).  FP64-ALU bound.  FLOPs per launch from the
+    sum-factorised algorithm: per element 4 (p+1)^3 FMA for the four 1-D
+    contraction sweeps and 4 (p+1)^2 for the geometric factors, plus 2 (p+1)^2
+    for the dot, 2 FLOP per FMA."""
     L = prob.levels - 1
     shape = prob.level_shape(L)
     p, E = 8, 64 * 64
     x = _interior_random(torch, shape, torch.float64)
     y = torch.zeros_like(x)
-    ms = _time_graph(torch, lambda s: prob.apply(L, x, y, s))
-    flops = 2.0 * E * (4 * (p + 1) ** 3 + 4 * (p + 1) ** 2)
+    part = torch.zeros(8192, dtype=torch.float64, device="cuda")
+    ms = _time_graph(torch, lambda s: prob.apply_partials(L, x, y, part, s))
+    flops = 2.0 * E * (4 * (p + 1) ** 3 + 5 * (p + 1) ** 2)
     ach = flops / (ms / 1e3) / 1e9
-    return {"bound": "alu", "kernel": "apply_p_kernel<double, 2, 8> (fine-level FP64 stiffness apply)",
-            "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
-            "traffic": _traffic("apply_p_kernel<double,2,8>", "terrain2d_64x64_p8"),
+    peak, sms, mhz = _fp64_peak_gflops(torch)
+    return {"bound": "alu", "kernel": "apply_p_kernel<double, 2, 8, DOT> (fine-level FP64 apply with the fused "
+                                      "p.Ap partials, as launched by the outer iteration)",
+            "achieved": ach, "peak": peak, "unit": "GFLOP/s", "frac": ach / peak,
+            "traffic": _traffic("apply_p_kernel<double,2,8,DOT>", "terrain2d_64x64_p8"),
             "ms_per_launch": ms, "algorithmic_flops": flops,
-            "peak_source": "nominal FP64 rate of the recipe (1.25 TFLOP/s; none measured)",
-            "note": "FMA counted as 2 FLOP; 50 launches replayed from a CUDA graph, CUDA events"}
+            "peak_source": f"derived: 2 FP64 FMA/clk/SM x {sms} SMs (device properties) x {mhz:.0f} MHz "
+                           "(MEASURED_PEAKS.json sm_max_mhz); no FP64 peak is measured",
+            "note": "FMA counted as 2 FLOP; 50 launches replayed from a CUDA graph, CUDA events; y is not "
+                    "re-zeroed between the timed launches (same work)"}
 
 
 def _fp32_apply_kernel(d, p):
@@ -357,14 +371,28 @@ def _fp32_apply_kernel(d, p):
     return f"apply_p_kernel<float, {d}, {p}>", f"apply_p_kernel<float,{d},{p}>"
 
 
+def _line_operator_bytes(shape, p, s, block):
+    """FP32 bytes of the line operator along axis s read by one line solve:
+    the Def. 3.2 line blocks (per element segment (p-1)p/2 + 2(p-1) values,
+    per element-boundary vertex 2) or the band-1 (diag, off) pairs."""
+    d = len(shape)
+    n = shape[d - 1 - s]                      # nodes along s
+    lines = int(np.prod([shape[d - 1 - a] - 2 for a in range(d) if a != s]))
+    if not block:
+        return 8 * lines * (n - 2)
+    E = (n - 1) // p
+    return 4 * lines * E * ((p - 1) * p // 2 + 2 * (p - 1)) + 8 * lines * (E - 1)
+
+
 def smoother_rooflines(prob, glls, torch, inputs, flush):
     """FP32 smoother and operator kernels against HBM: the bench workload's
     fine level (L2-resident between launches, as inside a solve) and the 3-D
     16^3 p = 7 fine level (1.44M nodes; L2 flushed before every launch).
     Algorithmic bytes per launch: apply x + G + y (4 + 4 B per node plus
-    ncomp (p+1)^d 4 B per element); line solve (B^-1 g) band 8 B + g + x
-    4 B each per node; smoothing step (apply + damped line update, the K2
-    step of the scope table) x, r read, x written, band and G."""
+    ncomp (p+1)^d 4 B per element); line solve (B^-1 g) the line operator
+    (_line_operator_bytes) + g + x 4 B each per node; smoothing step (apply +
+    damped line update, the K2 step of the scope table) x, r read, x written,
+    the line operator and G."""
     peaks, src = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     out = []
@@ -395,10 +423,12 @@ def smoother_rooflines(prob, glls, torch, inputs, flush):
         kname, tkey = _fp32_apply_kernel(d, p)
         entry(kname, work, tm(lambda s: pb.apply(L, x, y, s)), 8 * N + G, cold, tkey)
         for ax in range(d):
-            entry(f"line_warp_kernel<float> B^-1 g, axis {ax}", work, tm(lambda s: pb.line_solve(L, ax, r, x, s)),
-                  16 * N, cold, f"line_warp_kernel<float>_ax{ax}")
-            entry(f"smoothing step (apply + line_warp_kernel MODE 1), axis {ax}", work,
-                  tm(lambda s: pb.smooth(L, ax, 0.5, r, x, s)), 20 * N + G, cold, None)
+            ob = _line_operator_bytes(shape, p, ax, True)
+            entry(f"line_block_kernel<float, {p}> B^-1 g, axis {ax}", work,
+                  tm(lambda s: pb.line_solve(L, ax, r, x, s)), 8 * N + ob, cold,
+                  f"line_block_kernel<float,{p}>_ax{ax}")
+            entry(f"smoothing step (apply + line_block_kernel MODE 1), axis {ax}", work,
+                  tm(lambda s: pb.smooth(L, ax, ALPHA, r, x, s)), 12 * N + G + ob, cold, None)
         if pb is not prob:
             pb.close()
     return {"peak_source": src, "kernels": out}
@@ -447,19 +477,19 @@ def batch_run(glls, inputs, torch, reps=3):
     """The batched uneven workload: 256 independent 2-D problems (n x n
     elements, n ~ U{4..64}, p ~ U{4..12}, amplitude ~ U(0, 0.2); 26.3 M DOF)
     solved together in one graph launch (glls_solve_batch), FP32 gamma-cycle
-    with the FEM line smoother (alpha = 0.16) inside FP64 flexible CG, to
+    with the GLL line-block smoother (alpha = 2/3) inside FP64 flexible CG, to
     1e-10.  Outputs stay on the device; CUDA events around each launch."""
     ws = inputs.batch_uneven()
     t0 = time.perf_counter()
     probs = []
     for w in ws:
-        pr, coords = glls.problem_for(w, glls.SMOOTHER_FEM)
+        pr, coords = glls.problem_for(w, glls.SMOOTHER_GLL)
         pr.set_rhs(w.sample_rhs(coords)[0])
         pr.set_dirichlet(w.sample_dirichlet(coords))
         probs.append(pr)
     setup_s = time.perf_counter() - t0
     outs = [torch.zeros(p.N, dtype=torch.float64, device="cuda") for p in probs]
-    o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=0.16, precision=glls.PREC_MIXED, max_iter=300)
+    o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED, max_iter=300)
     st = glls.solve_batch(probs, outs, o, raise_on_error=False)      # captures the batch graph
     stream = torch.cuda.current_stream()
     ms = []
@@ -477,9 +507,7 @@ def batch_run(glls, inputs, torch, reps=3):
            "converged": int(sum(x.status == glls.OK for x in st)),
            "iterations": {"median": float(np.median(its)), "p90": float(np.percentile(its, 90)),
                           "max": int(its.max())},
-           "smoother": "FEM band-1, alpha 0.16", "setup_s": setup_s,
-           "note": "the GLL band-1 smoother (alpha 0.5) leaves 96 of the 256 unconverged (p >= 9 or large "
-                   "amplitude); the FEM line smoother converges for all"}
+           "smoother": SMOOTHER, "setup_s": setup_s}
     for p in probs:
         p.close()
     return res
@@ -537,7 +565,37 @@ def serving_run(glls, inputs, nreq=120, rate=200.0, seed=5):
             "slots": 4, "pool": [p[0].name for p in pool]}
 
 
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(barrier, results):
+    """One host core: build the oracle hierarchy (untimed), wait for the
+    others, then one full FP64 oracle solve of the bench workload."""
+    from oracle import solve as osolve
+    from paper_2504_10710_gb300 import inputs
+    wl = inputs.terrain2d()
+    fine, h = osolve.build(wl, restriction="transpose")
+    barrier.wait()
+    t0 = time.perf_counter()
+    r = osolve.solve(wl, gamma=GAMMA, alpha=ALPHA, tol=1e-10, maxit=200, hierarchy=h)
+    results.put((time.perf_counter() - t0, fine.N, r.iterations[0]))
+
+
 def oracle_baseline(wl, u_ref_gpu=None):
+    """The FP64 oracle on the host cores: one solve on one core (with its
+    result, used for parity), then one solve per core on all cores at once
+    (spawned processes, one BLAS thread each; throughput = cores x DOF / wall
+    time from a common start)."""
+    import multiprocessing as mp
     from oracle import solve as osolve
     t0 = time.perf_counter()
     fine, h = osolve.build(wl, restriction="transpose")
@@ -546,9 +604,38 @@ def oracle_baseline(wl, u_ref_gpu=None):
     r = osolve.solve(wl, gamma=GAMMA, alpha=ALPHA, tol=1e-10, maxit=200, hierarchy=h)
     ts = time.perf_counter() - t0
     N = fine.N
-    out = {"value": N / ts, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-           "sample": f"one full FP64 solve of the same workload ({r.iterations[0]} FCG iterations, {ts:.1f} s; "
-                     f"setup {tb:.1f} s excluded)"}
+    one_core = N / ts
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores + 1)
+    results = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(barrier, results)) for _ in range(cores)]
+    for pr in procs:
+        pr.start()
+    all_cores, wall = None, None
+    try:
+        barrier.wait(timeout=600)
+        t0 = time.perf_counter()
+        got = [results.get(timeout=600) for _ in procs]
+        wall = time.perf_counter() - t0
+        all_cores = sum(n for _, n, _ in got) / wall
+    except Exception as exc:        # report the one-core figure if the pool fails
+        print(f"all-core oracle baseline failed: {exc!r}", file=sys.stderr)
+    for pr in procs:
+        pr.join(timeout=60)
+        if pr.is_alive():
+            pr.terminate()
+    model = _cpu_model()
+    if all_cores is not None:
+        out = {"value": all_cores, "unit": "DOF/s", "cores": cores, "kind": "oracle", "cpu_model": model,
+               "one_core_value": one_core,
+               "sample": f"{cores} concurrent full FP64 solves of the same workload, one per host core "
+                         f"({wall:.1f} s wall from a common start; {r.iterations[0]} FCG iterations each); "
+                         f"one core alone: {ts:.1f} s per solve; setup {tb:.1f} s excluded"}
+    else:
+        out = {"value": one_core, "unit": "DOF/s", "cores": 1, "kind": "oracle", "cpu_model": model,
+               "sample": f"one full FP64 solve of the same workload ({r.iterations[0]} FCG iterations, "
+                         f"{ts:.1f} s; setup {tb:.1f} s excluded)"}
     return out, r
 
 

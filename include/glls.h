@@ -6,7 +6,7 @@
  * Paper passages (arXiv 2504.10710):
  *   Sec. 2.2, eq. (discreteBilinear)   stiffness A_p, diagonal mass M_p
  *   Sec. 2.3                            Dirichlet lifting f0 = M f - A v, u = w + v
- *   Def. 3.1, Def. 3.2, Fig. 4          band-1 line systems, line preconditioners
+ *   Def. 3.1, Def. 3.2, Fig. 4          line systems R A_p P, line preconditioners
  *   Algorithm 1, Prop. 3.7, Thm. 3.8,
  *   Cor. 3.9                            cyclic reduction as a direct multigrid
  *   Sec. 3.3, Def. 3.12, Algorithm 2    p-transfers, gamma-cycle, M_0^-1 = A_0^-1
@@ -53,7 +53,17 @@ typedef enum {
 } glls_status;
 
 enum { GLLS_PREC_FP64 = 0, GLLS_PREC_MIXED = 1 };          /* gamma-cycle in FP64, or FP32 */
-enum { GLLS_SMOOTHER_GLL = 0, GLLS_SMOOTHER_FEM = 1 };     /* line systems from A_p or A~_p */
+/* Line systems of the line smoother (Def. 3.2):
+ *   GLL        the line blocks R A_p P, i.e. every coupling of A_p between two
+ *              nodes of the grid line (half-bandwidth p; solved exactly by
+ *              condensing each element segment's interior and cyclic reduction
+ *              on the element-boundary vertices, Thm. 3.8 / Prop. 3.7 /
+ *              Cor. 3.9).  Lines of at most 256 elements and 2047 interior
+ *              nodes; on p = 1 levels the block is tridiagonal.
+ *   FEM        R A~_p P of the bilinear FEM matrix on the GLL nodes (tridiagonal).
+ *   GLL_BAND1  the band-1 part (Def. 3.1, half-bandwidth 1) of the GLL line
+ *              blocks: diagonal and neighbour couplings along the line. */
+enum { GLLS_SMOOTHER_GLL = 0, GLLS_SMOOTHER_FEM = 1, GLLS_SMOOTHER_GLL_BAND1 = 2 };
 enum { GLLS_RESTRICT_TRANSPOSE = 0, GLLS_RESTRICT_INTERP = 1 };
 enum { GLLS_KRYLOV_FCG = 0, GLLS_KRYLOV_PCG = 1, GLLS_KRYLOV_GMRES = 2 };
 /* Exact solver of the coarsest level (A_0^-1 of Algorithm 2):
@@ -121,6 +131,7 @@ typedef struct {
     size_t device_bytes;        /* device memory held by the problem */
     int coarse_cr_levels;       /* block-CR levels of the coarsest solve (0 = dense inverse) */
     long long coarse_dense_unknowns;   /* size of the densely inverted system */
+    size_t instance_bytes;      /* device memory this instance owns alone: what a clone adds */
 } glls_info;
 
 /* Reference GLL(p) nodes and weights (Def. 2.1); xi, rho: host arrays of p+1. */
@@ -137,6 +148,11 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out);
  * copied.  Synchronous. */
 glls_status glls_problem_clone(const glls_problem* prob, glls_problem** out);
 void glls_problem_destroy(glls_problem* prob);
+/* Failure injection for tests (no counterpart in the paper): after n more
+ * device allocations by the library, further ones fail as if the device were
+ * out of memory (the calls report GLLS_ERR_OOM and free what they had
+ * allocated); n < 0 turns it off.  Process-wide. */
+void glls_debug_fail_alloc_after(long long n);
 glls_status glls_problem_info(const glls_problem* prob, glls_info* out);
 
 /* Dirichlet data g (N fine-grid values; only boundary entries are read) and
@@ -180,15 +196,19 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes);
  * and Krylov state) keyed by the mesh.  Requests are admitted in arrival
  * order as soon as a slot is free and the resident bytes plus the request's
  * estimate fit the budget (idle cached meshes are evicted, least recently
- * used first); a request whose mesh is resident but busy waits for it while
- * later requests for other meshes go ahead.  Admitted requests run
- * concurrently on the device.  A request whose estimate exceeds the whole
- * budget fails with GLLS_ERR_BUDGET. */
+ * used first).  A request for a resident mesh runs on an idle instance of it;
+ * when every instance is busy it runs on a new clone (glls_problem_clone:
+ * the mesh data is shared, the clone adds its instance_bytes) if those bytes
+ * fit, else it waits for an instance while later requests go ahead.  Admitted
+ * requests run concurrently on the device.  A request whose estimate exceeds
+ * the whole budget fails with GLLS_ERR_BUDGET. */
 typedef struct glls_server glls_server;
 typedef struct {
     unsigned long long submitted, completed, failed, queued, running;
     size_t resident_bytes, budget_bytes;
-    int cached_problems;
+    int cached_problems;         /* resident meshes */
+    int cached_instances;        /* their instances (set-up problems and clones) */
+    unsigned long long clones;   /* clones created so far */
 } glls_server_info;
 
 glls_status glls_server_create(int device, size_t hbm_budget_bytes, int slots, glls_server** out);
@@ -205,12 +225,25 @@ glls_status glls_submit(glls_server* server, const glls_mesh_desc* mesh, const d
  * finished ticket is released by the first poll that returns its result. */
 glls_status glls_poll(glls_server* server, unsigned long long ticket, int wait, glls_stats* stats);
 glls_status glls_server_info_get(glls_server* server, glls_server_info* out);
+/* Removes a request that is still queued: GLLS_OK (its ticket is released and
+ * u is never written), GLLS_NOT_READY if it is already running, or
+ * GLLS_ERR_INVALID for an unknown or released ticket. */
+glls_status glls_cancel(glls_server* server, unsigned long long ticket);
 
 /* ---- level operations on device vectors (parity tests, custom drivers) ----
  * Each exists as _f64 and _f32; the FP32 variant uses the FP32 copies of the
  * level data (the mixed-precision gamma-cycle). */
 
 /* y = A_l x on interior rows (boundary rows of y set to 0), eq. (discreteBilinear). */
+/* The FP64 apply as the outer iteration launches it (Sec. 2.2; the p.Ap of
+ * flexible CG fused): y += A_l x on interior rows, and `partials` (device,
+ * `capacity` doubles) receives the per-CTA partial sums of x.(A x), whose sum
+ * is x.(A x) for x zero on the boundary.  y must be zero on entry (element-
+ * boundary rows are accumulated); *count (host) is set to the number of
+ * partials, and GLLS_ERR_INVALID is returned without device work when
+ * capacity is smaller. */
+glls_status glls_apply_partials_f64(glls_problem* prob, int level, const double* x, double* y, double* partials,
+                                    int capacity, int* count, void* stream);
 glls_status glls_apply_f64(glls_problem* prob, int level, const double* x, double* y, void* stream);
 glls_status glls_apply_f32(glls_problem* prob, int level, const float* x, float* y, void* stream);
 
@@ -247,9 +280,10 @@ glls_status glls_precondition_f32(glls_problem* prob, const glls_solve_opts* opt
 glls_status glls_lift_f64(glls_problem* prob, const double* f, const double* g, double* f0, void* stream);
 
 /* rc = R_l (r - A_l x), like glls_restrict_f32, for callers that cannot
- * call cudaMalloc: code running while a stream is captured in global mode
- * (where allocation calls are prohibited) or under an external allocator that
- * owns all device memory.  This entry point allocates nothing and does not
+ * call cudaMalloc: code running under an external allocator that owns all
+ * device memory (a framework's caching pool sized to the whole GPU), or on a
+ * path that must not pay cudaMalloc's cost and implicit synchronisation
+ * between steps.  This entry point allocates nothing and does not
  * use the problem's own scratch: the apply result and the transfer
  * temporaries live in one fixed library-wide device array of 3 x 262,144
  * floats (3 MiB), which every GPU that loads the library holds until the

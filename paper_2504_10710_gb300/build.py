@@ -1,6 +1,6 @@
 """Builds the in-tree shared library ``libglls.so`` for sm_103a with nvcc.
 
-Three translation units (kernels, C ABI, host set-up) are compiled in
+The translation units (kernels, C ABI, host set-up) are compiled in
 parallel and linked; object files go to ``_build/`` at the repository root.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libglls.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "apply.cu", "apply_col.cu", "apply_eo.cu", "lines.cu", "api.cu", "server.cu", "setup.cpp"]
+SOURCES = ["kernels.cu", "apply.cu", "apply_col.cu", "apply_eo.cu", "lines.cu", "lines_block.cu", "api.cu", "server.cu", "setup.cpp"]
 
 
 def _nvcc() -> str:

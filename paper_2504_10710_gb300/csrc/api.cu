@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -21,10 +22,49 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// Device-wide operations of the library are serialised: stream capture (of
+// the solve graphs) on one side, and on the other the calls that synchronise
+// the whole device (cudaDeviceSynchronize, cudaFree) or change kernel
+// attributes, which are not allowed while any stream of the context is
+// capturing, whichever thread issues them.  Taken around each capture, the
+// device phase of problem_create / problem_clone, and glls_problem_destroy.
+std::recursive_mutex g_device_mutex;
+
+// Failure injection for tests (glls_debug_fail_alloc_after): when >= 0, the
+// number of device allocations that may still succeed; later ones fail with
+// cudaErrorMemoryAllocation as if cudaMalloc had run out of memory.
+std::atomic<long long> g_alloc_countdown{-1};
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    if (g_alloc_countdown.load() >= 0 && g_alloc_countdown.fetch_sub(1) <= 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 glls_status fail(glls_status s, const std::string& msg) {
     g_last_error = msg;
     return s;
 }
+
+// Makes the problem's device current for the duration of an entry point and
+// restores the caller's current device when it returns.
+struct DeviceScope {
+    int prev = -1;
+    bool restore = false;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceScope(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) {
+            err = cudaSetDevice(dev);
+            restore = err == cudaSuccess;
+        }
+    }
+    ~DeviceScope() {
+        if (restore) cudaSetDevice(prev);
+    }
+};
 
 #define CK(call)                                                                                   \
     do {                                                                                           \
@@ -53,7 +93,7 @@ struct SharedData {
     std::vector<void*> allocs;
     size_t bytes = 0;
     ~SharedData() {
-        cudaSetDevice(device);
+        DeviceScope scope(device);
         for (void* a : allocs) cudaFree(a);
     }
 };
@@ -100,7 +140,7 @@ struct glls_problem {
     template <typename T>
     cudaError_t alloc(T** ptr, size_t count) {
         void* p_ = nullptr;
-        cudaError_t e = cudaMalloc(&p_, sizeof(T) * (count ? count : 1));
+        cudaError_t e = dev_malloc(&p_, sizeof(T) * (count ? count : 1));
         if (e != cudaSuccess) return e;
         allocs.push_back(p_);
         bytes += sizeof(T) * (count ? count : 1);
@@ -113,7 +153,7 @@ struct glls_problem {
         T* d = nullptr;
         void* p_ = nullptr;
         const size_t count = src.size() ? src.size() : 1;
-        cudaError_t e = cudaMalloc(&p_, sizeof(T) * count);
+        cudaError_t e = dev_malloc(&p_, sizeof(T) * count);
         if (e != cudaSuccess) return e;
         shared->allocs.push_back(p_);
         shared->bytes += sizeof(T) * count;
@@ -128,6 +168,13 @@ struct glls_problem {
 namespace {
 
 // Per-instance work vectors of every level (zeroed: boundary entries stay zero).
+// Owns a problem under construction: a failed create or clone releases
+// everything allocated so far through glls_problem_destroy.
+struct ProblemDeleter {
+    void operator()(glls_problem* P) const { glls_problem_destroy(P); }
+};
+using ProblemPtr = std::unique_ptr<glls_problem, ProblemDeleter>;
+
 template <typename T>
 glls_status alloc_level_vectors(glls_problem* P, std::vector<LevelStore<T>>& Ls) {
     for (auto& s : Ls) {
@@ -209,12 +256,30 @@ glls_status upload_levels(glls_problem* P, const std::vector<LevelHost>& H, std:
             }
             V2* dptr = nullptr;
             void* p_ = nullptr;
-            CK(cudaMalloc(&p_, sizeof(V2) * packed.size()));
+            CK(dev_malloc(&p_, sizeof(V2) * packed.size()));
             P->shared->allocs.push_back(p_);
             P->shared->bytes += sizeof(V2) * packed.size();
             dptr = static_cast<V2*>(p_);
             CK(cudaMemcpy(dptr, packed.data(), sizeof(V2) * packed.size(), cudaMemcpyHostToDevice));
             d.band[a] = dptr;
+        }
+        if (h.lblock) {
+            using V2 = typename Vec2Of<T>::type;
+            for (int a = 0; a < h.dim; ++a) {
+                CK(P->upload(&d.blk[a], h.blk[a]));
+                const size_t nv = h.vband[a].size() / 2;
+                std::vector<V2> packed(nv ? nv : 1);
+                for (size_t i = 0; i < nv; ++i) {
+                    packed[i].x = (T)h.vband[a][2 * i];
+                    packed[i].y = (T)h.vband[a][2 * i + 1];
+                }
+                void* p_ = nullptr;
+                CK(dev_malloc(&p_, sizeof(V2) * packed.size()));
+                P->shared->allocs.push_back(p_);
+                P->shared->bytes += sizeof(V2) * packed.size();
+                CK(cudaMemcpy(p_, packed.data(), sizeof(V2) * packed.size(), cudaMemcpyHostToDevice));
+                d.vband[a] = static_cast<const V2*>(p_);
+            }
         }
         if (l > 0) {
             for (int a = 0; a < h.dim; ++a) {
@@ -502,6 +567,7 @@ cudaError_t capture_solve(glls_problem* P, const glls_solve_opts* o, cudaStream_
 // The whole solve as one cached graph (device-side loop).
 glls_status get_solve_graph(glls_problem* P, const glls_solve_opts* o) {
     if (P->solve_exec && same_solve_key(P->solve_key, *o)) return GLLS_OK;
+    std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
     if (P->solve_exec) {
         cudaGraphExecDestroy(P->solve_exec);
         P->solve_exec = nullptr;
@@ -572,6 +638,7 @@ glls_status get_iteration_graph(glls_problem* P, const glls_solve_opts* o) {
     if (P->iter_exec && P->g_gamma == o->gamma && P->g_m == o->m && P->g_prec == o->precision &&
         P->g_krylov == o->krylov && P->g_alpha == o->alpha)
         return GLLS_OK;
+    std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
     if (P->iter_exec) {
         cudaGraphExecDestroy(P->iter_exec);
         P->iter_exec = nullptr;
@@ -749,28 +816,41 @@ glls_status glls_gll(int p, double* xi, double* rho) {
     return GLLS_OK;
 }
 
-glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) {
+static glls_status problem_create(const glls_mesh_desc* desc, glls_problem** out) {
     if (!desc || !out) return fail(GLLS_ERR_INVALID, "null argument");
     *out = nullptr;
     if (desc->dim != 2 && desc->dim != 3) return fail(GLLS_ERR_INVALID, "dim must be 2 or 3");
-    if (desc->order < 1 || desc->order > 24) return fail(GLLS_ERR_INVALID, "order must be in 1..24");
+    // the generic apply stages an element in shared memory: (p+1)^2 (2-D) or (p+1)^3 (3-D) nodes
+    if (desc->order < 1 || desc->order > (desc->dim == 2 ? 64 : 16))
+        return fail(GLLS_ERR_INVALID, "order must be in 1..64 (2-D) or 1..16 (3-D)");
     for (int a = 0; a < desc->dim; ++a)
         if (desc->nelem[a] < 1 || desc->nelem[a] > 4096) return fail(GLLS_ERR_INVALID, "nelem out of range");
     if (!desc->coords) return fail(GLLS_ERR_INVALID, "coords is NULL");
     bool multi = desc->nelem[0] > 1 || desc->nelem[1] > 1 || (desc->dim == 3 && desc->nelem[2] > 1);
     if (!multi && desc->order < 2) return fail(GLLS_ERR_INVALID, "a single element needs order >= 2");
-    if (desc->smoother != GLLS_SMOOTHER_GLL && desc->smoother != GLLS_SMOOTHER_FEM)
+    if (desc->smoother != GLLS_SMOOTHER_GLL && desc->smoother != GLLS_SMOOTHER_FEM &&
+        desc->smoother != GLLS_SMOOTHER_GLL_BAND1)
         return fail(GLLS_ERR_INVALID, "bad smoother");
     if (desc->restriction != GLLS_RESTRICT_TRANSPOSE && desc->restriction != GLLS_RESTRICT_INTERP)
         return fail(GLLS_ERR_INVALID, "bad restriction");
+    if (desc->smoother == GLLS_SMOOTHER_GLL && desc->order >= 2)
+        for (int a = 0; a < desc->dim; ++a)
+            if (!line_block_supported(desc->nelem[a] * desc->order - 1, desc->nelem[a]))
+                return fail(GLLS_ERR_INVALID, "GLL line-block smoother: at most " + std::to_string(kMaxBlockSegments) +
+                                                  " elements and " + std::to_string(kMaxBlockLine) +
+                                                  " interior nodes per grid line");
     auto t0 = std::chrono::steady_clock::now();
-    CK(cudaSetDevice(desc->device));
+    DeviceScope scope(desc->device);
+    CK(scope.err);
     static std::once_flag once;
     static bool attrs_ok = false;
-    std::call_once(once, [] { attrs_ok = init_kernel_attributes(); });
+    std::call_once(once, [] {
+        std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
+        attrs_ok = init_kernel_attributes();
+    });
     if (!attrs_ok) return fail(GLLS_ERR_CUDA, "could not set kernel shared-memory attributes");
 
-    std::unique_ptr<glls_problem> P(new glls_problem());
+    ProblemPtr P(new glls_problem());
     P->shared = std::make_shared<SharedData>();
     P->shared->device = desc->device;
     P->device = desc->device;
@@ -811,6 +891,7 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
     if (!err.empty()) return fail(GLLS_ERR_BREAKDOWN, err);
     if (C.cr_levels > kMaxCrLevels) return fail(GLLS_ERR_INVALID, "too many block-CR levels");
 
+    std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
     glls_status st = upload_levels<double>(P.get(), H, P->L64);
     if (st != GLLS_OK) return st;
     st = upload_levels<float>(P.get(), H, P->L32);
@@ -832,11 +913,13 @@ glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) 
     return GLLS_OK;
 }
 
-glls_status glls_problem_clone(const glls_problem* src, glls_problem** out) {
+static glls_status problem_clone(const glls_problem* src, glls_problem** out) {
     if (!src || !out) return fail(GLLS_ERR_INVALID, "null argument");
     *out = nullptr;
-    CK(cudaSetDevice(src->device));
-    std::unique_ptr<glls_problem> P(new glls_problem());
+    DeviceScope scope(src->device);
+    CK(scope.err);
+    ProblemPtr P(new glls_problem());
+    std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
     P->shared = src->shared;
     P->device = src->device;
     P->dim = src->dim;
@@ -859,19 +942,39 @@ glls_status glls_problem_clone(const glls_problem* src, glls_problem** out) {
     glls_status st = alloc_level_vectors<double>(P.get(), P->L64);
     if (st == GLLS_OK) st = alloc_level_vectors<float>(P.get(), P->L32);
     if (st == GLLS_OK) st = alloc_instance(P.get());
-    if (st != GLLS_OK) {
-        for (void* a : P->allocs) cudaFree(a);
-        return st;
-    }
+    if (st != GLLS_OK) return st;
     CK(cudaDeviceSynchronize());
     *out = P.release();
     return GLLS_OK;
 }
 
+// Host allocations of the set-up (std::vector) report GLLS_ERR_OOM instead of
+// throwing across the ABI.
+glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) {
+    try {
+        return problem_create(desc, out);
+    } catch (const std::bad_alloc&) {
+        return fail(GLLS_ERR_OOM, "host allocation failed during set-up");
+    } catch (const std::exception& e) {
+        return fail(GLLS_ERR_INVALID, std::string("set-up failed: ") + e.what());
+    }
+}
+
+glls_status glls_problem_clone(const glls_problem* src, glls_problem** out) {
+    try {
+        return problem_clone(src, out);
+    } catch (const std::bad_alloc&) {
+        return fail(GLLS_ERR_OOM, "host allocation failed during clone");
+    }
+}
+
+void glls_debug_fail_alloc_after(long long n) { g_alloc_countdown.store(n < 0 ? -1 : n); }
+
 void glls_problem_destroy(glls_problem* P) {
     if (!P) return;
+    std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
     forget_batches_of(P);
-    cudaSetDevice(P->device);
+    DeviceScope scope(P->device);
     if (P->iter_exec) cudaGraphExecDestroy(P->iter_exec);
     if (P->solve_exec) cudaGraphExecDestroy(P->solve_exec);
     if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
@@ -895,12 +998,14 @@ glls_status glls_problem_info(const glls_problem* P, glls_info* out) {
     out->coarse_cr_levels = P->C64.cr_levels;
     out->coarse_dense_unknowns = P->C64.nr;
     out->device_bytes = P->bytes + (P->shared ? P->shared->bytes : 0);
+    out->instance_bytes = P->bytes;
     return GLLS_OK;
 }
 
 glls_status glls_set_dirichlet(glls_problem* P, const double* g, int on_device, void* stream) {
     if (!P || !g) return fail(GLLS_ERR_INVALID, "null argument");
-    CK(cudaSetDevice(P->device));
+    DeviceScope scope(P->device);
+    CK(scope.err);
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(P->g, g, sizeof(double) * P->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     if (!on_device) CK(cudaStreamSynchronize(st));
@@ -910,7 +1015,8 @@ glls_status glls_set_dirichlet(glls_problem* P, const double* g, int on_device, 
 
 glls_status glls_set_rhs(glls_problem* P, const double* f, int on_device, void* stream) {
     if (!P || !f) return fail(GLLS_ERR_INVALID, "null argument");
-    CK(cudaSetDevice(P->device));
+    DeviceScope scope(P->device);
+    CK(scope.err);
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(P->f, f, sizeof(double) * P->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     if (!on_device) CK(cudaStreamSynchronize(st));
@@ -930,13 +1036,14 @@ glls_status glls_lift_f64(glls_problem* P, const double* f, const double* g, dou
     return GLLS_OK;
 }
 
-glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int on_device, void* stream,
-                       glls_stats* stats) {
+static glls_status solve_impl(glls_problem* P, const glls_solve_opts* o, double* u, int on_device, void* stream,
+                              glls_stats* stats) {
     if (!P || !u) return fail(GLLS_ERR_INVALID, "null argument");
     glls_status s0 = check_opts(o);
     if (s0 != GLLS_OK) return s0;
     if (!P->has_rhs) return fail(GLLS_ERR_INVALID, "right-hand side not set");
-    CK(cudaSetDevice(P->device));
+    DeviceScope scope(P->device);
+    CK(scope.err);
     cudaStream_t st = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     const long long N = P->N;
@@ -1037,10 +1144,22 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
     return result;
 }
 
+// stats is filled on every return: its status is the call's status even where
+// the solve stopped before any iteration.
+glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int on_device, void* stream,
+                       glls_stats* stats) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    const glls_status r = solve_impl(P, o, u, on_device, stream, stats);
+    if (stats) stats->status = r;
+    return r;
+}
+
 glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
     if (!desc || !bytes) return fail(GLLS_ERR_INVALID, "null argument");
     if (desc->dim != 2 && desc->dim != 3) return fail(GLLS_ERR_INVALID, "dim must be 2 or 3");
-    if (desc->order < 1 || desc->order > 24) return fail(GLLS_ERR_INVALID, "order must be in 1..24");
+    // the generic apply stages an element in shared memory: (p+1)^2 (2-D) or (p+1)^3 (3-D) nodes
+    if (desc->order < 1 || desc->order > (desc->dim == 2 ? 64 : 16))
+        return fail(GLLS_ERR_INVALID, "order must be in 1..64 (2-D) or 1..16 (3-D)");
     const int d = desc->dim;
     long long ne[3] = {1, 1, 1}, E = 1;
     for (int a = 0; a < d; ++a) {
@@ -1069,6 +1188,15 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
         total += 12.0 * ((double)ncomp * E * nloc + (1 + d) * (double)N + (p + 1) * (p + 1)) + 12.0 * 5 * N;
         total += 24.0 * d * (double)N;
         total += 2.0 * d * (12.0 * (2 * p + 2) * (double)(ne[0] * p + 1) + 4.0 * (ne[0] * p + 1));
+        if (desc->smoother == GLLS_SMOOTHER_GLL && p >= 2) {
+            // condensed line blocks: per segment (p-1)p/2 + 2(p-1) values, per vertex 2 (FP64 + FP32)
+            for (int s = 0; s < d; ++s) {
+                double lines = 1.0;
+                for (int a = 0; a < d; ++a)
+                    if (a != s) lines *= (double)(ne[a] * p - 1);
+                total += 12.0 * lines * ne[s] * ((p - 1) * p / 2.0 + 2.0 * (p - 1)) + 24.0 * lines * ne[s];
+            }
+        }
     }
     // coarsest solve: block-CR operators (FP64 + FP32) and the dense inverse of what is left
     const int p0 = chain.back();
@@ -1107,13 +1235,16 @@ glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve
         for (int j = 0; j < i; ++j)
             if (probs[j] == probs[i]) return fail(GLLS_ERR_INVALID, "glls_solve_batch: a problem appears twice");
     }
-    CK(cudaSetDevice(dev));
+    DeviceScope scope(dev);
+    CK(scope.err);
     cudaStream_t st = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     for (int i = 0; i < n; ++i)
         if (!probs[i]->has_dirichlet) CK(cudaMemsetAsync(probs[i]->g, 0, sizeof(double) * probs[i]->N, st));
     cudaGraphExec_t exec = nullptr;
     {
+        // lock order: device, then batch (as in glls_problem_destroy)
+        std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
         std::lock_guard<std::mutex> lock(g_batch_mutex);
         std::vector<glls_problem*> key(probs, probs + n);
         for (size_t i = 0; i < g_batches.size(); ++i)
@@ -1187,7 +1318,8 @@ glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve
 
 glls_status glls_autotune(glls_problem* P, int* chosen, float* best_us) {
     if (!P) return fail(GLLS_ERR_INVALID, "null problem");
-    CK(cudaSetDevice(P->device));
+    DeviceScope scope(P->device);
+    CK(scope.err);
     const size_t cells = P->L64.size() * 2 * 3;
     if (chosen) std::fill(chosen, chosen + cells, 0);
     if (best_us) std::fill(best_us, best_us + cells, 0.f);
@@ -1200,11 +1332,31 @@ glls_status glls_autotune(glls_problem* P, int* chosen, float* best_us) {
     return s;
 }
 
+// The outer iteration's FP64 apply: y = A_l x with the per-CTA partial sums
+// of x.(A x) fused into the kernel (the consumer adds them).
+glls_status glls_apply_partials_f64(glls_problem* P, int level, const double* x, double* y, double* partials,
+                                    int capacity, int* count, void* stream) {
+    glls_status s = check_level(P, level, false);
+    if (s != GLLS_OK) return s;
+    if (!x || !y || !partials || !count) return fail(GLLS_ERR_INVALID, "null argument");
+    const DevLevel<double>& L = P->L64[level].dev;
+    const int n = apply_dot_partials<double>(L);
+    *count = n;
+    if (capacity < n) return fail(GLLS_ERR_INVALID, "partials: need " + std::to_string(n) + " entries");
+    DeviceScope scope(P->device);
+    CK(scope.err);
+    launch_apply<double>(L, x, y, true, (cudaStream_t)stream, true, partials, partials, nullptr);
+    CK(cudaGetLastError());
+    return GLLS_OK;
+}
+
 #define LEVEL_OPS(SUF, T)                                                                                      \
     glls_status glls_apply_##SUF(glls_problem* P, int level, const T* x, T* y, void* stream) {                  \
         glls_status s = check_level(P, level, false);                                                           \
         if (s != GLLS_OK) return s;                                                                             \
         if (!x || !y) return fail(GLLS_ERR_INVALID, "null vector");                                             \
+        DeviceScope scope(P->device);                                                                           \
+        CK(scope.err);                                                                                          \
         launch_apply<T>(levels_of<T>(P)[level].dev, x, y, true, (cudaStream_t)stream);                          \
         CK(cudaGetLastError());                                                                                 \
         return GLLS_OK;                                                                                         \
@@ -1214,6 +1366,8 @@ glls_status glls_autotune(glls_problem* P, int* chosen, float* best_us) {
         if (s != GLLS_OK) return s;                                                                             \
         if (axis < 0 || axis >= P->dim) return fail(GLLS_ERR_INVALID, "axis out of range");                     \
         if (!g || !x) return fail(GLLS_ERR_INVALID, "null vector");                                             \
+        DeviceScope scope(P->device);                                                                           \
+        CK(scope.err);                                                                                          \
         launch_line_solve<T>(levels_of<T>(P)[level].dev, axis, 0, g, nullptr, nullptr, x, T(1),                 \
                              (cudaStream_t)stream);                                                             \
         CK(cudaGetLastError());                                                                                 \
@@ -1225,6 +1379,8 @@ glls_status glls_autotune(glls_problem* P, int* chosen, float* best_us) {
         if (s != GLLS_OK) return s;                                                                             \
         if (axis < 0 || axis >= P->dim) return fail(GLLS_ERR_INVALID, "axis out of range");                     \
         if (!r || !x) return fail(GLLS_ERR_INVALID, "null vector");                                             \
+        DeviceScope scope(P->device);                                                                           \
+        CK(scope.err);                                                                                          \
         smooth<T>(P, level, axis, alpha, r, x, false, (cudaStream_t)stream);                                    \
         CK(cudaGetLastError());                                                                                 \
         return GLLS_OK;                                                                                         \
@@ -1233,6 +1389,8 @@ glls_status glls_autotune(glls_problem* P, int* chosen, float* best_us) {
         glls_status s = check_level(P, level, true);                                                            \
         if (s != GLLS_OK) return s;                                                                             \
         if (!r || !x || !rc) return fail(GLLS_ERR_INVALID, "null vector");                                      \
+        DeviceScope scope(P->device);                                                                           \
+        CK(scope.err);                                                                                          \
         auto& Ls = levels_of<T>(P);                                                                             \
         launch_apply<T>(Ls[level].dev, x, Ls[level].y, true, (cudaStream_t)stream, true);                       \
         restrict_residual<T>(P, level, r, Ls[level].y, rc, (cudaStream_t)stream);                               \
@@ -1244,12 +1402,16 @@ glls_status glls_autotune(glls_problem* P, int* chosen, float* best_us) {
         glls_status s = check_level(P, level, true);                                                            \
         if (s != GLLS_OK) return s;                                                                             \
         if (!e || !x) return fail(GLLS_ERR_INVALID, "null vector");                                             \
+        DeviceScope scope(P->device);                                                                           \
+        CK(scope.err);                                                                                          \
         prolong_add<T>(P, level, e, x, (cudaStream_t)stream);                                                   \
         CK(cudaGetLastError());                                                                                 \
         return GLLS_OK;                                                                                         \
     }                                                                                                           \
     glls_status glls_coarse_solve_##SUF(glls_problem* P, const T* r, T* e, void* stream) {                      \
         if (!P || !r || !e) return fail(GLLS_ERR_INVALID, "null argument");                                    \
+        DeviceScope scope(P->device);                                                                           \
+        CK(scope.err);                                                                                          \
         launch_coarse<T>(coarse_of<T>(P), levels_of<T>(P)[0].dev.N, r, e, levels_of<T>(P)[0].t1,               \
                          (cudaStream_t)stream);                                                                        \
         CK(cudaGetLastError());                                                                                 \
@@ -1260,6 +1422,8 @@ glls_status glls_autotune(glls_problem* P, int* chosen, float* best_us) {
         if (!P || !r || !z) return fail(GLLS_ERR_INVALID, "null argument");                                     \
         glls_status s = check_opts(o);                                                                          \
         if (s != GLLS_OK) return s;                                                                             \
+        DeviceScope scope(P->device);                                                                           \
+        CK(scope.err);                                                                                          \
         CK(cudaMemsetAsync(z, 0, sizeof(T) * levels_of<T>(P).back().dev.N, (cudaStream_t)stream));               \
         cycle<T>(P, (int)P->L64.size() - 1, r, z, o->gamma, o->m, (T)o->alpha, (cudaStream_t)stream);           \
         CK(cudaGetLastError());                                                                                 \
@@ -1316,9 +1480,8 @@ extern "C" glls_status glls_restrict_noalloc_f32(glls_problem* P, int level, con
         return fail(GLLS_ERR_INVALID, "glls_restrict_noalloc_f32: level has " + std::to_string(F.N) +
                                           " nodes, more than the fixed scratch limit of " +
                                           std::to_string(kNoAllocMaxNodes));
-    int cur_dev = -1;
-    CK(cudaGetDevice(&cur_dev));
-    if (cur_dev != P->device) CK(cudaSetDevice(P->device));
+    DeviceScope scope(P->device);
+    CK(scope.err);
     float* base = nullptr;
     s = noalloc_scratch(P->device, &base);
     if (s != GLLS_OK) return s;
@@ -1326,7 +1489,7 @@ extern "C" glls_status glls_restrict_noalloc_f32(glls_problem* P, int level, con
     float* t[2] = {base + kNoAllocMaxNodes, base + 2 * kNoAllocMaxNodes};
     cudaStream_t st = (cudaStream_t)stream;
     // y must start at zero: the apply sums element contributions into it
-    launch_apply<float>(F, x, y, true, st, false);
+    CK(launch_apply<float>(F, x, y, true, st, false));
     int cur[3] = {F.n[0], F.n[1], F.n[2]};
     const float* in = r;
     const float* in2 = y;

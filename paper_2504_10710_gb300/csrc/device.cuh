@@ -7,6 +7,8 @@
 //                     node index q = (k*(p+1) + j)*(p+1) + i
 //   diag, off[s]    : band-1 line-system coefficients on the global grid;
 //                     off[s][node] couples node and node + e_s
+//   blk[s], vband[s]: Def. 3.2 line blocks condensed per element segment
+//                     (GLL smoother, p >= 2), see DevLevel
 //   D               : (p+1)^2 derivative matrix, D[i*(p+1)+j] = pi_j'(xi_i)
 //   P[a], R[a]      : fixed-width row bands of the 1-D transfer matrices
 #pragma once
@@ -77,6 +79,12 @@ struct DevLevel {
     const typename Vec2Of<T>::type* band[3] = {nullptr, nullptr, nullptr};
     DevBand<T> P[3], R[3];
     int lpb[3] = {4, 4, 4};   // line-solve tile (lines per CTA) per direction, set by the autotuner
+    // Def. 3.2 line blocks condensed per element segment (GLL smoother, p >= 2;
+    // null otherwise): blk[s] [ncoef][nlines * ne[s]] = packed K_I^-1, w_L,
+    // w_R per segment; vband[s] [nlines][ne[s] - 1] = vertex Schur complement
+    // (diagonal, coupling to the next vertex).  See lines_block.cu.
+    const T* blk[3] = {nullptr, nullptr, nullptr};
+    const typename Vec2Of<T>::type* vband[3] = {nullptr, nullptr, nullptr};
 };
 
 // Exact coarsest solve: cr_levels levels of block cyclic reduction over the
@@ -117,6 +125,17 @@ template <typename T>
 bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
                       cudaStream_t st);
 bool init_line_warp_attributes();
+// Line solves with the condensed Def. 3.2 line blocks (lines_block.cu), used
+// whenever L.blk[s] is set; lines of at most kMaxBlockLine unknowns and
+// kMaxBlockSegments elements (checked at set-up).  Returns false only outside
+// that range or when the launch fails.
+constexpr int kMaxBlockLine = 2047;
+constexpr int kMaxBlockSegments = 256;
+bool line_block_supported(int n, int E);
+template <typename T>
+bool launch_line_block(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
+                       cudaStream_t st);
+bool init_line_block_attributes();
 // 3-D FP32 apply with one thread per element column (apply_col.cu), p <= 3
 // (the orders the even-odd kernel does not take); no x.(A x) product.
 // Returns false outside that range.
@@ -135,9 +154,11 @@ bool init_apply_eo_attributes();
 // ---- launchers (all asynchronous on `st`) ---------------------------------
 // y = A x; mask: boundary rows of y are not written.  y_is_zero: the caller
 // guarantees y == 0 on entry (otherwise it is zeroed first).  dot, part,
-// ticket: optional x.(A x) into dot[0] (FP64 only).
+// ticket: optional x.(A x) into dot[0] (FP64 only).  Returns the status of
+// the zeroing (cudaSuccess when y_is_zero); launch errors are left to
+// cudaGetLastError.
 template <typename T>
-void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st, bool y_is_zero = false,
+cudaError_t launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st, bool y_is_zero = false,
                   double* dot = nullptr, double* part = nullptr, unsigned* ticket = nullptr);
 
 // Line solves along axis s.  mode 0: x = B_s^-1 g; mode 1: x += alpha

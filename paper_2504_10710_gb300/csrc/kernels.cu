@@ -870,10 +870,13 @@ constexpr int kMaxDynSmem = 200 * 1024;
 // launchers
 // ---------------------------------------------------------------------------
 template <typename T>
-void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st, bool y_is_zero, double* dot,
-                  double* part, unsigned* ticket) {
-    if (!y_is_zero) cudaMemsetAsync(y, 0, sizeof(T) * L.N, st);
-    if (launch_apply_fixed<T>(L, x, y, mask, dot, part, ticket, st)) return;
+cudaError_t launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st, bool y_is_zero,
+                         double* dot, double* part, unsigned* ticket) {
+    if (!y_is_zero) {
+        const cudaError_t e = cudaMemsetAsync(y, 0, sizeof(T) * L.N, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (launch_apply_fixed<T>(L, x, y, mask, dot, part, ticket, st)) return cudaSuccess;
     int epc = 256 / L.nloc;
     if (epc < 1) epc = 1;
     const long long blocks = (L.E + epc - 1) / epc;
@@ -895,11 +898,18 @@ void launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_
                          part, dot, 0, 0, (unsigned*)nullptr, 0);
         }
     }
+    return cudaSuccess;
 }
 
 template <typename T>
 void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
                        cudaStream_t st) {
+    // levels with Def. 3.2 line blocks: the condensed block solve (set-up
+    // guarantees the sizes it takes)
+    if (L.blk[s] != nullptr) {
+        launch_line_block<T>(L, s, mode, g, r, y, x, alpha, st);
+        return;
+    }
     if (launch_line_warp<T>(L, s, mode, g, r, y, x, alpha, st)) return;
     LineArgs<T> A;
     A.n = L.n[s] - 2;
@@ -1086,13 +1096,14 @@ bool init_kernel_attributes() {
     for (const void* f : fns)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess)
             return false;
-    return init_line_warp_attributes() && init_apply_col_attributes() && init_apply_eo_attributes();
+    return init_line_warp_attributes() && init_line_block_attributes() && init_apply_col_attributes() &&
+           init_apply_eo_attributes();
 }
 
 // explicit instantiations
-template void launch_apply<double>(const DevLevel<double>&, const double*, double*, bool, cudaStream_t, bool, double*,
+template cudaError_t launch_apply<double>(const DevLevel<double>&, const double*, double*, bool, cudaStream_t, bool, double*,
                                    double*, unsigned*);
-template void launch_apply<float>(const DevLevel<float>&, const float*, float*, bool, cudaStream_t, bool, double*,
+template cudaError_t launch_apply<float>(const DevLevel<float>&, const float*, float*, bool, cudaStream_t, bool, double*,
                                   double*, unsigned*);
 template void launch_line_solve<double>(const DevLevel<double>&, int, int, const double*, const double*, double*,
                                         double*, double, cudaStream_t);

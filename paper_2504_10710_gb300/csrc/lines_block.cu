@@ -1,0 +1,358 @@
+// Line smoothing with the Def. 3.2 line blocks R A_p P (GLL smoother,
+// levels with p >= 2).
+//
+// A line's block couples every pair of its nodes that share an element, so it
+// is the sum of (p+1) x (p+1) element-segment blocks overlapping at the
+// element-boundary vertices.  The set-up (setup.cpp, line_blocks) condenses
+// it: one step of Algorithm 1 with S = the block diagonal of the segment
+// interiors K_I (Thm. 3.8: exact when S inverts those blocks exactly) leaves
+// the Schur complement on the vertices (Prop. 3.7), which is tridiagonal and
+// is solved by cyclic reduction (Cor. 3.9).  Per segment the set-up stores
+// K_I^-1 (upper triangle) and w_L, w_R = K_I^-1 K_{I,v} for its two vertices;
+// per line the vertex system.  One application of the block inverse to g:
+//   z   = K_I^-1 g_I                          every segment
+//   c_v = g_v - w_R(v-1) . g_I(v-1) - w_L(v) . g_I(v)     (c = R (g - K x))
+//   S nu = c                                  vertex CR, one warp per line
+//   x_I = z - w_L nu_left - w_R nu_right,  x_v = nu_v       (y = x + P e)
+//
+// A CTA of 256 threads owns LPC = min(16, 256 / E) lines of one direction
+// (E segments each), so that every thread has at most one segment task.  All
+// global loads are issued at entry: the line values (coalesced: along the
+// line for x-lines, across adjacent lines for strided directions), the
+// vertex systems, and each thread's segment operator into registers; after
+// one barrier the segment work, the vertex CR (one warp per line, warps
+// taking a second line when LPC > 8) and the back substitution run in
+// registers and shared memory, and the results are stored.  P is the
+// compile-time order (2..8); P = 0 takes the order at run time, reads its
+// operator from global memory inside the loops and accumulates K_I^-1 g_I in
+// shared memory.
+#include "cr_warp.cuh"
+#include "device.cuh"
+
+#include <algorithm>
+
+namespace glls {
+namespace {
+
+template <typename T>
+struct BlockLineArgs {
+    int n, nlines, stride, m1, st1, st2, contiguous, mode;
+    int p, E, span, cv, lpc;
+    long long ntask;
+    T alpha;
+    const T* blk;                              // [ncoef][ntask]
+    const typename Vec2Of<T>::type* vband;     // [nlines][E - 1]
+    const T* g;
+    const T* r;
+    T* y;
+    T* x;
+};
+
+constexpr int kBlockThreads = 256;
+constexpr int kMaxLinesPerCta = 16;
+
+// shared-memory index with one pad word per 32
+__device__ __forceinline__ int padk(int k) { return k + (k >> 5); }
+
+// Vertex system of one line (E - 1 unknowns; vertex k is line unknown
+// (k + 1) p - 1), right-hand side c_k = g_v - dr[k] - dl[k + 1], operator
+// from shared memory (vb: diagonal and coupling to the next vertex per
+// vertex); the solution overwrites the vertex entries of `line`.
+template <typename T, int C>
+__device__ __forceinline__ void vertex_solve(T* line, const T* dl, const T* dr, const T* vb, int E, int p,
+                                             int lane) {
+    const int nv = E - 1;
+    T a[C], l[C], u[C], g[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const int k = C * lane + j;
+        if (k < nv) {
+            a[j] = vb[2 * k];
+            u[j] = k < nv - 1 ? vb[2 * k + 1] : T(0);
+            l[j] = k > 0 ? vb[2 * k - 1] : T(0);
+            g[j] = line[padk((k + 1) * p - 1)] - dr[k] - dl[k + 1];
+        } else {
+            a[j] = T(1); l[j] = T(0); u[j] = T(0); g[j] = T(0);
+        }
+    }
+    warp_cr_solve<T, C>(a, l, u, g, lane);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        const int k = C * lane + j;
+        if (k < nv) line[padk((k + 1) * p - 1)] = g[j];
+    }
+}
+
+// Segment operator of one task in registers (compile-time order).
+template <typename T, int P>
+struct SegOp {
+    static constexpr int MI = P > 1 ? P - 1 : 1;
+    static constexpr int NPK = MI * (MI + 1) / 2;
+    T t[NPK], wl[MI], wr[MI];
+};
+
+// MODE 0: x = B^-1 g.  MODE 1: x += alpha B^-1 (r - y), and y is reset to 0
+// on element-boundary nodes (the apply that produced y plain-stores element-
+// interior nodes and adds into element-boundary ones).  MODE 2: x += alpha
+// B^-1 r.  MODE 3: x = alpha B^-1 r.
+template <typename T, int P>
+__global__ void __launch_bounds__(kBlockThreads) line_block_kernel(BlockLineArgs<T> A) {
+    grid_dep_sync();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = A.n, E = A.E, span = A.span, mode = A.mode, LPC = A.lpc;
+    const int p = P > 0 ? P : A.p;
+    const int mi = p - 1, npk = mi * (mi + 1) / 2;
+    const long long ntask = A.ntask;
+    T* sg = reinterpret_cast<T*>(smem_raw);   // [LPC][span]: g, then z / nu, then B^-1 g
+    T* sx = sg + LPC * span;                  // [LPC][span]: x on entry (MODE 1, 2)
+    T* sdl = sx + LPC * span;                 // [LPC][E]: w_L . g_I per segment
+    T* sdr = sdl + LPC * E;                   // [LPC][E]: w_R . g_I
+    T* svb = sdr + LPC * E;                   // [LPC][2 (E - 1)]: vertex systems
+    T* sz = svb + 2 * LPC * (E - 1);          // [LPC][span]: z accumulation (P = 0)
+    const int l0 = blockIdx.x * LPC;
+    const int Wc = min(LPC, A.nlines - l0);
+    const int tid = threadIdx.x;
+    // first node of line w of this CTA (interior indices c1, c2 of the other axes)
+    auto line_base = [&](int w) {
+        const int li = l0 + w;
+        return (li % A.m1 + 1) * A.st1 + (li / A.m1 + 1) * A.st2;
+    };
+    // this thread's segment task and its operator, loaded before anything waits
+    const int ntk = Wc * E;
+    const bool has_task = tid < ntk;
+    const int tw = has_task ? tid / E : 0, te = has_task ? tid - tw * E : 0;
+    const T* bp = A.blk + ((long long)(l0 + tw) * E + te);
+    SegOp<T, P> op;
+    if constexpr (P > 0) {
+        if (has_task) {
+#pragma unroll
+            for (int c = 0; c < SegOp<T, P>::NPK; ++c) op.t[c] = __ldg(bp + (long long)c * ntask);
+#pragma unroll
+            for (int i = 0; i < P - 1; ++i) {
+                op.wl[i] = __ldg(bp + (long long)(npk + i) * ntask);
+                op.wr[i] = __ldg(bp + (long long)(npk + mi + i) * ntask);
+            }
+        }
+    }
+    // line values: x-lines read along the line (warp-contiguous), strided
+    // directions across the CTA's adjacent lines
+    const bool contig = A.contiguous != 0;
+    const int total = Wc * n;
+#pragma unroll 4
+    for (int f = tid; f < total; f += kBlockThreads) {
+        int w, k;
+        if (contig) { w = f / n; k = f - w * n; }
+        else { k = f / Wc; w = f - k * Wc; }
+        const int node = line_base(w) + (k + 1) * A.stride;
+        T v;
+        if (mode == 0) v = A.g[node];
+        else if (mode == 1) v = A.r[node] - A.y[node];
+        else v = A.r[node];
+        sg[w * span + padk(k)] = v;
+        if (mode == 1 || mode == 2) sx[w * span + padk(k)] = A.x[node];
+    }
+    // vertex systems of the CTA's lines (contiguous in global memory)
+    if (E > 1) {
+        const T* vsrc = reinterpret_cast<const T*>(A.vband + (long long)l0 * (E - 1));
+        const int nvb = 2 * Wc * (E - 1);
+        for (int i = tid; i < nvb; i += kBlockThreads) svb[i] = __ldg(vsrc + i);
+    }
+    __syncthreads();
+
+    // ---- segments: z = K_I^-1 g_I and the two vertex dots
+    T z[SegOp<T, P>::MI];
+    if (has_task) {
+        T* line = sg + tw * span;
+        const int base = te * p;   // line unknown of the segment's first interior node
+        T dl = T(0), dr = T(0);
+        if constexpr (P > 0) {
+            T gi[P - 1];
+#pragma unroll
+            for (int i = 0; i < P - 1; ++i) {
+                gi[i] = line[padk(base + i)];
+                z[i] = T(0);
+            }
+            int c = 0;
+#pragma unroll
+            for (int i = 0; i < P - 1; ++i)
+#pragma unroll
+                for (int j = i; j < P - 1; ++j) {
+                    const T t = op.t[c++];
+                    z[i] += t * gi[j];
+                    if (j != i) z[j] += t * gi[i];
+                }
+#pragma unroll
+            for (int i = 0; i < P - 1; ++i) {
+                dl += op.wl[i] * gi[i];
+                dr += op.wr[i] * gi[i];
+            }
+        } else {
+            T* zz = sz + tw * span;
+            for (int i = 0; i < mi; ++i) zz[padk(base + i)] = T(0);
+            int c = 0;
+            for (int i = 0; i < mi; ++i) {
+                const T gi_ = line[padk(base + i)];
+                T zi = T(0);
+                for (int j = i; j < mi; ++j) {
+                    const T t = __ldg(bp + (long long)c * ntask);
+                    ++c;
+                    zi += t * line[padk(base + j)];
+                    if (j != i) zz[padk(base + j)] += t * gi_;
+                }
+                zz[padk(base + i)] += zi;
+                dl += __ldg(bp + (long long)(npk + i) * ntask) * gi_;
+                dr += __ldg(bp + (long long)(npk + mi + i) * ntask) * gi_;
+            }
+        }
+        // each task reads and writes only its own segment's interior nodes
+        if constexpr (P > 0) {
+#pragma unroll
+            for (int i = 0; i < P - 1; ++i) line[padk(base + i)] = z[i];
+        } else {
+            const T* zz = sz + tw * span;
+            for (int i = 0; i < mi; ++i) line[padk(base + i)] = zz[padk(base + i)];
+        }
+        sdl[tw * E + te] = dl;
+        sdr[tw * E + te] = dr;
+    }
+    __syncthreads();
+
+    // ---- vertex systems, one warp per line
+    const int warp = tid >> 5, lane = tid & 31;
+    if (E > 1) {
+        for (int w = warp; w < Wc; w += kBlockThreads / 32) {
+            T* line = sg + w * span;
+            const T* vb = svb + 2 * w * (E - 1);
+            switch (A.cv) {
+                case 1: vertex_solve<T, 1>(line, sdl + w * E, sdr + w * E, vb, E, p, lane); break;
+                case 2: vertex_solve<T, 2>(line, sdl + w * E, sdr + w * E, vb, E, p, lane); break;
+                case 4: vertex_solve<T, 4>(line, sdl + w * E, sdr + w * E, vb, E, p, lane); break;
+                default: vertex_solve<T, 8>(line, sdl + w * E, sdr + w * E, vb, E, p, lane); break;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- segments: x_I = z - w_L nu_left - w_R nu_right
+    if (has_task) {
+        T* line = sg + tw * span;
+        const int base = te * p;
+        const T nl = te > 0 ? line[padk(base - 1)] : T(0);
+        const T nr = te < E - 1 ? line[padk(base + mi)] : T(0);
+        if constexpr (P > 0) {
+#pragma unroll
+            for (int i = 0; i < P - 1; ++i) line[padk(base + i)] = z[i] - (op.wl[i] * nl + op.wr[i] * nr);
+        } else {
+            for (int i = 0; i < mi; ++i) {
+                const T wl = __ldg(bp + (long long)(npk + i) * ntask);
+                const T wr = __ldg(bp + (long long)(npk + mi + i) * ntask);
+                line[padk(base + i)] -= wl * nl + wr * nr;
+            }
+        }
+    }
+    __syncthreads();
+
+#pragma unroll 4
+    for (int f = tid; f < total; f += kBlockThreads) {
+        int w, k;
+        if (contig) { w = f / n; k = f - w * n; }
+        else { k = f / Wc; w = f - k * Wc; }
+        const int li = l0 + w;
+        const int c1 = li % A.m1 + 1, c2 = li / A.m1 + 1;
+        const int node = c1 * A.st1 + c2 * A.st2 + (k + 1) * A.stride;
+        const T v = sg[w * span + padk(k)];
+        A.x[node] = mode == 0 ? v : (mode == 3 ? A.alpha * v : sx[w * span + padk(k)] + A.alpha * v);
+        // the next apply stores element-interior nodes and adds into the
+        // element-boundary ones: only those must be reset (the line lies on
+        // an element boundary of another axis, or the node is a vertex)
+        const bool seam = (c1 % p == 0) || (A.st2 != 0 && c2 % p == 0) || ((k + 1) % p == 0);
+        if (mode == 1 && seam) A.y[node] = T(0);
+    }
+}
+
+template <typename T, int P>
+size_t block_smem(int lpc, int span, int E) {
+    return sizeof(T) * ((size_t)lpc * span * (P == 0 ? 3 : 2) + 2 * (size_t)lpc * E + 2 * (size_t)lpc * (E - 1));
+}
+
+template <typename T, int P>
+bool launch_p(BlockLineArgs<T> A, cudaStream_t st) {
+    int lpc = std::min(kMaxLinesPerCta, std::max(1, kBlockThreads / A.E));
+    while (lpc > 1 && block_smem<T, P>(lpc, A.span, A.E) > kMaxDynSmemBytes) lpc /= 2;
+    const size_t smem = block_smem<T, P>(lpc, A.span, A.E);
+    if (smem > kMaxDynSmemBytes) return false;
+    A.lpc = lpc;
+    const int blocks = (A.nlines + lpc - 1) / lpc;
+    return launch_k(line_block_kernel<T, P>, blocks, kBlockThreads, smem, st, A) == cudaSuccess;
+}
+
+template <typename T>
+bool set_attr_t() {
+    const int lim = (int)kMaxDynSmemBytes;
+    const void* fns[] = {(const void*)line_block_kernel<T, 0>, (const void*)line_block_kernel<T, 2>,
+                         (const void*)line_block_kernel<T, 3>, (const void*)line_block_kernel<T, 4>,
+                         (const void*)line_block_kernel<T, 5>, (const void*)line_block_kernel<T, 6>,
+                         (const void*)line_block_kernel<T, 7>, (const void*)line_block_kernel<T, 8>};
+    for (const void* f : fns)
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) return false;
+    return true;
+}
+
+}  // namespace
+
+bool init_line_block_attributes() { return set_attr_t<float>() && set_attr_t<double>(); }
+
+bool line_block_supported(int n, int E) { return n <= kMaxBlockLine && E <= kMaxBlockSegments; }
+
+template <typename T>
+bool launch_line_block(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
+                       cudaStream_t st) {
+    BlockLineArgs<T> A;
+    A.n = L.n[s] - 2;
+    if (A.n <= 0) return true;
+    A.E = L.ne[s];
+    if (!line_block_supported(A.n, A.E) || L.N > (1LL << 31) - 1) return false;
+    int o1, o2;
+    if (s == 0) { o1 = 1; o2 = 2; } else if (s == 1) { o1 = 0; o2 = 2; } else { o1 = 0; o2 = 1; }
+    const int strides[3] = {1, L.n[0], L.n[0] * L.n[1]};
+    A.m1 = L.n[o1] - 2;
+    const int m2 = L.dim == 3 ? L.n[o2] - 2 : 1;
+    A.nlines = A.m1 * m2;
+    if (A.nlines <= 0) return true;
+    A.ntask = (long long)A.nlines * A.E;
+    A.stride = strides[s];
+    A.st1 = strides[o1];
+    A.st2 = L.dim == 3 ? strides[o2] : 0;
+    A.contiguous = s == 0;
+    A.mode = mode;
+    A.p = L.p;
+    A.span = (A.n - 1) + ((A.n - 1) >> 5) + 1;
+    A.span = (A.span + 3) / 4 * 4;
+    A.lpc = 1;
+    const int nv = A.E - 1;
+    A.cv = nv <= 32 ? 1 : (nv <= 64 ? 2 : (nv <= 128 ? 4 : 8));
+    A.alpha = alpha;
+    A.blk = L.blk[s];
+    A.vband = L.vband[s];
+    A.g = g;
+    A.r = r;
+    A.y = y;
+    A.x = x;
+    switch (L.p) {
+        case 2: return launch_p<T, 2>(A, st);
+        case 3: return launch_p<T, 3>(A, st);
+        case 4: return launch_p<T, 4>(A, st);
+        case 5: return launch_p<T, 5>(A, st);
+        case 6: return launch_p<T, 6>(A, st);
+        case 7: return launch_p<T, 7>(A, st);
+        case 8: return launch_p<T, 8>(A, st);
+        default: return launch_p<T, 0>(A, st);
+    }
+}
+
+template bool launch_line_block<float>(const DevLevel<float>&, int, int, const float*, const float*, float*, float*,
+                                       float, cudaStream_t);
+template bool launch_line_block<double>(const DevLevel<double>&, int, int, const double*, const double*, double*,
+                                        double*, double, cudaStream_t);
+
+}  // namespace glls

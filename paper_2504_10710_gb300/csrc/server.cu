@@ -13,6 +13,7 @@
 #include <cstring>
 #include <deque>
 #include <functional>
+#include <list>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -62,12 +63,38 @@ struct Request {
     Clock::time_point submitted, started, finished;
 };
 
+// One instance of a resident mesh: the problem that set it up, or a clone
+// sharing its mesh data with its own right-hand side and Krylov state.
+struct Instance {
+    glls_problem* prob = nullptr;
+    bool busy = false;
+};
+
+// A resident mesh.  List nodes never move, so a worker may keep pointers to
+// its mesh and instance while it holds the instance busy: eviction only
+// removes meshes whose instances are all idle.
 struct Cached {
     MeshKey key;
-    glls_problem* prob = nullptr;
-    size_t bytes = 0;
-    bool busy = false;
+    std::list<Instance> inst;      // the set-up problem first, then clones
+    size_t shared_bytes = 0;       // mesh data, held until the last instance goes
+    size_t instance_bytes = 0;     // what each instance owns alone
+    int cloning = 0;               // clones being created (their bytes are reserved)
     Clock::time_point last_used;
+    bool idle() const {
+        if (cloning) return false;
+        for (const auto& i : inst)
+            if (i.busy) return false;
+        return true;
+    }
+    size_t bytes() const { return shared_bytes + inst.size() * instance_bytes; }
+};
+
+// What admit() hands a worker, decided under the server lock.
+struct Admission {
+    Request* r = nullptr;
+    Cached* mesh = nullptr;        // resident mesh (run or clone), or null (create)
+    glls_problem* prob = nullptr;  // idle instance taken, or null
+    size_t reserve = 0;            // bytes reserved for a new mesh or clone
 };
 
 }  // namespace
@@ -80,9 +107,9 @@ struct glls_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> queue;
     std::unordered_map<unsigned long long, std::unique_ptr<Request>> requests;
-    std::vector<Cached> cache;
-    size_t resident = 0;     // bytes of cached problems plus reservations being created
-    unsigned long long next_id = 1, submitted = 0, completed = 0, failed = 0, running = 0;
+    std::list<Cached> cache;
+    size_t resident = 0;     // bytes of cached meshes plus reservations being created
+    unsigned long long next_id = 1, submitted = 0, completed = 0, failed = 0, running = 0, clones = 0;
     bool stop = false;
     std::vector<std::thread> workers;
     std::vector<MeshKey> creating;   // meshes whose set-up is in progress
@@ -93,60 +120,81 @@ struct glls_server {
         return false;
     }
 
-    // Under the lock: choose the first queued request that can run now.
-    // Returns it with `slot` set to a cached problem index, or -1 with
-    // `reserve` bytes reserved for a new problem.  A request whose mesh is
-    // resident but busy waits for that instance (no duplicate set-up) while
-    // later requests for other meshes may proceed.
-    Request* admit(int* slot, size_t* reserve) {
-        for (auto it = queue.begin(); it != queue.end(); ++it) {
-            Request* r = *it;
-            bool resident_busy = false;
-            for (size_t i = 0; i < cache.size(); ++i)
-                if (cache[i].key == r->key) {
-                    if (cache[i].busy) {
-                        resident_busy = true;
-                        continue;
-                    }
-                    cache[i].busy = true;
-                    *slot = (int)i;
-                    *reserve = 0;
-                    queue.erase(it);
-                    return r;
-                }
-            if (resident_busy || pending_key(r->key)) continue;
-            if (r->estimate > budget) {       // can never fit: fail it here
-                r->status = GLLS_ERR_BUDGET;
-                r->state = 2;
-                r->finished = Clock::now();
-                ++failed;
-                queue.erase(it);
-                cv_done.notify_all();
-                return admit(slot, reserve);
-            }
-            // evict idle cached problems, least recently used first, until it fits
-            while (resident + r->estimate > budget) {
-                int victim = -1;
-                for (size_t i = 0; i < cache.size(); ++i)
-                    if (!cache[i].busy && (victim < 0 || cache[i].last_used < cache[victim].last_used))
-                        victim = (int)i;
-                if (victim < 0) break;
-                glls_problem_destroy(cache[victim].prob);
-                resident -= cache[victim].bytes;
-                cache.erase(cache.begin() + victim);
-            }
-            if (resident + r->estimate <= budget) {
-                resident += r->estimate;
-                *slot = -1;
-                *reserve = r->estimate;
-                creating.push_back(r->key);
-                queue.erase(it);
-                return r;
-            }
-            // the oldest request waits for memory: keep arrival order
-            return nullptr;
-        }
+    Cached* find(const MeshKey& k) {
+        for (auto& c : cache)
+            if (c.key == k) return &c;
         return nullptr;
+    }
+
+    void finish_failed(Request* r, glls_status st) {
+        r->status = st;
+        r->state = 2;
+        r->finished = Clock::now();
+        ++failed;
+        cv_done.notify_all();
+    }
+
+    // Evicts idle meshes other than `keep`, least recently used first, until
+    // `need` more bytes fit the budget.  Returns whether they fit.
+    bool make_room(size_t need, const Cached* keep) {
+        while (resident + need > budget) {
+            auto victim = cache.end();
+            for (auto it = cache.begin(); it != cache.end(); ++it)
+                if (&*it != keep && it->idle() && (victim == cache.end() || it->last_used < victim->last_used))
+                    victim = it;
+            if (victim == cache.end()) return false;
+            for (auto& i : victim->inst) glls_problem_destroy(i.prob);
+            resident -= victim->bytes();
+            cache.erase(victim);
+        }
+        return true;
+    }
+
+    // Under the lock: the first queued request that can run now, in arrival
+    // order.  A resident mesh with an idle instance runs on it; a resident
+    // mesh whose instances are all busy gets a clone when its bytes fit (else
+    // the request waits for an instance while later requests go ahead); a new
+    // mesh reserves its estimate, evicting idle meshes; the oldest new-mesh
+    // request that does not fit waits for memory and holds back the rest.
+    bool admit(Admission* a) {
+        for (auto it = queue.begin(); it != queue.end();) {
+            Request* r = *it;
+            Cached* c = find(r->key);
+            if (c) {
+                for (auto& i : c->inst)
+                    if (!i.busy) {
+                        i.busy = true;
+                        *a = Admission{r, c, i.prob, 0};
+                        queue.erase(it);
+                        return true;
+                    }
+                if (make_room(c->instance_bytes, c)) {
+                    resident += c->instance_bytes;
+                    ++c->cloning;
+                    *a = Admission{r, c, nullptr, c->instance_bytes};
+                    queue.erase(it);
+                    return true;
+                }
+                ++it;
+                continue;
+            }
+            if (pending_key(r->key)) {
+                ++it;
+                continue;
+            }
+            if (r->estimate > budget) {       // can never fit: fail it here
+                finish_failed(r, GLLS_ERR_BUDGET);
+                it = queue.erase(it);
+                continue;
+            }
+            if (!make_room(r->estimate, nullptr)) return false;
+            resident += r->estimate;
+            creating.push_back(r->key);
+            *a = Admission{r, nullptr, nullptr, r->estimate};
+            queue.erase(it);
+            return true;
+        }
+        return false;
     }
 
     void worker() {
@@ -154,29 +202,45 @@ struct glls_server {
         cudaStream_t stream = nullptr;
         cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
         for (;;) {
-            Request* r = nullptr;
-            int slot = -1;
-            size_t reserve = 0;
+            Admission a;
             {
                 std::unique_lock<std::mutex> lock(m);
-                cv_work.wait(lock, [&] { return stop || (r = admit(&slot, &reserve)) != nullptr; });
-                if (!r) break;
-                r->state = 1;
-                r->started = Clock::now();
+                cv_work.wait(lock, [&] { return stop || admit(&a); });
+                if (!a.r) break;
+                a.r->state = 1;
+                a.r->started = Clock::now();
                 ++running;
             }
-            glls_problem* prob = nullptr;
+            Request* r = a.r;
+            Cached* mesh = a.mesh;
+            glls_problem* prob = a.prob;
             glls_status st = GLLS_OK;
             double setup_ms = 0.0;
-            if (slot >= 0) {
+            if (!prob && mesh) {
+                // all instances of the resident mesh are busy: a clone shares its mesh data
+                glls_problem* base = mesh->inst.front().prob;
+                auto t0 = Clock::now();
+                st = glls_problem_clone(base, &prob);
+                setup_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
                 std::lock_guard<std::mutex> lock(m);
-                prob = cache[slot].prob;
-            } else {
+                --mesh->cloning;
+                resident -= a.reserve;
+                if (st == GLLS_OK) {
+                    glls_info inf;
+                    glls_problem_info(prob, &inf);
+                    Instance in;
+                    in.prob = prob;
+                    in.busy = true;
+                    mesh->inst.push_back(in);
+                    resident += mesh->instance_bytes;
+                    ++clones;
+                }
+            } else if (!prob) {
                 auto t0 = Clock::now();
                 st = glls_problem_create(&r->desc, &prob);
                 setup_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
                 std::lock_guard<std::mutex> lock(m);
-                resident -= reserve;
+                resident -= a.reserve;
                 for (size_t i = 0; i < creating.size(); ++i)
                     if (creating[i] == r->key) {
                         creating.erase(creating.begin() + i);
@@ -187,25 +251,31 @@ struct glls_server {
                     glls_problem_info(prob, &inf);
                     Cached c;
                     c.key = r->key;
-                    c.prob = prob;
-                    c.bytes = inf.device_bytes;
-                    c.busy = true;
-                    cache.push_back(c);
-                    resident += c.bytes;
-                    slot = (int)cache.size() - 1;
+                    c.instance_bytes = inf.instance_bytes;
+                    c.shared_bytes = inf.device_bytes - inf.instance_bytes;
+                    Instance in;
+                    in.prob = prob;
+                    in.busy = true;
+                    c.inst.push_back(in);
+                    c.last_used = Clock::now();
+                    cache.push_back(std::move(c));
+                    mesh = &cache.back();
+                    resident += mesh->bytes();
                 }
             }
+            // a new resident mesh or instance can admit waiting requests now
+            if (!a.prob) cv_work.notify_all();
             glls_stats stats{};
             if (st == GLLS_OK) st = glls_set_rhs(prob, r->f.data(), 0, stream);
             if (st == GLLS_OK && !r->g.empty()) st = glls_set_dirichlet(prob, r->g.data(), 0, stream);
             if (st == GLLS_OK) st = glls_solve(prob, &r->opts, r->u, 0, stream, &stats);
             {
                 std::lock_guard<std::mutex> lock(m);
-                for (auto& c : cache)
-                    if (c.prob == prob) {
-                        c.busy = false;
-                        c.last_used = Clock::now();
-                    }
+                if (mesh) {
+                    for (auto& i : mesh->inst)
+                        if (i.prob == prob) i.busy = false;
+                    mesh->last_used = Clock::now();
+                }
                 r->finished = Clock::now();
                 stats.setup_ms = setup_ms;
                 stats.solve_ms = std::chrono::duration<double, std::milli>(r->finished - r->submitted).count();
@@ -246,8 +316,8 @@ void glls_server_destroy(glls_server* S) {
     }
     S->cv_work.notify_all();
     for (auto& t : S->workers) t.join();
-    cudaSetDevice(S->device);
-    for (auto& c : S->cache) glls_problem_destroy(c.prob);
+    for (auto& c : S->cache)
+        for (auto& i : c.inst) glls_problem_destroy(i.prob);
     delete S;
 }
 
@@ -319,6 +389,29 @@ glls_status glls_server_info_get(glls_server* S, glls_server_info* out) {
     out->resident_bytes = S->resident;
     out->budget_bytes = S->budget;
     out->cached_problems = (int)S->cache.size();
+    out->clones = S->clones;
+    int inst = 0;
+    for (const auto& c : S->cache) inst += (int)c.inst.size();
+    out->cached_instances = inst;
+    return GLLS_OK;
+}
+
+glls_status glls_cancel(glls_server* S, unsigned long long ticket) {
+    if (!S) return GLLS_ERR_INVALID;
+    {
+        std::lock_guard<std::mutex> lock(S->m);
+        auto it = S->requests.find(ticket);
+        if (it == S->requests.end()) return GLLS_ERR_INVALID;
+        Request* r = it->second.get();
+        if (r->state != 0) return GLLS_NOT_READY;
+        for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+            if (*q == r) {
+                S->queue.erase(q);
+                break;
+            }
+        S->requests.erase(it);
+    }
+    S->cv_work.notify_all();
     return GLLS_OK;
 }
 

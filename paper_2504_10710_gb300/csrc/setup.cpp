@@ -3,9 +3,11 @@
 #include "setup.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <sstream>
+#include <thread>
 
 namespace glls {
 
@@ -223,6 +225,217 @@ void gll_band(LevelHost& lv) {
     }
 }
 
+// Def. 3.2's line system of an interior grid line is R A_p P: every coupling
+// of A_p between two nodes of the line.  Two nodes of a line couple only
+// through elements holding both, i.e. within one element segment of p
+// intervals, so the system is the sum over the segments of (p+1) x (p+1)
+// blocks that overlap at the element-boundary vertices.  Ordering the
+// element-interior nodes of every segment first, one step of Algorithm 1 with
+// S = the block diagonal of the segment interiors (Thm. 3.8: exact when S
+// inverts those blocks exactly) leaves the Schur complement on the vertices
+// (Prop. 3.7), a tridiagonal system solved by cyclic reduction (Cor. 3.9).
+// This stores, per segment, K_I^-1 and the vertex interpolation weights
+// w = K_I^-1 K_{I,v} (the columns of -P restricted to the segment), and per
+// line the vertex Schur complement.
+//
+// Entries of an element's stiffness between nodes m, m' of one local line
+// along s (eq. discreteBilinear with the nodal basis, m and m' differing only
+// in the s index i, i'):
+//   sum_q G_ss(q) D[q,i] D[q,i']                         (q along the line)
+// + sum_{b != s} ( D[i',i] G_sb(m') + G_bs(m) D[i,i'] ) D[m_b,m_b]
+// for i != i'; the diagonal is the element's full diagonal entry.
+
+struct SegBuilder {
+    const LevelHost& lv;
+    int s, o1, o2, p, n1, E;
+    // element contribution on the local line of element ec through local
+    // other indices lc (lc[s] ignored), added into M ((p+1) x (p+1))
+    void add_element(const int ec[3], const int lc_in[3], double* M) const {
+        const int d = lv.dim;
+        const std::vector<double>& D = lv.D;
+        long long e = ((long long)ec[2] * lv.ne[1] + ec[1]) * lv.ne[0] + ec[0];
+        int lc[3] = {lc_in[0], lc_in[1], lc_in[2]};
+        std::vector<int> qv(n1);   // local node index of the line nodes
+        for (int i = 0; i < n1; ++i) {
+            lc[s] = i;
+            qv[i] = local_index(lc, n1);
+        }
+        for (int i = 0; i < n1; ++i) {
+            // full diagonal entry of the element at line node i
+            lc[s] = i;
+            double v = 0.0;
+            for (int a = 0; a < d; ++a) {
+                for (int k = 0; k < n1; ++k) {
+                    int qc[3] = {lc[0], lc[1], lc[2]};
+                    qc[a] = k;
+                    double Dk = D[k * n1 + lc[a]];
+                    v += Gc(lv, a, a, e, local_index(qc, n1)) * Dk * Dk;
+                }
+                for (int b = 0; b < d; ++b)
+                    if (b != a) v += Gc(lv, a, b, e, qv[i]) * D[lc[a] * n1 + lc[a]] * D[lc[b] * n1 + lc[b]];
+            }
+            M[i * n1 + i] += v;
+            for (int i2 = i + 1; i2 < n1; ++i2) {
+                double o = 0.0;
+                for (int q = 0; q < n1; ++q) o += Gc(lv, s, s, e, qv[q]) * D[q * n1 + i] * D[q * n1 + i2];
+                for (int b = 0; b < d; ++b) {
+                    if (b == s) continue;
+                    const double Dbb = D[lc_in[b] * n1 + lc_in[b]];
+                    o += (D[i2 * n1 + i] * Gc(lv, s, b, e, qv[i2]) + Gc(lv, b, s, e, qv[i]) * D[i * n1 + i2]) * Dbb;
+                }
+                M[i * n1 + i2] += o;
+                M[i2 * n1 + i] += o;
+            }
+        }
+    }
+    // summed segment block of line (c1, c2) (global other indices) and segment seg
+    void segment(int c1, int c2, int seg, double* M) const {
+        std::fill(M, M + n1 * n1, 0.0);
+        const int d = lv.dim;
+        int e1[2], l1[2], n1c = 0, e2[2] = {0, 0}, l2[2] = {0, 0}, n2c = 1;
+        // elements along o1 (and o2) containing the global index c
+        auto holders = [&](int c, int a, int* ee, int* ll) {
+            int cnt = 0;
+            if (c % p == 0) {
+                if (c / p - 1 >= 0) { ee[cnt] = c / p - 1; ll[cnt] = p; ++cnt; }
+                if (c / p < lv.ne[a]) { ee[cnt] = c / p; ll[cnt] = 0; ++cnt; }
+            } else {
+                ee[cnt] = c / p; ll[cnt] = c % p; ++cnt;
+            }
+            return cnt;
+        };
+        n1c = holders(c1, o1, e1, l1);
+        if (d == 3) n2c = holders(c2, o2, e2, l2);
+        for (int a = 0; a < n1c; ++a)
+            for (int b = 0; b < n2c; ++b) {
+                int ec[3] = {0, 0, 0}, lc[3] = {0, 0, 0};
+                ec[s] = seg;
+                ec[o1] = e1[a];
+                lc[o1] = l1[a];
+                if (d == 3) { ec[o2] = e2[b]; lc[o2] = l2[b]; }
+                add_element(ec, lc, M);
+            }
+    }
+};
+
+// Cholesky inverse of the SPD matrix K (m x m, row-major, overwritten by the
+// inverse).  Returns false on a non-positive pivot.
+bool spd_inverse_small(double* K, int m) {
+    std::vector<double> L((size_t)m * m, 0.0), X((size_t)m * m, 0.0);
+    for (int j = 0; j < m; ++j) {
+        double s = K[j * m + j];
+        for (int k = 0; k < j; ++k) s -= L[j * m + k] * L[j * m + k];
+        if (!(s > 0.0)) return false;
+        const double ljj = std::sqrt(s);
+        L[j * m + j] = ljj;
+        for (int i = j + 1; i < m; ++i) {
+            double t = K[i * m + j];
+            for (int k = 0; k < j; ++k) t -= L[i * m + k] * L[j * m + k];
+            L[i * m + j] = t / ljj;
+        }
+    }
+    for (int c = 0; c < m; ++c) {
+        std::vector<double> y(m, 0.0);
+        for (int i = 0; i < m; ++i) {
+            double t = i == c ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= L[i * m + k] * y[k];
+            y[i] = t / L[i * m + i];
+        }
+        for (int i = m - 1; i >= 0; --i) {
+            double t = y[i];
+            for (int k = i + 1; k < m; ++k) t -= L[k * m + i] * X[k * m + c];
+            X[i * m + c] = t / L[i * m + i];
+        }
+    }
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) K[i * m + j] = 0.5 * (X[i * m + j] + X[j * m + i]);
+    return true;
+}
+
+std::string line_blocks(LevelHost& lv) {
+    const int d = lv.dim, p = lv.p, n1 = p + 1, mi = p - 1;
+    lv.lblock = 0;
+    if (p < 2) return "";
+    const int npk = mi * (mi + 1) / 2, ncoef = npk + 2 * mi;
+    for (int s = 0; s < d; ++s) {
+        int o1, o2;
+        if (s == 0) { o1 = 1; o2 = 2; } else if (s == 1) { o1 = 0; o2 = 2; } else { o1 = 0; o2 = 1; }
+        const int m1 = lv.n[o1] - 2, m2 = d == 3 ? lv.n[o2] - 2 : 1;
+        const int E = lv.ne[s];
+        const long long nlines = (long long)std::max(m1, 0) * std::max(m2, 0);
+        const long long ntask = nlines * E;
+        lv.blk[s].assign((size_t)ncoef * ntask, 0.0);
+        lv.vband[s].assign((size_t)nlines * std::max(E - 1, 0) * 2, 0.0);
+        SegBuilder sb{lv, s, o1, o2, p, n1, E};
+        std::atomic<long long> next(0);
+        std::atomic<bool> bad(false);
+        auto work = [&]() {
+            std::vector<double> M((size_t)E * n1 * n1), K((size_t)mi * mi);
+            std::vector<double> wl((size_t)E * mi), wr((size_t)E * mi);
+            for (;;) {
+                const long long li = next.fetch_add(1);
+                if (li >= nlines || bad.load()) break;
+                const int c1 = (int)(li % m1) + 1, c2 = (int)(li / m1) + 1;
+                for (int e = 0; e < E; ++e) sb.segment(c1, c2, e, &M[(size_t)e * n1 * n1]);
+                for (int e = 0; e < E; ++e) {
+                    const double* Me = &M[(size_t)e * n1 * n1];
+                    for (int i = 0; i < mi; ++i)
+                        for (int j = 0; j < mi; ++j) K[i * mi + j] = Me[(i + 1) * n1 + j + 1];
+                    if (!spd_inverse_small(K.data(), mi)) { bad = true; break; }
+                    const long long t = li * E + e;
+                    int c = 0;
+                    for (int i = 0; i < mi; ++i)
+                        for (int j = i; j < mi; ++j) lv.blk[s][(size_t)(c++) * ntask + t] = K[i * mi + j];
+                    for (int i = 0; i < mi; ++i) {
+                        double a = 0.0, b = 0.0;
+                        for (int j = 0; j < mi; ++j) {
+                            a += K[i * mi + j] * Me[(j + 1) * n1 + 0];
+                            b += K[i * mi + j] * Me[(j + 1) * n1 + p];
+                        }
+                        if (e == 0) a = 0.0;        // left end of the line: boundary node
+                        if (e == E - 1) b = 0.0;    // right end
+                        wl[(size_t)e * mi + i] = a;
+                        wr[(size_t)e * mi + i] = b;
+                        lv.blk[s][(size_t)(npk + i) * ntask + t] = a;
+                        lv.blk[s][(size_t)(npk + mi + i) * ntask + t] = b;
+                    }
+                }
+                if (bad.load()) break;
+                // vertex Schur complement: v = 1 .. E-1 between segments v-1 and v
+                for (int v = 1; v < E; ++v) {
+                    const double* Ml = &M[(size_t)(v - 1) * n1 * n1];
+                    const double* Mr = &M[(size_t)v * n1 * n1];
+                    double dg = Ml[p * n1 + p] + Mr[0];
+                    for (int i = 0; i < mi; ++i) {
+                        dg -= Ml[p * n1 + i + 1] * wr[(size_t)(v - 1) * mi + i];
+                        dg -= Mr[0 * n1 + i + 1] * wl[(size_t)v * mi + i];
+                    }
+                    double of = 0.0;
+                    if (v + 1 < E) {
+                        of = Mr[0 * n1 + p];
+                        for (int i = 0; i < mi; ++i) of -= Mr[0 * n1 + i + 1] * wr[(size_t)v * mi + i];
+                    }
+                    lv.vband[s][((size_t)li * (E - 1) + (v - 1)) * 2 + 0] = dg;
+                    lv.vband[s][((size_t)li * (E - 1) + (v - 1)) * 2 + 1] = of;
+                }
+            }
+        };
+        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        if (nlines < 64) nt = 1;
+        std::vector<std::thread> th;
+        for (unsigned k = 1; k < nt; ++k) th.emplace_back(work);
+        work();
+        for (auto& t : th) t.join();
+        if (bad.load()) {
+            std::ostringstream os;
+            os << "line block of order " << p << " along axis " << s << " is not positive definite";
+            return os.str();
+        }
+    }
+    lv.lblock = 1;
+    return "";
+}
+
 // Band-1 entries of the bilinear (trilinear) FEM matrix on the mesh of GLL
 // nodes, each cell a Q1 element on its physical vertices, 2-point Gauss rule.
 void fem_band(LevelHost& lv) {
@@ -424,7 +637,15 @@ std::string build_levels(int dim, const int nelem[3], int p_fine, const double* 
         }
         std::string err = geometry(lv);
         if (!err.empty()) return err;
-        if (smoother == 0) gll_band(lv); else fem_band(lv);
+        if (smoother == 1) {
+            fem_band(lv);
+        } else {
+            gll_band(lv);
+            if (smoother == 0) {
+                err = line_blocks(lv);
+                if (!err.empty()) return err;
+            }
+        }
     }
     // transfers between consecutive levels
     for (size_t l = 1; l < levels.size(); ++l) {

@@ -1,6 +1,8 @@
 // Host-side (FP64) construction of the level data of the GLL p-multigrid
-// solver: GLL tables, isoparametric geometry factors, band-1 line systems,
-// transfer operators and the coarsest-level factor.  Runs once per problem.
+// solver: GLL tables, isoparametric geometry factors, line systems (the
+// Def. 3.2 line blocks condensed per element segment, and their band-1
+// part), transfer operators and the coarsest-level factor.  Runs once per
+// problem.
 #pragma once
 #include <cstdint>
 #include <string>
@@ -29,6 +31,21 @@ struct LevelHost {
     std::vector<double> diag;     // [N] line-system diagonal (A or A~)
     std::vector<double> off[3];   // [N] line-system coupling node -> node + e_s
     std::vector<double> D;        // (p+1)^2, D[i*(p+1)+j] = pi_j'(xi_i)
+    // Def. 3.2 line blocks R A_p P (GLL smoother, p >= 2), condensed per
+    // element segment of each interior grid line along axis s.  Lines are
+    // numbered li = (c2 - 1) * (n[o1] - 2) + (c1 - 1) over the interior
+    // indices c1, c2 of the other axes o1 < o2; segment e = 0 .. ne[s]-1 holds
+    // the p - 1 element-interior nodes e p + 1 .. e p + p - 1 of the line, and
+    // vertex v = 1 .. ne[s]-1 is the node v p.  Task t = li * ne[s] + e.
+    //   blk[s]   [ncoef][ntask]: inverse of the segment's interior block K_I
+    //            (upper triangle, row-major: (p-1)p/2 values), then
+    //            w_L = K_I^-1 K_{I,v=e}, then w_R = K_I^-1 K_{I,v=e+1}
+    //            (zero where that vertex is a boundary node)
+    //   vband[s] [nlines][ne[s]-1][2]: the Schur complement on the vertices
+    //            (tridiagonal): diagonal, coupling to the next vertex
+    int lblock = 0;
+    std::vector<double> blk[3];
+    std::vector<double> vband[3];
     Band1D P[3];                  // prolongation (this level <- level-1), per axis
     Band1D R[3];                  // restriction  (this level -> level-1), per axis
 };

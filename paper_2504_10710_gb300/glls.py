@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libglls.so")
 NOT_READY, OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 1, 0, -1, -2, -3, -4, -5
 ERR_TIMEOUT, ERR_BUDGET = -6, -7
 PREC_FP64, PREC_MIXED = 0, 1
-SMOOTHER_GLL, SMOOTHER_FEM = 0, 1
+SMOOTHER_GLL, SMOOTHER_FEM, SMOOTHER_GLL_BAND1 = 0, 1, 2
 RESTRICT_TRANSPOSE, RESTRICT_INTERP = 0, 1
 KRYLOV_FCG, KRYLOV_PCG, KRYLOV_GMRES = 0, 1, 2
 COARSE_AUTO, COARSE_DENSE, COARSE_BLOCK_CR = 0, 1, 2
@@ -44,13 +44,15 @@ class Stats(C.Structure):
 class Info(C.Structure):
     _fields_ = [("dim", C.c_int), ("levels", C.c_int), ("order", C.c_int * 8), ("nodes", (C.c_int * 3) * 8),
                 ("ndof", C.c_longlong * 8), ("coarse_unknowns", C.c_longlong), ("device_bytes", C.c_size_t),
-                ("coarse_cr_levels", C.c_int), ("coarse_dense_unknowns", C.c_longlong)]
+                ("coarse_cr_levels", C.c_int), ("coarse_dense_unknowns", C.c_longlong),
+                ("instance_bytes", C.c_size_t)]
 
 
 class ServerInfo(C.Structure):
     _fields_ = [("submitted", C.c_ulonglong), ("completed", C.c_ulonglong), ("failed", C.c_ulonglong),
                 ("queued", C.c_ulonglong), ("running", C.c_ulonglong), ("resident_bytes", C.c_size_t),
-                ("budget_bytes", C.c_size_t), ("cached_problems", C.c_int)]
+                ("budget_bytes", C.c_size_t), ("cached_problems", C.c_int), ("cached_instances", C.c_int),
+                ("clones", C.c_ulonglong)]
 
 
 class GllsError(RuntimeError):
@@ -88,6 +90,8 @@ def lib():
             "glls_submit": [vp, C.POINTER(MeshDesc), vp, vp, C.POINTER(SolveOpts), vp, C.POINTER(C.c_ulonglong)],
             "glls_poll": [vp, C.c_ulonglong, i, C.POINTER(Stats)],
             "glls_server_info_get": [vp, C.POINTER(ServerInfo)],
+            "glls_cancel": [vp, C.c_ulonglong],
+            "glls_apply_partials_f64": [vp, i, vp, vp, vp, i, C.POINTER(i), vp],
         }
         for suf, real in (("f64", d), ("f32", C.c_float)):
             sig[f"glls_apply_{suf}"] = [vp, i, vp, vp, vp]
@@ -101,6 +105,8 @@ def lib():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_int
+        L.glls_debug_fail_alloc_after.argtypes = [C.c_longlong]
+        L.glls_debug_fail_alloc_after.restype = None
         L.glls_problem_destroy.argtypes = [vp]
         L.glls_problem_destroy.restype = None
         L.glls_server_destroy.argtypes = [vp]
@@ -244,6 +250,14 @@ class Problem:
     def apply(self, level, x, y, stream=None):
         _check(getattr(lib(), f"glls_apply_{self._suffix(x)}")(self.h, level, _ptr(x), _ptr(y), _stream(stream)))
 
+    def apply_partials(self, level, x, y, partials, stream=None):
+        """FP64 y += A x with the fused per-CTA x.(A x) partials (y zero on
+        entry); returns the number of partials written."""
+        n = C.c_int()
+        _check(lib().glls_apply_partials_f64(self.h, level, _ptr(x), _ptr(y), _ptr(partials), partials.numel(),
+                                             C.byref(n), _stream(stream)))
+        return n.value
+
     def line_solve(self, level, axis, g, x, stream=None):
         _check(getattr(lib(), f"glls_line_solve_{self._suffix(g)}")(self.h, level, axis, _ptr(g), _ptr(x),
                                                                        _stream(stream)))
@@ -352,6 +366,13 @@ class Server:
         inf = ServerInfo()
         _check(lib().glls_server_info_get(self.h, C.byref(inf)))
         return inf
+
+    def cancel(self, ticket):
+        """OK (removed before it ran), NOT_READY (already running) or ERR_INVALID."""
+        status = lib().glls_cancel(self.h, ticket)
+        if status == OK:
+            self._keep.pop(ticket, None)
+        return status
 
     def close(self):
         if getattr(self, "h", None):

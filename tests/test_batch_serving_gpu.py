@@ -163,17 +163,20 @@ def test_autotune_picks_valid_tiles_and_keeps_results():
     prob.close()
 
 
-def test_uneven_batch_sample_with_fem_smoother():
+@pytest.mark.parametrize("smoother,alpha", [(glls.SMOOTHER_GLL, 2.0 / 3.0), (glls.SMOOTHER_FEM, 0.16)],
+                         ids=["gll_blocks", "fem"])
+def test_uneven_batch_sample(smoother, alpha):
     """A sample of the batched uneven workload (n x n elements, n in 4..64,
     p in 4..12, amplitude up to 0.2), including its hardest draws (p = 12 and
-    amplitude near 0.2): with the FEM line smoother (alpha = 0.16) every
-    problem reaches 1e-10 in the batch, with the single solves' results."""
+    amplitude near 0.2): with the GLL line blocks (alpha = 2/3) and with the
+    FEM line smoother (alpha = 0.16) every problem reaches 1e-10 in the
+    batch, with the single solves' results."""
     ws = inputs.batch_uneven()
     pick = [w for w in ws if w.order == 12 and w.params["amp"] > 0.17][:2] + ws[:4]
-    o = glls.opts(tol=1e-10, gamma=1, alpha=0.16, precision=glls.PREC_MIXED, max_iter=300)
+    o = glls.opts(tol=1e-10, gamma=1, alpha=alpha, precision=glls.PREC_MIXED, max_iter=300)
     probs, single = [], []
     for w in pick:
-        prob, coords = glls.problem_for(w, glls.SMOOTHER_FEM)
+        prob, coords = glls.problem_for(w, smoother)
         prob.set_rhs(w.sample_rhs(coords)[0])
         prob.set_dirichlet(w.sample_dirichlet(coords))
         u = np.zeros(prob.N)
@@ -188,3 +191,86 @@ def test_uneven_batch_sample_with_fem_smoother():
         assert _rel(ub, u) < 1e-9
     for p in probs:
         p.close()
+
+
+def _alone(wl, coords, f, g, o):
+    prob, _ = glls.problem_for(wl)
+    prob.set_rhs(f)
+    prob.set_dirichlet(g)
+    u = np.zeros(prob.N)
+    assert prob.solve(u, o).status == glls.OK
+    prob.close()
+    return u
+
+
+def test_server_same_mesh_concurrent_requests_run_on_clones():
+    """Requests for one mesh that arrive together run at once on clones of
+    the resident problem (shared mesh data), each with its own right-hand
+    side; every result equals the solve of that right-hand side alone."""
+    o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_MIXED)
+    wl = inputs.random2d((32, 32), 8, amp=0.1, seed=27)
+    coords, f, g = _request(wl)
+    fs = [f * (1.0 + 0.5 * k) + k for k in range(4)]
+    srv = glls.Server(budget_bytes=8 << 30, slots=4)
+    outs = [np.zeros(f.size) for _ in fs]
+    tickets = [srv.submit(wl.dim, wl.nelem, wl.order, coords, fk, g, o, out) for fk, out in zip(fs, outs)]
+    for t in tickets:
+        st, stats = srv.poll(t, wait=True)
+        assert st == glls.OK and stats.rel_residual <= 1e-10
+    inf = srv.info()
+    assert inf.cached_problems == 1 and inf.clones >= 1 and inf.cached_instances == 1 + inf.clones
+    srv.close()
+    for fk, out in zip(fs, outs):
+        assert _rel(out, _alone(wl, coords, fk, g, o)) < 1e-10
+
+
+def test_server_eviction_while_other_meshes_are_busy():
+    """Several slots and a budget that holds about two of four meshes: idle
+    meshes are evicted while others are busy, and every result still equals
+    its mesh's solve alone (admission hands a worker its problem, never an
+    index that eviction can shift)."""
+    o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_MIXED)
+    wls = [MIX[0], MIX[1], MIX[4], MIX[5]]
+    reqs = [(wl,) + _request(wl) for wl in wls]
+    est = [glls.estimate_bytes(wl.dim, wl.nelem, wl.order, c) for wl, c, _, _ in reqs]
+    alone = [_alone(wl, c, f, g, o) for wl, c, f, g in reqs]
+    srv = glls.Server(budget_bytes=int(2.2 * max(est)), slots=3)
+    order = np.random.default_rng(5).integers(0, len(reqs), 24)
+    outs, tickets = [], []
+    for k in order:
+        wl, c, f, g = reqs[k]
+        out = np.zeros(f.size)
+        outs.append((k, out))
+        tickets.append(srv.submit(wl.dim, wl.nelem, wl.order, c, f, g, o, out))
+    for t in tickets:
+        st, _ = srv.poll(t, wait=True)
+        assert st == glls.OK
+    inf = srv.info()
+    assert inf.completed == len(order) and inf.resident_bytes <= inf.budget_bytes
+    srv.close()
+    for k, out in outs:
+        assert _rel(out, alone[k]) < 1e-10
+
+
+def test_server_cancel_queued_request():
+    """A queued request can be cancelled (its output is never written); a
+    running one cannot; unknown tickets are rejected."""
+    o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_FP64)
+    wl = inputs.random2d((48, 48), 8, amp=0.1, seed=28)
+    coords, f, g = _request(wl)
+    srv = glls.Server(budget_bytes=8 << 30, slots=1)
+    outs = [np.zeros(f.size) for _ in range(3)]
+    tickets = [srv.submit(wl.dim, wl.nelem, wl.order, coords, f, g, o, out) for out in outs]
+    deadline = time.time() + 60
+    while srv.info().running == 0 and time.time() < deadline:
+        time.sleep(0.001)
+    assert srv.cancel(tickets[2]) == glls.OK
+    assert srv.cancel(tickets[2]) == glls.ERR_INVALID
+    assert srv.cancel(12345678) == glls.ERR_INVALID
+    assert srv.cancel(tickets[0]) == glls.NOT_READY      # running (or finished, not yet polled)
+    for t in tickets[:2]:
+        st, _ = srv.poll(t, wait=True)
+        assert st == glls.OK
+    assert not outs[2].any()
+    assert srv.info().completed == 2
+    srv.close()

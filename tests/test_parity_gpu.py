@@ -27,7 +27,7 @@ def _built():
     __graft_entry__.build()
 
 
-SMOOTHERS = {"gll": glls.SMOOTHER_GLL, "fem": glls.SMOOTHER_FEM}
+SMOOTHERS = {"gll": glls.SMOOTHER_GLL, "fem": glls.SMOOTHER_FEM, "gll_band1": glls.SMOOTHER_GLL_BAND1}
 RESTRICTIONS = {"transpose": glls.RESTRICT_TRANSPOSE, "interp": glls.RESTRICT_INTERP}
 
 
@@ -78,6 +78,14 @@ CASES = [
     ("2d_66x66_p8_long_lines", lambda: inputs.random2d((66, 66), 8, amp=0.1, seed=13), "gll", "transpose", 4),
     ("3d_2x2x2_p8", lambda: inputs.random3d((2, 2, 2), 8, amp=0.1, seed=14), "gll", "transpose"),
     ("2d_3x2_p16", lambda: inputs.random2d((3, 2), 16, amp=0.1, seed=15), "gll", "transpose", 4),
+    # the band-1 reading of the GLL line systems (band-1 warp kernel), 2-D and 3-D
+    ("2d_7x5_p6_band1", lambda: inputs.random2d((7, 5), 6, amp=0.1, seed=3), "gll_band1", "transpose"),
+    ("3d_2x3x2_p3_band1", lambda: inputs.random3d((2, 3, 2), 3, amp=0.15, seed=5), "gll_band1", "transpose"),
+    # line blocks: more than 64 elements along x (vertex systems of 65..128
+    # unknowns), odd orders 3..7 with 3-D faces and edges shared by 2-4 elements
+    ("2d_70x3_p4_blocks", lambda: inputs.random2d((70, 3), 4, amp=0.1, seed=17), "gll", "transpose"),
+    ("3d_3x2x4_p7_blocks", lambda: inputs.random3d((3, 2, 4), 7, amp=0.1, seed=18), "gll", "transpose"),
+    ("3d_2x2x2_p5_blocks", lambda: inputs.random3d((2, 2, 2), 5, amp=0.15, seed=19), "gll", "transpose"),
 ]
 
 
@@ -168,7 +176,7 @@ def test_coarse_solve(case, dtype):
 def test_precondition_gamma_cycle(case, dtype, gamma):
     wl, prob, h, _, scale = case
     fine = h.levels[-1]
-    alpha = 0.16 if h.smoother == "fem" else 0.5
+    alpha = {"fem": 0.16, "gll": 2.0 / 3.0}.get(h.smoother, 0.5)
     r = interior_field(fine, 100 + gamma)
     z = torch.zeros(fine.N, dtype=dtype, device="cuda")
     prob.precondition(glls.opts(gamma=gamma, alpha=alpha), dev(r, dtype), z)
@@ -189,8 +197,8 @@ def test_lift(case):
 
 
 SOLVE_CASES = [
-    ("cfg1_square_sine", inputs.square_sine, "gll", "transpose", 2, 0.5),
-    ("2d_6x6_p8", lambda: inputs.random2d((6, 6), 8, amp=0.1, seed=2), "gll", "transpose", 1, 0.5),
+    ("cfg1_square_sine", inputs.square_sine, "gll", "transpose", 2, 2.0 / 3.0),
+    ("2d_6x6_p8", lambda: inputs.random2d((6, 6), 8, amp=0.1, seed=2), "gll", "transpose", 1, 2.0 / 3.0),
     ("2d_6x4_p8_fem", lambda: inputs.random2d((6, 4), 8, amp=0.15, seed=7), "fem", "transpose", 2, 0.16),
     ("2d_single_p8_interp", lambda: inputs.table1_problem3(8), "gll", "interp", 3, 2.0 / 3.0),
     ("2d_3x3_p1", lambda: inputs.random2d((3, 3), 1, amp=0.05, seed=8), "gll", "transpose", 1, 0.5),
@@ -200,6 +208,8 @@ SOLVE_CASES = [
     ("3d_2x2x2_p7_fem", lambda: inputs.random3d((2, 2, 2), 7, amp=0.15, seed=12), "fem", "transpose", 1, 0.16),
     ("3d_2x2x3_p6", lambda: inputs.random3d((2, 2, 3), 6, amp=0.1, seed=16), "gll", "transpose", 1, 0.5),
     ("2d_66x66_p8_long_lines", lambda: inputs.random2d((66, 66), 8, amp=0.1, seed=13), "gll", "transpose", 1, 0.5),
+    ("3d_3x3x2_p7", lambda: inputs.random3d((3, 3, 2), 7, amp=0.15, seed=20), "gll", "transpose", 1, 2.0 / 3.0),
+    ("2d_6x6_p8_band1", lambda: inputs.random2d((6, 6), 8, amp=0.1, seed=2), "gll_band1", "transpose", 1, 0.5),
 ]
 
 
@@ -255,15 +265,16 @@ def test_slowly_converging_case_same_solution():
 
 
 def test_cfg2_full_size_fp64_and_mixed():
-    """The benchmark workload (64x64 elements, p = 8, 263,169 nodes)."""
+    """The benchmark workload (64x64 elements, p = 8, 263,169 nodes) with the
+    line blocks at the paper's alpha = 2/3 (9 FCG iterations in the oracle)."""
     wl = inputs.terrain2d()
     prob, h, coords = make(wl, "gll", "transpose")
     prob.set_rhs(wl.sample_rhs(coords)[0])
     prob.set_dirichlet(wl.sample_dirichlet(coords))
-    ref = osolve.solve(wl, gamma=1, alpha=0.5, tol=1e-10, maxit=200, hierarchy=h)
+    ref = osolve.solve(wl, gamma=1, alpha=2.0 / 3.0, tol=1e-10, maxit=200, hierarchy=h)
     for prec in (glls.PREC_FP64, glls.PREC_MIXED):
         u = np.zeros(prob.N)
-        st = prob.solve(u, glls.opts(tol=1e-10, gamma=1, alpha=0.5, precision=prec))
+        st = prob.solve(u, glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=prec))
         err = relerr(u.reshape(h.levels[-1].shape), ref.u[0])
         assert err < (1e-9 if prec == glls.PREC_FP64 else 1e-8), (prec, err)
         assert abs(st.iterations - ref.iterations[0]) <= (1 if prec == glls.PREC_FP64 else 3)
@@ -283,4 +294,25 @@ def test_invalid_arguments_are_reported():
         prob.solve(np.zeros(prob.N), glls.opts(gamma=0))
     with pytest.raises(glls.GllsError):
         glls.Problem(2, (1, 1), 1, np.zeros((2, 4)))     # single element needs p >= 2
+    prob.close()
+
+
+@pytest.mark.parametrize("name,mk", [("2d_6x6_p8", lambda: inputs.random2d((6, 6), 8, amp=0.1, seed=2)),
+                                     ("3d_3x3x2_p7", lambda: inputs.random3d((3, 3, 2), 7, amp=0.15, seed=20)),
+                                     ("2d_3x2_p16", lambda: inputs.random2d((3, 2), 16, amp=0.1, seed=15))],
+                         ids=lambda v: v if isinstance(v, str) else "")
+def test_apply_with_fused_dot_partials(name, mk):
+    """The outer iteration's FP64 apply: y = A x and the partials of x.(A x)."""
+    wl = mk()
+    prob, h, _ = make(wl)
+    L = len(h.levels) - 1
+    lv = h.levels[L]
+    x = interior_field(lv, 7)
+    y = torch.zeros(lv.N, dtype=torch.float64, device="cuda")
+    part = torch.zeros(8192, dtype=torch.float64, device="cuda")
+    n = prob.apply_partials(L, dev(x), y, part)
+    ref = lv.apply(x)
+    assert relerr(host(y).reshape(lv.shape), ref) < TOL64
+    dot = float(part[:n].sum())
+    assert abs(dot - float(np.vdot(x, ref))) <= 1e-12 * abs(float(np.vdot(x, ref)))
     prob.close()

@@ -2,7 +2,8 @@
 (the paper's outer solver) with the gamma-cycle on a single GLL element,
 residual reduction 1e-8, interpolation-type restriction.  Iteration counts
 equal the oracle's GMRES counts (within one) and the printed Table 1 values
-(within one) for every gamma = 1..8; the GMRES solution equals the oracle's."""
+(within one; two for the GLL line blocks at p_L = 32) for every gamma = 1..8;
+the GMRES solution equals the oracle's."""
 import json
 import os
 
@@ -29,7 +30,11 @@ def _built():
 CASES = [("FEM", "problem1_lap_u_eq_minus1", 8), ("FEM", "problem1_lap_u_eq_minus1", 16),
          ("FEM", "problem3_sin_8pi_over_x_plus_y_plus_pi_10", 8),
          ("FEM", "problem3_sin_8pi_over_x_plus_y_plus_pi_10", 16),
-         ("GLL", "problem1_lap_u_eq_minus1", 8), ("GLL", "problem1_lap_u_eq_minus1", 16)]
+         ("GLL", "problem1_lap_u_eq_minus1", 8), ("GLL", "problem1_lap_u_eq_minus1", 16),
+         ("GLL", "problem1_lap_u_eq_minus1", 32)]
+# largest deviation from the printed counts (the oracle's own, see
+# tests/test_oracle_multigrid.py): GLL p_L = 32 gives 17 for the printed 19 at gamma = 1
+PRINTED_DEV = {("GLL", 32): 2}
 
 
 @pytest.mark.parametrize("smoother,problem,pL", CASES, ids=[f"{a}-{b[:8]}-p{c}" for a, b, c in CASES])
@@ -55,7 +60,8 @@ def test_table1_gmres_counts_on_gpu(smoother, problem, pL):
         ora.append(ref.iterations[0])
         np.testing.assert_allclose(u, ref.u[0].ravel(), atol=1e-9 * np.abs(ref.u[0]).max())
     assert all(abs(a - b) <= 1 for a, b in zip(gpu, ora)), (gpu, ora)
-    assert all(abs(a - b) <= 1 for a, b in zip(gpu, printed)), (gpu, printed)
+    dev = PRINTED_DEV.get((smoother, pL), 1)
+    assert all(abs(a - b) <= dev for a, b in zip(gpu, printed)), (gpu, printed)
     prob.close()
 
 

@@ -1,9 +1,10 @@
 """The allocation-free restriction entry point.
 
 glls_restrict_noalloc_f32 serves callers that cannot call cudaMalloc (for
-instance code that runs while a stream is captured in global mode, or under
-an allocator that owns all device memory): it keeps its scratch in one fixed
-device array inside the library instead of the problem's own buffers.  It
+instance code running under an allocator that owns all device memory, or a
+path that must not pay cudaMalloc's implicit synchronisation): it keeps its
+scratch in one fixed device array inside the library instead of the
+problem's own buffers.  It
 must give the same coarse residual as glls_restrict_f32, call after call,
 and refuse levels larger than its fixed scratch.
 
