@@ -71,10 +71,14 @@ enum { GLLS_KRYLOV_FCG = 0, GLLS_KRYLOV_PCG = 1, GLLS_KRYLOV_GMRES = 2 };
  *            (lines in 2-D, planes in 3-D) to the depth a launch-and-bytes
  *            cost model prefers, then the dense inverse of what is left
  *            (depth 0 = the dense inverse of A_0);
- *   DENSE    the dense inverse of A_0 (one matrix-vector product);
+ *   DENSE    the dense inverse of A_0 (one matrix-vector product; at most
+ *            16384 interior unknowns, larger systems are refused);
  *   BLOCK_CR coarse_cr_levels levels of block CR (0 = the model's depth, at
  *            least one), clamped to floor(log2(blocks)).
- * Every choice gives A_0^-1 r up to rounding. */
+ * Every choice gives A_0^-1 r up to rounding.  AUTO takes at least one level
+ * of block CR above 16384 unknowns; block CR stores dense blocks of the
+ * slowest axis (lines in 2-D, planes in 3-D) and refuses blocks of more than
+ * 2048 unknowns. */
 enum { GLLS_COARSE_AUTO = 0, GLLS_COARSE_DENSE = 1, GLLS_COARSE_BLOCK_CR = 2 };
 
 typedef struct glls_problem glls_problem;   /* opaque, library-owned */
@@ -254,6 +258,14 @@ glls_status glls_apply_f32(glls_problem* prob, int level, const float* x, float*
 glls_status glls_line_solve_f64(glls_problem* prob, int level, int axis, const double* g, double* x, void* stream);
 glls_status glls_line_solve_f32(glls_problem* prob, int level, int axis, const float* g, float* x, void* stream);
 
+/* The line update of a smoothing step alone (Def. 3.2, Algorithm 2), as the
+ * gamma-cycle launches it after y = A_l x: x += alpha B_s^-1 (r - y) on
+ * interior nodes.  y is consumed: its element-boundary entries are reset to
+ * 0 (the accumulating apply needs them zero), its other entries are left. */
+glls_status glls_line_update_f64(glls_problem* prob, int level, int axis, double alpha, const double* r, double* y,
+                                 double* x, void* stream);
+glls_status glls_line_update_f32(glls_problem* prob, int level, int axis, float alpha, const float* r, float* y,
+                                 float* x, void* stream);
 /* One damped line-smoothing step x <- x + alpha B_s^-1 (r - A_l x) (Algorithm 2). */
 glls_status glls_smooth_f64(glls_problem* prob, int level, int axis, double alpha, const double* r, double* x, void* stream);
 glls_status glls_smooth_f32(glls_problem* prob, int level, int axis, float alpha, const float* r, float* x, void* stream);

@@ -879,16 +879,13 @@ static glls_status problem_create(const glls_mesh_desc* desc, glls_problem** out
     }
     if (desc->coarse_solver < 0 || desc->coarse_solver > 2 || desc->coarse_cr_levels < 0)
         return fail(GLLS_ERR_INVALID, "coarse_solver must be GLLS_COARSE_* and coarse_cr_levels >= 0");
-    {
-        long long n0 = 1;
-        for (int a = 0; a < H[0].dim; ++a) n0 *= H[0].n[a] - 2;
-        if (n0 > 16384)
-            return fail(GLLS_ERR_INVALID, "coarsest level has more than 16384 interior unknowns (its matrix is "
-                                          "assembled densely on the host at set-up)");
-    }
     CoarseHost C;
     err = build_coarse(H[0], desc->coarse_solver, desc->coarse_cr_levels, C);
-    if (!err.empty()) return fail(GLLS_ERR_BREAKDOWN, err);
+    if (!err.empty())
+        return fail(err.find("too large") != std::string::npos || err.find("more than") != std::string::npos
+                        ? GLLS_ERR_INVALID
+                        : GLLS_ERR_BREAKDOWN,
+                    err);
     if (C.cr_levels > kMaxCrLevels) return fail(GLLS_ERR_INVALID, "too many block-CR levels");
 
     std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
@@ -1207,6 +1204,8 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
                      max_cr_levels(nb));
     else if (desc->coarse_solver == 0)
         k = auto_cr_levels(nb, m);
+    if (k == 0 && (long long)nb * m > 16384 && desc->coarse_solver != 1)   // as build_coarse
+        k = std::max(1, std::min(max_cr_levels(nb), auto_cr_levels(nb, m)));
     const double ldm = (double)((m + 3) / 4 * 4);
     for (int l = 0; l < k; ++l) {
         const int a = nb >> l;
@@ -1382,6 +1381,18 @@ glls_status glls_apply_partials_f64(glls_problem* P, int level, const double* x,
         DeviceScope scope(P->device);                                                                           \
         CK(scope.err);                                                                                          \
         smooth<T>(P, level, axis, alpha, r, x, false, (cudaStream_t)stream);                                    \
+        CK(cudaGetLastError());                                                                                 \
+        return GLLS_OK;                                                                                         \
+    }                                                                                                           \
+    glls_status glls_line_update_##SUF(glls_problem* P, int level, int axis, T alpha, const T* r, T* y, T* x,    \
+                                       void* stream) {                                                          \
+        glls_status s = check_level(P, level, false);                                                           \
+        if (s != GLLS_OK) return s;                                                                             \
+        if (axis < 0 || axis >= P->dim) return fail(GLLS_ERR_INVALID, "axis out of range");                     \
+        if (!r || !y || !x) return fail(GLLS_ERR_INVALID, "null vector");                                       \
+        DeviceScope scope(P->device);                                                                           \
+        CK(scope.err);                                                                                          \
+        launch_line_solve<T>(levels_of<T>(P)[level].dev, axis, 1, nullptr, r, y, x, alpha, (cudaStream_t)stream); \
         CK(cudaGetLastError());                                                                                 \
         return GLLS_OK;                                                                                         \
     }                                                                                                           \

@@ -15,8 +15,9 @@
 //   S nu = c                                  vertex CR, one warp per line
 //   x_I = z - w_L nu_left - w_R nu_right,  x_v = nu_v       (y = x + P e)
 //
-// A CTA of 256 threads owns LPC = min(16, 256 / E) lines of one direction
-// (E segments each), so that every thread has at most one segment task.  All
+// A CTA owns LPC <= min(16, 256 / E) lines of one direction (E segments
+// each) with LPC E threads (rounded up to a warp), one segment task per
+// thread; small levels take fewer lines per CTA so that every SM gets work.  All
 // global loads are issued at entry: the line values (coalesced: along the
 // line for x-lines, across adjacent lines for strided directions), the
 // vertex systems, and each thread's segment operator into registers; after
@@ -50,6 +51,16 @@ struct BlockLineArgs {
 
 constexpr int kBlockThreads = 256;
 constexpr int kMaxLinesPerCta = 16;
+
+// SMs of the current device (cached per process: one device type).
+int sm_count() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        return cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0 ? v : 152;
+    }();
+    return n;
+}
 
 // shared-memory index with one pad word per 32
 __device__ __forceinline__ int padk(int k) { return k + (k >> 5); }
@@ -95,8 +106,12 @@ struct SegOp {
 // on element-boundary nodes (the apply that produced y plain-stores element-
 // interior nodes and adds into element-boundary ones).  MODE 2: x += alpha
 // B^-1 r.  MODE 3: x = alpha B^-1 r.
-template <typename T, int P>
-__global__ void __launch_bounds__(kBlockThreads) line_block_kernel(BlockLineArgs<T> A) {
+// Register budget: FP32 four CTAs per SM (<= 64 registers), three for order 8
+// and the run-time order (<= 85: the 42 operator values of a segment stay in
+// registers), FP64 two (<= 128).
+template <typename T, int P, int CV>
+__global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 || P == 0 ? 3 : 4))
+    line_block_kernel(BlockLineArgs<T> A) {
     grid_dep_sync();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.n, E = A.E, span = A.span, mode = A.mode, LPC = A.lpc;
@@ -134,28 +149,39 @@ __global__ void __launch_bounds__(kBlockThreads) line_block_kernel(BlockLineArgs
             }
         }
     }
-    // line values: x-lines read along the line (warp-contiguous), strided
-    // directions across the CTA's adjacent lines
+    // line values, staged without divisions: x-lines are walked along the
+    // line by whole warps (coalesced along x); strided directions by threads
+    // that each keep one line of the CTA and step over its rows, adjacent
+    // threads on adjacent lines (coalesced across the lines)
     const bool contig = A.contiguous != 0;
-    const int total = Wc * n;
-#pragma unroll 4
-    for (int f = tid; f < total; f += kBlockThreads) {
-        int w, k;
-        if (contig) { w = f / n; k = f - w * n; }
-        else { k = f / Wc; w = f - k * Wc; }
-        const int node = line_base(w) + (k + 1) * A.stride;
+    const int nthr = blockDim.x, nwarp = nthr >> 5;
+    const int rows_per_pass = nthr / LPC;     // strided: rows covered per pass
+    const int sw = contig ? 0 : tid % LPC, sk0 = contig ? 0 : tid / LPC;
+    const bool s_active = !contig && sw < Wc && sk0 < rows_per_pass;
+    const int s_base = s_active ? line_base(sw) : 0;
+    auto stage = [&](int w, int k, int node) {
         T v;
         if (mode == 0) v = A.g[node];
         else if (mode == 1) v = A.r[node] - A.y[node];
         else v = A.r[node];
         sg[w * span + padk(k)] = v;
         if (mode == 1 || mode == 2) sx[w * span + padk(k)] = A.x[node];
+    };
+    if (contig) {
+        for (int w = tid >> 5; w < Wc; w += nwarp) {
+            const int b = line_base(w);
+#pragma unroll 2
+            for (int k = tid & 31; k < n; k += 32) stage(w, k, b + (k + 1) * A.stride);
+        }
+    } else if (s_active) {
+#pragma unroll 2
+        for (int k = sk0; k < n; k += rows_per_pass) stage(sw, k, s_base + (k + 1) * A.stride);
     }
     // vertex systems of the CTA's lines (contiguous in global memory)
     if (E > 1) {
         const T* vsrc = reinterpret_cast<const T*>(A.vband + (long long)l0 * (E - 1));
         const int nvb = 2 * Wc * (E - 1);
-        for (int i = tid; i < nvb; i += kBlockThreads) svb[i] = __ldg(vsrc + i);
+        for (int i = tid; i < nvb; i += nthr) svb[i] = __ldg(vsrc + i);
     }
     __syncthreads();
 
@@ -220,15 +246,10 @@ __global__ void __launch_bounds__(kBlockThreads) line_block_kernel(BlockLineArgs
     // ---- vertex systems, one warp per line
     const int warp = tid >> 5, lane = tid & 31;
     if (E > 1) {
-        for (int w = warp; w < Wc; w += kBlockThreads / 32) {
+        for (int w = warp; w < Wc; w += nwarp) {
             T* line = sg + w * span;
             const T* vb = svb + 2 * w * (E - 1);
-            switch (A.cv) {
-                case 1: vertex_solve<T, 1>(line, sdl + w * E, sdr + w * E, vb, E, p, lane); break;
-                case 2: vertex_solve<T, 2>(line, sdl + w * E, sdr + w * E, vb, E, p, lane); break;
-                case 4: vertex_solve<T, 4>(line, sdl + w * E, sdr + w * E, vb, E, p, lane); break;
-                default: vertex_solve<T, 8>(line, sdl + w * E, sdr + w * E, vb, E, p, lane); break;
-            }
+            vertex_solve<T, CV>(line, sdl + w * E, sdr + w * E, vb, E, p, lane);
         }
     }
     __syncthreads();
@@ -252,21 +273,31 @@ __global__ void __launch_bounds__(kBlockThreads) line_block_kernel(BlockLineArgs
     }
     __syncthreads();
 
-#pragma unroll 4
-    for (int f = tid; f < total; f += kBlockThreads) {
-        int w, k;
-        if (contig) { w = f / n; k = f - w * n; }
-        else { k = f / Wc; w = f - k * Wc; }
-        const int li = l0 + w;
-        const int c1 = li % A.m1 + 1, c2 = li / A.m1 + 1;
-        const int node = c1 * A.st1 + c2 * A.st2 + (k + 1) * A.stride;
+    // seam test: the line lies on an element boundary of another axis, or the
+    // node is a vertex of the line
+    auto put = [&](int w, int k, int base, bool line_seam) {
+        const int node = base + (k + 1) * A.stride;
         const T v = sg[w * span + padk(k)];
         A.x[node] = mode == 0 ? v : (mode == 3 ? A.alpha * v : sx[w * span + padk(k)] + A.alpha * v);
         // the next apply stores element-interior nodes and adds into the
-        // element-boundary ones: only those must be reset (the line lies on
-        // an element boundary of another axis, or the node is a vertex)
-        const bool seam = (c1 % p == 0) || (A.st2 != 0 && c2 % p == 0) || ((k + 1) % p == 0);
-        if (mode == 1 && seam) A.y[node] = T(0);
+        // element-boundary ones: only those must be reset
+        if (mode == 1 && (line_seam || (k + 1) % p == 0)) A.y[node] = T(0);
+    };
+    auto seam_of = [&](int w) {
+        const int li = l0 + w;
+        return ((li % A.m1 + 1) % p == 0) || (A.st2 != 0 && (li / A.m1 + 1) % p == 0);
+    };
+    if (contig) {
+        for (int w = tid >> 5; w < Wc; w += nwarp) {
+            const int b = line_base(w);
+            const bool ls = seam_of(w);
+#pragma unroll 2
+            for (int k = tid & 31; k < n; k += 32) put(w, k, b, ls);
+        }
+    } else if (s_active) {
+        const bool ls = seam_of(sw);
+#pragma unroll 2
+        for (int k = sk0; k < n; k += rows_per_pass) put(sw, k, s_base, ls);
     }
 }
 
@@ -275,27 +306,61 @@ size_t block_smem(int lpc, int span, int E) {
     return sizeof(T) * ((size_t)lpc * span * (P == 0 ? 3 : 2) + 2 * (size_t)lpc * E + 2 * (size_t)lpc * (E - 1));
 }
 
-template <typename T, int P>
-bool launch_p(BlockLineArgs<T> A, cudaStream_t st) {
+// Orders 2..8 are compiled for vertex chunks of 1 and 2 per lane (lines of up
+// to 65 elements); longer lines and other orders take the run-time order.
+template <typename T, int P, int CV>
+bool launch_pc(BlockLineArgs<T> A, cudaStream_t st) {
+    // lines per CTA: at most 256 segment tasks and 16 lines, fewer while the
+    // level would have less than about four CTAs per SM (small levels are
+    // latency bound: more, smaller CTAs run their phases side by side)
     int lpc = std::min(kMaxLinesPerCta, std::max(1, kBlockThreads / A.E));
+    while (lpc > 1 && (A.nlines + lpc - 1) / lpc < 4 * sm_count()) lpc /= 2;
     while (lpc > 1 && block_smem<T, P>(lpc, A.span, A.E) > kMaxDynSmemBytes) lpc /= 2;
     const size_t smem = block_smem<T, P>(lpc, A.span, A.E);
     if (smem > kMaxDynSmemBytes) return false;
     A.lpc = lpc;
+    const int threads = std::min(kBlockThreads, std::max(32, (lpc * A.E + 31) / 32 * 32));
     const int blocks = (A.nlines + lpc - 1) / lpc;
-    return launch_k(line_block_kernel<T, P>, blocks, kBlockThreads, smem, st, A) == cudaSuccess;
+    return launch_k(line_block_kernel<T, P, CV>, blocks, threads, smem, st, A) == cudaSuccess;
+}
+
+template <typename T, int P>
+bool launch_p(BlockLineArgs<T> A, cudaStream_t st) {
+    if constexpr (P > 0) {
+        if (A.cv == 1) return launch_pc<T, P, 1>(A, st);
+        if (A.cv == 2) return launch_pc<T, P, 2>(A, st);
+        return launch_p<T, 0>(A, st);
+    } else {
+        switch (A.cv) {
+            case 1: return launch_pc<T, 0, 1>(A, st);
+            case 2: return launch_pc<T, 0, 2>(A, st);
+            case 4: return launch_pc<T, 0, 4>(A, st);
+            default: return launch_pc<T, 0, 8>(A, st);
+        }
+    }
+}
+
+template <typename T, int P>
+bool set_attr_p() {
+    const int lim = (int)kMaxDynSmemBytes;
+    if constexpr (P > 0) {
+        return cudaFuncSetAttribute((const void*)line_block_kernel<T, P, 1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess &&
+               cudaFuncSetAttribute((const void*)line_block_kernel<T, P, 2>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+    } else {
+        const void* fns[] = {(const void*)line_block_kernel<T, 0, 1>, (const void*)line_block_kernel<T, 0, 2>,
+                             (const void*)line_block_kernel<T, 0, 4>, (const void*)line_block_kernel<T, 0, 8>};
+        for (const void* f : fns)
+            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) return false;
+        return true;
+    }
 }
 
 template <typename T>
 bool set_attr_t() {
-    const int lim = (int)kMaxDynSmemBytes;
-    const void* fns[] = {(const void*)line_block_kernel<T, 0>, (const void*)line_block_kernel<T, 2>,
-                         (const void*)line_block_kernel<T, 3>, (const void*)line_block_kernel<T, 4>,
-                         (const void*)line_block_kernel<T, 5>, (const void*)line_block_kernel<T, 6>,
-                         (const void*)line_block_kernel<T, 7>, (const void*)line_block_kernel<T, 8>};
-    for (const void* f : fns)
-        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) return false;
-    return true;
+    return set_attr_p<T, 0>() && set_attr_p<T, 2>() && set_attr_p<T, 3>() && set_attr_p<T, 4>() &&
+           set_attr_p<T, 5>() && set_attr_p<T, 6>() && set_attr_p<T, 7>() && set_attr_p<T, 8>();
 }
 
 }  // namespace

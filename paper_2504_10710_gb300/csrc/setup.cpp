@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <sstream>
 #include <thread>
 
@@ -608,30 +609,54 @@ std::string build_levels(int dim, const int nelem[3], int p_fine, const double* 
         if (c == 0) {
             std::memcpy(lv.coords.data(), coords, sizeof(double) * dim * lv.N);
         } else {
-            // coarse nodes: the finer element's coordinate polynomial at coarse GLL points
+            // coarse nodes: the finer element's coordinate polynomial at coarse
+            // GLL points, i.e. the 1-D interpolation J applied along each axis
+            // of the element's fine nodal coordinates (sum factorisation)
             const LevelHost& f = levels[chain.size() - c];
             const int pf = f.p, pc = lv.p, n1f = pf + 1, n1c = pc + 1;
-            std::vector<double> J = interpolation(pf, pc);   // [(pc+1) x (pf+1)]
+            const std::vector<double> J = interpolation(pf, pc);   // [(pc+1) x (pf+1)]
+            const int nzf = dim == 3 ? n1f : 1, nzc = dim == 3 ? n1c : 1;
+            std::vector<double> a((size_t)nzf * n1f * n1f), b((size_t)nzf * n1f * n1c), cc((size_t)nzf * n1c * n1c),
+                out((size_t)nzc * n1c * n1c);
             for (long long e = 0; e < lv.E; ++e) {
                 int ec[3];
                 element_coords(lv, e, ec);
-                for (int qc = 0; qc < lv.nloc; ++qc) {
-                    int lc[3];
-                    local_coords(qc, n1c, dim, lc);
-                    long long gc = ((long long)(dim == 3 ? ec[2] * pc + lc[2] : 0) * lv.n[1] + ec[1] * pc + lc[1]) * lv.n[0] + ec[0] * pc + lc[0];
-                    for (int b = 0; b < dim; ++b) {
-                        double v = 0.0;
-                        for (int qf = 0; qf < f.nloc; ++qf) {
-                            int lf[3];
-                            local_coords(qf, n1f, dim, lf);
-                            double wgt = J[lc[0] * n1f + lf[0]] * J[lc[1] * n1f + lf[1]];
-                            if (dim == 3) wgt *= J[lc[2] * n1f + lf[2]];
-                            if (wgt == 0.0) continue;
-                            long long gf = ((long long)(dim == 3 ? ec[2] * pf + lf[2] : 0) * f.n[1] + ec[1] * pf + lf[1]) * f.n[0] + ec[0] * pf + lf[0];
-                            v += wgt * f.coords[(size_t)b * f.N + gf];
-                        }
-                        lv.coords[(size_t)b * lv.N + gc] = v;
-                    }
+                for (int bdim = 0; bdim < dim; ++bdim) {
+                    for (int k = 0; k < nzf; ++k)
+                        for (int j = 0; j < n1f; ++j)
+                            for (int i = 0; i < n1f; ++i) {
+                                const long long gf = ((long long)(dim == 3 ? ec[2] * pf + k : 0) * f.n[1] + ec[1] * pf + j) *
+                                                         f.n[0] + ec[0] * pf + i;
+                                a[((size_t)k * n1f + j) * n1f + i] = f.coords[(size_t)bdim * f.N + gf];
+                            }
+                    // along x, then y, then z
+                    for (int k = 0; k < nzf; ++k)
+                        for (int j = 0; j < n1f; ++j)
+                            for (int i = 0; i < n1c; ++i) {
+                                double v = 0.0;
+                                for (int q = 0; q < n1f; ++q) v += J[i * n1f + q] * a[((size_t)k * n1f + j) * n1f + q];
+                                b[((size_t)k * n1f + j) * n1c + i] = v;
+                            }
+                    for (int k = 0; k < nzf; ++k)
+                        for (int j = 0; j < n1c; ++j)
+                            for (int i = 0; i < n1c; ++i) {
+                                double v = 0.0;
+                                for (int q = 0; q < n1f; ++q) v += J[j * n1f + q] * b[((size_t)k * n1f + q) * n1c + i];
+                                cc[((size_t)k * n1c + j) * n1c + i] = v;
+                            }
+                    for (int k = 0; k < nzc; ++k)
+                        for (int j = 0; j < n1c; ++j)
+                            for (int i = 0; i < n1c; ++i) {
+                                double v = 0.0;
+                                if (dim == 3) {
+                                    for (int q = 0; q < n1f; ++q) v += J[k * n1f + q] * cc[((size_t)q * n1c + j) * n1c + i];
+                                } else {
+                                    v = cc[(size_t)j * n1c + i];
+                                }
+                                const long long gc = ((long long)(dim == 3 ? ec[2] * pc + k : 0) * lv.n[1] + ec[1] * pc + j) *
+                                                         lv.n[0] + ec[0] * pc + i;
+                                lv.coords[(size_t)bdim * lv.N + gc] = v;
+                            }
                 }
             }
         }
@@ -668,11 +693,32 @@ std::string build_levels(int dim, const int nelem[3], int p_fine, const double* 
     return "";
 }
 
-// Dense inverse of the interior block of A_0 (assembled from element
-// matrices), via a banded Cholesky factorisation and one solve per column.
+// Runs fn(i) for i in [0, count) on up to `threads` host threads.
+void parallel_for(long long count, int threads, const std::function<void(long long)>& fn) {
+    const int nt = (int)std::max(1LL, std::min<long long>(count, threads));
+    if (nt <= 1) {
+        for (long long i = 0; i < count; ++i) fn(i);
+        return;
+    }
+    std::atomic<long long> next(0);
+    auto work = [&]() {
+        for (long long i = next.fetch_add(1); i < count; i = next.fetch_add(1)) fn(i);
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+}
+
+int host_threads() { return (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency())); }
+
 // Inverse of an SPD matrix with half bandwidth bw (dense n x n row-major):
-// banded Cholesky A = L L^T, then L L^T x = e_c for every column c.
-std::string spd_band_inverse(const std::vector<double>& A, long long n, long long bw, std::vector<double>& inv) {
+// banded Cholesky A = L L^T, then L L^T x = e_c for every column c (columns
+// split over `threads` host threads).  The back substitution reads a
+// transposed copy of the band, and the inverse, being symmetric, is written
+// by rows.
+std::string spd_band_inverse(const std::vector<double>& A, long long n, long long bw, std::vector<double>& inv,
+                             int threads = 1) {
     // banded Cholesky A = L L^T, L stored dense (lower band used)
     std::vector<double> L((size_t)n * n, 0.0);
     for (long long j = 0; j < n; ++j) {
@@ -689,11 +735,15 @@ std::string spd_band_inverse(const std::vector<double>& A, long long n, long lon
             L[(size_t)i * n + j] = t / ljj;
         }
     }
+    // U[i][k - i] = L[k][i] for i <= k <= i + bw
+    const long long w = bw + 1;
+    std::vector<double> U((size_t)n * w, 0.0);
+    for (long long i = 0; i < n; ++i)
+        for (long long k = i; k <= std::min(n - 1, i + bw); ++k) U[(size_t)i * w + (k - i)] = L[(size_t)k * n + i];
     inv.assign((size_t)n * n, 0.0);
-    std::vector<double> y(n);
-    for (long long c = 0; c < n; ++c) {
+    parallel_for(n, threads, [&](long long c) {
+        std::vector<double> y(n, 0.0);
         // forward L y = e_c
-        std::fill(y.begin(), y.end(), 0.0);
         for (long long i = c; i < n; ++i) {
             double t = (i == c) ? 1.0 : 0.0;
             for (long long k = std::max(c, i - bw); k < i; ++k) t -= L[(size_t)i * n + k] * y[k];
@@ -702,11 +752,13 @@ std::string spd_band_inverse(const std::vector<double>& A, long long n, long lon
         // backward L^T x = y
         for (long long i = n - 1; i >= 0; --i) {
             double t = y[i];
-            for (long long k = i + 1; k <= std::min(n - 1, i + bw); ++k) t -= L[(size_t)k * n + i] * y[k];
-            y[i] = t / L[(size_t)i * n + i];
+            const long long kmax = std::min(n - 1, i + bw);
+            for (long long k = i + 1; k <= kmax; ++k) t -= U[(size_t)i * w + (k - i)] * y[k];
+            y[i] = t / U[(size_t)i * w];
         }
-        for (long long i = 0; i < n; ++i) inv[(size_t)i * n + c] = y[i];
-    }
+        // A^-1 is symmetric: column c is row c
+        std::copy(y.begin(), y.end(), inv.begin() + (size_t)c * n);
+    });
     return "";
 }
 
@@ -714,14 +766,26 @@ namespace {
 
 using Mat = std::vector<double>;
 
+// c = a b for m x m row-major blocks, tiled so that a 64 x 256 tile of b
+// stays in cache while every row of a sweeps it
 Mat matmul(const Mat& a, const Mat& b, int m) {
     Mat c((size_t)m * m, 0.0);
-    for (int i = 0; i < m; ++i)
-        for (int k = 0; k < m; ++k) {
-            const double aik = a[(size_t)i * m + k];
-            if (aik == 0.0) continue;
-            for (int j = 0; j < m; ++j) c[(size_t)i * m + j] += aik * b[(size_t)k * m + j];
+    constexpr int TK = 64, TJ = 256;
+    for (int j0 = 0; j0 < m; j0 += TJ) {
+        const int j1 = std::min(m, j0 + TJ);
+        for (int k0 = 0; k0 < m; k0 += TK) {
+            const int k1 = std::min(m, k0 + TK);
+            for (int i = 0; i < m; ++i) {
+                double* ci = &c[(size_t)i * m];
+                for (int k = k0; k < k1; ++k) {
+                    const double aik = a[(size_t)i * m + k];
+                    if (aik == 0.0) continue;
+                    const double* bk = &b[(size_t)k * m];
+                    for (int j = j0; j < j1; ++j) ci[j] += aik * bk[j];
+                }
+            }
         }
+    }
     return c;
 }
 
@@ -765,53 +829,55 @@ int auto_cr_levels(int nb, int m) {
     return best;
 }
 
-// Block cyclic reduction of the block-tridiagonal A (Def. 3.5 blocks of size
-// m, nb blocks) for k levels (Thm. 3.8 with m > 1, Prop. 3.7, Cor. 3.9), then
-// the dense inverse of the remaining coarse system.  At each level the odd
-// blocks (1-based) are eliminated: stored A_j^-1, A_j^-1 L_j, A_j^-1 U_j; the
-// even blocks are kept: stored L_i A_{i-1}^-1 and U_i A_{i+1}^-1, and their
-// coarse blocks follow Prop. 3.7.
-std::string build_block_cr(const std::vector<double>& A, long long n, int nb, int m, int k, CoarseHost& out) {
+// Block cyclic reduction of the block-tridiagonal matrix with diagonal blocks
+// Ab, sub-diagonal Lb and super-diagonal Ub (Def. 3.5 blocks of size m, nb
+// blocks) for k levels (Thm. 3.8 with m > 1, Prop. 3.7, Cor. 3.9), then the
+// dense inverse of the remaining coarse system.  At each level the odd blocks
+// (1-based) are eliminated: stored A_j^-1, A_j^-1 L_j, A_j^-1 U_j; the even
+// blocks are kept: stored L_i A_{i-1}^-1 and U_i A_{i+1}^-1, and their coarse
+// blocks follow Prop. 3.7.  The blocks of a level are processed in parallel.
+std::string build_block_cr(std::vector<Mat> Ab, std::vector<Mat> Lb, std::vector<Mat> Ub, int m, int k,
+                           CoarseHost& out) {
     const Mat zero((size_t)m * m, 0.0);
-    auto block = [&](int bi, int bj) {
-        Mat B((size_t)m * m);
-        for (int r = 0; r < m; ++r)
-            for (int c = 0; c < m; ++c) B[(size_t)r * m + c] = A[(size_t)((long long)bi * m + r) * n + (long long)bj * m + c];
-        return B;
-    };
-    std::vector<Mat> Ab(nb), Lb(nb), Ub(nb);
-    for (int i = 0; i < nb; ++i) {
-        Ab[i] = block(i, i);
-        Lb[i] = i > 0 ? block(i, i - 1) : zero;
-        Ub[i] = i + 1 < nb ? block(i, i + 1) : zero;
-    }
+    const int threads = host_threads();
+    const size_t mm = (size_t)m * m;
     out.fh.assign(k, Mat());
     out.agk.assign(k, Mat());
     for (int l = 0; l < k; ++l) {
         const int a = (int)Ab.size();
+        const int ne = (a + 1) / 2, nk = a / 2;
         std::vector<Mat> Ainv(a);
-        for (int t = 0; t < a; t += 2) {             // eliminated (1-based odd)
-            std::string e = spd_band_inverse(Ab[t], m, m - 1, Ainv[t]);
-            if (!e.empty()) return e;
+        out.agk[l].assign(3 * mm * ne, 0.0);
+        std::vector<std::string> errs(a);
+        parallel_for(ne, threads, [&](long long q) {      // eliminated (1-based odd)
+            const int t = (int)(2 * q);
+            errs[t] = spd_band_inverse(Ab[t], m, m - 1, Ainv[t]);
+            if (!errs[t].empty()) return;
             const Mat G = matmul(Ainv[t], Lb[t], m), K = matmul(Ainv[t], Ub[t], m);
-            out.agk[l].insert(out.agk[l].end(), Ainv[t].begin(), Ainv[t].end());
-            out.agk[l].insert(out.agk[l].end(), G.begin(), G.end());
-            out.agk[l].insert(out.agk[l].end(), K.begin(), K.end());
-        }
-        std::vector<Mat> A2, L2, U2;
-        for (int t = 1; t < a; t += 2) {             // kept (1-based even)
+            double* dst = &out.agk[l][3 * mm * q];
+            std::copy(Ainv[t].begin(), Ainv[t].end(), dst);
+            std::copy(G.begin(), G.end(), dst + mm);
+            std::copy(K.begin(), K.end(), dst + 2 * mm);
+        });
+        for (const auto& e : errs)
+            if (!e.empty()) return e;
+        std::vector<Mat> A2(nk), L2(nk), U2(nk);
+        out.fh[l].assign(2 * mm * nk, 0.0);
+        parallel_for(nk, threads, [&](long long q) {      // kept (1-based even)
+            const int t = (int)(2 * q + 1);
             const bool right = t + 1 < a;
             const Mat F = matmul(Lb[t], Ainv[t - 1], m);
             const Mat H = right ? matmul(Ub[t], Ainv[t + 1], m) : zero;
-            out.fh[l].insert(out.fh[l].end(), F.begin(), F.end());
-            out.fh[l].insert(out.fh[l].end(), H.begin(), H.end());
+            double* dst = &out.fh[l][2 * mm * q];
+            std::copy(F.begin(), F.end(), dst);
+            std::copy(H.begin(), H.end(), dst + mm);
             Mat An = Ab[t];
             sub_into(An, matmul(F, Ub[t - 1], m));
             if (right) sub_into(An, matmul(H, Lb[t + 1], m));
-            A2.push_back(An);
-            L2.push_back(negated(matmul(F, Lb[t - 1], m)));
-            U2.push_back(right ? negated(matmul(H, Ub[t + 1], m)) : zero);
-        }
+            A2[q] = std::move(An);
+            L2[q] = negated(matmul(F, Lb[t - 1], m));
+            U2[q] = right ? negated(matmul(H, Ub[t + 1], m)) : zero;
+        });
         Ab.swap(A2);
         Lb.swap(L2);
         Ub.swap(U2);
@@ -828,7 +894,7 @@ std::string build_block_cr(const std::vector<double>& A, long long n, int nb, in
                 if (t > 0) Ar[row + (size_t)(t - 1) * m + c] = Lb[t][(size_t)r * m + c];
                 if (t + 1 < a) Ar[row + (size_t)(t + 1) * m + c] = Ub[t][(size_t)r * m + c];
             }
-    return spd_band_inverse(Ar, nr, std::min<long long>(nr - 1, 2LL * m - 1), out.inv);
+    return spd_band_inverse(Ar, nr, std::min<long long>(nr - 1, 2LL * m - 1), out.inv, threads);
 }
 
 std::string build_coarse(const LevelHost& lv, int coarse_solver, int cr_levels, CoarseHost& out) {
@@ -843,22 +909,43 @@ std::string build_coarse(const LevelHost& lv, int coarse_solver, int cr_levels, 
     const long long n = (long long)out.index.size();
     out.n = n;
     if (n == 0) return "coarsest level has no interior unknowns";
-    // The coarsest matrix is assembled densely on the host before its block
-    // factorisation; beyond this size that costs gigabytes and minutes.
-    constexpr long long kMaxCoarseUnknowns = 16384;
-    if (n > kMaxCoarseUnknowns)
-        return "coarsest level has more than 16384 interior unknowns (dense host assembly); use fewer elements";
-    // half bandwidth in the interior numbering
+    // blocks: one per interior index of the slowest axis (grid lines in 2-D,
+    // planes in 3-D); the lexicographic numbering makes them contiguous, and
+    // A_0 couples a block only to itself and its two neighbours
+    out.nb = lv.n[d - 1] - 2;
+    out.m = (int)(n / out.nb);
+    const int nb = out.nb, m = out.m;
+    int k = 0;
+    if (coarse_solver == 2)
+        k = std::min(cr_levels > 0 ? cr_levels : std::max(1, auto_cr_levels(nb, m)), max_cr_levels(nb));
+    else if (coarse_solver == 0) k = auto_cr_levels(nb, m);
+    // the dense inverse of the whole system is kept to moderate sizes; larger
+    // systems take at least one level of block CR
+    constexpr long long kMaxDenseUnknowns = 16384;
+    if (k == 0 && n > kMaxDenseUnknowns) {
+        if (coarse_solver == 1)
+            return "coarsest level has more than 16384 interior unknowns: use GLLS_COARSE_AUTO or GLLS_COARSE_BLOCK_CR";
+        k = std::max(1, std::min(max_cr_levels(nb), auto_cr_levels(nb, m)));
+    }
+    if (k == 0 && n > kMaxDenseUnknowns) return "coarsest level too large for a dense inverse";
+    // block CR stores dense m x m blocks: bound their size and number
+    constexpr int kMaxBlock = 2048;
+    if (k > 0 && (m > kMaxBlock || (double)nb * m * m * 8.0 * 6.0 > 24e9))
+        return "coarsest level too large for block cyclic reduction (blocks of " + std::to_string(m) + " unknowns)";
+    out.cr_levels = k;
+    // assemble the blocks from the element matrices:
+    // A_e[m][m2] = sum_q sum_ab G_ab(q) B_a(q, m) B_b(q, m2)
+    const size_t mm = (size_t)m * m;
+    std::vector<Mat> Ab(nb, Mat(mm, 0.0)), Lb(nb, Mat(mm, 0.0)), Ub(nb, Mat(mm, 0.0));
     long long bw = 0;
     Geo geo{d, p, n1, nloc, &lv};
-    std::vector<double> A((size_t)n * n, 0.0);
     const std::vector<double>& D = lv.D;
     for (long long e = 0; e < lv.E; ++e) {
         int ec[3];
         element_coords(lv, e, ec);
-        for (int m = 0; m < nloc; ++m) {
+        for (int mq = 0; mq < nloc; ++mq) {
             int mc[3];
-            local_coords(m, n1, d, mc);
+            local_coords(mq, n1, d, mc);
             long long gm = id[geo.gnode(ec, mc)];
             if (gm < 0) continue;
             for (int m2 = 0; m2 < nloc; ++m2) {
@@ -866,7 +953,6 @@ std::string build_coarse(const LevelHost& lv, int coarse_solver, int cr_levels, 
                 local_coords(m2, n1, d, mc2);
                 long long gm2 = id[geo.gnode(ec, mc2)];
                 if (gm2 < 0) continue;
-                // A_e[m][m2] = sum_q sum_ab G_ab(q) B_a(q, m) B_b(q, m2)
                 double v = 0.0;
                 for (int q = 0; q < nloc; ++q) {
                     int qc[3];
@@ -884,25 +970,30 @@ std::string build_coarse(const LevelHost& lv, int coarse_solver, int cr_levels, 
                         }
                     }
                 }
-                A[(size_t)gm * n + gm2] += v;
+                const long long bi = gm / m, bj = gm2 / m;
+                const size_t o = (size_t)(gm % m) * m + (size_t)(gm2 % m);
+                if (bj == bi) Ab[bi][o] += v;
+                else if (bj == bi - 1) Lb[bi][o] += v;
+                else if (bj == bi + 1) Ub[bi][o] += v;
+                else return "coarsest-level matrix is not block tridiagonal over the slowest axis";
                 bw = std::max(bw, std::llabs(gm - gm2));
             }
         }
     }
-    // blocks: one per interior index of the slowest axis (grid lines in 2-D,
-    // planes in 3-D); the lexicographic numbering makes them contiguous
-    out.nb = lv.n[d - 1] - 2;
-    out.m = (int)(n / out.nb);
-    int k = 0;
-    if (coarse_solver == 2)
-        k = std::min(cr_levels > 0 ? cr_levels : std::max(1, auto_cr_levels(out.nb, out.m)), max_cr_levels(out.nb));
-    else if (coarse_solver == 0) k = auto_cr_levels(out.nb, out.m);
-    out.cr_levels = k;
     if (k == 0) {       // dense A_0^-1
+        std::vector<double> A((size_t)n * n, 0.0);
+        for (int t = 0; t < nb; ++t)
+            for (int r = 0; r < m; ++r)
+                for (int c = 0; c < m; ++c) {
+                    const size_t row = (size_t)((long long)t * m + r) * n;
+                    A[row + (size_t)t * m + c] = Ab[t][(size_t)r * m + c];
+                    if (t > 0) A[row + (size_t)(t - 1) * m + c] = Lb[t][(size_t)r * m + c];
+                    if (t + 1 < nb) A[row + (size_t)(t + 1) * m + c] = Ub[t][(size_t)r * m + c];
+                }
         out.nr = n;
-        return spd_band_inverse(A, n, bw, out.inv);
+        return spd_band_inverse(A, n, bw, out.inv, host_threads());
     }
-    return build_block_cr(A, n, out.nb, out.m, k, out);
+    return build_block_cr(std::move(Ab), std::move(Lb), std::move(Ub), m, k, out);
 }
 
 }  // namespace glls

@@ -97,6 +97,7 @@ def lib():
             sig[f"glls_apply_{suf}"] = [vp, i, vp, vp, vp]
             sig[f"glls_line_solve_{suf}"] = [vp, i, i, vp, vp, vp]
             sig[f"glls_smooth_{suf}"] = [vp, i, i, real, vp, vp, vp]
+            sig[f"glls_line_update_{suf}"] = [vp, i, i, real, vp, vp, vp, vp]
             sig[f"glls_restrict_{suf}"] = [vp, i, vp, vp, vp, vp]
             sig[f"glls_prolong_add_{suf}"] = [vp, i, vp, vp, vp]
             sig[f"glls_coarse_solve_{suf}"] = [vp, vp, vp, vp]
@@ -265,6 +266,12 @@ class Problem:
     def smooth(self, level, axis, alpha, r, x, stream=None):
         _check(getattr(lib(), f"glls_smooth_{self._suffix(r)}")(self.h, level, axis, alpha, _ptr(r), _ptr(x),
                                                                    _stream(stream)))
+
+    def line_update(self, level, axis, alpha, r, y, x, stream=None):
+        """x += alpha B_s^-1 (r - y) (the smoothing step's line update after
+        y = A x); y's element-boundary entries are reset to 0."""
+        _check(getattr(lib(), f"glls_line_update_{self._suffix(r)}")(self.h, level, axis, alpha, _ptr(r), _ptr(y),
+                                                                        _ptr(x), _stream(stream)))
 
     def restrict(self, level, r, x, rc, stream=None):
         _check(getattr(lib(), f"glls_restrict_{self._suffix(r)}")(self.h, level, _ptr(r), _ptr(x), _ptr(rc),

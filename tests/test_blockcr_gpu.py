@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import blockcr  # noqa: E402
 from oracle.discretize import Level  # noqa: E402
-from oracle.multigrid import Hierarchy  # noqa: E402
+from oracle.multigrid import Hierarchy, coarse_coords  # noqa: E402
 from paper_2504_10710_gb300 import glls, inputs  # noqa: E402
 
 
@@ -145,11 +145,61 @@ def test_estimate_bytes_tracks_block_cr_allocation(k):
     prob.close()
 
 
-def test_oversized_coarsest_level_is_refused():
+def _coarse_residual(wl, prob, lv, seed):
+    """||r - A_0 e|| / ||r|| for e = the library's coarse solve of a random r,
+    with A_0 applied by the oracle's matrix-free operator."""
+    r = np.where(lv.interior, inputs.random_field(lv.shape, seed), 0.0)
+    out = []
+    for dtype in (torch.float64, torch.float32):
+        e = torch.zeros(lv.N, dtype=dtype, device="cuda")
+        prob.coarse_solve(torch.tensor(r.ravel(), dtype=dtype, device="cuda"), e)
+        torch.cuda.synchronize()
+        ev = e.double().cpu().numpy().reshape(lv.shape)
+        out.append(np.linalg.norm(r - lv.apply(ev)) / np.linalg.norm(r))
+    return out
+
+
+def test_coarsest_level_above_the_dense_limit_takes_block_cr():
     """27^3 elements put 26^3 = 17,576 unknowns on the p = 1 level, above the
-    16,384 the dense host assembly accepts: GLLS_ERR_INVALID, no allocation."""
+    16,384 of the dense inverse: AUTO takes block CR over the 26 planes, the
+    coarse solve inverts A_0 (residual check with the oracle's operator), the
+    whole solve converges, and the dense solver alone is refused."""
     wl = inputs.random3d((27, 27, 27), 2, amp=0.1, seed=47)
     xi, _ = glls.gll(wl.order)
+    coords = wl.coords(xi)
     with pytest.raises(glls.GllsError) as err:
-        glls.Problem(wl.dim, wl.nelem, wl.order, wl.coords(xi))
+        glls.Problem(wl.dim, wl.nelem, wl.order, coords, coarse_solver=glls.COARSE_DENSE)
     assert err.value.status == glls.ERR_INVALID
+    prob = glls.Problem(wl.dim, wl.nelem, wl.order, coords)
+    assert prob.info.coarse_cr_levels >= 1 and prob.info.coarse_unknowns == 26 ** 3
+    fine = Level(wl.dim, wl.nelem, wl.order, coords)
+    lv0 = Level(3, wl.nelem, 1, coarse_coords(fine, 1))
+    r64, r32 = _coarse_residual(wl, prob, lv0, 9)
+    assert r64 < 1e-10 and r32 < 1e-4, (r64, r32)
+    prob.set_rhs(wl.sample_rhs(coords)[0])
+    prob.set_dirichlet(wl.sample_dirichlet(coords))
+    u = np.zeros(prob.N)
+    st = prob.solve(u, glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_MIXED))
+    assert st.status == glls.OK and st.rel_residual <= 1e-10
+    prob.close()
+
+
+def test_largest_serving_coarsest_level_32_cubed():
+    """The largest 3-D serving mesh, 32^3 elements, has 31^3 = 29,791
+    unknowns on its p = 1 level.  At p = 1 that level is the whole problem:
+    block CR over 31 planes of 961 unknowns is its exact inverse, so the
+    preconditioned solve converges in one iteration."""
+    wl = inputs.random3d((32, 32, 32), 1, amp=0.15, seed=48)
+    xi, _ = glls.gll(1)
+    coords = wl.coords(xi)
+    prob = glls.Problem(wl.dim, wl.nelem, 1, coords)
+    assert prob.info.coarse_unknowns == 31 ** 3 and prob.info.coarse_cr_levels >= 1
+    lv = Level(3, wl.nelem, 1, coords)
+    r64, r32 = _coarse_residual(wl, prob, lv, 10)
+    assert r64 < 1e-10 and r32 < 1e-4, (r64, r32)
+    prob.set_rhs(wl.sample_rhs(coords)[0])
+    prob.set_dirichlet(wl.sample_dirichlet(coords))
+    u = np.zeros(prob.N)
+    st = prob.solve(u, glls.opts(tol=1e-10, precision=glls.PREC_FP64))
+    assert st.status == glls.OK and st.iterations <= 2
+    prob.close()

@@ -142,6 +142,26 @@ def test_smooth(case, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+def test_line_update_after_apply(case, dtype):
+    """The smoothing step as two entry points: y = A x, then the line update
+    x += alpha B_s^-1 (r - y), which also leaves y zero on element seams."""
+    wl, prob, h, _, scale = case
+    tol = TOL64 * scale if dtype == torch.float64 else TOL32
+    alpha = 2.0 / 3.0
+    for l in range(1, len(h.levels)):
+        lv = h.levels[l]
+        for s in range(lv.dim):
+            x0 = interior_field(lv, 140 + l)
+            r = interior_field(lv, 150 + l)
+            x = dev(x0, dtype)
+            y = torch.zeros(lv.N, dtype=dtype, device="cuda")
+            prob.apply(l, x, y)
+            prob.line_update(l, s, alpha, dev(r, dtype), y, x)
+            ref = h.smoothers[l][s].smooth(x0, r, alpha)
+            assert relerr(host(x).reshape(lv.shape), ref) < tol * 10, (l, s)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
 def test_restrict_and_prolong(case, dtype):
     wl, prob, h, _, scale = case
     tol = TOL64 * scale if dtype == torch.float64 else TOL32
