@@ -60,6 +60,11 @@ def parse():
                     help="only the warm-up and timed mixed-precision solves (for an ncu launch list)")
     ap.add_argument("--profile3d", action="store_true",
                     help="as --profile, on the 3-D 16^3 p = 7 workload with one right-hand side")
+    ap.add_argument("--probe", choices=["line2d", "line3d", "apply64"],
+                    help="launch one kernel a few times on its workload, nothing else (small ncu captures): "
+                         "line2d / line3d = the fine-level FP32 line update (MODE 1) of every axis after one "
+                         "apply, on the 2-D bench workload / the 3-D 16^3 p = 7 workload; apply64 = the 2-D "
+                         "fine-level FP64 apply with fused p.Ap partials, then without")
     return ap.parse_args()
 
 
@@ -478,13 +483,47 @@ def smoother_rooflines(prob, glls, torch, inputs, flush):
 
 def multirhs_run(glls, inputs, torch, reps=3):
     """The 3-D multi-RHS workload: 16^3 hexahedra, p = 7 (1,442,897 nodes),
-    32 seeded right-hand sides solved together (the problem and 31 clones
-    sharing its mesh data, one glls_solve_batch launch), FP32 gamma-cycle
-    inside FP64 flexible CG, to 1e-10.  Outputs on the device, CUDA events."""
+    32 seeded right-hand sides, FP32 gamma-cycle inside FP64 flexible CG, to
+    1e-10, two ways: one problem created with nrhs = 32 (every kernel launch
+    covers all right-hand sides, reading the mesh data once), and the problem
+    plus 31 clones sharing its mesh data in one glls_solve_batch launch.
+    Outputs on the device, CUDA events."""
     wl = inputs.terrain3d()
+    stream = torch.cuda.current_stream()
+    o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED, max_iter=300)
+
+    def timed(fn):
+        st = fn()                  # first call captures the graph
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return st, float(np.median(ms))
+
+    # one problem, nrhs = 32
+    t0 = time.perf_counter()
+    multi, coords = glls.problem_for(wl, glls.SMOOTHER_GLL, nrhs=wl.nrhs)
+    F = np.ascontiguousarray(wl.sample_rhs(coords).reshape(wl.nrhs, -1))
+    multi.set_rhs(F)
+    multi.set_dirichlet(wl.sample_dirichlet(coords).ravel())
+    setup_multi = time.perf_counter() - t0
+    U = torch.zeros(wl.nrhs * multi.N, dtype=torch.float64, device="cuda")
+    st, ms_multi = timed(lambda: multi.solve(U, o, stream, raise_on_error=False))
+    its = np.array([x.iterations for x in st])
+    dof = multi.N * wl.nrhs
+    res = {"workload": wl.name, "nrhs": wl.nrhs, "dof": dof, "ms": ms_multi, "dof_per_s": dof / (ms_multi / 1e3),
+           "converged": int(sum(x.status == glls.OK for x in st)),
+           "iterations": {"median": float(np.median(its)), "max": int(its.max())}, "setup_s": setup_multi,
+           "form": "one problem with nrhs = 32 (each launch covers all right-hand sides)"}
+    multi.close()
+
+    # the problem and 31 clones in one batch launch
     t0 = time.perf_counter()
     base, coords = glls.problem_for(wl, glls.SMOOTHER_GLL)
-    F = wl.sample_rhs(coords)
     g = wl.sample_dirichlet(coords)
     probs = [base] + [base.clone() for _ in range(len(F) - 1)]
     for pr, f in zip(probs, F):
@@ -492,23 +531,12 @@ def multirhs_run(glls, inputs, torch, reps=3):
         pr.set_dirichlet(g)
     setup_s = time.perf_counter() - t0
     outs = [torch.zeros(base.N, dtype=torch.float64, device="cuda") for _ in probs]
-    o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED, max_iter=300)
-    st = glls.solve_batch(probs, outs, o, raise_on_error=False)      # captures the batch graph
-    stream = torch.cuda.current_stream()
-    ms = []
-    for _ in range(reps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        st = glls.solve_batch(probs, outs, o, stream, raise_on_error=False)
-        b.record(stream)
-        b.synchronize()
-        ms.append(a.elapsed_time(b))
+    st, ms_clones = timed(lambda: glls.solve_batch(probs, outs, o, stream, raise_on_error=False))
     its = np.array([x.iterations for x in st])
-    dof = base.N * len(probs)
-    res = {"workload": wl.name, "nrhs": len(probs), "dof": dof, "ms": float(np.median(ms)),
-           "dof_per_s": dof / (float(np.median(ms)) / 1e3),
-           "converged": int(sum(x.status == glls.OK for x in st)),
-           "iterations": {"median": float(np.median(its)), "max": int(its.max())}, "setup_s": setup_s}
+    res["clones"] = {"ms": ms_clones, "dof_per_s": dof / (ms_clones / 1e3),
+                     "converged": int(sum(x.status == glls.OK for x in st)),
+                     "iterations": {"median": float(np.median(its)), "max": int(its.max())}, "setup_s": setup_s,
+                     "form": "problem + 31 clones sharing the mesh data, one glls_solve_batch launch"}
     for pr in probs[1:]:
         pr.close()
     base.close()
@@ -681,6 +709,39 @@ def oracle_baseline(wl, u_ref_gpu=None):
     return out, r
 
 
+def probe(name, reps=3):
+    """Launch one kernel `reps` times per axis on its workload (see --probe)."""
+    import torch
+
+    import __graft_entry__
+    from paper_2504_10710_gb300 import glls, inputs
+    __graft_entry__.build()
+    wl = inputs.terrain3d(nrhs=1) if name == "line3d" else inputs.terrain2d()
+    prob, _ = glls.problem_for(wl, glls.SMOOTHER_GLL, glls.RESTRICT_TRANSPOSE)
+    L = prob.levels - 1
+    shape = prob.level_shape(L)
+    if name == "apply64":
+        x = _interior_random(torch, shape, torch.float64)
+        y = torch.zeros_like(x)
+        part = torch.zeros(8192, dtype=torch.float64, device="cuda")
+        for _ in range(reps):
+            y.zero_()
+            prob.apply_partials(L, x, y, part)
+        for _ in range(reps):           # the same apply without the partials
+            prob.apply(L, x, y)
+    else:
+        x = _interior_random(torch, shape, torch.float32)
+        r = _interior_random(torch, shape, torch.float32)
+        y = torch.zeros_like(x)
+        for ax in range(len(shape)):
+            for _ in range(reps):
+                prob.apply(L, x, y)
+                prob.line_update(L, ax, ALPHA, r, y, x)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": name, "workload": wl.name, "reps": reps}))
+    prob.close()
+
+
 def main():
     args = parse()
     rank, world = dist_init(args.gpus)
@@ -726,6 +787,9 @@ def main():
             "cpu_baseline": {"value": val, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
+        return
+    if args.probe:
+        probe(args.probe)
         return
     if args.roofline_3d:
         import torch

@@ -136,6 +136,7 @@ typedef struct {
     int coarse_cr_levels;       /* block-CR levels of the coarsest solve (0 = dense inverse) */
     long long coarse_dense_unknowns;   /* size of the densely inverted system */
     size_t instance_bytes;      /* device memory this instance owns alone: what a clone adds */
+    int nrhs;                   /* right-hand sides solved together (glls_problem_create_nrhs) */
 } glls_info;
 
 /* Reference GLL(p) nodes and weights (Def. 2.1); xi, rho: host arrays of p+1. */
@@ -144,6 +145,20 @@ glls_status glls_gll(int p, double* xi, double* rho);
 /* Build every level: geometry factors, line bands, CR-ready data, transfers and
  * the coarsest-level factor, and upload them to the device.  Synchronous. */
 glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out);
+/* As glls_problem_create, with nrhs >= 1 right-hand sides solved together:
+ * glls_set_rhs takes nrhs x N values ([nrhs][N], right-hand side j at j N),
+ * glls_set_dirichlet one N-vector shared by all, and glls_solve writes nrhs x
+ * N values into u and fills stats[0 .. nrhs-1].  Every kernel of the solve
+ * processes all right-hand sides in one launch with the right-hand side
+ * fastest in its CTA order, so the mesh data (geometry factors, line blocks,
+ * coarsest-level operators) is read from HBM about once per launch for all
+ * of them.  Each right-hand side has its own flexible-CG scalars and stops
+ * on its own (converged or broken down) while the others continue; the
+ * call returns the worst status.  Solves with nrhs > 1 run as one graph with
+ * a device-side loop (use_graph = 2) with FCG or PCG; level operations act
+ * on a single vector as for nrhs = 1.  (Multi-RHS block CR: Thm. 3.8 with
+ * the block products applied to all right-hand sides of a launch.) */
+glls_status glls_problem_create_nrhs(const glls_mesh_desc* desc, int nrhs, glls_problem** out);
 /* A second problem on the same mesh: it shares every read-only device array of
  * prob (geometry factors, line bands, transfers, coarsest inverse, mass; held
  * until the last of them is destroyed) and owns its own right-hand side,
@@ -223,6 +238,15 @@ void glls_server_destroy(glls_server* server);
  * the request completes and must stay valid until then.  Returns a ticket. */
 glls_status glls_submit(glls_server* server, const glls_mesh_desc* mesh, const double* f, const double* g,
                         const glls_solve_opts* opts, double* u, unsigned long long* ticket);
+/* Registers a mesh with the server (its coordinates are copied and keyed
+ * once) and returns an id for glls_submit_mesh; nothing is set up until the
+ * first request on it runs.  Registered meshes stay known until the server
+ * is destroyed (their device data is still subject to eviction). */
+glls_status glls_server_register(glls_server* server, const glls_mesh_desc* mesh, unsigned long long* mesh_id);
+/* As glls_submit, on a registered mesh: f and g (N host values each; g may
+ * be NULL) are copied, u is written when the request completes. */
+glls_status glls_submit_mesh(glls_server* server, unsigned long long mesh_id, const double* f, const double* g,
+                             const glls_solve_opts* opts, double* u, unsigned long long* ticket);
 /* GLLS_NOT_READY while queued or running (wait = 0), else the request's
  * status with stats filled (queue + solve time in stats->solve_ms, set-up of a
  * newly created problem in stats->setup_ms); wait = 1 blocks until done.  A

@@ -105,6 +105,7 @@ struct glls_problem {
     int nelem[3] = {1, 1, 1};
     int p = 1;
     int smoother = 0, restriction = 0;
+    int nrhs = 1;          // right-hand sides solved together (vectors hold nrhs copies of their grid)
     std::vector<int> orders;
     std::vector<LevelStore<double>> L64;
     std::vector<LevelStore<float>> L32;
@@ -178,7 +179,7 @@ using ProblemPtr = std::unique_ptr<glls_problem, ProblemDeleter>;
 template <typename T>
 glls_status alloc_level_vectors(glls_problem* P, std::vector<LevelStore<T>>& Ls) {
     for (auto& s : Ls) {
-        const long long n = s.dev.N;
+        const long long n = s.dev.N * P->nrhs;
         CK(P->alloc(&s.r, n));
         CK(P->alloc(&s.x, n));
         CK(P->alloc(&s.y, n));
@@ -192,22 +193,29 @@ glls_status alloc_level_vectors(glls_problem* P, std::vector<LevelStore<T>>& Ls)
 }
 
 // Per-instance Krylov state, scalars, streams.
+// Per right-hand side: f, f0 and the Krylov vectors; g and the lifting v
+// are shared.  Scalars, partial sums and tickets per right-hand side.
 glls_status alloc_instance(glls_problem* P) {
-    const long long N = P->N;
-    double** vecs[] = {&P->f, &P->g, &P->v, &P->f0, &P->xk, &P->rk, &P->pk, &P->qk, &P->zk, &P->yk};
+    const long long N = P->N, k = P->nrhs;
+    double** vecs[] = {&P->f, &P->f0, &P->xk, &P->rk, &P->pk, &P->qk, &P->zk, &P->yk};
     for (double** vp : vecs) {
+        CK(P->alloc(vp, N * k));
+        CK(cudaMemset(*vp, 0, sizeof(double) * N * k));
+    }
+    double** shared_vecs[] = {&P->g, &P->v};
+    for (double** vp : shared_vecs) {
         CK(P->alloc(vp, N));
         CK(cudaMemset(*vp, 0, sizeof(double) * N));
     }
-    CK(P->alloc(&P->S, S_COUNT));
-    CK(P->alloc(&P->part, std::max<long long>(2 * kMaxReduceBlocks, 3 * kDotBlocks + P->L64.back().dev.E + 1)));
-    CK(P->alloc(&P->ticket, 1));
-    CK(cudaMemset(P->ticket, 0, sizeof(unsigned)));
-    CK(P->alloc(&P->r32, N));
-    CK(P->alloc(&P->z32, N));
-    CK(cudaMemset(P->r32, 0, sizeof(float) * N));
-    CK(cudaMemset(P->z32, 0, sizeof(float) * N));
-    CK(cudaMallocHost(&P->hostS, sizeof(double) * S_COUNT));
+    CK(P->alloc(&P->S, S_COUNT * k));
+    CK(P->alloc(&P->part, k * std::max<long long>(2 * kMaxReduceBlocks, 3 * kDotBlocks + P->L64.back().dev.E + 1)));
+    CK(P->alloc(&P->ticket, k));
+    CK(cudaMemset(P->ticket, 0, sizeof(unsigned) * k));
+    CK(P->alloc(&P->r32, N * k));
+    CK(P->alloc(&P->z32, N * k));
+    CK(cudaMemset(P->r32, 0, sizeof(float) * N * k));
+    CK(cudaMemset(P->z32, 0, sizeof(float) * N * k));
+    CK(cudaMallocHost(&P->hostS, sizeof(double) * S_COUNT * k));
     CK(cudaStreamCreateWithFlags(&P->capture_stream, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&P->capture_stream2, cudaStreamNonBlocking));
     return GLLS_OK;
@@ -348,15 +356,16 @@ const DevCoarse<float>& coarse_of<float>(glls_problem* P) { return P->C32; }
 
 // rc = R_l (r - y) on level l-1
 template <typename T>
-void restrict_residual(glls_problem* P, int l, const T* r, const T* y, T* rc, cudaStream_t st) {
+void restrict_residual(glls_problem* P, int l, const T* r, const T* y, T* rc, cudaStream_t st, int nrhs = 1) {
     auto& Ls = levels_of<T>(P);
     const DevLevel<T>& F = Ls[l].dev;
     const DevLevel<T>& C = Ls[l - 1].dev;
     // axes 0 and 1 in one fused launch (then axis 2 in 3-D)
     const int mid[3] = {C.n[0], C.n[1], F.n[2]};
     const bool only2 = F.dim == 2;
-    if (launch_transfer2<T>(F.R[0], F.R[1], F.n, mid, r, y, only2 ? rc : Ls[l].t1, false, only2, st)) {
-        if (!only2) launch_transfer<T>(F.R[2], 2, mid, C.n, Ls[l].t1, nullptr, rc, false, true, st);
+    if (launch_transfer2<T>(F.R[0], F.R[1], F.n, mid, r, y, only2 ? rc : Ls[l].t1, false, only2, st, nullptr,
+                            nrhs)) {
+        if (!only2) launch_transfer<T>(F.R[2], 2, mid, C.n, Ls[l].t1, nullptr, rc, false, true, st, nullptr, nrhs);
         return;
     }
     int cur[3] = {F.n[0], F.n[1], F.n[2]};
@@ -367,7 +376,7 @@ void restrict_residual(glls_problem* P, int l, const T* r, const T* y, T* rc, cu
         nxt[a] = C.n[a];
         const bool last = a == F.dim - 1;
         T* out = last ? rc : (a % 2 == 0 ? Ls[l].t1 : Ls[l].t2);
-        launch_transfer<T>(F.R[a], a, cur, nxt, in, in2, out, false, last, st);
+        launch_transfer<T>(F.R[a], a, cur, nxt, in, in2, out, false, last, st, nullptr, nrhs);
         in = out;
         in2 = nullptr;
         for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
@@ -376,15 +385,15 @@ void restrict_residual(glls_problem* P, int l, const T* r, const T* y, T* rc, cu
 
 // x += P_l e; clear (optional, level-l sized) is reset to 0 by the last pass
 template <typename T>
-void prolong_add(glls_problem* P, int l, const T* e, T* x, cudaStream_t st, T* clear = nullptr) {
+void prolong_add(glls_problem* P, int l, const T* e, T* x, cudaStream_t st, T* clear = nullptr, int nrhs = 1) {
     auto& Ls = levels_of<T>(P);
     const DevLevel<T>& F = Ls[l].dev;
     const DevLevel<T>& C = Ls[l - 1].dev;
     const int mid[3] = {F.n[0], F.n[1], C.n[2]};
     const bool only2 = F.dim == 2;
     if (launch_transfer2<T>(F.P[0], F.P[1], C.n, mid, e, nullptr, only2 ? x : Ls[l].t1, only2, false, st,
-                            only2 ? clear : nullptr)) {
-        if (!only2) launch_transfer<T>(F.P[2], 2, mid, F.n, Ls[l].t1, nullptr, x, true, false, st, clear);
+                            only2 ? clear : nullptr, nrhs)) {
+        if (!only2) launch_transfer<T>(F.P[2], 2, mid, F.n, Ls[l].t1, nullptr, x, true, false, st, clear, nrhs);
         return;
     }
     int cur[3] = {C.n[0], C.n[1], C.n[2]};
@@ -394,7 +403,7 @@ void prolong_add(glls_problem* P, int l, const T* e, T* x, cudaStream_t st, T* c
         nxt[a] = F.n[a];
         const bool last = a == F.dim - 1;
         T* out = last ? x : (a % 2 == 0 ? Ls[l].t1 : Ls[l].t2);
-        launch_transfer<T>(F.P[a], a, cur, nxt, in, nullptr, out, last, false, st, last ? clear : nullptr);
+        launch_transfer<T>(F.P[a], a, cur, nxt, in, nullptr, out, last, false, st, last ? clear : nullptr, nrhs);
         in = out;
         for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
     }
@@ -404,39 +413,40 @@ void prolong_add(glls_problem* P, int l, const T* e, T* x, cudaStream_t st, T* c
 // the apply.  The level scratch y is zero on entry and on exit: the apply
 // accumulates into it and the line solve resets what it reads.
 template <typename T>
-void smooth(glls_problem* P, int l, int s, T alpha, const T* r, T* x, bool x_is_zero, cudaStream_t st) {
+void smooth(glls_problem* P, int l, int s, T alpha, const T* r, T* x, bool x_is_zero, cudaStream_t st,
+            int nrhs = 1) {
     auto& Ls = levels_of<T>(P);
     if (x_is_zero) {
-        launch_line_solve<T>(Ls[l].dev, s, 3, nullptr, r, nullptr, x, alpha, st);
+        launch_line_solve<T>(Ls[l].dev, s, 3, nullptr, r, nullptr, x, alpha, st, nrhs);
     } else {
-        launch_apply<T>(Ls[l].dev, x, Ls[l].y, true, st, true);
-        launch_line_solve<T>(Ls[l].dev, s, 1, nullptr, r, Ls[l].y, x, alpha, st);
+        launch_apply<T>(Ls[l].dev, x, Ls[l].y, true, st, true, nullptr, nullptr, nullptr, nrhs);
+        launch_line_solve<T>(Ls[l].dev, s, 1, nullptr, r, Ls[l].y, x, alpha, st, nrhs);
     }
 }
 
 // Algorithm 2: x = M_l^-1 r from x0 = 0
 template <typename T>
-void cycle(glls_problem* P, int l, const T* r, T* x, int gamma, int m, T alpha, cudaStream_t st) {
+void cycle(glls_problem* P, int l, const T* r, T* x, int gamma, int m, T alpha, cudaStream_t st, int nrhs = 1) {
     auto& Ls = levels_of<T>(P);
     // x: boundary entries are zero and stay zero (only interior entries are written)
     if (l == 0) {
-        launch_coarse<T>(coarse_of<T>(P), Ls[0].dev.N, r, x, Ls[0].t1, st, true);
+        launch_coarse<T>(coarse_of<T>(P), Ls[0].dev.N, r, x, Ls[0].t1, st, true, nrhs);
         return;
     }
     const int d = Ls[l].dev.dim;
     bool zero = true;
     for (int s = 0; s < d; ++s)
         for (int k = 0; k < m; ++k) {
-            smooth<T>(P, l, s, alpha, r, x, zero, st);
+            smooth<T>(P, l, s, alpha, r, x, zero, st, nrhs);
             zero = false;
         }
     for (int g = 0; g < gamma; ++g) {
-        launch_apply<T>(Ls[l].dev, x, Ls[l].y, true, st, true);
-        restrict_residual<T>(P, l, r, Ls[l].y, Ls[l - 1].r, st);
-        cycle<T>(P, l - 1, Ls[l - 1].r, Ls[l - 1].x, gamma, m, alpha, st);
-        prolong_add<T>(P, l, Ls[l - 1].x, x, st, Ls[l].y);
+        launch_apply<T>(Ls[l].dev, x, Ls[l].y, true, st, true, nullptr, nullptr, nullptr, nrhs);
+        restrict_residual<T>(P, l, r, Ls[l].y, Ls[l - 1].r, st, nrhs);
+        cycle<T>(P, l - 1, Ls[l - 1].r, Ls[l - 1].x, gamma, m, alpha, st, nrhs);
+        prolong_add<T>(P, l, Ls[l - 1].x, x, st, Ls[l].y, nrhs);
         for (int s = d - 1; s >= 0; --s)
-            for (int k = 0; k < m; ++k) smooth<T>(P, l, s, alpha, r, x, false, st);
+            for (int k = 0; k < m; ++k) smooth<T>(P, l, s, alpha, r, x, false, st, nrhs);
     }
 }
 
@@ -473,36 +483,40 @@ glls_status check_opts(const glls_solve_opts* o) {
 void outer_iteration(glls_problem* P, const glls_solve_opts* o, cudaStream_t st) {
     const int L = (int)P->L64.size() - 1;
     const long long N = P->N;
+    const int k = P->nrhs;
     const bool mixed = o->precision == GLLS_PREC_MIXED;
-    if (mixed) cycle<float>(P, L, P->r32, P->z32, o->gamma, o->m, (float)o->alpha, st);
-    else cycle<double>(P, L, P->rk, P->zk, o->gamma, o->m, o->alpha, st);
-    // partial sums: r.z and z.q (kDotBlocks each), r.r (kDotBlocks), p.q (one per apply CTA)
+    if (mixed) cycle<float>(P, L, P->r32, P->z32, o->gamma, o->m, (float)o->alpha, st, k);
+    else cycle<double>(P, L, P->rk, P->zk, o->gamma, o->m, o->alpha, st, k);
+    // partial sums per right-hand side: r.z and z.q (kDotBlocks each), r.r
+    // (kDotBlocks), p.q (one per apply CTA)
     double* prz = P->part;
-    double* pzq = prz + kDotBlocks;
-    double* prr = pzq + kDotBlocks;
-    double* ppq = prr + kDotBlocks;
+    double* pzq = prz + (long long)k * kDotBlocks;
+    double* prr = pzq + (long long)k * kDotBlocks;
+    double* ppq = prr + (long long)k * kDotBlocks;
     const int npq = apply_dot_partials<double>(P->L64[L].dev);
-    launch_dots_rz_zq(P->rk, P->zk, mixed ? P->z32 : nullptr, P->qk, N, prz, pzq, st);
-    launch_fcg_direction(P->pk, P->zk, N, prz, pzq, kDotBlocks, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, st);
-    launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st, true, P->S + S_PQ, ppq, nullptr);
+    launch_dots_rz_zq(P->rk, P->zk, mixed ? P->z32 : nullptr, P->qk, N, prz, pzq, st, k);
+    launch_fcg_direction(P->pk, P->zk, N, prz, pzq, kDotBlocks, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, st, k);
+    launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st, true, P->S + S_PQ, ppq, nullptr, k);
     launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, ppq, npq, prz, kDotBlocks, prr, P->S, P->ticket,
-                      mixed ? P->r32 : nullptr, st);
+                      mixed ? P->r32 : nullptr, st, k);
 }
 
 // Lifting and Krylov initialisation (x = p = q = 0, r = f0, S_RR0 = r.r).
+// The lifting v of the (shared) Dirichlet data and A v are computed once;
+// f0 = M f - A v for every right-hand side.
 void solve_prologue(glls_problem* P, const glls_solve_opts* o, cudaStream_t st) {
-    const long long N = P->N;
+    const long long N = P->N, NK = P->N * P->nrhs;
     const int L = (int)P->L64.size() - 1;
     const DevLevel<double>& F = P->L64[L].dev;
     launch_boundary_only(P->g, P->v, F.n, F.dim, st);
     launch_apply<double>(F, P->v, P->yk, false, st);
-    launch_lift_rhs(P->mass, P->f, P->yk, P->f0, F.n, F.dim, st);
-    cudaMemsetAsync(P->xk, 0, sizeof(double) * N, st);
-    cudaMemsetAsync(P->pk, 0, sizeof(double) * N, st);
-    cudaMemsetAsync(P->qk, 0, sizeof(double) * N, st);
-    cudaMemcpyAsync(P->rk, P->f0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
-    launch_dots(P->rk, P->rk, nullptr, nullptr, 1, N, P->part, P->S, S_RR0, S_RR0, P->ticket, st);
-    if (o->precision == GLLS_PREC_MIXED) launch_cast<double, float>(P->rk, P->r32, N, st);
+    launch_lift_rhs(P->mass, P->f, P->yk, P->f0, F.n, F.dim, st, P->nrhs);
+    cudaMemsetAsync(P->xk, 0, sizeof(double) * NK, st);
+    cudaMemsetAsync(P->pk, 0, sizeof(double) * NK, st);
+    cudaMemsetAsync(P->qk, 0, sizeof(double) * NK, st);
+    cudaMemcpyAsync(P->rk, P->f0, sizeof(double) * NK, cudaMemcpyDeviceToDevice, st);
+    launch_dots(P->rk, P->rk, nullptr, nullptr, 1, N, P->part, P->S, S_RR0, S_RR0, P->ticket, st, P->nrhs);
+    if (o->precision == GLLS_PREC_MIXED) launch_cast<double, float>(P->rk, P->r32, NK, st);
 }
 
 bool same_solve_key(const glls_solve_opts& a, const glls_solve_opts& b) {
@@ -535,7 +549,7 @@ cudaError_t capture_solve(glls_problem* P, const glls_solve_opts* o, cudaStream_
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, capg, 0, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) return e;
     solve_prologue(P, o, cs);
-    launch_solve_init(P->S, handle, o->tol, o->max_iter, cs);
+    launch_solve_init(P->S, handle, o->tol, o->max_iter, cs, P->nrhs);
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
     e = cudaStreamGetCaptureInfo(cs, &stt, nullptr, &capg, &deps, nullptr, &ndeps);
@@ -552,14 +566,14 @@ cudaError_t capture_solve(glls_problem* P, const glls_solve_opts* o, cudaStream_
         e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             outer_iteration(P, o, cs2);
-            launch_solve_cond(P->S, handle, o->max_iter, cs2);
+            launch_solve_cond(P->S, handle, o->max_iter, cs2, P->nrhs);
             e = cudaStreamEndCapture(cs2, &body);
             if (e == cudaSuccess) P->kern_iter = count_kernel_nodes(body);
         }
     }
-    if (e == cudaSuccess) {
-        cudaMemcpyAsync(P->yk, P->xk, sizeof(double) * P->N, cudaMemcpyDeviceToDevice, cs);
-        launch_axpy(P->yk, P->v, 1.0, P->N, cs);
+    if (e == cudaSuccess) {   // u = w + v for every right-hand side
+        cudaMemcpyAsync(P->yk, P->xk, sizeof(double) * P->N * P->nrhs, cudaMemcpyDeviceToDevice, cs);
+        launch_axpy(P->yk, P->v, 1.0, P->N, cs, P->nrhs, true);
     }
     return e;
 }
@@ -587,24 +601,32 @@ glls_status get_solve_graph(glls_problem* P, const glls_solve_opts* o) {
 }
 
 // Fills stats / status of a finished device-loop solve from the host copy of S.
+// Fills stats[j] for every right-hand side j (stats: nrhs entries) and
+// returns the worst status (breakdown, then not converged, then OK).
 glls_status solve_result(glls_problem* P, const double* h, glls_stats* stats, double t_ms) {
-    glls_status result = GLLS_OK;
-    double rel = 0.0;
-    if (h[S_FLAG] != 0.0) {
-        result = GLLS_ERR_BREAKDOWN;
-    } else if (h[S_RR0] > 0.0) {
-        rel = std::sqrt(h[S_RR] / h[S_RR0]);
-        result = h[S_RR] <= h[S_TOL2] ? GLLS_OK : GLLS_ERR_NOT_CONVERGED;
+    glls_status worst = GLLS_OK;
+    for (int j = 0; j < P->nrhs; ++j) {
+        const double* hj = h + (long long)j * S_COUNT;
+        glls_status result = GLLS_OK;
+        double rel = 0.0;
+        if (hj[S_FLAG] != 0.0) {
+            result = GLLS_ERR_BREAKDOWN;
+        } else if (hj[S_RR0] > 0.0) {
+            rel = std::sqrt(hj[S_RR] / hj[S_RR0]);
+            result = hj[S_RR] <= hj[S_TOL2] ? GLLS_OK : GLLS_ERR_NOT_CONVERGED;
+        }
+        if (result == GLLS_ERR_BREAKDOWN || (result == GLLS_ERR_NOT_CONVERGED && worst == GLLS_OK)) worst = result;
+        if (stats) {
+            glls_stats& sj = stats[j];
+            sj.iterations = (int)(hj[S_DONE] != 0.0 ? hj[S_ITS] : hj[S_ITER]);
+            sj.rel_residual = rel;
+            sj.setup_ms = P->setup_ms;
+            sj.solve_ms = t_ms;
+            sj.status = result;
+            sj.kernels = P->kern_fixed + P->kern_iter * (long long)h[S_ITER];
+        }
     }
-    if (stats) {
-        stats->iterations = (int)h[S_ITER];
-        stats->rel_residual = rel;
-        stats->setup_ms = P->setup_ms;
-        stats->solve_ms = t_ms;
-        stats->status = result;
-        stats->kernels = P->kern_fixed + P->kern_iter * (long long)h[S_ITER];
-    }
-    return result;
+    return worst;
 }
 
 // Batched solves: one graph whose parallel branches are the whole solves of
@@ -816,7 +838,7 @@ glls_status glls_gll(int p, double* xi, double* rho) {
     return GLLS_OK;
 }
 
-static glls_status problem_create(const glls_mesh_desc* desc, glls_problem** out) {
+static glls_status problem_create(const glls_mesh_desc* desc, int nrhs, glls_problem** out) {
     if (!desc || !out) return fail(GLLS_ERR_INVALID, "null argument");
     *out = nullptr;
     if (desc->dim != 2 && desc->dim != 3) return fail(GLLS_ERR_INVALID, "dim must be 2 or 3");
@@ -850,7 +872,9 @@ static glls_status problem_create(const glls_mesh_desc* desc, glls_problem** out
     });
     if (!attrs_ok) return fail(GLLS_ERR_CUDA, "could not set kernel shared-memory attributes");
 
+    if (nrhs < 1 || nrhs > 4096) return fail(GLLS_ERR_INVALID, "nrhs must be in 1..4096");
     ProblemPtr P(new glls_problem());
+    P->nrhs = nrhs;
     P->shared = std::make_shared<SharedData>();
     P->shared->device = desc->device;
     P->device = desc->device;
@@ -917,6 +941,7 @@ static glls_status problem_clone(const glls_problem* src, glls_problem** out) {
     CK(scope.err);
     ProblemPtr P(new glls_problem());
     std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
+    P->nrhs = src->nrhs;
     P->shared = src->shared;
     P->device = src->device;
     P->dim = src->dim;
@@ -948,8 +973,12 @@ static glls_status problem_clone(const glls_problem* src, glls_problem** out) {
 // Host allocations of the set-up (std::vector) report GLLS_ERR_OOM instead of
 // throwing across the ABI.
 glls_status glls_problem_create(const glls_mesh_desc* desc, glls_problem** out) {
+    return glls_problem_create_nrhs(desc, 1, out);
+}
+
+glls_status glls_problem_create_nrhs(const glls_mesh_desc* desc, int nrhs, glls_problem** out) {
     try {
-        return problem_create(desc, out);
+        return problem_create(desc, nrhs, out);
     } catch (const std::bad_alloc&) {
         return fail(GLLS_ERR_OOM, "host allocation failed during set-up");
     } catch (const std::exception& e) {
@@ -996,6 +1025,7 @@ glls_status glls_problem_info(const glls_problem* P, glls_info* out) {
     out->coarse_dense_unknowns = P->C64.nr;
     out->device_bytes = P->bytes + (P->shared ? P->shared->bytes : 0);
     out->instance_bytes = P->bytes;
+    out->nrhs = P->nrhs;
     return GLLS_OK;
 }
 
@@ -1015,7 +1045,8 @@ glls_status glls_set_rhs(glls_problem* P, const double* f, int on_device, void* 
     DeviceScope scope(P->device);
     CK(scope.err);
     cudaStream_t st = (cudaStream_t)stream;
-    CK(cudaMemcpyAsync(P->f, f, sizeof(double) * P->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P->f, f, sizeof(double) * P->N * P->nrhs,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     if (!on_device) CK(cudaStreamSynchronize(st));
     P->has_rhs = true;
     return GLLS_OK;
@@ -1023,6 +1054,8 @@ glls_status glls_set_rhs(glls_problem* P, const double* f, int on_device, void* 
 
 glls_status glls_lift_f64(glls_problem* P, const double* f, const double* g, double* f0, void* stream) {
     if (!P || !f || !g || !f0) return fail(GLLS_ERR_INVALID, "null argument");
+    DeviceScope scope(P->device);
+    CK(scope.err);
     cudaStream_t st = (cudaStream_t)stream;
     const int L = (int)P->L64.size() - 1;
     const DevLevel<double>& F = P->L64[L].dev;
@@ -1036,6 +1069,8 @@ glls_status glls_lift_f64(glls_problem* P, const double* f, const double* g, dou
 static glls_status solve_impl(glls_problem* P, const glls_solve_opts* o, double* u, int on_device, void* stream,
                               glls_stats* stats) {
     if (!P || !u) return fail(GLLS_ERR_INVALID, "null argument");
+    if (P->nrhs > 1 && o && (o->use_graph != 2 || o->krylov == GLLS_KRYLOV_GMRES))
+        return fail(GLLS_ERR_INVALID, "several right-hand sides: use_graph = 2 and FCG or PCG");
     glls_status s0 = check_opts(o);
     if (s0 != GLLS_OK) return s0;
     if (!P->has_rhs) return fail(GLLS_ERR_INVALID, "right-hand side not set");
@@ -1072,9 +1107,9 @@ static glls_status solve_impl(glls_problem* P, const glls_solve_opts* o, double*
         glls_status gs = get_solve_graph(P, o);
         if (gs != GLLS_OK) return gs;
         CK(cudaGraphLaunch(P->solve_exec, st));
-        CK(cudaMemcpyAsync(u, P->yk, sizeof(double) * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                           st));
-        CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(u, P->yk, sizeof(double) * N * P->nrhs,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT * P->nrhs, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         CK(cudaGetLastError());
         result = solve_result(P, P->hostS, stats,
@@ -1145,9 +1180,16 @@ static glls_status solve_impl(glls_problem* P, const glls_solve_opts* o, double*
 // the solve stopped before any iteration.
 glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int on_device, void* stream,
                        glls_stats* stats) {
-    if (stats) std::memset(stats, 0, sizeof(*stats));
+    const int k = P ? P->nrhs : 1;
+    if (stats) std::memset(stats, 0, sizeof(*stats) * k);
     const glls_status r = solve_impl(P, o, u, on_device, stream, stats);
-    if (stats) stats->status = r;
+    if (stats) {
+        if (k == 1) {
+            stats[0].status = r;
+        } else if (r != GLLS_OK && r != GLLS_ERR_NOT_CONVERGED && r != GLLS_ERR_BREAKDOWN) {
+            for (int j = 0; j < k; ++j) stats[j].status = r;   // nothing ran: every right-hand side failed
+        }
+    }
     return r;
 }
 
@@ -1231,6 +1273,9 @@ glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve
         if (!probs[i] || !u[i]) return fail(GLLS_ERR_INVALID, "glls_solve_batch: null problem or output");
         if (probs[i]->device != dev) return fail(GLLS_ERR_INVALID, "glls_solve_batch: problems on different devices");
         if (!probs[i]->has_rhs) return fail(GLLS_ERR_INVALID, "glls_solve_batch: right-hand side not set");
+        if (probs[i]->nrhs != 1)
+            return fail(GLLS_ERR_INVALID, "glls_solve_batch: problems with one right-hand side only (glls_solve "
+                                          "takes several)");
         for (int j = 0; j < i; ++j)
             if (probs[j] == probs[i]) return fail(GLLS_ERR_INVALID, "glls_solve_batch: a problem appears twice");
     }

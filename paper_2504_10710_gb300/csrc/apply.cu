@@ -56,8 +56,13 @@ __device__ __forceinline__ float dot_cs(const float* a, const float* b) {
 // 0.5-1 % slower than the 48 registers the compiler picks with one.)
 template <typename T, int DIM, int P, bool DOT>
 __global__ void __launch_bounds__(256, 1) apply_p_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
-                                                         int mask, double* dot, double* part, unsigned* ticket) {
+                                                         int mask, double* dot, double* part, unsigned* ticket,
+                                                         int nrhs) {
     grid_dep_sync();
+    // right-hand side fastest in the CTA order (see device.cuh)
+    const int rhs = blockIdx.x % nrhs, bx = blockIdx.x / nrhs, nbx = gridDim.x / nrhs;
+    x += (long long)rhs * L.N;
+    y += (long long)rhs * L.N;
     constexpr int N1 = P + 1;
     constexpr int NLOC = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
     constexpr int EPB = NLOC >= 256 ? 1 : 256 / NLOC;
@@ -75,7 +80,7 @@ __global__ void __launch_bounds__(256, 1) apply_p_kernel(DevLevel<T> L, const T*
     const int E = (int)L.E;
     const int n0 = L.n[0], n1 = L.n[1];
     const int EN = E * NLOC;
-    const int e0 = blockIdx.x * EPB;
+    const int e0 = bx * EPB;
     const int total = min(EPB, E - e0) * NLOC;
     if (threadIdx.x < EPB && e0 + (int)threadIdx.x < E) {
         const int e = e0 + threadIdx.x, ne0 = L.ne[0], ne1 = L.ne[1];
@@ -180,8 +185,8 @@ __global__ void __launch_bounds__(256, 1) apply_p_kernel(DevLevel<T> L, const T*
         // them into dot[0], without one the consumer sums the partials
         __shared__ double red[32];
         const double tsum = block_sum(local, red);
-        if (threadIdx.x == 0) part[blockIdx.x] = tsum;
-        if (ticket && last_block(ticket)) {
+        if (threadIdx.x == 0) part[(long long)rhs * nbx + bx] = tsum;
+        if (ticket && last_block(ticket)) {   // single right-hand side only
             finalize_partials(part, 1, gridDim.x, dot, 0, 0, red);
             if (threadIdx.x == 0) *ticket = 0u;
         }
@@ -199,27 +204,30 @@ int apply_blocks(const DevLevel<T>& L) {
 
 template <typename T, int DIM, int P>
 bool launch_p(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part, unsigned* ticket,
-              cudaStream_t st) {
+              cudaStream_t st, int nrhs) {
     constexpr int N1 = P + 1;
     constexpr int NLOC = DIM == 2 ? N1 * N1 : N1 * N1 * N1;
     constexpr int EPB = NLOC >= 256 ? 1 : 256 / NLOC;
-    const int blocks = (int)((L.E + EPB - 1) / EPB);
+    const long long blocks = (L.E + EPB - 1) / EPB * nrhs;
+    if (blocks > 0x7fffffffLL) return false;
     if (dot) {
-        launch_k(apply_p_kernel<T, DIM, P, true>, blocks, 256, 0, st, L, x, y, mask ? 1 : 0, dot, part, ticket);
+        launch_k(apply_p_kernel<T, DIM, P, true>, (unsigned)blocks, 256, 0, st, L, x, y, mask ? 1 : 0, dot, part,
+                 ticket, nrhs);
     } else {
-        launch_k(apply_p_kernel<T, DIM, P, false>, blocks, 256, 0, st, L, x, y, mask ? 1 : 0, nullptr, nullptr, nullptr);
+        launch_k(apply_p_kernel<T, DIM, P, false>, (unsigned)blocks, 256, 0, st, L, x, y, mask ? 1 : 0, nullptr,
+                 nullptr, nullptr, nrhs);
     }
     return true;
 }
 
 template <typename T, int DIM, int P>
 bool dispatch(int p, const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part, unsigned* ticket,
-              cudaStream_t st) {
+              cudaStream_t st, int nrhs) {
     if constexpr (P == 0) {
         return false;
     } else {
-        if (p == P) return launch_p<T, DIM, P>(L, x, y, mask, dot, part, ticket, st);
-        return dispatch<T, DIM, P - 1>(p, L, x, y, mask, dot, part, ticket, st);
+        if (p == P) return launch_p<T, DIM, P>(L, x, y, mask, dot, part, ticket, st, nrhs);
+        return dispatch<T, DIM, P - 1>(p, L, x, y, mask, dot, part, ticket, st, nrhs);
     }
 }
 
@@ -245,26 +253,26 @@ template int apply_dot_partials<double>(const DevLevel<double>&);
 // Returns false when the order has no specialisation (the caller falls back).
 template <typename T>
 bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part,
-                        unsigned* ticket, cudaStream_t st) {
+                        unsigned* ticket, cudaStream_t st, int nrhs) {
     if (L.N > (1LL << 31) - 1 || L.E * L.nloc * (L.dim == 2 ? 3 : 6) > (1LL << 31) - 1) return false;
     for (int a = 0; a < L.dim; ++a)
         if (L.ne[a] >= 1024) return false;   // element coordinates are packed in 10 bits
     // 3-D: the even-odd line kernel where it was measured fastest, then the
     // FP32 column kernel, else the node-per-thread kernel below
-    if (launch_apply_eo<T>(L, x, y, mask, dot, part, ticket, st)) return true;
+    if (launch_apply_eo<T>(L, x, y, mask, dot, part, ticket, st, nrhs)) return true;
     if constexpr (sizeof(T) == 4) {
-        if (L.dim == 3 && !dot && launch_apply_col(L, x, y, mask, st)) return true;
+        if (L.dim == 3 && !dot && launch_apply_col(L, x, y, mask, st, nrhs)) return true;
     }
-    if (L.dim == 2) return dispatch<T, 2, 16>(L.p, L, x, y, mask, dot, part, ticket, st);
+    if (L.dim == 2) return dispatch<T, 2, 16>(L.p, L, x, y, mask, dot, part, ticket, st, nrhs);
     // 3-D FP32 is served by the even-odd and column kernels above at every
     // order up to 8; this kernel keeps 3-D FP64
-    if constexpr (sizeof(T) == 8) return dispatch<T, 3, 8>(L.p, L, x, y, mask, dot, part, ticket, st);
+    if constexpr (sizeof(T) == 8) return dispatch<T, 3, 8>(L.p, L, x, y, mask, dot, part, ticket, st, nrhs);
     return false;
 }
 
 template bool launch_apply_fixed<float>(const DevLevel<float>&, const float*, float*, bool, double*, double*,
-                                        unsigned*, cudaStream_t);
+                                        unsigned*, cudaStream_t, int);
 template bool launch_apply_fixed<double>(const DevLevel<double>&, const double*, double*, bool, double*, double*,
-                                         unsigned*, cudaStream_t);
+                                         unsigned*, cudaStream_t, int);
 
 }  // namespace glls

@@ -73,8 +73,12 @@ __device__ __forceinline__ float coldot(const float (&a)[N1], const float* col) 
 template <int P>
 __global__ void __launch_bounds__(256, ColShape<P>::MINB) apply_col_kernel(DevLevel<float> L, DParam<P + 1> Dk,
                                                            const float* __restrict__ x, float* __restrict__ y,
-                                                           int mask) {
+                                                           int mask, int nrhs) {
     grid_dep_sync();
+    // right-hand side fastest in the CTA order (see device.cuh)
+    const int rhs = blockIdx.x % nrhs, cta = blockIdx.x / nrhs;
+    x += (long long)rhs * L.N;
+    y += (long long)rhs * L.N;
     using S = ColShape<P>;
     constexpr int N1 = S::N1, NP = S::NP, NLOC = S::NLOC, EPB = S::EPB;
     constexpr bool VEC = S::VEC;
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(256, ColShape<P>::MINB) apply_col_kernel(DevLe
     const int nplane = n0 * n1;
     const int tid = threadIdx.x;
     const int el = tid / NP, c = tid - el * NP, i = c % N1, j = c / N1;
-    const int e = blockIdx.x * EPB + el;
+    const int e = cta * EPB + el;
     const bool act = el < EPB && e < E;
     int base = 0, I = 0, J = 0, K0 = 0;
     if (act) {
@@ -194,13 +198,14 @@ const float* d_table(int p) {
 }
 
 template <int P>
-bool launch_col(const DevLevel<float>& L, const float* x, float* y, bool mask, cudaStream_t st) {
+bool launch_col(const DevLevel<float>& L, const float* x, float* y, bool mask, cudaStream_t st, int nrhs) {
     DParam<P + 1> Dk;
     const float* d = d_table(P);
     for (int t = 0; t < (P + 1) * (P + 1); ++t) Dk.d[t] = d[t];
     constexpr int EPB = ColShape<P>::EPB;
-    const int blocks = (int)((L.E + EPB - 1) / EPB);
-    launch_k(apply_col_kernel<P>, blocks, 256, 0, st, L, Dk, x, y, mask ? 1 : 0);
+    const long long nb = (L.E + EPB - 1) / EPB * nrhs;
+    if (nb > 0x7fffffffLL) return false;
+    launch_k(apply_col_kernel<P>, (unsigned)nb, 256, 0, st, L, Dk, x, y, mask ? 1 : 0, nrhs);
     return true;
 }
 
@@ -215,12 +220,12 @@ bool prefer_shared() {
 // Shared-memory carveout for the column apply (p <= 3: up to 27 KB per CTA).
 bool init_apply_col_attributes() { return prefer_shared<1>() && prefer_shared<2>() && prefer_shared<3>(); }
 
-bool launch_apply_col(const DevLevel<float>& L, const float* x, float* y, bool mask, cudaStream_t st) {
+bool launch_apply_col(const DevLevel<float>& L, const float* x, float* y, bool mask, cudaStream_t st, int nrhs) {
     if (L.dim != 3 || L.p < 1 || L.p > 3) return false;
     switch (L.p) {
-        case 1: return launch_col<1>(L, x, y, mask, st);
-        case 2: return launch_col<2>(L, x, y, mask, st);
-        default: return launch_col<3>(L, x, y, mask, st);
+        case 1: return launch_col<1>(L, x, y, mask, st, nrhs);
+        case 2: return launch_col<2>(L, x, y, mask, st, nrhs);
+        default: return launch_col<3>(L, x, y, mask, st, nrhs);
     }
 }
 

@@ -112,7 +112,7 @@ __device__ __forceinline__ bool on_bd(int I, int J, int K, const int n[3]) {
 template <typename T, int P, bool DOT>
 __global__ void __launch_bounds__(256, 2)
     apply_eo3_kernel(DevLevel<T> L, const __grid_constant__ EoParams<T, P + 1> M, const T* __restrict__ x,
-                     T* __restrict__ y, int mask, double* dot, double* part, unsigned* ticket, int epb) {
+                     T* __restrict__ y, int mask, double* dot, double* part, unsigned* ticket, int epb, int nrhs) {
     using S = EoShape<T, P + 1>;
     constexpr int N = P + 1, NP = S::NP, NLOC = S::NLOC, RS = S::RS, PS = S::PS, ES = S::ES;
     extern __shared__ __align__(16) unsigned char eo_smem3[];
@@ -120,11 +120,15 @@ __global__ void __launch_bounds__(256, 2)
     T* sU = sX + epb * ES;
     T* sV = sU + epb * ES;
     grid_dep_sync();
+    // right-hand side fastest in the CTA order (see device.cuh)
+    const int rhs = blockIdx.x % nrhs, bx = blockIdx.x / nrhs, nbx = gridDim.x / nrhs;
+    x += (long long)rhs * L.N;
+    y += (long long)rhs * L.N;
     const int E = (int)L.E, n0 = L.n[0], n1 = L.n[1];
     const int nplane = n0 * n1;
     const int tid = threadIdx.x;
     const int el = tid / NP, c = tid - el * NP, a = c % N, b = c / N;
-    const int e = blockIdx.x * epb + el;
+    const int e = bx * epb + el;
     const bool act = el < epb && e < E;
     const int elo = act ? el : 0;
     T* X = sX + elo * ES;
@@ -216,8 +220,8 @@ __global__ void __launch_bounds__(256, 2)
     if (DOT) {
         __shared__ double red[32];
         const double tsum = block_sum(local, red);
-        if (tid == 0) part[blockIdx.x] = tsum;
-        if (ticket && last_block(ticket)) {
+        if (tid == 0) part[(long long)rhs * nbx + bx] = tsum;
+        if (ticket && last_block(ticket)) {   // single right-hand side only
             finalize_partials(part, 1, gridDim.x, dot, 0, 0, red);
             if (tid == 0) *ticket = 0u;
         }
@@ -259,17 +263,19 @@ EoParams<T, N> eo_params() {
 
 template <typename T, int P>
 bool launch_eo(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part, unsigned* ticket,
-               cudaStream_t st) {
+               cudaStream_t st, int nrhs) {
     using S = EoShape<T, P + 1>;
     const EoParams<T, P + 1> M = eo_params<T, P + 1>();
     const int epb = eo_epb(P, L.E);
-    const int blocks = (int)((L.E + epb - 1) / epb);
+    const long long nb = (L.E + epb - 1) / epb * nrhs;
+    if (nb > 0x7fffffffLL) return false;
+    const int blocks = (int)nb;
     const int threads = (epb * S::NP + 31) / 32 * 32;
     const size_t smem = sizeof(T) * S::NBUF * epb * S::ES;
     if (dot) launch_k(apply_eo3_kernel<T, P, true>, blocks, threads, smem, st, L, M, x, y, mask ? 1 : 0, dot, part,
-                      ticket, epb);
+                      ticket, epb, nrhs);
     else launch_k(apply_eo3_kernel<T, P, false>, blocks, threads, smem, st, L, M, x, y, mask ? 1 : 0,
-                  (double*)nullptr, (double*)nullptr, (unsigned*)nullptr, epb);
+                  (double*)nullptr, (double*)nullptr, (unsigned*)nullptr, epb, nrhs);
     return true;
 }
 
@@ -303,27 +309,27 @@ int apply_eo_blocks(int p, long long E) {
 
 template <typename T>
 bool launch_apply_eo(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part,
-                     unsigned* ticket, cudaStream_t st) {
+                     unsigned* ticket, cudaStream_t st, int nrhs) {
     if (!apply_eo_selected(L.dim, L.p, sizeof(T) == 8)) return false;
     if constexpr (sizeof(T) == 8) {
         switch (L.p) {
-            case 6: return launch_eo<T, 6>(L, x, y, mask, dot, part, ticket, st);
-            default: return launch_eo<T, 7>(L, x, y, mask, dot, part, ticket, st);
+            case 6: return launch_eo<T, 6>(L, x, y, mask, dot, part, ticket, st, nrhs);
+            default: return launch_eo<T, 7>(L, x, y, mask, dot, part, ticket, st, nrhs);
         }
     } else {
         switch (L.p) {
-            case 4: return launch_eo<T, 4>(L, x, y, mask, dot, part, ticket, st);
-            case 5: return launch_eo<T, 5>(L, x, y, mask, dot, part, ticket, st);
-            case 6: return launch_eo<T, 6>(L, x, y, mask, dot, part, ticket, st);
-            case 7: return launch_eo<T, 7>(L, x, y, mask, dot, part, ticket, st);
-            default: return launch_eo<T, 8>(L, x, y, mask, dot, part, ticket, st);
+            case 4: return launch_eo<T, 4>(L, x, y, mask, dot, part, ticket, st, nrhs);
+            case 5: return launch_eo<T, 5>(L, x, y, mask, dot, part, ticket, st, nrhs);
+            case 6: return launch_eo<T, 6>(L, x, y, mask, dot, part, ticket, st, nrhs);
+            case 7: return launch_eo<T, 7>(L, x, y, mask, dot, part, ticket, st, nrhs);
+            default: return launch_eo<T, 8>(L, x, y, mask, dot, part, ticket, st, nrhs);
         }
     }
 }
 template bool launch_apply_eo<float>(const DevLevel<float>&, const float*, float*, bool, double*, double*,
-                                     unsigned*, cudaStream_t);
+                                     unsigned*, cudaStream_t, int);
 template bool launch_apply_eo<double>(const DevLevel<double>&, const double*, double*, bool, double*, double*,
-                                      unsigned*, cudaStream_t);
+                                      unsigned*, cudaStream_t, int);
 
 bool init_apply_eo_attributes() {
     return set_eo_attr<float, 4>() && set_eo_attr<float, 5>() && set_eo_attr<float, 6>() && set_eo_attr<float, 7>() &&

@@ -11,6 +11,15 @@
 //                     (GLL smoother, p >= 2), see DevLevel
 //   D               : (p+1)^2 derivative matrix, D[i*(p+1)+j] = pi_j'(xi_i)
 //   P[a], R[a]      : fixed-width row bands of the 1-D transfer matrices
+//
+// Several right-hand sides (nrhs > 1 in the launchers): a vector argument
+// holds nrhs consecutive copies of its level's grid, right-hand side j at
+// offset j N.  Kernels that read level data (apply, line solves, transfers,
+// coarsest solve) put the right-hand side fastest in their CTA order, so the
+// nrhs CTAs that read one element, line or block tile run together and the
+// tile comes from HBM about once per launch.  Per-right-hand-side partial
+// sums, tickets and Krylov scalars follow one another (stride given where
+// they are used).
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -120,10 +129,10 @@ constexpr size_t kMaxDynSmemBytes = 200 * 1024;
 // `ticket` (see launch_dots).
 template <typename T>
 bool launch_apply_fixed(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part,
-                        unsigned* ticket, cudaStream_t st);
+                        unsigned* ticket, cudaStream_t st, int nrhs = 1);
 template <typename T>
 bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
-                      cudaStream_t st);
+                      cudaStream_t st, int nrhs = 1);
 bool init_line_warp_attributes();
 // Line solves with the condensed Def. 3.2 line blocks (lines_block.cu), used
 // whenever L.blk[s] is set; lines of at most kMaxBlockLine unknowns and
@@ -134,12 +143,13 @@ constexpr int kMaxBlockSegments = 256;
 bool line_block_supported(int n, int E);
 template <typename T>
 bool launch_line_block(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
-                       cudaStream_t st);
+                       cudaStream_t st, int nrhs = 1);
 bool init_line_block_attributes();
 // 3-D FP32 apply with one thread per element column (apply_col.cu), p <= 3
 // (the orders the even-odd kernel does not take); no x.(A x) product.
 // Returns false outside that range.
-bool launch_apply_col(const DevLevel<float>& L, const float* x, float* y, bool mask, cudaStream_t st);
+bool launch_apply_col(const DevLevel<float>& L, const float* x, float* y, bool mask, cudaStream_t st,
+                      int nrhs = 1);
 bool init_apply_col_attributes();
 // 3-D apply with one thread per element grid line and even-odd derivative
 // sweeps (apply_eo.cu), for the orders apply_eo_selected names, with the
@@ -147,7 +157,7 @@ bool init_apply_col_attributes();
 bool apply_eo_selected(int dim, int p, bool f64);
 template <typename T>
 bool launch_apply_eo(const DevLevel<T>& L, const T* x, T* y, bool mask, double* dot, double* part,
-                     unsigned* ticket, cudaStream_t st);
+                     unsigned* ticket, cudaStream_t st, int nrhs = 1);
 int apply_eo_blocks(int p, long long E);
 bool init_apply_eo_attributes();
 
@@ -159,21 +169,21 @@ bool init_apply_eo_attributes();
 // cudaGetLastError.
 template <typename T>
 cudaError_t launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st, bool y_is_zero = false,
-                  double* dot = nullptr, double* part = nullptr, unsigned* ticket = nullptr);
+                  double* dot = nullptr, double* part = nullptr, unsigned* ticket = nullptr, int nrhs = 1);
 
 // Line solves along axis s.  mode 0: x = B_s^-1 g; mode 1: x += alpha
 // B_s^-1 (r - y) and y is reset to 0 where read; mode 2: x += alpha B_s^-1 r;
 // mode 3: x = alpha B_s^-1 r.  Only interior entries of x are written.
 template <typename T>
 void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y,
-                       T* x, T alpha, cudaStream_t st);
+                       T* x, T alpha, cudaStream_t st, int nrhs = 1);
 
 // One tensor-product factor of a transfer: out = M in (or in - in2) along
 // axis a; grids nin/nout differ only along a.  add: out += ...; mask: zero
 // the output's boundary nodes; clear (optional, output-grid sized): set to 0.
 template <typename T>
 void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nout[3], const T* in,
-                     const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear = nullptr);
+                     const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear = nullptr, int nrhs = 1);
 
 // The first two tensor-product factors of a transfer in one launch: out =
 // M1 (M0 (in - in2)) along axes 0 and 1, for every index of axis 2 (nin and
@@ -183,20 +193,20 @@ void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nou
 // caller then runs the two passes separately).
 template <typename T>
 bool launch_transfer2(const DevBand<T>& M0, const DevBand<T>& M1, const int nin[3], const int nout[3], const T* in,
-                      const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear = nullptr);
+                      const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear = nullptr, int nrhs = 1);
 
 // e = A_0^-1 r on the interior of the coarsest level; e's boundary entries
 // are zeroed first unless e_boundary_zero.  w: scratch of C.n values (used
 // when C.cr_levels > 0; must not alias r or e).
 template <typename T>
 void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, T* w, cudaStream_t st,
-                   bool e_boundary_zero = false);
+                   bool e_boundary_zero = false, int nrhs = 1);
 
 // ---- vector kernels -------------------------------------------------------
 template <typename Ti, typename To>
 void launch_cast(const Ti* in, To* out, long long n, cudaStream_t st);
 template <typename T>
-void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st);
+void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st, int nrhs = 1);
 
 // Deterministic dot products in one launch: partial sums per block into
 // `part` (ndots * nblocks); the last block adds them in block order into
@@ -205,15 +215,17 @@ void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st);
 constexpr int kDotBlocks = 304;   // 2 x 152 SMs
 constexpr int kMaxReduceBlocks = 8192;
 void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots,
-                 long long n, double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st);
+                 long long n, double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st, int nrhs = 1);
 // Outer-iteration dots without a grid-wide finish: kDotBlocks per-block
 // partials of r.z into prz and of z.q into pzq; z is first taken from z32
 // when given (z = double(z32)); q is reset to 0 after it is read.
 void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* prz, double* pzq,
-                       cudaStream_t st);
+                       cudaStream_t st, int nrhs = 1);
 
 // Krylov scalar slots in the device array S.
-enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZNEW, S_ZQ, S_RR0, S_ALPHA, S_FLAG, S_TOL2, S_ITER, S_COUNT };
+// Per right-hand side j the slots sit at S + j * S_COUNT.  S_DONE: 0 while
+// iterating, 1 converged, 2 broken down; S_ITS: iterations when it stopped.
+enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZNEW, S_ZQ, S_RR0, S_ALPHA, S_FLAG, S_TOL2, S_ITER, S_DONE, S_ITS, S_COUNT };
 
 // q-independent update: p.q (npq partials from the apply) and r.z (nrz
 // partials) are summed in every block, alpha = r.z / p.q; x += alpha p;
@@ -222,19 +234,21 @@ enum Slot { S_RZ = 0, S_PQ, S_RR, S_RZNEW, S_ZQ, S_RR0, S_ALPHA, S_FLAG, S_TOL2,
 // r32 = float(r) for the FP32 gamma-cycle.
 void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, const double* ppq,
                        int npq, const double* prz, int nrz, double* prr, double* S, unsigned* ticket, float* r32,
-                       cudaStream_t st);
+                       cudaStream_t st, int nrhs = 1);
 // p = z + beta p with beta = -S_ALPHA zq / S_RZ (flexible) or rz_new / S_RZ,
 // rz_new and zq summed from the nd partials of launch_dots_rz_zq.
 void launch_fcg_direction(double* p, const double* z, long long n, const double* prz, const double* pzq, int nd,
-                          const double* S, int flexible, cudaStream_t st);
+                          const double* S, int flexible, cudaStream_t st, int nrhs = 1);
 // Dot partials launch_apply writes for L when asked for x.(A x) without a ticket.
 template <typename T>
 int apply_dot_partials(const DevLevel<T>& L);
 // f0 = M f - y on interior nodes (0 on the boundary); v = g on the boundary, 0 inside.
 void launch_lift_rhs(const double* mass, const double* f, const double* y, double* f0, const int n[3], int dim,
-                     cudaStream_t st);
+                     cudaStream_t st, int nrhs = 1);
 void launch_boundary_only(const double* g, double* v, const int n[3], int dim, cudaStream_t st);
-void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st);   // y += a x
+// y += a x; nrhs vectors of n values each, x the same for all when x_shared
+void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st, int nrhs = 1,
+                 bool x_shared = false);
 // GMRES: h[j] = V_j . w (j < k1, deterministic, part holds 64 k1 partials);
 // w += sign sum_j h[j] V_j; out = in / sqrt(nrm2[0]).
 void launch_multidot(const double* V, long long ld, int k1, const double* w, long long n, double* part, double* h,
@@ -246,7 +260,7 @@ void launch_scale_by_norm(double* out, const double* in, const double* nrm2, lon
 // Device-side solve loop: after S_RR0 is computed, initialise S and set the
 // WHILE handle (r0 != 0); at the end of each iteration count it and set the
 // handle to (r.r > tol^2 r0.r0, it < maxit, no breakdown).
-void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st);
-void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st);
+void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st, int nrhs = 1);
+void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st, int nrhs = 1);
 
 }  // namespace glls

@@ -46,15 +46,20 @@ __device__ __forceinline__ bool on_boundary(long long g, const int n[3], int dim
 // ---------------------------------------------------------------------------
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) apply_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
-                                                    int mask, int epc) {
+                                                    int mask, int epc, int nrhs) {
     grid_dep_sync();
+    // right-hand side fastest in the CTA order (see device.cuh)
+    const int rhs = blockIdx.x % nrhs;
+    const long long bx = blockIdx.x / nrhs;
+    x += (long long)rhs * L.N;
+    y += (long long)rhs * L.N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sD = reinterpret_cast<T*>(smem_raw);
     const int n1 = L.n1, nloc = L.nloc, p = L.p;
     T* sx = sD + n1 * n1;
     T* sw = sx + epc * nloc;
     for (int t = threadIdx.x; t < n1 * n1; t += blockDim.x) sD[t] = L.D[t];
-    const long long e0 = (long long)blockIdx.x * epc;
+    const long long e0 = bx * epc;
     const int ecount = (int)min((long long)epc, L.E - e0);
     const int total = ecount * nloc;
     const long long EN = L.E * nloc;
@@ -234,18 +239,25 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs<T> A) {
 template <typename T, int WB>
 __global__ void transfer_kernel(DevBand<T> M, int a, int3 nin, int3 nout, const T* __restrict__ in,
                                 const T* __restrict__ in2, T* __restrict__ out, int add, int mask, int dim,
-                                T* __restrict__ clear) {
+                                T* __restrict__ clear, int nrhs) {
     grid_dep_sync();
     const int total = nout.x * nout.y * nout.z;
+    const long long tin = (long long)nin.x * nin.y * nin.z;
     const int sin_a = a == 0 ? 1 : (a == 1 ? nin.x : nin.x * nin.y);
     const int W = M.width;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        if (clear) clear[idx] = T(0);
+    const long long all = (long long)total * nrhs;
+    for (long long gidx = blockIdx.x * (long long)blockDim.x + threadIdx.x; gidx < all;
+         gidx += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(gidx / total), idx = (int)(gidx - (long long)j * total);
+        const T* in_j = in + j * tin;
+        const T* in2_j = in2 ? in2 + j * tin : nullptr;
+        T* out_j = out + (long long)j * total;
+        if (clear) clear[gidx] = T(0);
         const int c0 = idx % nout.x, c1 = (idx / nout.x) % nout.y, c2 = idx / (nout.x * nout.y);
         if (mask) {
             const bool bnd = c0 == 0 || c0 == nout.x - 1 || c1 == 0 || c1 == nout.y - 1 ||
                              (dim == 3 && (c2 == 0 || c2 == nout.z - 1));
-            if (bnd) { if (!add) out[idx] = T(0); continue; }
+            if (bnd) { if (!add) out_j[idx] = T(0); continue; }
         }
         const int K = a == 0 ? c0 : (a == 1 ? c1 : c2);
         const int b0 = a == 0 ? 0 : c0, b1 = a == 1 ? 0 : c1, b2 = a == 2 ? 0 : c2;
@@ -260,16 +272,16 @@ __global__ void transfer_kernel(DevBand<T> M, int a, int3 nin, int3 nout, const 
                 iv[k] = T(0);
                 if (k < W) {
                     cv[k] = cf[k];
-                    iv[k] = in2 ? in[base + k * sin_a] - in2[base + k * sin_a] : in[base + k * sin_a];
+                    iv[k] = in2_j ? in_j[base + k * sin_a] - in2_j[base + k * sin_a] : in_j[base + k * sin_a];
                 }
             }
 #pragma unroll
             for (int k = 0; k < (WB > 0 ? WB : 1); ++k) v += cv[k] * iv[k];
         } else {
             for (int k = 0; k < W; ++k)
-                v += cf[k] * (in2 ? in[base + k * sin_a] - in2[base + k * sin_a] : in[base + k * sin_a]);
+                v += cf[k] * (in2_j ? in_j[base + k * sin_a] - in2_j[base + k * sin_a] : in_j[base + k * sin_a]);
         }
-        out[idx] = add ? out[idx] + v : v;
+        out_j[idx] = add ? out_j[idx] + v : v;
     }
 }
 
@@ -290,8 +302,14 @@ template <typename T>
 __global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, const long long* __restrict__ index,
                                                      const T* __restrict__ inv, const T* __restrict__ src,
                                                      const long long* __restrict__ src_index, int m, int H,
-                                                     T* __restrict__ e) {
+                                                     T* __restrict__ e, int nrhs, long long vstride) {
     grid_dep_sync();
+    // right-hand side fastest in the CTA order (see device.cuh); src and e
+    // hold vstride values per right-hand side
+    const int rhs = blockIdx.x % nrhs;
+    const long long bx = blockIdx.x / nrhs, nbx = gridDim.x / nrhs;
+    src += rhs * vstride;
+    e += rhs * vstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* rs = reinterpret_cast<T*>(smem_raw);
     for (long long t = threadIdx.x; t < ld; t += blockDim.x) {
@@ -311,7 +329,7 @@ __global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, 
     // sums), so a row costs about one memory latency instead of one per chunk
     constexpr int U = 8;
     const long long nvec = ld / V;
-    for (long long row = (long long)blockIdx.x * wpb + warp; row < n; row += (long long)gridDim.x * wpb) {
+    for (long long row = bx * wpb + warp; row < n; row += nbx * wpb) {
         const Vec* a = reinterpret_cast<const Vec*>(inv + row * ld);
         T part[U];
 #pragma unroll
@@ -355,15 +373,18 @@ constexpr int kBcrRows = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) bcr_forward_kernel(const T* __restrict__ FH, int l, int nb, int m, int ldm,
                                                           const long long* __restrict__ index,
-                                                          const T* __restrict__ r, T* w) {
+                                                          const T* __restrict__ r, T* w, int nrhs, long long nvec) {
     grid_dep_sync();
+    const int rhs = blockIdx.x % nrhs;
+    r += rhs * nvec;
+    w += rhs * nvec;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* xl = reinterpret_cast<T*>(smem_raw);
     T* xr = xl + m;
     const int h = 1 << l, nk = (nb >> l) / 2;
     const int row0 = blockIdx.y * kBcrRows;
     const bool lvl0 = l == 0;
-    const int q = blockIdx.x;
+    const int q = blockIdx.x / nrhs;
     if (q >= nk) {                                   // level 0: copy eliminated block 2 (q - nk)
         const long long b = 2LL * (q - nk);
         for (int rr = threadIdx.x; rr < kBcrRows; rr += blockDim.x) {
@@ -403,15 +424,18 @@ __global__ void __launch_bounds__(256) bcr_forward_kernel(const T* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256) bcr_backward_kernel(const T* __restrict__ AGK, int l, int nb, int m, int ldm,
                                                            const long long* __restrict__ index,
-                                                           const T* __restrict__ w, T* e) {
+                                                           const T* __restrict__ w, T* e, int nrhs, long long nvec) {
     grid_dep_sync();
+    const int rhs = blockIdx.x % nrhs;
+    w += rhs * nvec;
+    e += rhs * nvec;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* xw = reinterpret_cast<T*>(smem_raw);
     T* xl = xw + m;
     T* xr = xl + m;
     const int h = 1 << l;
     const int row0 = blockIdx.y * kBcrRows;
-    const long long s_ = blockIdx.x;
+    const long long s_ = blockIdx.x / nrhs;
     const long long b = (2 * s_ + 1) * h - 1, lb = b - h, rb = b + h;
     const bool left = lb >= 0, right = rb < nb;
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -558,12 +582,13 @@ __global__ void cast_kernel(const Ti* __restrict__ in, To* __restrict__ out, lon
 }
 
 template <typename T>
-__global__ void zero_boundary_kernel(T* v, int3 n, int dim) {
+__global__ void zero_boundary_kernel(T* v, int3 n, int dim, int nrhs) {
     grid_dep_sync();
     const long long total = (long long)n.x * n.y * n.z;
     const int nn[3] = {n.x, n.y, n.z};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
-        if (on_boundary(i, nn, dim)) v[i] = T(0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total * nrhs;
+         i += (long long)gridDim.x * blockDim.x)
+        if (on_boundary(i % total, nn, dim)) v[i] = T(0);
 }
 
 __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0, const double* __restrict__ b0,
@@ -571,6 +596,18 @@ __global__ void __launch_bounds__(256) dots_kernel(const double* __restrict__ a0
                                                    int ndots, long long n, double* part, double* S, int slot0,
                                                    int slot1, unsigned* ticket, int rotate) {
     grid_dep_sync();
+    // right-hand side blockIdx.y: vectors at j n, partials at j ndots
+    // gridDim.x, scalars at j S_COUNT, ticket j
+    const long long j = blockIdx.y;
+    a0 += j * n;
+    b0 += j * n;
+    if (ndots > 1) {
+        a1 += j * n;
+        b1 += j * n;
+    }
+    part += j * ndots * gridDim.x;
+    S += j * S_COUNT;
+    if (ticket) ticket += j;
     __shared__ double red[32];
     double s0 = 0.0, s1 = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -611,6 +648,13 @@ __global__ void __launch_bounds__(256) dots_rz_zq_kernel(const double* __restric
                                                          long long n, double* __restrict__ prz,
                                                          double* __restrict__ pzq) {
     grid_dep_sync();
+    const long long jr = blockIdx.y;       // right-hand side
+    r += jr * n;
+    z += jr * n;
+    if (z32) z32 += jr * n;
+    q += jr * n;
+    prz += jr * gridDim.x;
+    pzq += jr * gridDim.x;
     __shared__ double red[32];
     double s0 = 0.0, s1 = 0.0;
     // kVecU elements per thread per trip, all loads issued before use (same
@@ -655,6 +699,19 @@ __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x,
                                                          int nrz, double* prr, double* S, unsigned* ticket,
                                                          float* __restrict__ r32) {
     grid_dep_sync();
+    const long long jr = blockIdx.y;       // right-hand side
+    x += jr * n;
+    r += jr * n;
+    p += jr * n;
+    q += jr * n;
+    if (r32) r32 += jr * n;
+    ppq += jr * npq;
+    prz += jr * nrz;
+    prr += jr * gridDim.x;
+    S += jr * S_COUNT;
+    ticket += jr;
+    // a right-hand side that has stopped keeps its x and r
+    const bool active = S[S_DONE] == 0.0;
     __shared__ double red[32];
     __shared__ double sh[3];
     const double pq = sum_partials(ppq, npq, red);
@@ -668,7 +725,7 @@ __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x,
     const double alpha = sh[0];
     double s = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += kVecU * stride) {
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; active && i0 < n; i0 += kVecU * stride) {
         double xv[kVecU], rv[kVecU], pv[kVecU], qv[kVecU];
 #pragma unroll
         for (int u = 0; u < kVecU; ++u) {
@@ -696,14 +753,16 @@ __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x,
     const double t = block_sum(s, red);
     if (threadIdx.x == 0) prr[blockIdx.x] = t;
     if (last_block(ticket)) {
-        finalize_partials(prr, 1, gridDim.x, S, S_RR, S_RR, red);
-        if (threadIdx.x == 0) {
-            S[S_ALPHA] = alpha;
-            S[S_PQ] = sh[1];
-            S[S_RZ] = sh[2];
-            if (!(sh[1] > 0.0) || !isfinite(alpha)) S[S_FLAG] = 1.0;
-            *ticket = 0u;
+        if (active) {
+            finalize_partials(prr, 1, gridDim.x, S, S_RR, S_RR, red);
+            if (threadIdx.x == 0) {
+                S[S_ALPHA] = alpha;
+                S[S_PQ] = sh[1];
+                S[S_RZ] = sh[2];
+                if (!(sh[1] > 0.0) || !isfinite(alpha)) S[S_FLAG] = 1.0;
+            }
         }
+        if (threadIdx.x == 0) *ticket = 0u;
     }
 }
 
@@ -714,6 +773,13 @@ __global__ void __launch_bounds__(256) fcg_direction_kernel(double* __restrict__
                                                             long long n, const double* prz, const double* pzq, int nd,
                                                             const double* __restrict__ S, int flexible) {
     grid_dep_sync();
+    const long long jr = blockIdx.y;       // right-hand side
+    S += jr * S_COUNT;
+    if (S[S_DONE] != 0.0) return;           // stopped: p is no longer used
+    p += jr * n;
+    z += jr * n;
+    prz += jr * nd;
+    pzq += jr * nd;
     __shared__ double red[32];
     __shared__ double sh_beta;
     const double rz_new = sum_partials(prz, nd, red);
@@ -792,42 +858,73 @@ __global__ void scale_by_norm_kernel(double* __restrict__ out, const double* __r
 // Device-side loop control for the captured solve graph (conditional WHILE
 // node): solve_init_kernel runs once after r0.r0 is known, solve_cond_kernel
 // ends every outer iteration.
-__global__ void solve_init_kernel(double* S, cudaGraphConditionalHandle h, double tol, int maxit) {
+// With several right-hand sides the loop runs while any of them is still
+// iterating; each one stops (S_DONE, S_ITS) when it converges or breaks down.
+__global__ void solve_init_kernel(double* S0, cudaGraphConditionalHandle h, double tol, int maxit, int nrhs) {
     grid_dep_sync();
     if (threadIdx.x != 0) return;
-    const double rr0 = S[S_RR0];
-    S[S_RR] = rr0;
-    S[S_TOL2] = tol * tol * rr0;
-    S[S_ITER] = 0.0;
-    S[S_RZ] = 1.0;
-    S[S_ALPHA] = 0.0;
-    S[S_FLAG] = 0.0;
-    S[S_ZQ] = 0.0;
-    S[S_PQ] = 0.0;
-    S[S_RZNEW] = 0.0;
-    const bool go = rr0 > 0.0 && isfinite(rr0) && maxit > 0;
-    if (!isfinite(rr0)) S[S_FLAG] = 1.0;
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+    bool go = false;
+    for (int j = 0; j < nrhs; ++j) {
+        double* S = S0 + (long long)j * S_COUNT;
+        const double rr0 = S[S_RR0];
+        S[S_RR] = rr0;
+        S[S_TOL2] = tol * tol * rr0;
+        S[S_ITER] = 0.0;
+        S[S_RZ] = 1.0;
+        S[S_ALPHA] = 0.0;
+        S[S_FLAG] = 0.0;
+        S[S_ZQ] = 0.0;
+        S[S_PQ] = 0.0;
+        S[S_RZNEW] = 0.0;
+        S[S_ITS] = 0.0;
+        S[S_DONE] = 0.0;
+        if (!isfinite(rr0)) {
+            S[S_FLAG] = 1.0;
+            S[S_DONE] = 2.0;
+        } else if (!(rr0 > 0.0)) {
+            S[S_DONE] = 1.0;
+        }
+        go = go || S[S_DONE] == 0.0;
+    }
+    cudaGraphSetConditional(h, go && maxit > 0 ? 1u : 0u);
 }
 
-__global__ void solve_cond_kernel(double* S, cudaGraphConditionalHandle h, int maxit) {
+__global__ void solve_cond_kernel(double* S0, cudaGraphConditionalHandle h, int maxit, int nrhs) {
     grid_dep_sync();
     if (threadIdx.x != 0) return;
-    const double it = S[S_ITER] + 1.0;
-    S[S_ITER] = it;
-    const double rr = S[S_RR];
-    const bool go = rr > S[S_TOL2] && it < (double)maxit && S[S_FLAG] == 0.0 && isfinite(rr);
-    if (!isfinite(rr)) S[S_FLAG] = 1.0;
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+    bool any = false;
+    double it = 0.0;
+    for (int j = 0; j < nrhs; ++j) {
+        double* S = S0 + (long long)j * S_COUNT;
+        it = S[S_ITER] + 1.0;
+        S[S_ITER] = it;
+        if (S[S_DONE] != 0.0) continue;
+        const double rr = S[S_RR];
+        if (!isfinite(rr) || S[S_FLAG] != 0.0) {
+            S[S_FLAG] = 1.0;
+            S[S_DONE] = 2.0;
+            S[S_ITS] = it;
+        } else if (rr <= S[S_TOL2]) {
+            S[S_DONE] = 1.0;
+            S[S_ITS] = it;
+        } else {
+            any = true;
+        }
+    }
+    cudaGraphSetConditional(h, any && it < (double)maxit ? 1u : 0u);
 }
 
+// f and f0 hold nrhs vectors; mass and y (A v of the shared lifting) one.
 __global__ void lift_rhs_kernel(const double* __restrict__ mass, const double* __restrict__ f,
-                                const double* __restrict__ y, double* __restrict__ f0, int3 n, int dim) {
+                                const double* __restrict__ y, double* __restrict__ f0, int3 n, int dim, int nrhs) {
     grid_dep_sync();
     const long long total = (long long)n.x * n.y * n.z;
     const int nn[3] = {n.x, n.y, n.z};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
-        f0[i] = on_boundary(i, nn, dim) ? 0.0 : mass[i] * f[i] - y[i];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total * nrhs;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long li = i % total;
+        f0[i] = on_boundary(li, nn, dim) ? 0.0 : mass[li] * f[i] - y[li];
+    }
 }
 
 __global__ void boundary_only_kernel(const double* __restrict__ g, double* __restrict__ v, int3 n, int dim) {
@@ -838,10 +935,13 @@ __global__ void boundary_only_kernel(const double* __restrict__ g, double* __res
         v[i] = on_boundary(i, nn, dim) ? g[i] : 0.0;
 }
 
-__global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a, long long n) {
+// y (nrhs vectors of n values) += a x; x one vector for all when x_shared
+__global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a, long long n, int nrhs,
+                            int x_shared) {
     grid_dep_sync();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        y[i] += a * x[i];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * nrhs;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] += a * x[x_shared ? i % n : i];
 }
 
 // One element per thread (more loads in flight than a grid-stride loop);
@@ -871,29 +971,29 @@ constexpr int kMaxDynSmem = 200 * 1024;
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cudaStream_t st, bool y_is_zero,
-                         double* dot, double* part, unsigned* ticket) {
+                         double* dot, double* part, unsigned* ticket, int nrhs) {
     if (!y_is_zero) {
-        const cudaError_t e = cudaMemsetAsync(y, 0, sizeof(T) * L.N, st);
+        const cudaError_t e = cudaMemsetAsync(y, 0, sizeof(T) * L.N * nrhs, st);
         if (e != cudaSuccess) return e;
     }
-    if (launch_apply_fixed<T>(L, x, y, mask, dot, part, ticket, st)) return cudaSuccess;
+    if (launch_apply_fixed<T>(L, x, y, mask, dot, part, ticket, st, nrhs)) return cudaSuccess;
     int epc = 256 / L.nloc;
     if (epc < 1) epc = 1;
-    const long long blocks = (L.E + epc - 1) / epc;
+    const long long blocks = (L.E + epc - 1) / epc * nrhs;
     const size_t smem = sizeof(T) * (L.n1 * L.n1 + (size_t)epc * L.nloc * (1 + L.dim));
     if (L.dim == 2) {
-        launch_k(apply_kernel<T, 2>, (unsigned)blocks, 256, smem, st, L, x, y, mask ? 1 : 0, epc);
+        launch_k(apply_kernel<T, 2>, (unsigned)blocks, 256, smem, st, L, x, y, mask ? 1 : 0, epc, nrhs);
     } else {
-        launch_k(apply_kernel<T, 3>, (unsigned)blocks, 256, smem, st, L, x, y, mask ? 1 : 0, epc);
+        launch_k(apply_kernel<T, 3>, (unsigned)blocks, 256, smem, st, L, x, y, mask ? 1 : 0, epc, nrhs);
     }
     // orders outside the specialised range: x.(A x) as a separate product
     if (dot) {
         if constexpr (sizeof(T) == 8) {
-            if (ticket)
+            if (ticket)    // single right-hand side only
                 launch_dots(reinterpret_cast<const double*>(x), reinterpret_cast<const double*>(y), nullptr, nullptr,
                             1, L.N, part, dot, 0, 0, ticket, st);
-            else   // kDotBlocks partials only
-                launch_k(dots_kernel, kDotBlocks, 256, 0, st, reinterpret_cast<const double*>(x),
+            else   // kDotBlocks partials per right-hand side only
+                launch_k(dots_kernel, dim3(kDotBlocks, nrhs), 256, 0, st, reinterpret_cast<const double*>(x),
                          reinterpret_cast<const double*>(y), (const double*)nullptr, (const double*)nullptr, 1, L.N,
                          part, dot, 0, 0, (unsigned*)nullptr, 0);
         }
@@ -903,14 +1003,23 @@ cudaError_t launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cuda
 
 template <typename T>
 void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
-                       cudaStream_t st) {
+                       cudaStream_t st, int nrhs) {
     // levels with Def. 3.2 line blocks: the condensed block solve (set-up
     // guarantees the sizes it takes)
     if (L.blk[s] != nullptr) {
-        launch_line_block<T>(L, s, mode, g, r, y, x, alpha, st);
+        launch_line_block<T>(L, s, mode, g, r, y, x, alpha, st, nrhs);
         return;
     }
-    if (launch_line_warp<T>(L, s, mode, g, r, y, x, alpha, st)) return;
+    if (launch_line_warp<T>(L, s, mode, g, r, y, x, alpha, st, nrhs)) return;
+    // long band-1 lines: the shared-memory kernel, one launch per right-hand side
+    if (nrhs > 1) {
+        for (int j = 0; j < nrhs; ++j) {
+            const long long o = (long long)j * L.N;
+            launch_line_solve<T>(L, s, mode, g ? g + o : nullptr, r ? r + o : nullptr, y ? y + o : nullptr, x + o,
+                                 alpha, st, 1);
+        }
+        return;
+    }
     LineArgs<T> A;
     A.n = L.n[s] - 2;
     if (A.n <= 0) return;
@@ -948,27 +1057,32 @@ void launch_line_solve(const DevLevel<T>& L, int s, int mode, const T* g, const 
 
 template <typename T>
 void launch_transfer(const DevBand<T>& M, int a, const int nin[3], const int nout[3], const T* in, const T* in2, T* out,
-                     bool add, bool mask, cudaStream_t st, T* clear) {
+                     bool add, bool mask, cudaStream_t st, T* clear, int nrhs) {
     const long long total = (long long)nout[0] * nout[1] * nout[2];
     const int dim = nout[2] > 1 ? 3 : 2;
     const int3 ni = make_int3(nin[0], nin[1], nin[2]), no = make_int3(nout[0], nout[1], nout[2]);
-    const int g = grid_for(total);
+    const int g = grid_for(total * nrhs);
     const int ad = add ? 1 : 0, mk = mask ? 1 : 0;
-    if (M.width <= 4) launch_k(transfer_kernel<T, 4>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear);
-    else if (M.width <= 8) launch_k(transfer_kernel<T, 8>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear);
-    else if (M.width <= 16) launch_k(transfer_kernel<T, 16>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear);
-    else if (M.width <= 32) launch_k(transfer_kernel<T, 32>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear);
-    else launch_k(transfer_kernel<T, 0>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear);
+    if (M.width <= 4)
+        launch_k(transfer_kernel<T, 4>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear, nrhs);
+    else if (M.width <= 8)
+        launch_k(transfer_kernel<T, 8>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear, nrhs);
+    else if (M.width <= 16)
+        launch_k(transfer_kernel<T, 16>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear, nrhs);
+    else if (M.width <= 32)
+        launch_k(transfer_kernel<T, 32>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear, nrhs);
+    else launch_k(transfer_kernel<T, 0>, g, 256, 0, st, M, a, ni, no, in, in2, out, ad, mk, dim, clear, nrhs);
 }
 
 template <typename T>
 bool launch_transfer2(const DevBand<T>& M0, const DevBand<T>& M1, const int nin[3], const int nout[3], const T* in,
-                      const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear) {
+                      const T* in2, T* out, bool add, bool mask, cudaStream_t st, T* clear, int nrhs) {
     constexpr int TY = 8;
     const size_t smem = sizeof(T) * (size_t)M1.span8 * (M0.span32 + 32);
     const int W = M0.width > M1.width ? M0.width : M1.width;
     if (M0.span32 <= 0 || M1.span8 <= 0 || smem > kMaxDynSmem || W > 32) return false;
-    const dim3 grid((unsigned)((nout[0] + 31) / 32), (unsigned)((nout[1] + TY - 1) / TY), (unsigned)nout[2]);
+    // the nrhs right-hand sides follow one another: nrhs x nout[2] planes of axis 2
+    const dim3 grid((unsigned)((nout[0] + 31) / 32), (unsigned)((nout[1] + TY - 1) / TY), (unsigned)(nout[2] * nrhs));
     const int3 ni = make_int3(nin[0], nin[1], nin[2]), no = make_int3(nout[0], nout[1], nout[2]);
     const int ad = add ? 1 : 0, mk = mask ? 1 : 0;
     if (W <= 4) launch_k(transfer2_kernel<T, 4, TY>, grid, 256, smem, st, M0, M1, ni, no, in, in2, out, ad, mk, clear);
@@ -979,27 +1093,30 @@ bool launch_transfer2(const DevBand<T>& M0, const DevBand<T>& M1, const int nin[
 }
 
 template <typename T>
-void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, T* w, cudaStream_t st, bool e_boundary_zero) {
-    if (!e_boundary_zero) cudaMemsetAsync(e, 0, sizeof(T) * N0, st);
+void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, T* w, cudaStream_t st, bool e_boundary_zero,
+                   int nrhs) {
+    // r, e, w: nrhs vectors of N0 values each (the right-hand side fastest
+    // in every kernel's CTA order, so each block operator is read once)
+    if (!e_boundary_zero) cudaMemsetAsync(e, 0, sizeof(T) * N0 * nrhs, st);
     const int k = C.cr_levels, m = C.m;
     const unsigned rows = (unsigned)((m + kBcrRows - 1) / kBcrRows);
     for (int l = 0; l < k; ++l) {
         const int a = C.nb >> l, nk = a / 2, ne = (a + 1) / 2;
-        const unsigned gx = (unsigned)(l == 0 ? nk + ne : nk);
+        const unsigned gx = (unsigned)(l == 0 ? nk + ne : nk) * nrhs;
         launch_k(bcr_forward_kernel<T>, dim3(gx, rows), 256, 2 * sizeof(T) * (size_t)m, st, C.fh[l], l, C.nb, m,
-                 C.ldm, C.index, r, w);
+                 C.ldm, C.index, r, w, nrhs, N0);
     }
     const size_t smem = sizeof(T) * (size_t)C.ld;
     long long blocks = (C.nr + 7) / 8;
     if (blocks > 2 * 152) blocks = 2 * 152;
     const T* src = k > 0 ? w : r;
     const long long* src_index = k > 0 ? nullptr : C.index;
-    launch_k(coarse_kernel<T>, (unsigned)blocks, 256, smem, st, C.nr, C.ld, C.index, C.inv, src, src_index, m,
-             1 << k, e);
+    launch_k(coarse_kernel<T>, (unsigned)(blocks * nrhs), 256, smem, st, C.nr, C.ld, C.index, C.inv, src, src_index,
+             m, 1 << k, e, nrhs, N0);
     for (int l = k - 1; l >= 0; --l) {
-        const unsigned ne = (unsigned)(((C.nb >> l) + 1) / 2);
+        const unsigned ne = (unsigned)(((C.nb >> l) + 1) / 2) * nrhs;
         launch_k(bcr_backward_kernel<T>, dim3(ne, rows), 256, 3 * sizeof(T) * (size_t)m, st, C.agk[l], l, C.nb, m,
-                 C.ldm, C.index, (const T*)w, e);
+                 C.ldm, C.index, (const T*)w, e, nrhs, N0);
     }
 }
 
@@ -1009,36 +1126,39 @@ void launch_cast(const Ti* in, To* out, long long n, cudaStream_t st) {
 }
 
 template <typename T>
-void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st) {
+void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st, int nrhs) {
     const long long total = (long long)n[0] * n[1] * n[2];
-    launch_k(zero_boundary_kernel<T>, grid_for(total), 256, 0, st, v, make_int3(n[0], n[1], n[2]), dim);
+    launch_k(zero_boundary_kernel<T>, grid_for(total * nrhs), 256, 0, st, v, make_int3(n[0], n[1], n[2]), dim, nrhs);
 }
 
 void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots, long long n,
-                 double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st) {
-    launch_k(dots_kernel, kDotBlocks, 256, 0, st, a0, b0, a1, b1, ndots, n, part, S, slot0, slot1, ticket, 0);
+                 double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st, int nrhs) {
+    launch_k(dots_kernel, dim3(kDotBlocks, nrhs), 256, 0, st, a0, b0, a1, b1, ndots, n, part, S, slot0, slot1, ticket,
+             0);
 }
 
 void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, const double* ppq,
                        int npq, const double* prz, int nrz, double* prr, double* S, unsigned* ticket, float* r32,
-                       cudaStream_t st) {
-    launch_k(fcg_update_kernel, kDotBlocks, 256, 0, st, x, r, p, q, n, ppq, npq, prz, nrz, prr, S, ticket, r32);
+                       cudaStream_t st, int nrhs) {
+    launch_k(fcg_update_kernel, dim3(kDotBlocks, nrhs), 256, 0, st, x, r, p, q, n, ppq, npq, prz, nrz, prr, S, ticket,
+             r32);
 }
 
 void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* prz, double* pzq,
-                       cudaStream_t st) {
-    launch_k(dots_rz_zq_kernel, kDotBlocks, 256, 0, st, r, z, z32, q, n, prz, pzq);
+                       cudaStream_t st, int nrhs) {
+    launch_k(dots_rz_zq_kernel, dim3(kDotBlocks, nrhs), 256, 0, st, r, z, z32, q, n, prz, pzq);
 }
 
 void launch_fcg_direction(double* p, const double* z, long long n, const double* prz, const double* pzq, int nd,
-                          const double* S, int flexible, cudaStream_t st) {
-    launch_k(fcg_direction_kernel, kDotBlocks, 256, 0, st, p, z, n, prz, pzq, nd, S, flexible);
+                          const double* S, int flexible, cudaStream_t st, int nrhs) {
+    launch_k(fcg_direction_kernel, dim3(kDotBlocks, nrhs), 256, 0, st, p, z, n, prz, pzq, nd, S, flexible);
 }
 
 void launch_lift_rhs(const double* mass, const double* f, const double* y, double* f0, const int n[3], int dim,
-                     cudaStream_t st) {
+                     cudaStream_t st, int nrhs) {
     const long long total = (long long)n[0] * n[1] * n[2];
-    launch_k(lift_rhs_kernel, grid_for(total), 256, 0, st, mass, f, y, f0, make_int3(n[0], n[1], n[2]), dim);
+    launch_k(lift_rhs_kernel, grid_for(total * nrhs), 256, 0, st, mass, f, y, f0, make_int3(n[0], n[1], n[2]), dim,
+             nrhs);
 }
 
 void launch_boundary_only(const double* g, double* v, const int n[3], int dim, cudaStream_t st) {
@@ -1062,16 +1182,16 @@ void launch_scale_by_norm(double* out, const double* in, const double* nrm2, lon
     launch_k(scale_by_norm_kernel, grid_for(n), 256, 0, st, out, in, nrm2, n);
 }
 
-void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st) {
-    launch_k(solve_init_kernel, 1, 32, 0, st, S, h, tol, maxit);
+void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st, int nrhs) {
+    launch_k(solve_init_kernel, 1, 32, 0, st, S, h, tol, maxit, nrhs);
 }
 
-void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st) {
-    launch_k(solve_cond_kernel, 1, 32, 0, st, S, h, maxit);
+void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st, int nrhs) {
+    launch_k(solve_cond_kernel, 1, 32, 0, st, S, h, maxit, nrhs);
 }
 
-void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st) {
-    launch_k(axpy_kernel, grid_for(n), 256, 0, st, y, x, a, n);
+void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st, int nrhs, bool x_shared) {
+    launch_k(axpy_kernel, grid_for(n * nrhs), 256, 0, st, y, x, a, n, nrhs, x_shared ? 1 : 0);
 }
 
 bool pdl_enabled() {
@@ -1102,27 +1222,28 @@ bool init_kernel_attributes() {
 
 // explicit instantiations
 template cudaError_t launch_apply<double>(const DevLevel<double>&, const double*, double*, bool, cudaStream_t, bool, double*,
-                                   double*, unsigned*);
+                                   double*, unsigned*, int);
 template cudaError_t launch_apply<float>(const DevLevel<float>&, const float*, float*, bool, cudaStream_t, bool, double*,
-                                  double*, unsigned*);
+                                  double*, unsigned*, int);
 template void launch_line_solve<double>(const DevLevel<double>&, int, int, const double*, const double*, double*,
-                                        double*, double, cudaStream_t);
+                                        double*, double, cudaStream_t, int);
 template void launch_line_solve<float>(const DevLevel<float>&, int, int, const float*, const float*, float*,
-                                       float*, float, cudaStream_t);
+                                       float*, float, cudaStream_t, int);
 template void launch_transfer<double>(const DevBand<double>&, int, const int*, const int*, const double*, const double*,
-                                      double*, bool, bool, cudaStream_t, double*);
+                                      double*, bool, bool, cudaStream_t, double*, int);
 template void launch_transfer<float>(const DevBand<float>&, int, const int*, const int*, const float*, const float*,
-                                     float*, bool, bool, cudaStream_t, float*);
+                                     float*, bool, bool, cudaStream_t, float*, int);
 template void launch_coarse<double>(const DevCoarse<double>&, long long, const double*, double*, double*, cudaStream_t,
-                                    bool);
-template void launch_coarse<float>(const DevCoarse<float>&, long long, const float*, float*, float*, cudaStream_t, bool);
+                                    bool, int);
+template void launch_coarse<float>(const DevCoarse<float>&, long long, const float*, float*, float*, cudaStream_t, bool,
+                                   int);
 template bool launch_transfer2<double>(const DevBand<double>&, const DevBand<double>&, const int*, const int*,
-                                       const double*, const double*, double*, bool, bool, cudaStream_t, double*);
+                                       const double*, const double*, double*, bool, bool, cudaStream_t, double*, int);
 template bool launch_transfer2<float>(const DevBand<float>&, const DevBand<float>&, const int*, const int*,
-                                      const float*, const float*, float*, bool, bool, cudaStream_t, float*);
+                                      const float*, const float*, float*, bool, bool, cudaStream_t, float*, int);
 template void launch_cast<double, float>(const double*, float*, long long, cudaStream_t);
 template void launch_cast<float, double>(const float*, double*, long long, cudaStream_t);
-template void launch_zero_boundary<double>(double*, const int*, int, cudaStream_t);
-template void launch_zero_boundary<float>(float*, const int*, int, cudaStream_t);
+template void launch_zero_boundary<double>(double*, const int*, int, cudaStream_t, int);
+template void launch_zero_boundary<float>(float*, const int*, int, cudaStream_t, int);
 
 }  // namespace glls

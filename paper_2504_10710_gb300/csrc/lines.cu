@@ -17,6 +17,8 @@ template <typename T>
 struct WarpLineArgs {
     int n, nlines, stride, m1, st1, st2, contiguous, mode;
     int p;              // element order: element-boundary nodes are multiples of p
+    int nrhs;           // right-hand sides (vectors of N values each)
+    long long N;
     T alpha;
     const typename Vec2Of<T>::type* band;   // (diag, off) per node
     const T* g;
@@ -36,6 +38,15 @@ __device__ __forceinline__ int padi(int k) { return k + (k >> 5); }
 template <typename T, int C, int LPB, int MODE>
 __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) {
     grid_dep_sync();
+    // right-hand side fastest in the CTA order (see device.cuh)
+    const int rhs = blockIdx.x % A.nrhs, bx = blockIdx.x / A.nrhs;
+    {
+        const long long off = (long long)rhs * A.N;
+        if (A.g) A.g += off;
+        if (A.r) A.r += off;
+        if (A.y) A.y += off;
+        A.x += off;
+    }
     constexpr int SPAN = 32 * C + C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sd = reinterpret_cast<T*>(smem_raw);
@@ -44,7 +55,7 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
     __shared__ int sbase[LPB];
     __shared__ int sseam[LPB];   // the whole line lies on element boundaries
     const int n = A.n;
-    const int l0 = blockIdx.x * LPB;
+    const int l0 = bx * LPB;
     const int Wc = min(LPB, A.nlines - l0);
     const int tid = threadIdx.x;
     if (tid < LPB) {
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(32 * LPB) line_warp_kernel(WarpLineArgs<T> A) 
 template <typename T, int C, int LPB>
 void launch_lpb(const WarpLineArgs<T>& A, cudaStream_t st) {
     const size_t smem = sizeof(T) * 3 * LPB * (32 * C + C);
-    const int blocks = (A.nlines + LPB - 1) / LPB;
+    const int blocks = (A.nlines + LPB - 1) / LPB * A.nrhs;
     switch (A.mode) {
         case 0: launch_k(line_warp_kernel<T, C, LPB, 0>, blocks, 32 * LPB, smem, st, A); break;
         case 1: launch_k(line_warp_kernel<T, C, LPB, 1>, blocks, 32 * LPB, smem, st, A); break;
@@ -195,8 +206,10 @@ bool init_line_warp_attributes() {
 
 template <typename T>
 bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
-                      cudaStream_t st) {
+                      cudaStream_t st, int nrhs) {
     WarpLineArgs<T> A;
+    A.nrhs = nrhs;
+    A.N = L.N;
     A.n = L.n[s] - 2;
     const int cmax = sizeof(T) == 4 ? 32 : 16;
     if (A.n > 32 * cmax || L.N > (1LL << 31) - 1) return false;
@@ -237,8 +250,8 @@ bool launch_line_warp(const DevLevel<T>& L, int s, int mode, const T* g, const T
 }
 
 template bool launch_line_warp<float>(const DevLevel<float>&, int, int, const float*, const float*, float*,
-                                      float*, float, cudaStream_t);
+                                      float*, float, cudaStream_t, int);
 template bool launch_line_warp<double>(const DevLevel<double>&, int, int, const double*, const double*,
-                                       double*, double*, double, cudaStream_t);
+                                       double*, double*, double, cudaStream_t, int);
 
 }  // namespace glls

@@ -39,6 +39,8 @@ template <typename T>
 struct BlockLineArgs {
     int n, nlines, stride, m1, st1, st2, contiguous, mode;
     int p, E, span, cv, lpc;
+    int nrhs;           // right-hand sides (vectors of N values each)
+    long long N;
     long long ntask;
     T alpha;
     const T* blk;                              // [ncoef][ntask]
@@ -113,6 +115,16 @@ template <typename T, int P, int CV>
 __global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 || P == 0 ? 3 : 4))
     line_block_kernel(BlockLineArgs<T> A) {
     grid_dep_sync();
+    // right-hand side fastest in the CTA order (see device.cuh): the nrhs CTAs
+    // of one line group read the same segment operators
+    const int rhs = blockIdx.x % A.nrhs, bx = blockIdx.x / A.nrhs;
+    {
+        const long long vo = (long long)rhs * A.N;
+        if (A.g) A.g += vo;
+        if (A.r) A.r += vo;
+        if (A.y) A.y += vo;
+        A.x += vo;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = A.n, E = A.E, span = A.span, mode = A.mode, LPC = A.lpc;
     const int p = P > 0 ? P : A.p;
@@ -124,7 +136,7 @@ __global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 ||
     T* sdr = sdl + LPC * E;                   // [LPC][E]: w_R . g_I
     T* svb = sdr + LPC * E;                   // [LPC][2 (E - 1)]: vertex systems
     T* sz = svb + 2 * LPC * (E - 1);          // [LPC][span]: z accumulation (P = 0)
-    const int l0 = blockIdx.x * LPC;
+    const int l0 = bx * LPC;
     const int Wc = min(LPC, A.nlines - l0);
     const int tid = threadIdx.x;
     // first node of line w of this CTA (interior indices c1, c2 of the other axes)
@@ -314,14 +326,15 @@ bool launch_pc(BlockLineArgs<T> A, cudaStream_t st) {
     // level would have less than about four CTAs per SM (small levels are
     // latency bound: more, smaller CTAs run their phases side by side)
     int lpc = std::min(kMaxLinesPerCta, std::max(1, kBlockThreads / A.E));
-    while (lpc > 1 && (A.nlines + lpc - 1) / lpc < 4 * sm_count()) lpc /= 2;
+    while (lpc > 1 && (long long)(A.nlines + lpc - 1) / lpc * A.nrhs < 4 * sm_count()) lpc /= 2;
     while (lpc > 1 && block_smem<T, P>(lpc, A.span, A.E) > kMaxDynSmemBytes) lpc /= 2;
     const size_t smem = block_smem<T, P>(lpc, A.span, A.E);
     if (smem > kMaxDynSmemBytes) return false;
     A.lpc = lpc;
     const int threads = std::min(kBlockThreads, std::max(32, (lpc * A.E + 31) / 32 * 32));
-    const int blocks = (A.nlines + lpc - 1) / lpc;
-    return launch_k(line_block_kernel<T, P, CV>, blocks, threads, smem, st, A) == cudaSuccess;
+    const long long blocks = (long long)(A.nlines + lpc - 1) / lpc * A.nrhs;
+    if (blocks > 0x7fffffffLL) return false;
+    return launch_k(line_block_kernel<T, P, CV>, (unsigned)blocks, threads, smem, st, A) == cudaSuccess;
 }
 
 template <typename T, int P>
@@ -371,8 +384,10 @@ bool line_block_supported(int n, int E) { return n <= kMaxBlockLine && E <= kMax
 
 template <typename T>
 bool launch_line_block(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
-                       cudaStream_t st) {
+                       cudaStream_t st, int nrhs) {
     BlockLineArgs<T> A;
+    A.nrhs = nrhs;
+    A.N = L.N;
     A.n = L.n[s] - 2;
     if (A.n <= 0) return true;
     A.E = L.ne[s];
@@ -416,8 +431,8 @@ bool launch_line_block(const DevLevel<T>& L, int s, int mode, const T* g, const 
 }
 
 template bool launch_line_block<float>(const DevLevel<float>&, int, int, const float*, const float*, float*, float*,
-                                       float, cudaStream_t);
+                                       float, cudaStream_t, int);
 template bool launch_line_block<double>(const DevLevel<double>&, int, int, const double*, const double*, double*,
-                                        double*, double, cudaStream_t);
+                                        double*, double, cudaStream_t, int);
 
 }  // namespace glls

@@ -38,20 +38,40 @@ struct MeshKey {
     }
 };
 
+// FNV-1a over 64-bit words (then the tail bytes): the mesh key of a
+// coordinate array, computed once per registered mesh.
 unsigned long long fnv1a(const void* data, size_t n) {
     const unsigned char* p = static_cast<const unsigned char*>(data);
     unsigned long long h = 1469598103934665603ULL;
-    for (size_t i = 0; i < n; ++i) {
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        unsigned long long w;
+        std::memcpy(&w, p + i, 8);
+        h ^= w;
+        h *= 1099511628211ULL;
+    }
+    for (; i < n; ++i) {
         h ^= p[i];
         h *= 1099511628211ULL;
     }
     return h;
 }
 
+// A mesh known to the server: its description with its own copy of the
+// coordinates, key and memory estimate.  Requests point at it.
+struct MeshRec {
+    glls_mesh_desc desc{};
+    std::vector<double> coords;
+    MeshKey key;
+    size_t estimate = 0;
+    long long N = 0;
+};
+
 struct Request {
     unsigned long long id = 0;
     glls_mesh_desc desc{};
-    std::vector<double> coords, f, g;
+    std::vector<double> f, g;
+    std::shared_ptr<const MeshRec> mesh;
     glls_solve_opts opts{};
     double* u = nullptr;
     MeshKey key;
@@ -113,6 +133,8 @@ struct glls_server {
     bool stop = false;
     std::vector<std::thread> workers;
     std::vector<MeshKey> creating;   // meshes whose set-up is in progress
+    std::unordered_map<unsigned long long, std::shared_ptr<const MeshRec>> meshes;   // registered
+    unsigned long long next_mesh = 1;
 
     bool pending_key(const MeshKey& k) const {
         for (const auto& c : creating)
@@ -321,34 +343,41 @@ void glls_server_destroy(glls_server* S) {
     delete S;
 }
 
-glls_status glls_submit(glls_server* S, const glls_mesh_desc* mesh, const double* f, const double* g,
-                        const glls_solve_opts* opts, double* u, unsigned long long* ticket) {
-    if (!S || !mesh || !f || !opts || !u || !ticket || !mesh->coords) return GLLS_ERR_INVALID;
-    auto r = std::make_unique<Request>();
-    size_t est = 0;
-    glls_status st = glls_estimate_bytes(mesh, &est);
-    if (st != GLLS_OK) return st;
+static std::shared_ptr<MeshRec> make_mesh(glls_server* S, const glls_mesh_desc* mesh, glls_status* st) {
+    auto m = std::make_shared<MeshRec>();
+    *st = glls_estimate_bytes(mesh, &m->estimate);
+    if (*st != GLLS_OK) return nullptr;
     long long N = 1;
     for (int a = 0; a < mesh->dim; ++a) N *= (long long)mesh->nelem[a] * mesh->order + 1;
-    r->N = N;
-    r->coords.assign(mesh->coords, mesh->coords + (size_t)mesh->dim * N);
-    r->f.assign(f, f + N);
-    if (g) r->g.assign(g, g + N);
-    r->desc = *mesh;
-    r->desc.coords = r->coords.data();
-    r->desc.device = S->device;
+    m->N = N;
+    m->coords.assign(mesh->coords, mesh->coords + (size_t)mesh->dim * N);
+    m->desc = *mesh;
+    m->desc.coords = m->coords.data();
+    m->desc.device = S->device;
+    m->key.dim = mesh->dim;
+    m->key.order = mesh->order;
+    m->key.smoother = mesh->smoother;
+    m->key.restriction = mesh->restriction;
+    m->key.coarse_solver = mesh->coarse_solver;
+    m->key.coarse_cr_levels = mesh->coarse_cr_levels;
+    for (int a = 0; a < 3; ++a) m->key.nelem[a] = a < mesh->dim ? mesh->nelem[a] : 1;
+    m->key.ncoords = m->coords.size();
+    m->key.hash = fnv1a(m->coords.data(), sizeof(double) * m->coords.size());
+    return m;
+}
+
+static glls_status enqueue(glls_server* S, std::shared_ptr<const MeshRec> m, const double* f, const double* g,
+                           const glls_solve_opts* opts, double* u, unsigned long long* ticket) {
+    auto r = std::make_unique<Request>();
+    r->mesh = m;
+    r->N = m->N;
+    r->f.assign(f, f + m->N);
+    if (g) r->g.assign(g, g + m->N);
+    r->desc = m->desc;
     r->opts = *opts;
     r->u = u;
-    r->estimate = est;
-    r->key.dim = mesh->dim;
-    r->key.order = mesh->order;
-    r->key.smoother = mesh->smoother;
-    r->key.restriction = mesh->restriction;
-    r->key.coarse_solver = mesh->coarse_solver;
-    r->key.coarse_cr_levels = mesh->coarse_cr_levels;
-    for (int a = 0; a < 3; ++a) r->key.nelem[a] = a < mesh->dim ? mesh->nelem[a] : 1;
-    r->key.ncoords = r->coords.size();
-    r->key.hash = fnv1a(r->coords.data(), sizeof(double) * r->coords.size());
+    r->estimate = m->estimate;
+    r->key = m->key;
     r->submitted = Clock::now();
     {
         std::lock_guard<std::mutex> lock(S->m);
@@ -360,6 +389,53 @@ glls_status glls_submit(glls_server* S, const glls_mesh_desc* mesh, const double
     }
     S->cv_work.notify_all();
     return GLLS_OK;
+}
+
+glls_status glls_submit(glls_server* S, const glls_mesh_desc* mesh, const double* f, const double* g,
+                        const glls_solve_opts* opts, double* u, unsigned long long* ticket) {
+    if (!S || !mesh || !f || !opts || !u || !ticket || !mesh->coords) return GLLS_ERR_INVALID;
+    glls_status st = GLLS_OK;
+    std::shared_ptr<MeshRec> m;
+    try {
+        m = make_mesh(S, mesh, &st);
+    } catch (const std::bad_alloc&) {
+        return GLLS_ERR_OOM;
+    }
+    if (!m) return st;
+    return enqueue(S, m, f, g, opts, u, ticket);
+}
+
+glls_status glls_server_register(glls_server* S, const glls_mesh_desc* mesh, unsigned long long* mesh_id) {
+    if (!S || !mesh || !mesh_id || !mesh->coords) return GLLS_ERR_INVALID;
+    glls_status st = GLLS_OK;
+    std::shared_ptr<MeshRec> m;
+    try {
+        m = make_mesh(S, mesh, &st);
+    } catch (const std::bad_alloc&) {
+        return GLLS_ERR_OOM;
+    }
+    if (!m) return st;
+    std::lock_guard<std::mutex> lock(S->m);
+    *mesh_id = S->next_mesh++;
+    S->meshes.emplace(*mesh_id, std::move(m));
+    return GLLS_OK;
+}
+
+glls_status glls_submit_mesh(glls_server* S, unsigned long long mesh_id, const double* f, const double* g,
+                             const glls_solve_opts* opts, double* u, unsigned long long* ticket) {
+    if (!S || !f || !opts || !u || !ticket) return GLLS_ERR_INVALID;
+    std::shared_ptr<const MeshRec> m;
+    {
+        std::lock_guard<std::mutex> lock(S->m);
+        auto it = S->meshes.find(mesh_id);
+        if (it == S->meshes.end()) return GLLS_ERR_INVALID;
+        m = it->second;
+    }
+    try {
+        return enqueue(S, m, f, g, opts, u, ticket);
+    } catch (const std::bad_alloc&) {
+        return GLLS_ERR_OOM;
+    }
 }
 
 glls_status glls_poll(glls_server* S, unsigned long long ticket, int wait, glls_stats* stats) {

@@ -7,12 +7,33 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <sstream>
 #include <thread>
 
 namespace glls {
 
 namespace {
+
+// Runs fn(i) for i in [0, count) on up to `threads` host threads.
+void parallel_for(long long count, int threads, const std::function<void(long long)>& fn) {
+    const int nt = (int)std::max(1LL, std::min<long long>(count, threads));
+    if (nt <= 1) {
+        for (long long i = 0; i < count; ++i) fn(i);
+        return;
+    }
+    std::atomic<long long> next(0);
+    auto work = [&]() {
+        for (long long i = next.fetch_add(1); i < count; i = next.fetch_add(1)) fn(i);
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+}
+
+int host_threads() { return (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency())); }
+
 
 // Legendre L_p and L_p' at x by the recurrences
 //   (n+1) L_{n+1} = (2n+1) x L_n - n L_{n-1},   L_{n+1}' = L_{n-1}' + (2n+1) L_n.
@@ -100,6 +121,24 @@ void local_coords(int q, int n1, int dim, int lc[3]) {
 
 int local_index(const int lc[3], int n1) { return (lc[2] * n1 + lc[1]) * n1 + lc[0]; }
 
+// Runs fn(e) for every element e, the elements of one parity colour (the
+// parities of its element coordinates) at a time, in parallel: two elements
+// of one colour share no node, so per-node accumulation needs no locking.
+void for_elements_colored(const LevelHost& lv, const std::function<void(long long)>& fn) {
+    const int d = lv.dim;
+    for (int c = 0; c < (1 << d); ++c) {
+        const long long h[3] = {(lv.ne[0] - (c & 1) + 1) / 2, (lv.ne[1] - ((c >> 1) & 1) + 1) / 2,
+                                d == 3 ? (lv.ne[2] - ((c >> 2) & 1) + 1) / 2 : 1};
+        const long long cnt = h[0] * h[1] * h[2];
+        parallel_for(cnt, host_threads(), [&](long long i) {
+            const long long ex = 2 * (i % h[0]) + (c & 1);
+            const long long ey = 2 * ((i / h[0]) % h[1]) + ((c >> 1) & 1);
+            const long long ez = d == 3 ? 2 * (i / (h[0] * h[1])) + ((c >> 2) & 1) : 0;
+            fn((ez * lv.ne[1] + ey) * lv.ne[0] + ex);
+        });
+    }
+}
+
 std::string geometry(LevelHost& lv) {
     const int d = lv.dim, p = lv.p, n1 = p + 1, nloc = lv.nloc;
     std::vector<double> w1;
@@ -108,8 +147,10 @@ std::string geometry(LevelHost& lv) {
     lv.G.assign((size_t)lv.ncomp * lv.E * nloc, 0.0);
     lv.mass.assign(lv.N, 0.0);
     Geo geo{d, p, n1, nloc, &lv};
-    std::vector<double> X((size_t)d * nloc);
-    for (long long e = 0; e < lv.E; ++e) {
+    std::mutex err_m;
+    std::string err;
+    for_elements_colored(lv, [&](long long e) {
+        std::vector<double> X((size_t)d * nloc);
         int ec[3];
         element_coords(lv, e, ec);
         for (int q = 0; q < nloc; ++q) {
@@ -155,7 +196,9 @@ std::string geometry(LevelHost& lv) {
             if (!(det > 0.0)) {
                 std::ostringstream os;
                 os << "non-positive Jacobian " << det << " in element " << e << " (order " << p << ")";
-                return os.str();
+                std::lock_guard<std::mutex> lock(err_m);
+                if (err.empty()) err = os.str();
+                return;
             }
             double w = 1.0;
             for (int a = 0; a < d; ++a) w *= w1[lc[a]];
@@ -167,8 +210,8 @@ std::string geometry(LevelHost& lv) {
                 }
             lv.mass[geo.gnode(ec, lc)] += w * det;
         }
-    }
-    return "";
+    });
+    return err;
 }
 
 inline double Gc(const LevelHost& lv, int a, int b, long long e, int q) {
@@ -183,7 +226,7 @@ void gll_band(LevelHost& lv) {
     lv.diag.assign(lv.N, 0.0);
     for (int s = 0; s < 3; ++s) lv.off[s].assign(lv.N, 0.0);
     Geo geo{d, p, n1, nloc, &lv};
-    for (long long e = 0; e < lv.E; ++e) {
+    for_elements_colored(lv, [&](long long e) {
         int ec[3];
         element_coords(lv, e, ec);
         for (int q = 0; q < nloc; ++q) {
@@ -223,7 +266,7 @@ void gll_band(LevelHost& lv) {
                 lv.off[s][g] += o;
             }
         }
-    }
+    });
 }
 
 // Def. 3.2's line system of an interior grid line is R A_p P: every coupling
@@ -693,25 +736,6 @@ std::string build_levels(int dim, const int nelem[3], int p_fine, const double* 
     return "";
 }
 
-// Runs fn(i) for i in [0, count) on up to `threads` host threads.
-void parallel_for(long long count, int threads, const std::function<void(long long)>& fn) {
-    const int nt = (int)std::max(1LL, std::min<long long>(count, threads));
-    if (nt <= 1) {
-        for (long long i = 0; i < count; ++i) fn(i);
-        return;
-    }
-    std::atomic<long long> next(0);
-    auto work = [&]() {
-        for (long long i = next.fetch_add(1); i < count; i = next.fetch_add(1)) fn(i);
-    };
-    std::vector<std::thread> th;
-    for (int t = 1; t < nt; ++t) th.emplace_back(work);
-    work();
-    for (auto& t : th) t.join();
-}
-
-int host_threads() { return (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency())); }
-
 // Inverse of an SPD matrix with half bandwidth bw (dense n x n row-major):
 // banded Cholesky A = L L^T, then L L^T x = e_c for every column c (columns
 // split over `threads` host threads).  The back substitution reads a
@@ -914,16 +938,25 @@ std::string build_coarse(const LevelHost& lv, int coarse_solver, int cr_levels, 
     // A_0 couples a block only to itself and its two neighbours
     out.nb = lv.n[d - 1] - 2;
     out.m = (int)(n / out.nb);
-    const int nb = out.nb, m = out.m;
+    // at p > 1 (a grid with one element along some axis stops at p = 2) a
+    // node couples to nodes up to p slowest-axis indices away: the system is
+    // not block tridiagonal over those indices, and the dense inverse is used
+    const bool block_tridiagonal = p == 1;
+    const int nb = block_tridiagonal ? out.nb : 1, m = block_tridiagonal ? out.m : (int)n;
+    if (!block_tridiagonal) {
+        out.nb = 1;
+        out.m = (int)n;
+    }
     int k = 0;
-    if (coarse_solver == 2)
+    if (!block_tridiagonal) k = 0;
+    else if (coarse_solver == 2)
         k = std::min(cr_levels > 0 ? cr_levels : std::max(1, auto_cr_levels(nb, m)), max_cr_levels(nb));
     else if (coarse_solver == 0) k = auto_cr_levels(nb, m);
     // the dense inverse of the whole system is kept to moderate sizes; larger
     // systems take at least one level of block CR
     constexpr long long kMaxDenseUnknowns = 16384;
     if (k == 0 && n > kMaxDenseUnknowns) {
-        if (coarse_solver == 1)
+        if (coarse_solver == 1 || !block_tridiagonal)
             return "coarsest level has more than 16384 interior unknowns: use GLLS_COARSE_AUTO or GLLS_COARSE_BLOCK_CR";
         k = std::max(1, std::min(max_cr_levels(nb), auto_cr_levels(nb, m)));
     }
@@ -936,7 +969,8 @@ std::string build_coarse(const LevelHost& lv, int coarse_solver, int cr_levels, 
     // assemble the blocks from the element matrices:
     // A_e[m][m2] = sum_q sum_ab G_ab(q) B_a(q, m) B_b(q, m2)
     const size_t mm = (size_t)m * m;
-    std::vector<Mat> Ab(nb, Mat(mm, 0.0)), Lb(nb, Mat(mm, 0.0)), Ub(nb, Mat(mm, 0.0));
+    // (one block: the whole system, no coupling blocks)
+    std::vector<Mat> Ab(nb, Mat(mm, 0.0)), Lb(nb, Mat(nb > 1 ? mm : 0, 0.0)), Ub(nb, Mat(nb > 1 ? mm : 0, 0.0));
     long long bw = 0;
     Geo geo{d, p, n1, nloc, &lv};
     const std::vector<double>& D = lv.D;

@@ -45,7 +45,7 @@ class Info(C.Structure):
     _fields_ = [("dim", C.c_int), ("levels", C.c_int), ("order", C.c_int * 8), ("nodes", (C.c_int * 3) * 8),
                 ("ndof", C.c_longlong * 8), ("coarse_unknowns", C.c_longlong), ("device_bytes", C.c_size_t),
                 ("coarse_cr_levels", C.c_int), ("coarse_dense_unknowns", C.c_longlong),
-                ("instance_bytes", C.c_size_t)]
+                ("instance_bytes", C.c_size_t), ("nrhs", C.c_int)]
 
 
 class ServerInfo(C.Structure):
@@ -76,6 +76,7 @@ def lib():
         sig = {
             "glls_gll": [i, C.POINTER(d), C.POINTER(d)],
             "glls_problem_create": [C.POINTER(MeshDesc), C.POINTER(vp)],
+            "glls_problem_create_nrhs": [C.POINTER(MeshDesc), i, C.POINTER(vp)],
             "glls_problem_info": [vp, C.POINTER(Info)],
             "glls_problem_clone": [vp, C.POINTER(vp)],
             "glls_set_dirichlet": [vp, vp, i, vp],
@@ -91,6 +92,8 @@ def lib():
             "glls_poll": [vp, C.c_ulonglong, i, C.POINTER(Stats)],
             "glls_server_info_get": [vp, C.POINTER(ServerInfo)],
             "glls_cancel": [vp, C.c_ulonglong],
+            "glls_server_register": [vp, C.POINTER(MeshDesc), C.POINTER(C.c_ulonglong)],
+            "glls_submit_mesh": [vp, C.c_ulonglong, vp, vp, C.POINTER(SolveOpts), vp, C.POINTER(C.c_ulonglong)],
             "glls_apply_partials_f64": [vp, i, vp, vp, vp, i, C.POINTER(i), vp],
         }
         for suf, real in (("f64", d), ("f32", C.c_float)):
@@ -153,13 +156,14 @@ class Problem:
     """Owns a ``glls_problem``: mesh levels resident on the device."""
 
     def __init__(self, dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE,
-                 device=0, coarse_solver=COARSE_AUTO, coarse_cr_levels=0):
+                 device=0, coarse_solver=COARSE_AUTO, coarse_cr_levels=0, nrhs=1):
         desc, coords = mesh_desc(dim, nelem, order, coords, smoother, restriction, device, coarse_solver,
                                  coarse_cr_levels)
         self._coords = coords
         h = C.c_void_p()
-        _check(lib().glls_problem_create(C.byref(desc), C.byref(h)))
+        _check(lib().glls_problem_create_nrhs(C.byref(desc), nrhs, C.byref(h)))
         self.h = h
+        self.nrhs = nrhs
         self.dim = dim
         self.info = self._info()
         self.N = int(self.info.ndof[self.info.levels - 1])
@@ -169,7 +173,7 @@ class Problem:
         h = C.c_void_p()
         _check(lib().glls_problem_clone(self.h, C.byref(h)))
         c = Problem.__new__(Problem)
-        c.h, c.dim, c._coords = h, self.dim, self._coords
+        c.h, c.dim, c._coords, c.nrhs = h, self.dim, self._coords, self.nrhs
         c.info = c._info()
         c.N = self.N
         return c
@@ -215,17 +219,18 @@ class Problem:
 
     def solve(self, out, o: SolveOpts, stream=None, raise_on_error=True):
         """Solve into ``out`` (numpy float64 host array or torch CUDA float64
-        tensor).  Returns the Stats structure."""
-        st = Stats()
+        tensor of nrhs x N values).  Returns the Stats structure (a list of
+        nrhs of them when nrhs > 1)."""
+        st = (Stats * self.nrhs)()
         if isinstance(out, np.ndarray):
-            assert out.dtype == np.float64 and out.flags.c_contiguous
-            status = lib().glls_solve(self.h, C.byref(o), out.ctypes.data_as(C.c_void_p), 0, _stream(stream),
-                                      C.byref(st))
+            assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.N * self.nrhs
+            status = lib().glls_solve(self.h, C.byref(o), out.ctypes.data_as(C.c_void_p), 0, _stream(stream), st)
         else:
-            status = lib().glls_solve(self.h, C.byref(o), _ptr(out), 1, _stream(stream), C.byref(st))
+            assert out.numel() == self.N * self.nrhs
+            status = lib().glls_solve(self.h, C.byref(o), _ptr(out), 1, _stream(stream), st)
         if raise_on_error:
             _check(status)
-        return st
+        return st[0] if self.nrhs == 1 else list(st)
 
     def autotune(self):
         """Pick the line-solve tile per level/precision/direction by timing;
@@ -360,6 +365,24 @@ class Server:
         self._keep[t.value] = out          # the output buffer must outlive the request
         return t.value
 
+    def register(self, dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE):
+        """Registers a mesh; returns its id for submit_mesh."""
+        desc, coords = mesh_desc(dim, nelem, order, coords, smoother, restriction)
+        mid = C.c_ulonglong()
+        _check(lib().glls_server_register(self.h, C.byref(desc), C.byref(mid)))
+        return mid.value
+
+    def submit_mesh(self, mesh_id, f, g, o: SolveOpts, out):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+        assert out.dtype == np.float64 and out.flags.c_contiguous
+        t = C.c_ulonglong()
+        _check(lib().glls_submit_mesh(self.h, mesh_id, f.ctypes.data_as(C.c_void_p),
+                                      None if g is None else g.ctypes.data_as(C.c_void_p), C.byref(o),
+                                      out.ctypes.data_as(C.c_void_p), C.byref(t)))
+        self._keep[t.value] = out
+        return t.value
+
     def poll(self, ticket, wait=False):
         """(status, stats) or (NOT_READY, None)."""
         st = Stats()
@@ -394,10 +417,10 @@ class Server:
 
 
 def problem_for(workload, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0,
-                coarse_solver=COARSE_AUTO, coarse_cr_levels=0):
+                coarse_solver=COARSE_AUTO, coarse_cr_levels=0, nrhs=1):
     """Problem of a workload description, with nodes placed at the library's
     own GLL points."""
     xi, _ = gll(workload.order)
     coords = workload.coords(xi)
     return Problem(workload.dim, workload.nelem, workload.order, coords, smoother, restriction, device,
-                   coarse_solver, coarse_cr_levels), coords
+                   coarse_solver, coarse_cr_levels, nrhs), coords

@@ -26,6 +26,9 @@ Workloads (seeds are numpy.random.default_rng(2504_10710 + 1000*cfg + i)):
   * ``random2d/3d``      any element grid / order / amplitude, for parity tests.
   * ``batch_uneven``     independent 2-D problems, n x n elements with n ~ U{4..64},
                          p ~ U{4..12}, amplitude ~ U(0, 0.2), terrain2d generators.
+  * ``serving_stream``   Poisson arrivals over a pool of 2-D (batch_uneven
+                         distribution) and 3-D (n^3, n ~ U{8..32}, p ~ U{4..8})
+                         meshes, several seeded right-hand sides per mesh.
 """
 from __future__ import annotations
 
@@ -272,6 +275,60 @@ def batch_uneven(count: int = 256) -> list[Workload]:
         out.append(Workload(f"batch{i}_{n}x{n}_p{p}_a{amp:.3f}", 2, (n, n), p, terrain2d_map(amp), [f], g,
                             params=dict(amp=amp, f=fp, g=gp)))
     return out
+
+
+def serving_stream(nreq: int = 2000, rate: float = 200.0, pool2d: int = 16, pool3d: int = 8,
+                   nmax3d: int = 32, rhs_per_mesh: int = 4, seed: int = 0):
+    """Poisson-arrival request stream of the serving workload.
+
+    A pool of meshes drawn from the serving distributions: ``pool2d`` 2-D
+    meshes from the batch_uneven generator (n ~ U{4..64}, n x n elements,
+    p ~ U{4..12}, amplitude ~ U(0, 0.2)) and ``pool3d`` 3-D meshes with
+    n ~ U{8..nmax3d} (n^3 elements), p ~ U{4..8} and the terrain3d map at
+    amplitude 0.15; the largest 3-D draw is replaced by n = nmax3d, p = 8 so
+    that the pool covers the top of the range.  Every mesh carries
+    ``rhs_per_mesh`` seeded right-hand sides (16 Fourier modes) and seeded
+    smooth Dirichlet data.  Then ``nreq`` requests, half 2-D and half 3-D in
+    a seeded order, each on a mesh drawn uniformly from its half of the pool
+    with one of that mesh's right-hand sides, arrival gaps exponential with
+    mean 1/rate (seeds 2504_10710 + 5000 + i).
+
+    Returns (meshes, requests): meshes a list of Workload (one right-hand
+    side function per seeded RHS), requests a list of (arrival_s,
+    mesh_index, rhs_index)."""
+    rng = rng_for(5, seed)
+    meshes = []
+    for i in range(pool2d):
+        r = rng_for(5, 1000 + i)
+        n = int(r.integers(4, 65))
+        p = int(r.integers(4, 13))
+        amp = float(r.uniform(0.0, 0.2))
+        fs = [fourier_rhs_2d(r)[0] for _ in range(rhs_per_mesh)]
+        g, _ = smooth_dirichlet_2d(r)
+        meshes.append(Workload(f"serve2d{i}_{n}x{n}_p{p}_a{amp:.3f}", 2, (n, n), p, terrain2d_map(amp), fs, g,
+                               params=dict(amp=amp)))
+    draws = []
+    for i in range(pool3d):
+        r = rng_for(5, 2000 + i)
+        draws.append((int(r.integers(8, nmax3d + 1)), int(r.integers(4, 9)), r))
+    big = max(range(pool3d), key=lambda i: draws[i][0] ** 3 * draws[i][1] ** 3) if pool3d else None
+    for i, (n, p, r) in enumerate(draws):
+        if i == big:
+            n, p = nmax3d, 8
+        fs = [fourier_rhs_3d(r)[0] for _ in range(rhs_per_mesh)]
+        g, _ = smooth_dirichlet_3d(r)
+        meshes.append(Workload(f"serve3d{i}_{n}^3_p{p}", 3, (n, n, n), p, terrain3d_map(0.15), fs, g,
+                               params=dict(amp=0.15)))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    kinds = rng.permutation(np.arange(nreq) % 2)          # 0: 2-D, 1: 3-D
+    reqs = []
+    for k in range(nreq):
+        if kinds[k] == 0 or pool3d == 0:
+            mi = int(rng.integers(0, pool2d))
+        else:
+            mi = pool2d + int(rng.integers(0, pool3d))
+        reqs.append((float(arrivals[k]), mi, int(rng.integers(0, rhs_per_mesh))))
+    return meshes, reqs
 
 
 def random_field(shape, seed: int) -> np.ndarray:

@@ -1,8 +1,10 @@
-"""Several right-hand sides on one mesh: clones share the mesh data and are
-solved together in one batched graph launch.  Small 3-D case against the
-oracle; the full 16^3 p = 7 workload with 32 right-hand sides checked on
-sampled right-hand sides through the oracle's own FP64 operator (the true
-residual), which holds at any size."""
+"""Several right-hand sides on one mesh, two ways: one problem created with
+nrhs right-hand sides, whose kernels process all of them per launch; and
+clones that share the mesh data, solved together in one batched graph
+launch.  Small cases against the oracle and against single solves; the full
+16^3 p = 7 workload with 32 right-hand sides checked on sampled right-hand
+sides through the oracle's own FP64 operator (the true residual), which
+holds at any size."""
 import numpy as np
 import pytest
 
@@ -64,4 +66,92 @@ def test_terrain3d_full_size_32_rhs_true_residual():
         assert res <= 2e-10, (j, res)
     for c in clones:
         c.close()
+    prob.close()
+
+
+MULTI = [("2d_7x5_p6", lambda: inputs.random2d((7, 5), 6, amp=0.1, seed=33, nrhs=3)),
+         ("3d_3x3x2_p5", lambda: inputs.random3d((3, 3, 2), 5, amp=0.15, seed=31, nrhs=4)),
+         ("2d_4x3_p1", lambda: inputs.random2d((4, 3), 1, amp=0.05, seed=34, nrhs=3)),
+         ("3d_2x3x2_p3", lambda: inputs.random3d((2, 3, 2), 3, amp=0.1, seed=35, nrhs=5))]
+
+
+@pytest.mark.parametrize("prec", [glls.PREC_FP64, glls.PREC_MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("name,mk", MULTI, ids=[m[0] for m in MULTI])
+def test_nrhs_problem_equals_single_solves(name, mk, prec):
+    """A problem with nrhs right-hand sides gives, for each, the solution and
+    iteration count of a one-right-hand-side solve of it, and the oracle's."""
+    wl = mk()
+    prob, coords = glls.problem_for(wl, nrhs=wl.nrhs)
+    F = wl.sample_rhs(coords).reshape(wl.nrhs, -1)
+    g = wl.sample_dirichlet(coords).ravel()
+    prob.set_rhs(np.ascontiguousarray(F))
+    prob.set_dirichlet(g)
+    o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=prec)
+    U = np.zeros((wl.nrhs, prob.N))
+    stats = prob.solve(U, o)
+    single = glls.problem_for(wl)[0]
+    single.set_dirichlet(g)
+    fine = Level(wl.dim, wl.nelem, wl.order, coords)
+    ref = osolve.solve(wl, gamma=1, alpha=2.0 / 3.0, tol=1e-10, hierarchy=Hierarchy(fine, restriction="transpose"))
+    for j in range(wl.nrhs):
+        single.set_rhs(F[j])
+        u1 = np.zeros(prob.N)
+        s1 = single.solve(u1, o)
+        assert stats[j].status == glls.OK and stats[j].rel_residual <= 1e-10
+        assert stats[j].iterations == s1.iterations, (j, stats[j].iterations, s1.iterations)
+        assert np.abs(U[j] - u1).max() <= 1e-11 * np.abs(u1).max(), j
+        r = ref.u[j].ravel()
+        assert np.abs(U[j] - r).max() <= (1e-9 if prec == glls.PREC_FP64 else 1e-8) * np.abs(r).max()
+    single.close()
+    prob.close()
+
+
+def test_nrhs_each_right_hand_side_stops_on_its_own():
+    """Zero data stops at once with u = 0, a NaN right-hand side breaks down,
+    a scaled copy takes the same iterations; the others are unaffected and
+    the call reports the worst status."""
+    wl = inputs.random2d((6, 5), 5, amp=0.1, seed=36, nrhs=1)
+    prob, coords = glls.problem_for(wl, nrhs=4)
+    f = wl.sample_rhs(coords).reshape(-1)
+    F = np.stack([f, np.zeros_like(f), 1e6 * f, f.copy()])
+    nx = prob.level_shape(prob.levels - 1)[-1]
+    F[3, 10 * nx + 10] = np.nan          # an interior node (boundary values of f are not used)
+    prob.set_rhs(np.ascontiguousarray(F))
+    prob.set_dirichlet(np.zeros(prob.N))
+    U = np.zeros((4, prob.N))
+    stats = prob.solve(U, glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_MIXED),
+                       raise_on_error=False)
+    assert stats[0].status == glls.OK and stats[0].iterations > 3
+    assert stats[1].status == glls.OK and stats[1].iterations == 0 and not U[1].any()
+    assert stats[2].status == glls.OK and abs(stats[2].iterations - stats[0].iterations) <= 1
+    assert np.abs(U[2] - 1e6 * U[0]).max() <= 1e-8 * np.abs(U[2]).max()
+    assert stats[3].status == glls.ERR_BREAKDOWN
+    with pytest.raises(glls.GllsError) as ei:
+        prob.solve(U, glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_MIXED))
+    assert ei.value.status == glls.ERR_BREAKDOWN
+    # several right-hand sides need the device-loop graph and FCG / PCG
+    with pytest.raises(glls.GllsError):
+        prob.solve(U, glls.opts(use_graph=1))
+    prob.close()
+
+
+def test_terrain3d_full_size_32_rhs_in_one_problem():
+    """The 3-D workload's 32 right-hand sides as one problem with nrhs = 32
+    (every kernel launch covers all of them): each converges to 1e-10 and
+    its true FP64 residual, by the oracle's operator, agrees."""
+    wl = inputs.terrain3d()
+    prob, coords = glls.problem_for(wl, nrhs=wl.nrhs)
+    F = np.ascontiguousarray(wl.sample_rhs(coords).reshape(wl.nrhs, -1))
+    g = np.zeros(prob.N)
+    prob.set_rhs(F)
+    prob.set_dirichlet(g)
+    U = np.zeros((wl.nrhs, prob.N))
+    stats = prob.solve(U, glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_MIXED))
+    assert all(st.status == glls.OK and st.rel_residual <= 1e-10 for st in stats)
+    fine = Level(wl.dim, wl.nelem, wl.order, coords)
+    for j in (0, 17, 31):
+        f0, v = lift(fine, F[j].reshape(fine.shape), g.reshape(fine.shape))
+        w = U[j].reshape(fine.shape) - v
+        res = np.linalg.norm((f0 - fine.apply(w))[fine.interior]) / np.linalg.norm(f0[fine.interior])
+        assert res <= 2e-10, (j, res)
     prob.close()
