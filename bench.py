@@ -60,7 +60,9 @@ def parse():
                     help="only the warm-up and timed mixed-precision solves (for an ncu launch list)")
     ap.add_argument("--profile3d", action="store_true",
                     help="as --profile, on the 3-D 16^3 p = 7 workload with one right-hand side")
-    ap.add_argument("--probe", choices=["line2d", "line3d", "apply64"],
+    ap.add_argument("--serving-only", action="store_true",
+                    help="only the serving-stream measurement (prints its JSON object)")
+    ap.add_argument("--probe", choices=["line2d", "line3d", "apply64", "setup"],
                     help="launch one kernel a few times on its workload, nothing else (small ncu captures): "
                          "line2d / line3d = the fine-level FP32 line update (MODE 1) of every axis after one "
                          "apply, on the 2-D bench workload / the 3-D 16^3 p = 7 workload; apply64 = the 2-D "
@@ -428,7 +430,7 @@ def _line_operator_bytes(shape, p, s, block):
     return 4 * lines * E * ((p - 1) * p // 2 + 2 * (p - 1)) + 8 * lines * (E - 1)
 
 
-def smoother_rooflines(prob, glls, torch, inputs, flush):
+def smoother_rooflines(prob, glls, torch, inputs, flush, large=True):
     """FP32 smoother and operator kernels against HBM: the bench workload's
     fine level (L2-resident between launches, as inside a solve) and the 3-D
     16^3 p = 7 fine level (1.44M nodes; L2 flushed before every launch).
@@ -436,7 +438,8 @@ def smoother_rooflines(prob, glls, torch, inputs, flush):
     ncomp (p+1)^d 4 B per element); line solve (B^-1 g) the line operator
     (_line_operator_bytes) + g + x 4 B each per node; smoothing step (apply +
     damped line update, the K2 step of the scope table) x, r read, x written,
-    the line operator and G."""
+    the line operator and G.  With `large`, also the 3-D 32^3 p = 8 fine
+    level (17.0 M nodes), whose working set is several times L2."""
     peaks, src = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     out = []
@@ -449,9 +452,15 @@ def smoother_rooflines(prob, glls, torch, inputs, flush):
                     "l2": "flushed before each launch" if cold else "resident (graph replay)"})
 
     cases = [("terrain2d_64x64_p8", prob, False)] if prob is not None else []
-    wl3 = inputs.terrain3d()
+    wl3 = inputs.terrain3d(nrhs=1)
     p3, _ = glls.problem_for(wl3)
     cases.append(("terrain3d_16x16x16_p7", p3, True))
+    if large:
+        # working set far above L2: the largest serving mesh (17.0 M nodes,
+        # about 0.7 GB per FP32 apply)
+        wl4 = inputs.terrain3d(nelem=32, order=8, nrhs=1)
+        p4, _ = glls.problem_for(wl4)
+        cases.append(("terrain3d_32x32x32_p8", p4, True))
     for work, pb, cold in cases:
         L = pb.levels - 1
         shape = pb.level_shape(L)
@@ -577,62 +586,139 @@ def batch_run(glls, inputs, torch, reps=3):
            "converged": int(sum(x.status == glls.OK for x in st)),
            "iterations": {"median": float(np.median(its)), "p90": float(np.percentile(its, 90)),
                           "max": int(its.max())},
-           "smoother": SMOOTHER, "setup_s": setup_s}
+           "smoother": SMOOTHER, "setup_s": setup_s,
+           "form": "one graph launch, one branch per problem (each with its own device-side loop)"}
+    # the work-list form: one launch per step over all problems of an order chain
+    outs_w = [torch.zeros(p.N, dtype=torch.float64, device="cuda") for p in probs]
+    t0 = time.perf_counter()
+    st_w = glls.solve_batch(probs, outs_w, o, stream, raise_on_error=False, worklist=True)   # plan + capture
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    ms_w = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st_w = glls.solve_batch(probs, outs_w, o, stream, raise_on_error=False, worklist=True)
+        b.record(stream)
+        b.synchronize()
+        ms_w.append(a.elapsed_time(b))
+    its_w = np.array([x.iterations for x in st_w])
+    diff = max(float((x - y).abs().max() / y.abs().max()) for x, y in zip(outs_w, outs))
+    res["worklist"] = {"ms": float(np.median(ms_w)), "dof_per_s": dof / (float(np.median(ms_w)) / 1e3),
+                       "converged": int(sum(x.status == glls.OK for x in st_w)),
+                       "iterations": {"median": float(np.median(its_w)), "max": int(its_w.max())},
+                       "kernels_per_launch": int(st_w[0].kernels),
+                       "groups": len({tuple(p.info.order[:p.info.levels]) for p in probs}),
+                       "plan_s": plan_s, "max_rel_diff_vs_branches": diff,
+                       "form": "glls_solve_batch_worklist: problems grouped by order chain, one launch per step "
+                               "over each group's work list of (problem, level, tile range) items, one graph "
+                               "branch and device-side loop per group"}
     for p in probs:
         p.close()
     return res
 
 
-def serving_run(glls, inputs, nreq=120, rate=200.0, seed=5):
-    """Native serving loop under Poisson arrivals (mean `rate` per second):
-    requests drawn from a pool of 8 resident meshes, four 2-D (16..40
-    elements per side, p 4..8, amplitude 0..0.1) and four 3-D (8..12 per
-    side, p 4..6, amplitude 0.15), each a mixed-precision solve to 1e-10.
-    Reports achieved DOF/s and p50/p99 latency (submit -> result in host
-    memory) of requests for resident meshes."""
-    rng = np.random.default_rng(seed)
-    pool = []
-    for k in range(8):
-        if k < 4:
-            n = int(rng.integers(16, 41))
-            wl = inputs.random2d((n, n), int(rng.integers(4, 9)), amp=float(rng.uniform(0.0, 0.1)), seed=100 + k)
-        else:
-            n = int(rng.integers(8, 13))
-            wl = inputs.random3d((n, n, n), int(rng.integers(4, 7)), amp=0.15, seed=100 + k)
-        xi, _ = glls.gll(wl.order)
-        coords = wl.coords(xi)
-        pool.append((wl, coords, wl.sample_rhs(coords)[0], wl.sample_dirichlet(coords)))
-    srv = glls.Server(budget_bytes=16 << 30, slots=4)
-    o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED)
-    # warm the mesh cache (set-up) so that the stream measures serving, not set-up
-    for wl, coords, f, g in pool:
-        out = np.zeros(f.size)
-        srv.poll(srv.submit(wl.dim, wl.nelem, wl.order, coords, f, g, o, out), wait=True)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
-    choice = rng.integers(0, len(pool), nreq)
-    tickets, dofs = [], 0
+def serving_run(glls, inputs, nreq=2000, rate=200.0, slots=8, budget_gb=200, max_group=8, max_wait_s=240.0):
+    """The serving stream: ``nreq`` Poisson arrivals (mean ``rate`` per
+    second) over a pool of 16 2-D meshes (batch-uneven sizes) and 8 3-D meshes
+    (n^3 elements, n ~ U{8..32}, p ~ U{4..8}, including 32^3 at p = 8), each
+    request one mixed-precision solve to 1e-10.  The meshes are registered
+    with the server (coordinates copied once) but nothing is set up before
+    the stream starts: the first request on a mesh pays its set-up, later
+    concurrent requests on a busy mesh run on clones, and queued requests of
+    one mesh are solved together as one multi-right-hand-side solve (up to
+    ``max_group``; continuous batching).  Latency is submission
+    to the solution in host memory.  The client-side input generation
+    (coordinates, right-hand sides) happens before the stream and is not
+    part of any figure."""
+    from concurrent.futures import ThreadPoolExecutor
+    meshes, reqs = inputs.serving_stream(nreq=nreq, rate=rate)
     t0 = time.perf_counter()
-    for k in range(nreq):
-        delay = t0 + arrivals[k] - time.perf_counter()
+
+    def make(w):
+        xi, _ = glls.gll(w.order)
+        c = np.ascontiguousarray(w.coords(xi), dtype=np.float64).reshape(w.dim, -1)
+        F = [np.ascontiguousarray(f(*c), dtype=np.float64) for f in w.rhs]
+        g = np.ascontiguousarray(w.sample_dirichlet(c), dtype=np.float64)
+        return c, F, g
+    with ThreadPoolExecutor(8) as ex:
+        data = list(ex.map(make, meshes))
+    inputs_s = time.perf_counter() - t0
+    srv = glls.Server(budget_bytes=budget_gb << 30, slots=slots)
+    srv.set_max_group(max_group)
+    ids = [srv.register(w.dim, w.nelem, w.order, c) for w, (c, _, _) in zip(meshes, data)]
+    o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED, max_iter=300)
+    outs = {}
+    tickets = []
+    t0 = time.perf_counter()
+    lag = []
+    for k, (arr, mi, ri) in enumerate(reqs):
+        delay = t0 + arr - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        wl, coords, f, g = pool[choice[k]]
-        out = np.zeros(f.size)
-        tickets.append((srv.submit(wl.dim, wl.nelem, wl.order, coords, f, g, o, out), out))
-        dofs += f.size
-    lat, fails = [], 0
-    for t, _out in tickets:
-        st, stats = srv.poll(t, wait=True)
-        if st != glls.OK:
-            fails += 1
         else:
-            lat.append(stats.solve_ms)
-    wall = time.perf_counter() - t0
+            lag.append(-delay)
+        _, F, g = data[mi]
+        out = np.empty(F[ri].size)
+        tickets.append((srv.submit_mesh(ids[mi], F[ri], g, o, out), mi, time.perf_counter() - t0))
+    submit_span = time.perf_counter() - t0
+    # collect with a deadline: a request still unfinished then is reported,
+    # not waited for
+    res_all, pending = [], list(tickets)
+    deadline = time.perf_counter() + max_wait_s
+    while pending and time.perf_counter() < deadline:
+        left = []
+        for t, mi, ts in pending:
+            st, stats = srv.poll(t, wait=False)
+            if st == glls.NOT_READY:
+                left.append((t, mi, ts))
+            else:
+                res_all.append((mi, st, ts, stats.solve_ms, stats.queue_ms, stats.setup_ms, stats.setup_kind,
+                                stats.iterations, stats.group))
+        pending = left
+        if pending:
+            time.sleep(0.002)
+    for t, _, _ in pending:
+        srv.cancel(t)
+    info = srv.info()
     srv.close()
-    lat = np.array(lat)
-    return {"requests": nreq, "offered_per_s": rate, "achieved_per_s": nreq / wall, "dof_per_s": dofs / wall,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)), "failed": fails,
-            "slots": 4, "pool": [p[0].name for p in pool]}
+    ok = [r for r in res_all if r[1] == glls.OK]
+    end = max(ts + lat / 1e3 for _, _, ts, lat, *_ in res_all)
+    dof = sum(data[mi][2].size for mi, st, *_ in res_all if st == glls.OK)
+    dof_offered = sum(data[mi][2].size for _, mi, _ in reqs)
+    span = reqs[-1][0]
+    lat = np.array([r[3] for r in ok])
+    resident = np.array([r[3] for r in ok if r[6] == 0])
+    creates = [(meshes[r[0]].name, r[5]) for r in res_all if r[6] == 1]
+    clones = [r[5] for r in res_all if r[6] == 2]
+    its = np.array([r[7] for r in ok])
+    service = np.array([r[3] - r[4] - r[5] for r in ok])
+    gsz = np.array([r[8] for r in ok])
+
+    def pct(a, q):
+        return float(np.percentile(a, q)) if len(a) else None
+    d3 = [i for i, w in enumerate(meshes) if w.dim == 3]
+    return {"requests": nreq, "completed": len(ok), "failed": len(res_all) - len(ok), "unfinished": len(pending),
+            "offered": {"requests_per_s": nreq / span, "dof_per_s": dof_offered / span, "arrival_span_s": span},
+            "achieved": {"requests_per_s": len(ok) / end, "dof_per_s": dof / end, "wall_s": end},
+            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": float(lat.max()) if len(lat) else None,
+                           "what": "submission to solution in host memory (queue, set-up if any, solve)"},
+            "latency_resident_ms": {"p50": pct(resident, 50), "p99": pct(resident, 99), "n": int(len(resident)),
+                                    "what": "requests served by an instance that was already resident"},
+            "setup": {"creates": len(creates), "create_ms": {n: round(ms, 1) for n, ms in creates},
+                      "clones": len(clones), "clone_ms_median": pct(np.array(clones), 50),
+                      "what": "paid inside the latency of the request that triggered it"},
+            "service_ms": {"p50": pct(service, 50), "p99": pct(service, 99),
+                           "what": "latency minus queue and set-up: the solve itself, on a GPU shared with the "
+                                   "other slots"},
+            "grouping": {"max_group": max_group, "grouped_requests": int((gsz > 1).sum()),
+                         "group_sizes": {str(k): int((gsz == k).sum()) for k in sorted(set(gsz.tolist()))}},
+            "iterations": {"median": pct(its, 50), "max": int(its.max()) if len(its) else None},
+            "submit_lag_ms": {"p99": 1e3 * pct(np.array(lag), 99) if lag else 0.0, "late": len(lag)},
+            "slots": slots, "budget_gb": budget_gb, "resident_bytes_end": int(info.resident_bytes),
+            "server_clones": int(info.clones), "inputs_s": inputs_s,
+            "pool": {"2d": [w.name for w in meshes if w.dim == 2], "3d": [meshes[i].name for i in d3],
+                     "dof_max": int(max(data[i][2].size for i in d3))}}
 
 
 def _cpu_model():
@@ -710,12 +796,31 @@ def oracle_baseline(wl, u_ref_gpu=None):
 
 
 def probe(name, reps=3):
-    """Launch one kernel `reps` times per axis on its workload (see --probe)."""
+    """Launch one kernel `reps` times per axis on its workload (see --probe);
+    `setup` instead creates the 3-D serving meshes, the 2-D bench mesh and the
+    3-D 16^3 p = 7 mesh one after another and prints the set-up phases."""
     import torch
 
     import __graft_entry__
     from paper_2504_10710_gb300 import glls, inputs
     __graft_entry__.build()
+    if name == "setup":
+        meshes, _ = inputs.serving_stream(nreq=10)
+        wls = [inputs.terrain2d(), inputs.terrain3d(nrhs=1)] + [w for w in meshes if w.dim == 3]
+        for w in wls:
+            xi, _ = glls.gll(w.order)
+            c = np.ascontiguousarray(w.coords(xi)).reshape(w.dim, -1)
+            t0 = time.perf_counter()
+            pr = glls.Problem(w.dim, w.nelem, w.order, c)
+            ms = 1e3 * (time.perf_counter() - t0)
+            inf = pr._info()
+            print(json.dumps({"workload": w.name, "dof": int(pr.N), "create_ms": round(ms, 1),
+                              "phases_ms": dict(zip(["coords", "geometry", "lines", "transfers", "coarse", "upload"],
+                                                    [round(v, 1) for v in inf.setup_phase_ms])),
+                              "coarse": [int(inf.coarse_unknowns), int(inf.coarse_cr_levels)],
+                              "device_gb": round(inf.device_bytes / 2**30, 2)}), flush=True)
+            pr.close()
+        return
     wl = inputs.terrain3d(nrhs=1) if name == "line3d" else inputs.terrain2d()
     prob, _ = glls.problem_for(wl, glls.SMOOTHER_GLL, glls.RESTRICT_TRANSPOSE)
     L = prob.levels - 1
@@ -744,6 +849,12 @@ def probe(name, reps=3):
 
 def main():
     args = parse()
+    if args.serving_only:
+        import __graft_entry__
+        from paper_2504_10710_gb300 import glls, inputs
+        __graft_entry__.build()
+        print(json.dumps(serving_run(glls, inputs)))
+        return
     rank, world = dist_init(args.gpus)
     if args.impl == "reference":
         if rank != 0:

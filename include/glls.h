@@ -124,6 +124,9 @@ typedef struct {
     double solve_ms;
     int status;
     long long kernels;   /* kernels this solve launched (graph kernel nodes x loop trips) */
+    double queue_ms;     /* served requests: submission to the start of their work (else 0) */
+    int setup_kind;      /* served requests: 0 resident instance, 1 mesh set up for it, 2 clone made for it */
+    int group;           /* served requests: requests solved together with it, itself included (else 0) */
 } glls_stats;
 
 typedef struct {
@@ -137,6 +140,9 @@ typedef struct {
     long long coarse_dense_unknowns;   /* size of the densely inverted system */
     size_t instance_bytes;      /* device memory this instance owns alone: what a clone adds */
     int nrhs;                   /* right-hand sides solved together (glls_problem_create_nrhs) */
+    double setup_phase_ms[6];   /* set-up wall time by phase: coarse-level coordinates, geometry
+                                   factors, line data (bands, line blocks), transfers, coarsest-level
+                                   factorisation (all host), device upload and allocation */
 } glls_info;
 
 /* Reference GLL(p) nodes and weights (Def. 2.1); xi, rho: host arrays of p+1. */
@@ -166,6 +172,9 @@ glls_status glls_problem_create_nrhs(const glls_mesh_desc* desc, int nrhs, glls_
  * solved together as clones in one glls_solve_batch.  Autotuned tiles are
  * copied.  Synchronous. */
 glls_status glls_problem_clone(const glls_problem* prob, glls_problem** out);
+/* As glls_problem_clone, with nrhs right-hand sides solved together (as
+ * glls_problem_create_nrhs) whatever the count of prob. */
+glls_status glls_problem_clone_nrhs(const glls_problem* prob, int nrhs, glls_problem** out);
 void glls_problem_destroy(glls_problem* prob);
 /* Failure injection for tests (no counterpart in the paper): after n more
  * device allocations by the library, further ones fail as if the device were
@@ -196,6 +205,23 @@ glls_status glls_solve(glls_problem* prob, const glls_solve_opts* opts, double* 
  * first failure status (per-problem status in stats[i].status). */
 glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve_opts* opts, double* const* u,
                              int on_device, void* stream, glls_stats* stats);
+/* The same batched solve with work-list kernels (the batched form of the
+ * solve loop): the problems are grouped by their chain of orders, and inside
+ * a group every step of the outer iteration (each apply, line solve,
+ * transfer, coarsest-solve step and outer-Krylov kernel) is one launch over
+ * a work list whose items are (problem, level, tile range): item j carries
+ * problem j's level data and vectors and owns a contiguous range of the
+ * launch's CTAs.  Each group is one branch of one graph with its own
+ * device-side loop that runs while any of its problems is active; a
+ * problem that has stopped keeps its iterate.  The launch covers every
+ * problem whatever its element count, so a step costs one launch per group
+ * instead of one per problem.  Requirements: 2-D, one right-hand side per
+ * problem, the GLL line-block smoother, orders up to 16, FCG or PCG
+ * (GLLS_ERR_INVALID otherwise).  The plan (item arrays and graph) is cached
+ * per problem list and options and released with its problems.  stats[0].kernels
+ * holds the kernels of the whole launch. */
+glls_status glls_solve_batch_worklist(glls_problem* const* probs, int n, const glls_solve_opts* opts,
+                                      double* const* u, int on_device, void* stream, glls_stats* stats);
 
 /* Autotuner: for every level >= 1, precision and direction, time the line
  * solve with 2, 4, 8 and (FP32 only) 16 lines per CTA on the problem's own
@@ -228,6 +254,7 @@ typedef struct {
     int cached_problems;         /* resident meshes */
     int cached_instances;        /* their instances (set-up problems and clones) */
     unsigned long long clones;   /* clones created so far */
+    unsigned long long grouped;  /* requests served by multi-right-hand-side solves */
 } glls_server_info;
 
 glls_status glls_server_create(int device, size_t hbm_budget_bytes, int slots, glls_server** out);
@@ -243,16 +270,29 @@ glls_status glls_submit(glls_server* server, const glls_mesh_desc* mesh, const d
  * first request on it runs.  Registered meshes stay known until the server
  * is destroyed (their device data is still subject to eviction). */
 glls_status glls_server_register(glls_server* server, const glls_mesh_desc* mesh, unsigned long long* mesh_id);
-/* As glls_submit, on a registered mesh: f and g (N host values each; g may
- * be NULL) are copied, u is written when the request completes. */
+/* As glls_submit, on a registered mesh, without copying: f and g (N host
+ * values each; g may be NULL) are read when the request runs, so they stay
+ * valid and unchanged, like u, until its ticket is polled to completion or
+ * cancelled. */
 glls_status glls_submit_mesh(glls_server* server, unsigned long long mesh_id, const double* f, const double* g,
                              const glls_solve_opts* opts, double* u, unsigned long long* ticket);
 /* GLLS_NOT_READY while queued or running (wait = 0), else the request's
- * status with stats filled (queue + solve time in stats->solve_ms, set-up of a
- * newly created problem in stats->setup_ms); wait = 1 blocks until done.  A
+ * status with stats filled: stats->solve_ms is the request's latency
+ * (submission to result in u: queue, any set-up and the solve),
+ * stats->queue_ms the part before a worker took it, stats->setup_ms and
+ * stats->setup_kind the set-up or clone done for it; wait = 1 blocks until done.  A
  * finished ticket is released by the first poll that returns its result. */
 glls_status glls_poll(glls_server* server, unsigned long long ticket, int wait, glls_stats* stats);
 glls_status glls_server_info_get(glls_server* server, glls_server_info* out);
+/* Grouping (default 1: off).  With max_group > 1 a worker that takes a
+ * request for a resident mesh also takes the queued requests of that mesh
+ * with the same Dirichlet data pointer and options, up to the largest power
+ * of two <= max_group available, and solves them together on an instance
+ * with that many right-hand sides (glls_problem_clone_nrhs), so the mesh
+ * data is read once per kernel launch for all of them.  Only requests with
+ * use_graph = 2 and FCG or PCG are grouped.  Each request still gets its own
+ * solution, status and stats (stats->group = the group size). */
+glls_status glls_server_set_max_group(glls_server* server, int max_group);
 /* Removes a request that is still queued: GLLS_OK (its ticket is released and
  * u is never written), GLLS_NOT_READY if it is already running, or
  * GLLS_ERR_INVALID for an unknown or released ticket. */

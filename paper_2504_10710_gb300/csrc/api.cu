@@ -10,6 +10,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -123,6 +124,7 @@ struct glls_problem {
     std::vector<void*> allocs;
     size_t bytes = 0;
     double setup_ms = 0.0;
+    double setup_phase_ms[6] = {0, 0, 0, 0, 0, 0};   // see glls_info
     cudaStream_t capture_stream = nullptr, capture_stream2 = nullptr;
     // cached graph of one outer iteration (host-driven loop) and of the whole
     // solve (device-driven loop)
@@ -641,8 +643,21 @@ struct BatchEntry {
 std::mutex g_batch_mutex;
 std::vector<BatchEntry> g_batches;   // small LRU, newest last
 
+struct WlPlan;
+void destroy_plan(WlPlan* W);
+bool plan_uses(const WlPlan* W, const glls_problem* P);
+extern std::vector<WlPlan*> g_wplans;
+
 void forget_batches_of(glls_problem* P) {
     std::lock_guard<std::mutex> lock(g_batch_mutex);
+    for (size_t i = 0; i < g_wplans.size();) {
+        if (plan_uses(g_wplans[i], P)) {
+            destroy_plan(g_wplans[i]);
+            g_wplans.erase(g_wplans.begin() + i);
+        } else {
+            ++i;
+        }
+    }
     for (size_t i = 0; i < g_batches.size();) {
         bool hit = false;
         for (auto* q : g_batches[i].probs) hit = hit || q == P;
@@ -825,6 +840,550 @@ glls_status gmres_solve(glls_problem* P, const glls_solve_opts* o, cudaStream_t 
 // ===========================================================================
 // C ABI
 // ===========================================================================
+// ---------------------------------------------------------------------------
+// Work-list batched solve.  The problems are grouped by their order chain;
+// inside a group every step of the solve loop (each apply, line solve,
+// transfer, coarsest-solve step and outer-Krylov kernel of Algorithm 2 and
+// the flexible CG iteration) is ONE launch over the work list of all the
+// group's problems: item j of a launch carries problem j's level data and
+// vectors and owns a contiguous range of the launch's CTAs.  Each group is
+// one branch of one graph, with its own device-side loop that runs while any
+// of its problems is active (stopped problems are frozen as stopped
+// right-hand sides are).
+// ---------------------------------------------------------------------------
+namespace {
+
+enum WlKind { WL_APPLY = 0, WL_LINE, WL_T2, WL_BCR_F, WL_COARSE, WL_BCR_B, WL_FCG };
+
+struct WlRecord {
+    int kind = 0;
+    bool dbl = false;                  // FP64 items
+    int p = 0, cv = 1, wb = 0, ty = 0, l = 0, step = 0;
+    bool mask = false, dot = false, add = false;
+    int blocks = 0, threads = 256, nitems = 0;
+    size_t smem = 0;
+    std::vector<unsigned char> items;  // host copy of the item array
+    std::vector<int> start{0};         // CTA offsets, nitems + 1
+    std::vector<int> owner;            // the group position of each item's problem
+    size_t item_bytes = 0, done_at = 0;   // item size and offset of its stop-flag pointer
+    size_t off_items = 0, off_start = 0;
+
+    template <class Item>
+    void put(const Item& it, int nblocks, int who) {
+        const unsigned char* b = reinterpret_cast<const unsigned char*>(&it);
+        items.insert(items.end(), b, b + sizeof(Item));
+        start.push_back(start.back() + nblocks);
+        owner.push_back(who);
+        item_bytes = sizeof(Item);
+        done_at = offsetof(Item, done);
+        ++nitems;
+        blocks = start.back();
+    }
+};
+
+struct WlGroup {
+    std::vector<glls_problem*> probs;
+    std::vector<int> index;            // position of each problem in the batch
+    std::vector<WlRecord> body;        // one outer iteration
+    size_t off_S = 0;                  // [n][S_COUNT] scalars in the plan's block
+    cudaStream_t s1 = nullptr, s2 = nullptr;
+    long long kernels_iter = 0;        // kernel nodes of one pass of the group's loop
+};
+
+struct WlPlan {
+    std::vector<glls_problem*> probs;
+    glls_solve_opts key{};
+    std::vector<WlGroup> groups;
+    void* dev = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t master = nullptr;
+    long long kernels_fixed = 0;
+};
+
+std::vector<WlPlan*> g_wplans;   // guarded by g_batch_mutex (newest last)
+
+bool plan_uses(const WlPlan* W, const glls_problem* P) {
+    for (const glls_problem* q : W->probs)
+        if (q == P) return true;
+    return false;
+}
+
+void destroy_plan(WlPlan* W) {
+    if (W->exec) cudaGraphExecDestroy(W->exec);
+    for (auto& g : W->groups) {
+        if (g.s1) cudaStreamDestroy(g.s1);
+        if (g.s2) cudaStreamDestroy(g.s2);
+    }
+    if (W->master) cudaStreamDestroy(W->master);
+    if (W->dev) cudaFree(W->dev);
+    delete W;
+}
+
+// Builds the records of one outer iteration of a group in precision T (the
+// gamma-cycle) around the FP64 outer kernels; returns "" or why the group
+// cannot run as a work list.
+template <typename T>
+struct WlBuilder {
+    WlGroup& G;
+    const glls_solve_opts& o;
+    bool mixed;
+
+    T* rv(glls_problem* P, int l) {
+        auto& Ls = levels_of<T>(P);
+        if (l == (int)Ls.size() - 1) return mixed ? (T*)(void*)P->r32 : (T*)(void*)P->rk;
+        return Ls[l].r;
+    }
+    T* xv(glls_problem* P, int l) {
+        auto& Ls = levels_of<T>(P);
+        if (l == (int)Ls.size() - 1) return mixed ? (T*)(void*)P->z32 : (T*)(void*)P->zk;
+        return Ls[l].x;
+    }
+
+    std::string apply(int l) {
+        WlRecord r;
+        r.kind = WL_APPLY;
+        r.dbl = sizeof(T) == 8;
+        r.mask = true;
+        for (size_t j = 0; j < G.probs.size(); ++j) {
+            glls_problem* P = G.probs[j];
+            const DevLevel<T>& L = levels_of<T>(P)[l].dev;
+            r.p = L.p;
+            ApplyItem<T> it{L, xv(P, l), levels_of<T>(P)[l].y, nullptr, nullptr};
+            r.put(it, apply_list_blocks(L.p, L.E), (int)j);
+        }
+        G.body.push_back(std::move(r));
+        return "";
+    }
+
+    std::string line(int l, int s, int mode) {
+        WlRecord r;
+        r.kind = WL_LINE;
+        r.dbl = sizeof(T) == 8;
+        r.threads = 32;
+        std::vector<size_t> sm0, sm1;
+        std::vector<unsigned char> buf(line_block_item_bytes<T>());
+        r.item_bytes = buf.size();
+        r.done_at = line_block_item_done_offset<T>();
+        for (size_t j = 0; j < G.probs.size(); ++j) {
+            glls_problem* P = G.probs[j];
+            auto& Ls = levels_of<T>(P);
+            int blocks = 0, threads = 0, cv = 1;
+            size_t smem[2] = {0, 0};
+            const int k = line_block_list_item<T>(Ls[l].dev, s, mode, nullptr, rv(P, l), mode == 1 ? Ls[l].y : nullptr,
+                                                  xv(P, l), (T)o.alpha, buf.data(), &blocks, &threads, smem, &cv);
+            if (k < 0) return "a level's grid lines are outside the line-block kernel's range";
+            if (k == 0) continue;
+            r.p = Ls[l].dev.p;
+            r.items.insert(r.items.end(), buf.begin(), buf.end());
+            r.start.push_back(r.start.back() + blocks);
+            r.owner.push_back((int)j);
+            ++r.nitems;
+            r.blocks = r.start.back();
+            r.threads = std::max(r.threads, threads);
+            r.cv = std::max(r.cv, cv);
+            sm0.push_back(smem[0]);
+            sm1.push_back(smem[1]);
+        }
+        const bool spec = line_block_list_specialised(r.p, r.cv);
+        for (size_t i = 0; i < sm0.size(); ++i) r.smem = std::max(r.smem, spec ? sm0[i] : sm1[i]);
+        if (r.nitems) G.body.push_back(std::move(r));
+        return "";
+    }
+
+    std::string smooth(int l, int s, bool zero) {
+        if (zero) return line(l, s, 3);
+        std::string e = apply(l);
+        return e.empty() ? line(l, s, 1) : e;
+    }
+
+    // restriction (prolong = false: rc = R (r - y)) or x += P e, clearing y
+    std::string transfer(int l, bool prolong) {
+        WlRecord r;
+        r.kind = WL_T2;
+        r.dbl = sizeof(T) == 8;
+        r.add = prolong;
+        r.mask = !prolong;
+        for (size_t j = 0; j < G.probs.size(); ++j) {
+            glls_problem* P = G.probs[j];
+            auto& Ls = levels_of<T>(P);
+            const DevLevel<T>& F = Ls[l].dev;
+            const DevLevel<T>& C = Ls[l - 1].dev;
+            Transfer2Item<T> it{};
+            int nout[3];
+            if (!prolong) {
+                it.M0 = F.R[0];
+                it.M1 = F.R[1];
+                it.nin = make_int3(F.n[0], F.n[1], F.n[2]);
+                nout[0] = C.n[0]; nout[1] = C.n[1]; nout[2] = F.n[2];
+                it.in = rv(P, l);
+                it.in2 = Ls[l].y;
+                it.out = rv(P, l - 1);
+                it.clear = nullptr;
+            } else {
+                it.M0 = F.P[0];
+                it.M1 = F.P[1];
+                it.nin = make_int3(C.n[0], C.n[1], C.n[2]);
+                nout[0] = F.n[0]; nout[1] = F.n[1]; nout[2] = C.n[2];
+                it.in = xv(P, l - 1);
+                it.in2 = nullptr;
+                it.out = xv(P, l);
+                it.clear = Ls[l].y;
+            }
+            it.nout = make_int3(nout[0], nout[1], nout[2]);
+            int gx = 0, gy = 0, wb = 0, ty = 0;
+            size_t smem = 0;
+            if (!transfer2_list_config<T>(it.M0, it.M1, nout, &gx, &gy, &wb, &ty, &smem))
+                return "a transfer is outside the fused transfer kernel's range";
+            it.gx = gx;
+            it.gy = gy;
+            r.wb = std::max(r.wb, wb);
+            r.ty = ty;
+            r.smem = std::max(r.smem, smem);
+            r.put(it, gx * gy * nout[2], (int)j);
+        }
+        G.body.push_back(std::move(r));
+        return "";
+    }
+
+    std::string coarse() {
+        int kmax = 0;
+        for (glls_problem* P : G.probs) kmax = std::max(kmax, coarse_of<T>(P).cr_levels);
+        for (int l = 0; l < kmax; ++l) {
+            WlRecord r;
+            r.kind = WL_BCR_F;
+            r.dbl = sizeof(T) == 8;
+            r.l = l;
+            for (size_t j = 0; j < G.probs.size(); ++j) {
+                glls_problem* P = G.probs[j];
+                const DevCoarse<T>& C = coarse_of<T>(P);
+                if (C.cr_levels <= l) continue;
+                const int a = C.nb >> l, nk = a / 2, ne = (a + 1) / 2;
+                const int rows = (C.m + 7) / 8;
+                BcrItem<T> it{C.fh[l], C.nb, C.m, C.ldm, C.index, rv(P, 0), levels_of<T>(P)[0].t1,
+                              l == 0 ? nk + ne : nk, rows};
+                r.smem = std::max(r.smem, 2 * sizeof(T) * (size_t)C.m);
+                r.put(it, it.gx * rows, (int)j);
+            }
+            if (r.nitems) G.body.push_back(std::move(r));
+        }
+        {
+            WlRecord r;
+            r.kind = WL_COARSE;
+            r.dbl = sizeof(T) == 8;
+            for (size_t j = 0; j < G.probs.size(); ++j) {
+                glls_problem* P = G.probs[j];
+                const DevCoarse<T>& C = coarse_of<T>(P);
+                const int k = C.cr_levels;
+                CoarseItem<T> it{C.nr, C.ld, C.index, C.inv, k > 0 ? (const T*)levels_of<T>(P)[0].t1 : rv(P, 0),
+                                 k > 0 ? nullptr : C.index, C.m, 1 << k, xv(P, 0)};
+                long long blocks = (C.nr + 7) / 8;
+                if (blocks > 2 * 152) blocks = 2 * 152;
+                r.smem = std::max(r.smem, sizeof(T) * (size_t)C.ld);
+                r.put(it, (int)blocks, (int)j);
+            }
+            if (r.smem > 200 * 1024) return "a coarsest dense system is too large for the work-list coarse kernel";
+            G.body.push_back(std::move(r));
+        }
+        for (int l = kmax - 1; l >= 0; --l) {
+            WlRecord r;
+            r.kind = WL_BCR_B;
+            r.dbl = sizeof(T) == 8;
+            r.l = l;
+            for (size_t j = 0; j < G.probs.size(); ++j) {
+                glls_problem* P = G.probs[j];
+                const DevCoarse<T>& C = coarse_of<T>(P);
+                if (C.cr_levels <= l) continue;
+                const int rows = (C.m + 7) / 8;
+                BcrItem<T> it{C.agk[l], C.nb, C.m, C.ldm, C.index, levels_of<T>(P)[0].t1, xv(P, 0),
+                              ((C.nb >> l) + 1) / 2, rows};
+                r.smem = std::max(r.smem, 3 * sizeof(T) * (size_t)C.m);
+                r.put(it, it.gx * rows, (int)j);
+            }
+            if (r.nitems) G.body.push_back(std::move(r));
+        }
+        return "";
+    }
+
+    // Algorithm 2 on level l (as cycle<T>)
+    std::string cycle(int l) {
+        if (l == 0) return coarse();
+        const int d = 2;
+        bool zero = true;
+        std::string e;
+        for (int s = 0; s < d && e.empty(); ++s)
+            for (int k = 0; k < o.m && e.empty(); ++k) {
+                e = smooth(l, s, zero);
+                zero = false;
+            }
+        for (int g = 0; g < o.gamma && e.empty(); ++g) {
+            e = apply(l);
+            if (e.empty()) e = transfer(l, false);
+            if (e.empty()) e = cycle(l - 1);
+            if (e.empty()) e = transfer(l, true);
+            for (int s = d - 1; s >= 0 && e.empty(); --s)
+                for (int k = 0; k < o.m && e.empty(); ++k) e = smooth(l, s, false);
+        }
+        return e;
+    }
+};
+
+// The outer iteration of a group (as outer_iteration): the gamma-cycle, the
+// dots, the direction, the FP64 apply with its p.q partials, the update.
+std::string build_group(WlGroup& G, const glls_solve_opts& o) {
+    const bool mixed = o.precision == GLLS_PREC_MIXED;
+    const int L = (int)G.probs[0]->L64.size() - 1;
+    std::string e;
+    if (mixed) {
+        WlBuilder<float> b{G, o, true};
+        e = b.cycle(L);
+    } else {
+        WlBuilder<double> b{G, o, false};
+        e = b.cycle(L);
+    }
+    if (!e.empty()) return e;
+    std::vector<FcgItem> items;
+    WlRecord ap;
+    ap.kind = WL_APPLY;
+    ap.dbl = true;
+    ap.mask = true;
+    ap.dot = true;
+    for (size_t j = 0; j < G.probs.size(); ++j) {
+        glls_problem* P = G.probs[j];
+        const DevLevel<double>& F = P->L64[L].dev;
+        double* prz = P->part;
+        double* pzq = prz + kDotBlocks;
+        double* prr = pzq + kDotBlocks;
+        double* ppq = prr + kDotBlocks;
+        FcgItem it{P->xk, P->rk, P->pk, P->qk, P->zk, mixed ? P->r32 : nullptr, mixed ? P->z32 : nullptr,
+                   P->N, prz, pzq, prr, ppq, apply_list_blocks(F.p, F.E), nullptr, P->ticket};
+        items.push_back(it);
+        ap.p = F.p;
+        ApplyItem<double> ai{F, P->pk, P->qk, ppq, nullptr};
+        ap.put(ai, apply_list_blocks(F.p, F.E), (int)j);
+    }
+    for (int step : {0, 1, -1, 2}) {
+        if (step == -1) {
+            G.body.push_back(ap);
+            continue;
+        }
+        WlRecord r;
+        r.kind = WL_FCG;
+        r.step = step;
+        r.dbl = true;
+        for (size_t j = 0; j < items.size(); ++j) {
+            const FcgItem& it = items[j];
+            const unsigned char* b = reinterpret_cast<const unsigned char*>(&it);
+            r.items.insert(r.items.end(), b, b + sizeof(FcgItem));
+            r.start.push_back(0);
+            r.owner.push_back((int)j);
+            ++r.nitems;
+        }
+        G.body.push_back(std::move(r));
+    }
+    return "";
+}
+
+// Problem j of a group uses S = (plan block) + off_S + j S_COUNT: the FCG
+// items get that pointer, every other item a pointer to its S_DONE flag,
+// once the block is allocated.
+void bind_scalars(WlGroup& G, unsigned char* base) {
+    double* S = reinterpret_cast<double*>(base + G.off_S);
+    for (auto& r : G.body)
+        for (int i = 0; i < r.nitems; ++i) {
+            double* Sj = S + (size_t)r.owner[i] * S_COUNT;
+            if (r.kind == WL_FCG) {
+                FcgItem it;
+                std::memcpy(&it, r.items.data() + sizeof(FcgItem) * i, sizeof(FcgItem));
+                it.S = Sj;
+                std::memcpy(r.items.data() + sizeof(FcgItem) * i, &it, sizeof(FcgItem));
+            } else {
+                const double* done = Sj + S_DONE;
+                std::memcpy(r.items.data() + r.item_bytes * i + r.done_at, &done, sizeof(done));
+            }
+        }
+}
+
+cudaError_t replay(const WlRecord& r, const unsigned char* base, int flexible, cudaStream_t st) {
+    const void* items = base + r.off_items;
+    const int* start = reinterpret_cast<const int*>(base + r.off_start);
+    bool ok = true;
+    switch (r.kind) {
+        case WL_APPLY:
+            ok = r.dbl ? launch_apply_list<double>(r.p, (const ApplyItem<double>*)items, start, r.nitems, r.blocks,
+                                                   r.mask, r.dot, st)
+                       : launch_apply_list<float>(r.p, (const ApplyItem<float>*)items, start, r.nitems, r.blocks,
+                                                  r.mask, r.dot, st);
+            break;
+        case WL_LINE:
+            ok = r.dbl ? launch_line_block_list<double>(r.p, r.cv, items, start, r.nitems, r.blocks, r.threads, r.smem,
+                                                        st)
+                       : launch_line_block_list<float>(r.p, r.cv, items, start, r.nitems, r.blocks, r.threads, r.smem,
+                                                       st);
+            break;
+        case WL_T2:
+            ok = r.dbl ? launch_transfer2_list<double>(r.wb, r.ty, (const Transfer2Item<double>*)items, start,
+                                                       r.nitems, r.blocks, r.smem, r.add, r.mask, st)
+                       : launch_transfer2_list<float>(r.wb, r.ty, (const Transfer2Item<float>*)items, start, r.nitems,
+                                                      r.blocks, r.smem, r.add, r.mask, st);
+            break;
+        case WL_BCR_F:
+        case WL_BCR_B:
+            if (r.dbl)
+                launch_bcr_list<double>(r.kind == WL_BCR_F, r.l, (const BcrItem<double>*)items, start, r.nitems,
+                                        r.blocks, r.smem, st);
+            else
+                launch_bcr_list<float>(r.kind == WL_BCR_F, r.l, (const BcrItem<float>*)items, start, r.nitems,
+                                       r.blocks, r.smem, st);
+            break;
+        case WL_COARSE:
+            if (r.dbl)
+                launch_coarse_list<double>((const CoarseItem<double>*)items, start, r.nitems, r.blocks, r.smem, st);
+            else
+                launch_coarse_list<float>((const CoarseItem<float>*)items, start, r.nitems, r.blocks, r.smem, st);
+            break;
+        default:
+            launch_fcg_list(r.step, (const FcgItem*)items, r.nitems, flexible, st);
+    }
+    if (!ok) return cudaErrorInvalidConfiguration;
+    return cudaGetLastError();
+}
+
+// Captures the whole batched solve of W (all groups as graph branches).
+cudaError_t capture_plan(WlPlan* W, const glls_solve_opts* o) {
+    unsigned char* base = static_cast<unsigned char*>(W->dev);
+    const int flexible = o->krylov == GLLS_KRYLOV_FCG ? 1 : 0;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins(W->groups.size(), nullptr);
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (size_t i = 0; i < joins.size() && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(W->master, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, W->master);
+    for (size_t gi = 0; gi < W->groups.size() && e == cudaSuccess; ++gi) {
+        WlGroup& G = W->groups[gi];
+        double* S = reinterpret_cast<double*>(base + G.off_S);
+        const int n = (int)G.probs.size();
+        e = cudaStreamWaitEvent(G.s1, fork, 0);
+        for (int j = 0; j < n && e == cudaSuccess; ++j) {
+            glls_problem* P = G.probs[j];
+            solve_prologue(P, o, G.s1);
+            e = cudaMemcpyAsync(S + (size_t)j * S_COUNT, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToDevice,
+                                G.s1);
+        }
+        cudaStreamCaptureStatus stt;
+        cudaGraph_t capg = nullptr;
+        cudaGraphConditionalHandle handle = 0;
+        if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(G.s1, &stt, nullptr, &capg, nullptr, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, capg, 0, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) break;
+        launch_solve_init(S, handle, o->tol, o->max_iter, G.s1, n);
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(G.s1, &stt, nullptr, &capg, &deps, nullptr, &ndeps);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, capg, deps, nullptr, ndeps, &cp);
+        if (e == cudaSuccess)
+            e = cudaStreamUpdateCaptureDependencies(G.s1, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(G.s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (const WlRecord& r : G.body)
+                    if (e == cudaSuccess) e = replay(r, base, flexible, G.s2);
+                launch_solve_cond(S, handle, o->max_iter, G.s2, n);
+                cudaError_t e2 = cudaStreamEndCapture(G.s2, &body);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) G.kernels_iter = count_kernel_nodes(body);
+            }
+        }
+        for (int j = 0; j < n && e == cudaSuccess; ++j) {   // u = w + v; the scalars back to the problem
+            glls_problem* P = G.probs[j];
+            e = cudaMemcpyAsync(P->yk, P->xk, sizeof(double) * P->N, cudaMemcpyDeviceToDevice, G.s1);
+            launch_axpy(P->yk, P->v, 1.0, P->N, G.s1);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(P->S, S + (size_t)j * S_COUNT, sizeof(double) * S_COUNT,
+                                    cudaMemcpyDeviceToDevice, G.s1);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(joins[gi], G.s1);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(W->master, joins[gi], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(W->master, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) W->kernels_fixed = count_kernel_nodes(graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&W->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (fork) cudaEventDestroy(fork);
+    for (auto ev : joins)
+        if (ev) cudaEventDestroy(ev);
+    return e;
+}
+
+glls_status make_plan(glls_problem* const* probs, int n, const glls_solve_opts* o, WlPlan** out) {
+    std::unique_ptr<WlPlan, void (*)(WlPlan*)> W(new WlPlan(), destroy_plan);
+    W->probs.assign(probs, probs + n);
+    W->key = *o;
+    for (int i = 0; i < n; ++i) {
+        glls_problem* P = probs[i];
+        if (P->dim != 2) return fail(GLLS_ERR_INVALID, "work-list batch: 2-D problems only");
+        if (P->smoother != GLLS_SMOOTHER_GLL) return fail(GLLS_ERR_INVALID, "work-list batch: GLL line-block smoother only");
+        for (size_t l = 0; l < P->L64.size(); ++l) {
+            const DevLevel<double>& L = P->L64[l].dev;
+            if (L.p > 16 || L.N > (1LL << 31) - 1 || L.ne[0] >= 1024 || L.ne[1] >= 1024)
+                return fail(GLLS_ERR_INVALID, "work-list batch: a level outside the specialised apply's range");
+            if (l > 0 && (!L.blk[0] || !L.blk[1]))
+                return fail(GLLS_ERR_INVALID, "work-list batch: a level without line blocks");
+        }
+        size_t gi = 0;
+        while (gi < W->groups.size() && W->groups[gi].probs[0]->orders != P->orders) ++gi;
+        if (gi == W->groups.size()) W->groups.emplace_back();
+        W->groups[gi].probs.push_back(P);
+        W->groups[gi].index.push_back(i);
+    }
+    // records, then one device block for every item array, start array and
+    // group scalar array
+    size_t bytes = 0;
+    auto take = [&](size_t b) {
+        const size_t at = bytes;
+        bytes += (b + 255) / 256 * 256;
+        return at;
+    };
+    for (auto& G : W->groups) {
+        std::string err = build_group(G, *o);
+        if (!err.empty()) return fail(GLLS_ERR_INVALID, "work-list batch: " + err);
+        G.off_S = take(sizeof(double) * S_COUNT * G.probs.size());
+        for (auto& r : G.body) {
+            r.off_items = take(r.items.size());
+            r.off_start = take(sizeof(int) * r.start.size());
+        }
+    }
+    CK(dev_malloc(&W->dev, bytes));
+    std::vector<unsigned char> host(bytes, 0);
+    for (auto& G : W->groups) {
+        bind_scalars(G, static_cast<unsigned char*>(W->dev));
+        for (auto& r : G.body) {
+            std::memcpy(host.data() + r.off_items, r.items.data(), r.items.size());
+            std::memcpy(host.data() + r.off_start, r.start.data(), sizeof(int) * r.start.size());
+        }
+    }
+    CK(cudaMemcpy(W->dev, host.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaStreamCreateWithFlags(&W->master, cudaStreamNonBlocking));
+    for (auto& G : W->groups) {
+        CK(cudaStreamCreateWithFlags(&G.s1, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&G.s2, cudaStreamNonBlocking));
+    }
+    CK(capture_plan(W.get(), o));
+    *out = W.release();
+    return GLLS_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* glls_last_error(void) { return g_last_error.c_str(); }
@@ -885,7 +1444,8 @@ static glls_status problem_create(const glls_mesh_desc* desc, int nrhs, glls_pro
     for (int a = 0; a < 3; ++a) P->nelem[a] = a < desc->dim ? desc->nelem[a] : 1;
     std::vector<LevelHost> H;
     std::string err = build_levels(desc->dim, P->nelem, desc->order, desc->coords, desc->smoother,
-                                   desc->restriction, H);
+                                   desc->restriction, H, P->setup_phase_ms);
+    auto t_coarse = std::chrono::steady_clock::now();
     if (!err.empty()) return fail(GLLS_ERR_BREAKDOWN, err);
     for (auto& h : H) {
         if (h.N > 2147483647LL || h.E * h.nloc * h.ncomp > 2147483647LL)
@@ -911,6 +1471,8 @@ static glls_status problem_create(const glls_mesh_desc* desc, int nrhs, glls_pro
                         : GLLS_ERR_BREAKDOWN,
                     err);
     if (C.cr_levels > kMaxCrLevels) return fail(GLLS_ERR_INVALID, "too many block-CR levels");
+    auto t_upload = std::chrono::steady_clock::now();
+    P->setup_phase_ms[4] = std::chrono::duration<double, std::milli>(t_upload - t_coarse).count();
 
     std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
     glls_status st = upload_levels<double>(P.get(), H, P->L64);
@@ -930,18 +1492,20 @@ static glls_status problem_create(const glls_mesh_desc* desc, int nrhs, glls_pro
     if (st != GLLS_OK) return st;
     CK(cudaDeviceSynchronize());
     P->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    P->setup_phase_ms[5] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_upload).count();
     *out = P.release();
     return GLLS_OK;
 }
 
-static glls_status problem_clone(const glls_problem* src, glls_problem** out) {
+static glls_status problem_clone(const glls_problem* src, int nrhs, glls_problem** out) {
     if (!src || !out) return fail(GLLS_ERR_INVALID, "null argument");
     *out = nullptr;
+    if (nrhs < 1 || nrhs > 4096) return fail(GLLS_ERR_INVALID, "nrhs must be in 1..4096");
     DeviceScope scope(src->device);
     CK(scope.err);
     ProblemPtr P(new glls_problem());
     std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
-    P->nrhs = src->nrhs;
+    P->nrhs = nrhs;
     P->shared = src->shared;
     P->device = src->device;
     P->dim = src->dim;
@@ -987,8 +1551,12 @@ glls_status glls_problem_create_nrhs(const glls_mesh_desc* desc, int nrhs, glls_
 }
 
 glls_status glls_problem_clone(const glls_problem* src, glls_problem** out) {
+    return glls_problem_clone_nrhs(src, src ? src->nrhs : 1, out);
+}
+
+glls_status glls_problem_clone_nrhs(const glls_problem* src, int nrhs, glls_problem** out) {
     try {
-        return problem_clone(src, out);
+        return problem_clone(src, nrhs, out);
     } catch (const std::bad_alloc&) {
         return fail(GLLS_ERR_OOM, "host allocation failed during clone");
     }
@@ -1026,6 +1594,7 @@ glls_status glls_problem_info(const glls_problem* P, glls_info* out) {
     out->device_bytes = P->bytes + (P->shared ? P->shared->bytes : 0);
     out->instance_bytes = P->bytes;
     out->nrhs = P->nrhs;
+    for (int k = 0; k < 6; ++k) out->setup_phase_ms[k] = P->setup_phase_ms[k];
     return GLLS_OK;
 }
 
@@ -1266,6 +1835,7 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
 glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve_opts* o, double* const* u,
                              int on_device, void* stream, glls_stats* stats) {
     if (!probs || n < 1 || !u) return fail(GLLS_ERR_INVALID, "glls_solve_batch: need n >= 1 problems and outputs");
+    if (stats) std::memset(stats, 0, sizeof(*stats) * n);
     glls_status s0 = check_opts(o);
     if (s0 != GLLS_OK) return s0;
     const int dev = probs[0] ? probs[0]->device : 0;
@@ -1354,6 +1924,91 @@ glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve
     for (int i = 0; i < n; ++i) {
         glls_status r = solve_result(probs[i], probs[i]->hostS, stats ? &stats[i] : nullptr, t_ms);
         if (r != GLLS_OK && worst == GLLS_OK) worst = r;
+    }
+    if (worst == GLLS_ERR_BREAKDOWN) fail(worst, "breakdown in at least one problem of the batch");
+    if (worst == GLLS_ERR_NOT_CONVERGED) fail(worst, "at least one problem of the batch reached max_iter");
+    return worst;
+}
+
+glls_status glls_solve_batch_worklist(glls_problem* const* probs, int n, const glls_solve_opts* o, double* const* u,
+                                      int on_device, void* stream, glls_stats* stats) {
+    if (!probs || n < 1 || !u) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: need n >= 1 problems and outputs");
+    if (stats) std::memset(stats, 0, sizeof(*stats) * n);
+    glls_status s0 = check_opts(o);
+    if (s0 != GLLS_OK) return s0;
+    if (o->krylov == GLLS_KRYLOV_GMRES) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: FCG or PCG only");
+    const int dev = probs[0] ? probs[0]->device : 0;
+    for (int i = 0; i < n; ++i) {
+        if (!probs[i] || !u[i]) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: null problem or output");
+        if (probs[i]->device != dev) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: problems on different devices");
+        if (!probs[i]->has_rhs) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: right-hand side not set");
+        if (probs[i]->nrhs != 1) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: one right-hand side per problem");
+        for (int j = 0; j < i; ++j)
+            if (probs[j] == probs[i]) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: a problem appears twice");
+    }
+    DeviceScope scope(dev);
+    CK(scope.err);
+    cudaStream_t st = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < n; ++i)
+        if (!probs[i]->has_dirichlet) CK(cudaMemsetAsync(probs[i]->g, 0, sizeof(double) * probs[i]->N, st));
+    cudaGraphExec_t exec = nullptr;
+    long long kfix = 0;
+    std::vector<std::pair<std::vector<int>, long long>> loops;   // problems of a group, kernels per pass
+    {
+        std::lock_guard<std::recursive_mutex> dev_lock(g_device_mutex);
+        std::lock_guard<std::mutex> lock(g_batch_mutex);
+        std::vector<glls_problem*> key(probs, probs + n);
+        for (size_t i = 0; i < g_wplans.size(); ++i)
+            if (g_wplans[i]->probs == key && same_solve_key(g_wplans[i]->key, *o)) {
+                WlPlan* hit = g_wplans[i];
+                g_wplans.erase(g_wplans.begin() + i);
+                g_wplans.push_back(hit);
+                exec = hit->exec;
+                kfix = hit->kernels_fixed;
+                for (const auto& G : hit->groups) loops.emplace_back(G.index, G.kernels_iter);
+                break;
+            }
+        if (!exec) {
+            WlPlan* W = nullptr;
+            glls_status ps = make_plan(probs, n, o, &W);
+            if (ps != GLLS_OK) return ps;
+            g_wplans.push_back(W);
+            if (g_wplans.size() > 4) {
+                destroy_plan(g_wplans.front());
+                g_wplans.erase(g_wplans.begin());
+            }
+            exec = W->exec;
+            kfix = W->kernels_fixed;
+            for (const auto& G : W->groups) loops.emplace_back(G.index, G.kernels_iter);
+        }
+    }
+    CK(cudaGraphLaunch(exec, st));
+    for (int i = 0; i < n; ++i) {
+        glls_problem* P = probs[i];
+        CK(cudaMemcpyAsync(u[i], P->yk, sizeof(double) * P->N,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(P->hostS, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    const double t_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    glls_status worst = GLLS_OK;
+    for (int i = 0; i < n; ++i) {
+        glls_status r = solve_result(probs[i], probs[i]->hostS, stats ? &stats[i] : nullptr, t_ms);
+        if (r != GLLS_OK && worst == GLLS_OK) worst = r;
+    }
+    if (stats) {
+        // kernels of the whole launch, reported on the first problem: the
+        // fixed nodes plus each group's loop body times its passes (the
+        // group loops while any of its problems is active)
+        long long total = kfix;
+        for (const auto& g : loops) {
+            double passes = 0;
+            for (int i : g.first) passes = std::max(passes, probs[i]->hostS[S_ITER]);
+            total += g.second * (long long)passes;
+        }
+        for (int i = 0; i < n; ++i) stats[i].kernels = i == 0 ? total : 0;
     }
     if (worst == GLLS_ERR_BREAKDOWN) fail(worst, "breakdown in at least one problem of the batch");
     if (worst == GLLS_ERR_NOT_CONVERGED) fail(worst, "at least one problem of the batch reached max_iter");

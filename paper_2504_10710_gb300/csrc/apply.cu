@@ -54,13 +54,13 @@ __device__ __forceinline__ float dot_cs(const float* a, const float* b) {
 // Launch bounds (256, 1): at least one resident CTA per SM.  (Eight for 2-D
 // FP32 would cap it at 32 registers; measured inside the solve that is
 // 0.5-1 % slower than the 48 registers the compiler picks with one.)
+// The CTA body: block `blk` of `nblk` (per right-hand side: the right-hand
+// side fastest in the CTA order, see device.cuh).
 template <typename T, int DIM, int P, bool DOT>
-__global__ void __launch_bounds__(256, 1) apply_p_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
-                                                         int mask, double* dot, double* part, unsigned* ticket,
-                                                         int nrhs) {
-    grid_dep_sync();
-    // right-hand side fastest in the CTA order (see device.cuh)
-    const int rhs = blockIdx.x % nrhs, bx = blockIdx.x / nrhs, nbx = gridDim.x / nrhs;
+__device__ __forceinline__ void apply_p_body(const DevLevel<T>& L, const T* __restrict__ x, T* __restrict__ y,
+                                             int mask, double* dot, double* part, unsigned* ticket, int nrhs, int blk,
+                                             int nblk) {
+    const int rhs = blk % nrhs, bx = blk / nrhs, nbx = nblk / nrhs;
     x += (long long)rhs * L.N;
     y += (long long)rhs * L.N;
     constexpr int N1 = P + 1;
@@ -186,11 +186,32 @@ __global__ void __launch_bounds__(256, 1) apply_p_kernel(DevLevel<T> L, const T*
         __shared__ double red[32];
         const double tsum = block_sum(local, red);
         if (threadIdx.x == 0) part[(long long)rhs * nbx + bx] = tsum;
-        if (ticket && last_block(ticket)) {   // single right-hand side only
-            finalize_partials(part, 1, gridDim.x, dot, 0, 0, red);
+        if (ticket && last_block(ticket)) {   // single right-hand side, single launch only
+            finalize_partials(part, 1, nblk, dot, 0, 0, red);
             if (threadIdx.x == 0) *ticket = 0u;
         }
     }
+}
+
+template <typename T, int DIM, int P, bool DOT>
+__global__ void __launch_bounds__(256, 1) apply_p_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
+                                                         int mask, double* dot, double* part, unsigned* ticket,
+                                                         int nrhs) {
+    grid_dep_sync();
+    apply_p_body<T, DIM, P, DOT>(L, x, y, mask, dot, part, ticket, nrhs, blockIdx.x, gridDim.x);
+}
+
+// Work-list form: item j (its own level, vectors and partials) owns the CTAs
+// [start[j], start[j + 1]) of the launch.
+template <typename T, int DIM, int P, bool DOT>
+__global__ void __launch_bounds__(256, 1) apply_p_list_kernel(const ApplyItem<T>* __restrict__ items,
+                                                              const int* __restrict__ start, int nitems, int mask) {
+    grid_dep_sync();
+    const int j = work_item(start, nitems, blockIdx.x);
+    const ApplyItem<T>& it = items[j];
+    if (it.done && *it.done != 0.0) return;
+    apply_p_body<T, DIM, P, DOT>(it.L, it.x, it.y, mask, nullptr, it.part, nullptr, 1, blockIdx.x - start[j],
+                                 start[j + 1] - start[j]);
 }
 
 // Number of CTAs (= dot partials) the specialised apply launches for L.
@@ -231,7 +252,43 @@ bool dispatch(int p, const DevLevel<T>& L, const T* x, T* y, bool mask, double* 
     }
 }
 
+template <typename T, int P>
+bool launch_list_p(int p, const ApplyItem<T>* items, const int* start, int nitems, int blocks, bool mask, bool dot,
+                   cudaStream_t st) {
+    if constexpr (P == 0) {
+        return false;
+    } else {
+        if (p != P) return launch_list_p<T, P - 1>(p, items, start, nitems, blocks, mask, dot, st);
+        if (dot)
+            launch_k(apply_p_list_kernel<T, 2, P, true>, (unsigned)blocks, 256, 0, st, items, start, nitems,
+                     mask ? 1 : 0);
+        else
+            launch_k(apply_p_list_kernel<T, 2, P, false>, (unsigned)blocks, 256, 0, st, items, start, nitems,
+                     mask ? 1 : 0);
+        return true;
+    }
+}
+
 }  // namespace
+
+// CTAs of the 2-D work-list apply for a level of order p with E elements
+// (one dot partial each).
+int apply_list_blocks(int p, long long E) {
+    const int nloc = (p + 1) * (p + 1);
+    const int epb = nloc >= 256 ? 1 : 256 / nloc;
+    return (int)((E + epb - 1) / epb);
+}
+
+// 2-D work-list apply (orders 1..16): every item's level has order p.
+template <typename T>
+bool launch_apply_list(int p, const ApplyItem<T>* items, const int* start, int nitems, int blocks, bool mask,
+                       bool dot, cudaStream_t st) {
+    if (nitems < 1 || blocks < 1) return true;
+    return launch_list_p<T, 16>(p, items, start, nitems, blocks, mask, dot, st);
+}
+template bool launch_apply_list<float>(int, const ApplyItem<float>*, const int*, int, int, bool, bool, cudaStream_t);
+template bool launch_apply_list<double>(int, const ApplyItem<double>*, const int*, int, int, bool, bool,
+                                        cudaStream_t);
 
 // Dot partials that launch_apply writes for L (one per CTA of the
 // specialised kernel, else one per block of the separate dot launch).

@@ -116,6 +116,105 @@ struct DevCoarse {
     const T* agk[kMaxCrLevels] = {};    // level l: [elim][3][m][ldm]: A_j^-1, A_j^-1 L_j, A_j^-1 U_j
 };
 
+// ---- work lists: one launch over the tiles of several problems ----------
+// Item j of a work-list launch owns the CTAs [start[j], start[j + 1]) of a
+// one-dimensional grid (start has nitems + 1 entries, start[0] = 0); every
+// item carries its own level data and vectors, so problems of different
+// sizes share a launch; an item whose problem has stopped (done flag set)
+// returns at once.  Returns the item of CTA b by bisection.
+__device__ __forceinline__ int work_item(const int* __restrict__ start, int nitems, int b) {
+    int lo = 0, hi = nitems - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+struct ApplyItem {               // y (+)= A x on one problem's level; dot partials (FP64 outer apply) in part
+    DevLevel<T> L;
+    const T* x;
+    T* y;
+    double* part;
+    const double* done;          // the problem's stop flag (nonzero: its CTAs return at once), or null
+};
+
+template <typename T>
+struct Transfer2Item {           // both in-plane factors of a restriction or prolongation (transfer2_kernel)
+    DevBand<T> M0, M1;
+    int3 nin, nout;
+    const T* in;
+    const T* in2;
+    T* out;
+    T* clear;
+    int gx, gy;                  // the item's tile grid (x: 32 outputs of axis 0, y: TY outputs of axis 1)
+    const double* done;
+};
+
+template <typename T>
+struct CoarseItem {              // dense part of the coarsest solve (coarse_kernel)
+    long long n, ld;
+    const long long* index;
+    const T* inv;
+    const T* src;
+    const long long* src_index;
+    int m, H;
+    T* e;
+    const double* done;
+};
+
+template <typename T>
+struct BcrItem {                 // one block-CR level of one problem (bcr_forward/backward_kernel)
+    const T* ops;                // fh[l] (forward) or agk[l] (backward)
+    int nb, m, ldm;
+    const long long* index;
+    const T* src;                // forward: r; backward: w
+    T* dst;                      // forward: w; backward: e
+    int gx, rows;                // the item's CTA grid
+    const double* done;
+};
+
+struct FcgItem {                 // one problem's outer Krylov vectors, partial sums and scalars
+    double *x, *r, *p, *q, *z;
+    float *r32, *z32;            // FP32 copies (mixed precision), else null
+    long long n;
+    double *prz, *pzq, *prr, *ppq;
+    int npq;                     // partials of p.q (CTAs of the problem's FP64 apply)
+    double* S;
+    unsigned* ticket;
+};
+
+int apply_list_blocks(int p, long long E);
+template <typename T>
+bool launch_apply_list(int p, const ApplyItem<T>* items, const int* start, int nitems, int blocks, bool mask,
+                       bool dot, cudaStream_t st);
+template <typename T>
+bool transfer2_list_config(const DevBand<T>& M0, const DevBand<T>& M1, const int nout[3], int* gx, int* gy,
+                           int* wb, int* ty, size_t* smem);
+template <typename T>
+bool launch_transfer2_list(int wb, int ty, const Transfer2Item<T>* items, const int* start, int nitems, int blocks,
+                           size_t smem, bool add, bool mask, cudaStream_t st);
+template <typename T>
+void launch_coarse_list(const CoarseItem<T>* items, const int* start, int nitems, int blocks, size_t smem,
+                        cudaStream_t st);
+template <typename T>
+void launch_bcr_list(bool forward, int l, const BcrItem<T>* items, const int* start, int nitems, int blocks,
+                     size_t smem, cudaStream_t st);
+void launch_fcg_list(int step, const FcgItem* items, int nitems, int flexible, cudaStream_t st);
+template <typename T>
+size_t line_block_item_bytes();
+template <typename T>
+size_t line_block_item_done_offset();
+template <typename T>
+int line_block_list_item(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
+                         void* item, int* blocks, int* threads, size_t smem[2], int* cv);
+bool line_block_list_specialised(int p, int cv);
+template <typename T>
+bool launch_line_block_list(int p, int cv, const void* items, const int* start, int nitems, int blocks, int threads,
+                            size_t smem, cudaStream_t st);
+
 // Opt every kernel into up to 200 KB of dynamic shared memory (call once per
 // device, outside stream capture).
 bool init_kernel_attributes();

@@ -299,15 +299,14 @@ __device__ __forceinline__ long long reduced_pos(long long t, int m, int H) {
 // src[src_index[pos(t)]] (nodal source) or src[pos(t)] (block-ordered
 // source); row i of the result goes to e[index[pos(i)]].
 template <typename T>
-__global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, const long long* __restrict__ index,
-                                                     const T* __restrict__ inv, const T* __restrict__ src,
-                                                     const long long* __restrict__ src_index, int m, int H,
-                                                     T* __restrict__ e, int nrhs, long long vstride) {
-    grid_dep_sync();
+__device__ __forceinline__ void coarse_body(long long n, long long ld, const long long* __restrict__ index,
+                                            const T* __restrict__ inv, const T* __restrict__ src,
+                                            const long long* __restrict__ src_index, int m, int H, T* __restrict__ e,
+                                            int nrhs, long long vstride, int blk, int nblk) {
     // right-hand side fastest in the CTA order (see device.cuh); src and e
     // hold vstride values per right-hand side
-    const int rhs = blockIdx.x % nrhs;
-    const long long bx = blockIdx.x / nrhs, nbx = gridDim.x / nrhs;
+    const int rhs = blk % nrhs;
+    const long long bx = blk / nrhs, nbx = nblk / nrhs;
     src += rhs * vstride;
     e += rhs * vstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -359,6 +358,26 @@ __global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, 
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) coarse_kernel(long long n, long long ld, const long long* __restrict__ index,
+                                                     const T* __restrict__ inv, const T* __restrict__ src,
+                                                     const long long* __restrict__ src_index, int m, int H,
+                                                     T* __restrict__ e, int nrhs, long long vstride) {
+    grid_dep_sync();
+    coarse_body<T>(n, ld, index, inv, src, src_index, m, H, e, nrhs, vstride, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) coarse_list_kernel(const CoarseItem<T>* __restrict__ items,
+                                                          const int* __restrict__ start, int nitems) {
+    grid_dep_sync();
+    const int j = work_item(start, nitems, blockIdx.x);
+    const CoarseItem<T>& it = items[j];
+    if (it.done && *it.done != 0.0) return;
+    coarse_body<T>(it.n, it.ld, it.index, it.inv, it.src, it.src_index, it.m, it.H, it.e, 1, 0,
+                   blockIdx.x - start[j], start[j + 1] - start[j]);
+}
+
 // Rows of a block per CTA in the block-CR kernels: one per warp, so that a
 // level with few blocks still spreads over many CTAs.
 constexpr int kBcrRows = 8;
@@ -371,20 +390,19 @@ constexpr int kBcrRows = 8;
 // past the kept blocks copy the eliminated blocks into w; deeper levels
 // update w in place (they read only blocks eliminated at this level).
 template <typename T>
-__global__ void __launch_bounds__(256) bcr_forward_kernel(const T* __restrict__ FH, int l, int nb, int m, int ldm,
-                                                          const long long* __restrict__ index,
-                                                          const T* __restrict__ r, T* w, int nrhs, long long nvec) {
-    grid_dep_sync();
-    const int rhs = blockIdx.x % nrhs;
+__device__ __forceinline__ void bcr_forward_body(const T* __restrict__ FH, int l, int nb, int m, int ldm,
+                                                 const long long* __restrict__ index, const T* __restrict__ r, T* w,
+                                                 int nrhs, long long nvec, int bx, int by) {
+    const int rhs = bx % nrhs;
     r += rhs * nvec;
     w += rhs * nvec;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* xl = reinterpret_cast<T*>(smem_raw);
     T* xr = xl + m;
     const int h = 1 << l, nk = (nb >> l) / 2;
-    const int row0 = blockIdx.y * kBcrRows;
+    const int row0 = by * kBcrRows;
     const bool lvl0 = l == 0;
-    const int q = blockIdx.x / nrhs;
+    const int q = bx / nrhs;
     if (q >= nk) {                                   // level 0: copy eliminated block 2 (q - nk)
         const long long b = 2LL * (q - nk);
         for (int rr = threadIdx.x; rr < kBcrRows; rr += blockDim.x) {
@@ -416,17 +434,24 @@ __global__ void __launch_bounds__(256) bcr_forward_kernel(const T* __restrict__ 
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) bcr_forward_kernel(const T* __restrict__ FH, int l, int nb, int m, int ldm,
+                                                          const long long* __restrict__ index,
+                                                          const T* __restrict__ r, T* w, int nrhs, long long nvec) {
+    grid_dep_sync();
+    bcr_forward_body<T>(FH, l, nb, m, ldm, index, r, w, nrhs, nvec, blockIdx.x, blockIdx.y);
+}
+
 // Block CR back substitution at level l, one CTA per (eliminated block,
 // kBcrRows rows): for b = (2s + 1) h - 1,
 //   x_b = A_b^-1 w_b - (A_b^-1 L_b) x_{b-h} - (A_b^-1 U_b) x_{b+h}
 // (y = x + P e of Algorithm 1); the kept neighbours' values are already in
 // e (solved at deeper levels), read and written through index.
 template <typename T>
-__global__ void __launch_bounds__(256) bcr_backward_kernel(const T* __restrict__ AGK, int l, int nb, int m, int ldm,
-                                                           const long long* __restrict__ index,
-                                                           const T* __restrict__ w, T* e, int nrhs, long long nvec) {
-    grid_dep_sync();
-    const int rhs = blockIdx.x % nrhs;
+__device__ __forceinline__ void bcr_backward_body(const T* __restrict__ AGK, int l, int nb, int m, int ldm,
+                                                  const long long* __restrict__ index, const T* __restrict__ w, T* e,
+                                                  int nrhs, long long nvec, int bx, int by) {
+    const int rhs = bx % nrhs;
     w += rhs * nvec;
     e += rhs * nvec;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -434,8 +459,8 @@ __global__ void __launch_bounds__(256) bcr_backward_kernel(const T* __restrict__
     T* xl = xw + m;
     T* xr = xl + m;
     const int h = 1 << l;
-    const int row0 = blockIdx.y * kBcrRows;
-    const long long s_ = blockIdx.x / nrhs;
+    const int row0 = by * kBcrRows;
+    const long long s_ = bx / nrhs;
     const long long b = (2 * s_ + 1) * h - 1, lb = b - h, rb = b + h;
     const bool left = lb >= 0, right = rb < nb;
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -461,6 +486,31 @@ __global__ void __launch_bounds__(256) bcr_backward_kernel(const T* __restrict__
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) bcr_backward_kernel(const T* __restrict__ AGK, int l, int nb, int m, int ldm,
+                                                           const long long* __restrict__ index,
+                                                           const T* __restrict__ w, T* e, int nrhs, long long nvec) {
+    grid_dep_sync();
+    bcr_backward_body<T>(AGK, l, nb, m, ldm, index, w, e, nrhs, nvec, blockIdx.x, blockIdx.y);
+}
+
+// Work-list forms of both block-CR steps: item j owns the CTAs [start[j],
+// start[j + 1]) (its gx x rows grid, x fastest).
+template <typename T>
+__global__ void __launch_bounds__(256) bcr_list_kernel(const BcrItem<T>* __restrict__ items,
+                                                       const int* __restrict__ start, int nitems, int l, int forward) {
+    grid_dep_sync();
+    const int j = work_item(start, nitems, blockIdx.x);
+    const BcrItem<T>& it = items[j];
+    if (it.done && *it.done != 0.0) return;
+    const int local = blockIdx.x - start[j];
+    const int bx = local % it.gx, by = local / it.gx;
+    if (forward)
+        bcr_forward_body<T>(it.ops, l, it.nb, it.m, it.ldm, it.index, it.src, it.dst, 1, 0, bx, by);
+    else
+        bcr_backward_body<T>(it.ops, l, it.nb, it.m, it.ldm, it.index, it.src, it.dst, 1, 0, bx, by);
+}
+
 // Fused two-factor transfer: a CTA of 32 x 8 threads computes a 32 x TY tile
 // of outputs (I, J) of one axis-2 plane.  Its input window (rows of axis 1 x
 // columns of axis 0 that the tile's bands touch) is staged in shared memory
@@ -468,14 +518,14 @@ __global__ void __launch_bounds__(256) bcr_backward_kernel(const T* __restrict__
 // axis 1:  out(I, J) = sum_k M1(J, k) sum_q M0(I, q) in(q, s1(J) + k).
 // Band rows are held in registers (width bucket WB >= both widths).
 template <typename T, int WB, int TY>
-__global__ void __launch_bounds__(256) transfer2_kernel(DevBand<T> M0, DevBand<T> M1, int3 nin, int3 nout,
-                                                        const T* __restrict__ in, const T* __restrict__ in2,
-                                                        T* __restrict__ out, int add, int mask, T* __restrict__ clear) {
-    grid_dep_sync();
+__device__ __forceinline__ void transfer2_body(const DevBand<T>& M0, const DevBand<T>& M1, int3 nin, int3 nout,
+                                               const T* __restrict__ in, const T* __restrict__ in2,
+                                               T* __restrict__ out, int add, int mask, T* __restrict__ clear, int bx,
+                                               int by, int z) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int win[4];                       // column lo, column count, row lo, row count
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int I0 = blockIdx.x * 32, J0 = blockIdx.y * TY, z = blockIdx.z;
+    const int I0 = bx * 32, J0 = by * TY;
     const int W0 = M0.width, W1 = M1.width;
     const int I = I0 + tx;
     const bool okI = I < nout.x;
@@ -571,6 +621,30 @@ __global__ void __launch_bounds__(256) transfer2_kernel(DevBand<T> M0, DevBand<T
     }
 }
 
+template <typename T, int WB, int TY>
+__global__ void __launch_bounds__(256) transfer2_kernel(DevBand<T> M0, DevBand<T> M1, int3 nin, int3 nout,
+                                                        const T* __restrict__ in, const T* __restrict__ in2,
+                                                        T* __restrict__ out, int add, int mask, T* __restrict__ clear) {
+    grid_dep_sync();
+    transfer2_body<T, WB, TY>(M0, M1, nin, nout, in, in2, out, add, mask, clear, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Work-list form: item j owns the CTAs [start[j], start[j + 1]), its
+// gx x gy x (planes) tile grid, x fastest.
+template <typename T, int WB, int TY>
+__global__ void __launch_bounds__(256) transfer2_list_kernel(const Transfer2Item<T>* __restrict__ items,
+                                                             const int* __restrict__ start, int nitems, int add,
+                                                             int mask) {
+    grid_dep_sync();
+    const int j = work_item(start, nitems, blockIdx.x);
+    const Transfer2Item<T>& it = items[j];
+    if (it.done && *it.done != 0.0) return;
+    const int local = blockIdx.x - start[j];
+    const int bx = local % it.gx, rest = local / it.gx;
+    transfer2_body<T, WB, TY>(it.M0, it.M1, it.nin, it.nout, it.in, it.in2, it.out, add, mask, it.clear, bx,
+                              rest % it.gy, rest / it.gy);
+}
+
 // ---------------------------------------------------------------------------
 // vector kernels
 // ---------------------------------------------------------------------------
@@ -643,18 +717,9 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
 // Outer-iteration dots, grid-stride over kDotBlocks CTAs: per-block partials
 // of r.z into prz and of z.q into pzq (summed by the consumers); z is taken
 // from z32 when given (z = double(z32)); q is reset to 0 after it is read.
-__global__ void __launch_bounds__(256) dots_rz_zq_kernel(const double* __restrict__ r, double* __restrict__ z,
-                                                         const float* __restrict__ z32, double* __restrict__ q,
-                                                         long long n, double* __restrict__ prz,
-                                                         double* __restrict__ pzq) {
-    grid_dep_sync();
-    const long long jr = blockIdx.y;       // right-hand side
-    r += jr * n;
-    z += jr * n;
-    if (z32) z32 += jr * n;
-    q += jr * n;
-    prz += jr * gridDim.x;
-    pzq += jr * gridDim.x;
+__device__ __forceinline__ void dots_rz_zq_body(const double* __restrict__ r, double* __restrict__ z,
+                                                const float* __restrict__ z32, double* __restrict__ q, long long n,
+                                                double* __restrict__ prz, double* __restrict__ pzq) {
     __shared__ double red[32];
     double s0 = 0.0, s1 = 0.0;
     // kVecU elements per thread per trip, all loads issued before use (same
@@ -689,27 +754,24 @@ __global__ void __launch_bounds__(256) dots_rz_zq_kernel(const double* __restric
     if (threadIdx.x == 0) pzq[blockIdx.x] = t1;
 }
 
+__global__ void __launch_bounds__(256) dots_rz_zq_kernel(const double* __restrict__ r, double* __restrict__ z,
+                                                         const float* __restrict__ z32, double* __restrict__ q,
+                                                         long long n, double* __restrict__ prz,
+                                                         double* __restrict__ pzq) {
+    grid_dep_sync();
+    const long long jr = blockIdx.y;       // right-hand side
+    dots_rz_zq_body(r + jr * n, z + jr * n, z32 ? z32 + jr * n : nullptr, q + jr * n, n, prz + jr * gridDim.x,
+                    pzq + jr * gridDim.x);
+}
+
 // q-independent update: every block sums the partials of p.q (npq, from the
 // apply) and of r.z (nrz), alpha = r.z / p.q; x += alpha p; r -= alpha q;
 // partials of r.r into prr; the last block publishes S_RR, S_RZ (for the next
 // direction), S_ALPHA, S_PQ and the breakdown flag.
-__global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x, double* __restrict__ r,
-                                                         const double* __restrict__ p, const double* __restrict__ q,
-                                                         long long n, const double* ppq, int npq, const double* prz,
-                                                         int nrz, double* prr, double* S, unsigned* ticket,
-                                                         float* __restrict__ r32) {
-    grid_dep_sync();
-    const long long jr = blockIdx.y;       // right-hand side
-    x += jr * n;
-    r += jr * n;
-    p += jr * n;
-    q += jr * n;
-    if (r32) r32 += jr * n;
-    ppq += jr * npq;
-    prz += jr * nrz;
-    prr += jr * gridDim.x;
-    S += jr * S_COUNT;
-    ticket += jr;
+__device__ __forceinline__ void fcg_update_body(double* __restrict__ x, double* __restrict__ r,
+                                                const double* __restrict__ p, const double* __restrict__ q,
+                                                long long n, const double* ppq, int npq, const double* prz, int nrz,
+                                                double* prr, double* S, unsigned* ticket, float* __restrict__ r32) {
     // a right-hand side that has stopped keeps its x and r
     const bool active = S[S_DONE] == 0.0;
     __shared__ double red[32];
@@ -766,20 +828,24 @@ __global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x,
     }
 }
 
+__global__ void __launch_bounds__(256) fcg_update_kernel(double* __restrict__ x, double* __restrict__ r,
+                                                         const double* __restrict__ p, const double* __restrict__ q,
+                                                         long long n, const double* ppq, int npq, const double* prz,
+                                                         int nrz, double* prr, double* S, unsigned* ticket,
+                                                         float* __restrict__ r32) {
+    grid_dep_sync();
+    const long long jr = blockIdx.y;       // right-hand side
+    fcg_update_body(x + jr * n, r + jr * n, p + jr * n, q + jr * n, n, ppq + jr * npq, npq, prz + jr * nrz, nrz,
+                    prr + jr * gridDim.x, S + jr * S_COUNT, ticket + jr, r32 ? r32 + jr * n : nullptr);
+}
+
 // p = z + beta p, beta = -alpha zq / rz_old (flexible) or rz_new / rz_old
 // (Fletcher-Reeves), with rz_new and zq summed from the dots' partials in
 // every block and rz_old, alpha from the previous update.
-__global__ void __launch_bounds__(256) fcg_direction_kernel(double* __restrict__ p, const double* __restrict__ z,
-                                                            long long n, const double* prz, const double* pzq, int nd,
-                                                            const double* __restrict__ S, int flexible) {
-    grid_dep_sync();
-    const long long jr = blockIdx.y;       // right-hand side
-    S += jr * S_COUNT;
+__device__ __forceinline__ void fcg_direction_body(double* __restrict__ p, const double* __restrict__ z,
+                                                   long long n, const double* prz, const double* pzq, int nd,
+                                                   const double* __restrict__ S, int flexible) {
     if (S[S_DONE] != 0.0) return;           // stopped: p is no longer used
-    p += jr * n;
-    z += jr * n;
-    prz += jr * nd;
-    pzq += jr * nd;
     __shared__ double red[32];
     __shared__ double sh_beta;
     const double rz_new = sum_partials(prz, nd, red);
@@ -805,6 +871,29 @@ __global__ void __launch_bounds__(256) fcg_direction_kernel(double* __restrict__
             if (i < n) p[i] = zv[u] + beta * pv[u];
         }
     }
+}
+
+__global__ void __launch_bounds__(256) fcg_direction_kernel(double* __restrict__ p, const double* __restrict__ z,
+                                                            long long n, const double* prz, const double* pzq, int nd,
+                                                            const double* __restrict__ S, int flexible) {
+    grid_dep_sync();
+    const long long jr = blockIdx.y;       // right-hand side
+    fcg_direction_body(p + jr * n, z + jr * n, n, prz + jr * nd, pzq + jr * nd, nd, S + jr * S_COUNT, flexible);
+}
+
+// Work-list form of the three outer-iteration kernels: item blockIdx.y is one
+// problem (its own vectors, length, partials and scalars), kDotBlocks CTAs
+// each.  step 0: dots r.z, z.q; 1: direction; 2: update.
+__global__ void __launch_bounds__(256) fcg_list_kernel(const FcgItem* __restrict__ items, int step, int flexible) {
+    grid_dep_sync();
+    const FcgItem& it = items[blockIdx.y];
+    if (step == 0)
+        dots_rz_zq_body(it.r, it.z, it.z32, it.q, it.n, it.prz, it.pzq);
+    else if (step == 1)
+        fcg_direction_body(it.p, it.z, it.n, it.prz, it.pzq, (int)gridDim.x, it.S, flexible);
+    else
+        fcg_update_body(it.x, it.r, it.p, it.q, it.n, it.ppq, it.npq, it.prz, (int)gridDim.x, it.prr, it.S,
+                        it.ticket, it.r32);
 }
 
 // ---- GMRES helpers (Arnoldi with classical Gram-Schmidt, twice) ----------
@@ -1092,6 +1181,70 @@ bool launch_transfer2(const DevBand<T>& M0, const DevBand<T>& M1, const int nin[
     return true;
 }
 
+// ---- work-list launchers ------------------------------------------------
+// Tile grid, band-width bucket, tile height and shared memory of a fused
+// transfer; false when the fused form does not apply (as launch_transfer2).
+template <typename T>
+bool transfer2_list_config(const DevBand<T>& M0, const DevBand<T>& M1, const int nout[3], int* gx, int* gy, int* wb,
+                           int* ty, size_t* smem) {
+    constexpr int TY = 8;
+    *smem = sizeof(T) * (size_t)M1.span8 * (M0.span32 + 32);
+    const int W = M0.width > M1.width ? M0.width : M1.width;
+    if (M0.span32 <= 0 || M1.span8 <= 0 || *smem > kMaxDynSmem || W > 32) return false;
+    *gx = (nout[0] + 31) / 32;
+    *gy = (nout[1] + TY - 1) / TY;
+    *ty = TY;
+    *wb = W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : 32;
+    return true;
+}
+
+template <typename T>
+bool launch_transfer2_list(int wb, int ty, const Transfer2Item<T>* items, const int* start, int nitems, int blocks,
+                           size_t smem, bool add, bool mask, cudaStream_t st) {
+    if (nitems < 1 || blocks < 1) return true;
+    if (ty != 8) return false;
+    const int ad = add ? 1 : 0, mk = mask ? 1 : 0;
+    cudaError_t e;
+    if (wb == 4) e = launch_k(transfer2_list_kernel<T, 4, 8>, blocks, 256, smem, st, items, start, nitems, ad, mk);
+    else if (wb == 8) e = launch_k(transfer2_list_kernel<T, 8, 8>, blocks, 256, smem, st, items, start, nitems, ad, mk);
+    else if (wb == 16)
+        e = launch_k(transfer2_list_kernel<T, 16, 8>, blocks, 256, smem, st, items, start, nitems, ad, mk);
+    else e = launch_k(transfer2_list_kernel<T, 32, 8>, blocks, 256, smem, st, items, start, nitems, ad, mk);
+    return e == cudaSuccess;
+}
+
+template <typename T>
+void launch_coarse_list(const CoarseItem<T>* items, const int* start, int nitems, int blocks, size_t smem,
+                        cudaStream_t st) {
+    if (nitems < 1 || blocks < 1) return;
+    launch_k(coarse_list_kernel<T>, blocks, 256, smem, st, items, start, nitems);
+}
+
+template <typename T>
+void launch_bcr_list(bool forward, int l, const BcrItem<T>* items, const int* start, int nitems, int blocks,
+                     size_t smem, cudaStream_t st) {
+    if (nitems < 1 || blocks < 1) return;
+    launch_k(bcr_list_kernel<T>, blocks, 256, smem, st, items, start, nitems, l, forward ? 1 : 0);
+}
+
+void launch_fcg_list(int step, const FcgItem* items, int nitems, int flexible, cudaStream_t st) {
+    if (nitems < 1) return;
+    launch_k(fcg_list_kernel, dim3(kDotBlocks, nitems), 256, 0, st, items, step, flexible);
+}
+
+template bool transfer2_list_config<float>(const DevBand<float>&, const DevBand<float>&, const int*, int*, int*, int*,
+                                           int*, size_t*);
+template bool transfer2_list_config<double>(const DevBand<double>&, const DevBand<double>&, const int*, int*, int*,
+                                            int*, int*, size_t*);
+template bool launch_transfer2_list<float>(int, int, const Transfer2Item<float>*, const int*, int, int, size_t, bool,
+                                           bool, cudaStream_t);
+template bool launch_transfer2_list<double>(int, int, const Transfer2Item<double>*, const int*, int, int, size_t, bool,
+                                            bool, cudaStream_t);
+template void launch_coarse_list<float>(const CoarseItem<float>*, const int*, int, int, size_t, cudaStream_t);
+template void launch_coarse_list<double>(const CoarseItem<double>*, const int*, int, int, size_t, cudaStream_t);
+template void launch_bcr_list<float>(bool, int, const BcrItem<float>*, const int*, int, int, size_t, cudaStream_t);
+template void launch_bcr_list<double>(bool, int, const BcrItem<double>*, const int*, int, int, size_t, cudaStream_t);
+
 template <typename T>
 void launch_coarse(const DevCoarse<T>& C, long long N0, const T* r, T* e, T* w, cudaStream_t st, bool e_boundary_zero,
                    int nrhs) {
@@ -1212,7 +1365,15 @@ bool init_kernel_attributes() {
                          (const void*)transfer2_kernel<double, 4, 8>, (const void*)transfer2_kernel<float, 4, 8>,
                          (const void*)transfer2_kernel<double, 8, 8>, (const void*)transfer2_kernel<float, 8, 8>,
                          (const void*)transfer2_kernel<double, 16, 8>, (const void*)transfer2_kernel<float, 16, 8>,
-                         (const void*)transfer2_kernel<double, 32, 8>, (const void*)transfer2_kernel<float, 32, 8>};
+                         (const void*)transfer2_kernel<double, 32, 8>, (const void*)transfer2_kernel<float, 32, 8>,
+                         (const void*)coarse_list_kernel<double>, (const void*)coarse_list_kernel<float>,
+                         (const void*)bcr_list_kernel<double>, (const void*)bcr_list_kernel<float>,
+                         (const void*)transfer2_list_kernel<double, 4, 8>, (const void*)transfer2_list_kernel<float, 4, 8>,
+                         (const void*)transfer2_list_kernel<double, 8, 8>, (const void*)transfer2_list_kernel<float, 8, 8>,
+                         (const void*)transfer2_list_kernel<double, 16, 8>,
+                         (const void*)transfer2_list_kernel<float, 16, 8>,
+                         (const void*)transfer2_list_kernel<double, 32, 8>,
+                         (const void*)transfer2_list_kernel<float, 32, 8>};
     for (const void* f : fns)
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess)
             return false;

@@ -31,6 +31,8 @@
 #include "device.cuh"
 
 #include <algorithm>
+#include <cstddef>
+#include <cstring>
 
 namespace glls {
 namespace {
@@ -49,6 +51,7 @@ struct BlockLineArgs {
     const T* r;
     T* y;
     T* x;
+    const double* done;                        // work lists: the problem's stop flag, or null
 };
 
 constexpr int kBlockThreads = 256;
@@ -111,13 +114,13 @@ struct SegOp {
 // Register budget: FP32 four CTAs per SM (<= 64 registers), three for order 8
 // and the run-time order (<= 85: the 42 operator values of a segment stay in
 // registers), FP64 two (<= 128).
+// The CTA body for block `blk` of the launch of A (any block size of at
+// least lpc E threads, rounded to whole warps).
 template <typename T, int P, int CV>
-__global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 || P == 0 ? 3 : 4))
-    line_block_kernel(BlockLineArgs<T> A) {
-    grid_dep_sync();
+__device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
     // right-hand side fastest in the CTA order (see device.cuh): the nrhs CTAs
     // of one line group read the same segment operators
-    const int rhs = blockIdx.x % A.nrhs, bx = blockIdx.x / A.nrhs;
+    const int rhs = blk % A.nrhs, bx = blk / A.nrhs;
     {
         const long long vo = (long long)rhs * A.N;
         if (A.g) A.g += vo;
@@ -313,6 +316,24 @@ __global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 ||
     }
 }
 
+template <typename T, int P, int CV>
+__global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 || P == 0 ? 3 : 4))
+    line_block_kernel(BlockLineArgs<T> A) {
+    grid_dep_sync();
+    line_block_body<T, P, CV>(A, blockIdx.x);
+}
+
+// Work-list form: item j (one problem's level, direction and vectors) owns
+// the CTAs [start[j], start[j + 1]).
+template <typename T, int P, int CV>
+__global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 || P == 0 ? 3 : 4))
+    line_block_list_kernel(const BlockLineArgs<T>* __restrict__ items, const int* __restrict__ start, int nitems) {
+    grid_dep_sync();
+    const int j = work_item(start, nitems, blockIdx.x);
+    if (items[j].done && *items[j].done != 0.0) return;
+    line_block_body<T, P, CV>(items[j], blockIdx.x - start[j]);
+}
+
 template <typename T, int P>
 size_t block_smem(int lpc, int span, int E) {
     return sizeof(T) * ((size_t)lpc * span * (P == 0 ? 3 : 2) + 2 * (size_t)lpc * E + 2 * (size_t)lpc * (E - 1));
@@ -357,13 +378,19 @@ template <typename T, int P>
 bool set_attr_p() {
     const int lim = (int)kMaxDynSmemBytes;
     if constexpr (P > 0) {
-        return cudaFuncSetAttribute((const void*)line_block_kernel<T, P, 1>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess &&
-               cudaFuncSetAttribute((const void*)line_block_kernel<T, P, 2>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+        const void* fns[] = {(const void*)line_block_kernel<T, P, 1>, (const void*)line_block_kernel<T, P, 2>,
+                             (const void*)line_block_list_kernel<T, P, 1>,
+                             (const void*)line_block_list_kernel<T, P, 2>};
+        for (const void* f : fns)
+            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) return false;
+        return true;
     } else {
         const void* fns[] = {(const void*)line_block_kernel<T, 0, 1>, (const void*)line_block_kernel<T, 0, 2>,
-                             (const void*)line_block_kernel<T, 0, 4>, (const void*)line_block_kernel<T, 0, 8>};
+                             (const void*)line_block_kernel<T, 0, 4>, (const void*)line_block_kernel<T, 0, 8>,
+                             (const void*)line_block_list_kernel<T, 0, 1>,
+                             (const void*)line_block_list_kernel<T, 0, 2>,
+                             (const void*)line_block_list_kernel<T, 0, 4>,
+                             (const void*)line_block_list_kernel<T, 0, 8>};
         for (const void* f : fns)
             if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) return false;
         return true;
@@ -382,23 +409,26 @@ bool init_line_block_attributes() { return set_attr_t<float>() && set_attr_t<dou
 
 bool line_block_supported(int n, int E) { return n <= kMaxBlockLine && E <= kMaxBlockSegments; }
 
+namespace {
+
+// Fills A for a line solve of L along s; 0: nothing to do, -1: outside the
+// supported range, 1: ready.
 template <typename T>
-bool launch_line_block(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
-                       cudaStream_t st, int nrhs) {
-    BlockLineArgs<T> A;
+int make_args(BlockLineArgs<T>& A, const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x,
+              T alpha, int nrhs) {
     A.nrhs = nrhs;
     A.N = L.N;
     A.n = L.n[s] - 2;
-    if (A.n <= 0) return true;
+    if (A.n <= 0) return 0;
     A.E = L.ne[s];
-    if (!line_block_supported(A.n, A.E) || L.N > (1LL << 31) - 1) return false;
+    if (!line_block_supported(A.n, A.E) || L.N > (1LL << 31) - 1) return -1;
     int o1, o2;
     if (s == 0) { o1 = 1; o2 = 2; } else if (s == 1) { o1 = 0; o2 = 2; } else { o1 = 0; o2 = 1; }
     const int strides[3] = {1, L.n[0], L.n[0] * L.n[1]};
     A.m1 = L.n[o1] - 2;
     const int m2 = L.dim == 3 ? L.n[o2] - 2 : 1;
     A.nlines = A.m1 * m2;
-    if (A.nlines <= 0) return true;
+    if (A.nlines <= 0) return 0;
     A.ntask = (long long)A.nlines * A.E;
     A.stride = strides[s];
     A.st1 = strides[o1];
@@ -418,6 +448,111 @@ bool launch_line_block(const DevLevel<T>& L, int s, int mode, const T* g, const 
     A.r = r;
     A.y = y;
     A.x = x;
+    A.done = nullptr;
+    return 1;
+}
+
+template <typename T, int P, int CV>
+bool launch_list_pc(const void* items, const int* start, int nitems, int blocks, int threads, size_t smem,
+                    cudaStream_t st) {
+    return launch_k(line_block_list_kernel<T, P, CV>, (unsigned)blocks, threads, smem, st,
+                    static_cast<const BlockLineArgs<T>*>(items), start, nitems) == cudaSuccess;
+}
+
+template <typename T, int P>
+bool launch_list_p(int cv, const void* items, const int* start, int nitems, int blocks, int threads, size_t smem,
+                   cudaStream_t st) {
+    if constexpr (P > 0) {
+        if (cv == 1) return launch_list_pc<T, P, 1>(items, start, nitems, blocks, threads, smem, st);
+        if (cv == 2) return launch_list_pc<T, P, 2>(items, start, nitems, blocks, threads, smem, st);
+        return launch_list_p<T, 0>(cv, items, start, nitems, blocks, threads, smem, st);
+    } else {
+        switch (cv) {
+            case 1: return launch_list_pc<T, 0, 1>(items, start, nitems, blocks, threads, smem, st);
+            case 2: return launch_list_pc<T, 0, 2>(items, start, nitems, blocks, threads, smem, st);
+            case 4: return launch_list_pc<T, 0, 4>(items, start, nitems, blocks, threads, smem, st);
+            default: return launch_list_pc<T, 0, 8>(items, start, nitems, blocks, threads, smem, st);
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+size_t line_block_item_bytes() {
+    return sizeof(BlockLineArgs<T>);
+}
+
+template <typename T>
+size_t line_block_item_done_offset() {
+    return offsetof(BlockLineArgs<T>, done);
+}
+
+// One work-list item: the line solve of L along s (as launch_line_block,
+// one right-hand side), written into `item` (line_block_item_bytes bytes);
+// its CTA count, block size, vertex chunk (cv, 1..8) and dynamic shared
+// memory for the order-specialised instance (smem[0]) and the run-time-order
+// instance (smem[1]).  Lines per CTA as for a single launch, without the
+// small-level split (a work-list launch has the CTAs of all its items).
+// 0: nothing to do; -1: unsupported.
+template <typename T>
+int line_block_list_item(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
+                         void* item, int* blocks, int* threads, size_t smem[2], int* cv) {
+    BlockLineArgs<T> A;
+    const int k = make_args<T>(A, L, s, mode, g, r, y, x, alpha, 1);
+    if (k <= 0) return k;
+    int lpc = std::min(kMaxLinesPerCta, std::max(1, kBlockThreads / A.E));
+    while (lpc > 1 && block_smem<T, 0>(lpc, A.span, A.E) > kMaxDynSmemBytes) lpc /= 2;
+    if (block_smem<T, 0>(lpc, A.span, A.E) > kMaxDynSmemBytes) return -1;
+    A.lpc = lpc;
+    smem[0] = block_smem<T, 2>(lpc, A.span, A.E);
+    smem[1] = block_smem<T, 0>(lpc, A.span, A.E);
+    *threads = std::min(kBlockThreads, std::max(32, (lpc * A.E + 31) / 32 * 32));
+    *blocks = (A.nlines + lpc - 1) / lpc;
+    *cv = A.cv;
+    std::memcpy(item, &A, sizeof(A));
+    return 1;
+}
+
+// Whether launch_line_block_list(p, cv, ...) runs the order-specialised
+// instance (smem[0] of the items) or the run-time-order one (smem[1]).
+bool line_block_list_specialised(int p, int cv) { return p >= 2 && p <= 8 && cv <= 2; }
+
+// One launch over the items (all of order p; cv: the largest vertex chunk of
+// the items).
+template <typename T>
+bool launch_line_block_list(int p, int cv, const void* items, const int* start, int nitems, int blocks, int threads,
+                            size_t smem, cudaStream_t st) {
+    if (nitems < 1 || blocks < 1) return true;
+    switch (line_block_list_specialised(p, cv) ? p : 0) {
+        case 2: return launch_list_p<T, 2>(cv, items, start, nitems, blocks, threads, smem, st);
+        case 3: return launch_list_p<T, 3>(cv, items, start, nitems, blocks, threads, smem, st);
+        case 4: return launch_list_p<T, 4>(cv, items, start, nitems, blocks, threads, smem, st);
+        case 5: return launch_list_p<T, 5>(cv, items, start, nitems, blocks, threads, smem, st);
+        case 6: return launch_list_p<T, 6>(cv, items, start, nitems, blocks, threads, smem, st);
+        case 7: return launch_list_p<T, 7>(cv, items, start, nitems, blocks, threads, smem, st);
+        case 8: return launch_list_p<T, 8>(cv, items, start, nitems, blocks, threads, smem, st);
+        default: return launch_list_p<T, 0>(cv, items, start, nitems, blocks, threads, smem, st);
+    }
+}
+
+template size_t line_block_item_bytes<float>();
+template size_t line_block_item_bytes<double>();
+template size_t line_block_item_done_offset<float>();
+template size_t line_block_item_done_offset<double>();
+template int line_block_list_item<float>(const DevLevel<float>&, int, int, const float*, const float*, float*, float*,
+                                         float, void*, int*, int*, size_t*, int*);
+template int line_block_list_item<double>(const DevLevel<double>&, int, int, const double*, const double*, double*,
+                                          double*, double, void*, int*, int*, size_t*, int*);
+template bool launch_line_block_list<float>(int, int, const void*, const int*, int, int, int, size_t, cudaStream_t);
+template bool launch_line_block_list<double>(int, int, const void*, const int*, int, int, int, size_t, cudaStream_t);
+
+template <typename T>
+bool launch_line_block(const DevLevel<T>& L, int s, int mode, const T* g, const T* r, T* y, T* x, T alpha,
+                       cudaStream_t st, int nrhs) {
+    BlockLineArgs<T> A;
+    const int k = make_args<T>(A, L, s, mode, g, r, y, x, alpha, nrhs);
+    if (k <= 0) return k == 0;
     switch (L.p) {
         case 2: return launch_p<T, 2>(A, st);
         case 3: return launch_p<T, 3>(A, st);

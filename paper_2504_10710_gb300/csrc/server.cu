@@ -70,7 +70,9 @@ struct MeshRec {
 struct Request {
     unsigned long long id = 0;
     glls_mesh_desc desc{};
-    std::vector<double> f, g;
+    std::vector<double> f, g;          // owned copies (glls_submit)
+    const double* fp = nullptr;        // the data read by the solve: the copies, or the
+    const double* gp = nullptr;        // caller's buffers (glls_submit_mesh)
     std::shared_ptr<const MeshRec> mesh;
     glls_solve_opts opts{};
     double* u = nullptr;
@@ -84,9 +86,11 @@ struct Request {
 };
 
 // One instance of a resident mesh: the problem that set it up, or a clone
-// sharing its mesh data with its own right-hand side and Krylov state.
+// sharing its mesh data with its own right-hand sides and Krylov state.
 struct Instance {
     glls_problem* prob = nullptr;
+    int nrhs = 1;                  // right-hand sides it solves together
+    size_t bytes = 0;              // device memory it owns alone
     bool busy = false;
 };
 
@@ -97,7 +101,7 @@ struct Cached {
     MeshKey key;
     std::list<Instance> inst;      // the set-up problem first, then clones
     size_t shared_bytes = 0;       // mesh data, held until the last instance goes
-    size_t instance_bytes = 0;     // what each instance owns alone
+    size_t instance_bytes = 0;     // what a one-right-hand-side instance owns alone
     int cloning = 0;               // clones being created (their bytes are reserved)
     Clock::time_point last_used;
     bool idle() const {
@@ -106,16 +110,29 @@ struct Cached {
             if (i.busy) return false;
         return true;
     }
-    size_t bytes() const { return shared_bytes + inst.size() * instance_bytes; }
+    size_t bytes() const {
+        size_t b = shared_bytes;
+        for (const auto& i : inst) b += i.bytes;
+        return b;
+    }
 };
 
-// What admit() hands a worker, decided under the server lock.
+// What admit() hands a worker, decided under the server lock: requests of
+// one mesh solved together (one, or a group sharing Dirichlet data and
+// options when grouping is on).
 struct Admission {
-    Request* r = nullptr;
+    std::vector<Request*> rs;
     Cached* mesh = nullptr;        // resident mesh (run or clone), or null (create)
     glls_problem* prob = nullptr;  // idle instance taken, or null
+    int nrhs = 1;                  // right-hand sides of the instance
     size_t reserve = 0;            // bytes reserved for a new mesh or clone
 };
+
+bool same_opts(const glls_solve_opts& a, const glls_solve_opts& b) {
+    return a.tol == b.tol && a.max_iter == b.max_iter && a.gamma == b.gamma && a.m == b.m && a.alpha == b.alpha &&
+           a.precision == b.precision && a.krylov == b.krylov && a.use_graph == b.use_graph &&
+           a.check_every == b.check_every;
+}
 
 }  // namespace
 
@@ -135,6 +152,8 @@ struct glls_server {
     std::vector<MeshKey> creating;   // meshes whose set-up is in progress
     std::unordered_map<unsigned long long, std::shared_ptr<const MeshRec>> meshes;   // registered
     unsigned long long next_mesh = 1;
+    int max_group = 1;               // requests solved together (1: no grouping)
+    unsigned long long grouped = 0;  // requests served by multi-right-hand-side solves
 
     bool pending_key(const MeshKey& k) const {
         for (const auto& c : creating)
@@ -178,23 +197,46 @@ struct glls_server {
     // the request waits for an instance while later requests go ahead); a new
     // mesh reserves its estimate, evicting idle meshes; the oldest new-mesh
     // request that does not fit waits for memory and holds back the rest.
+    // With grouping (max_group > 1), queued requests of a resident mesh that
+    // share its Dirichlet data and options are taken together, up to the
+    // largest power of two <= max_group available, and solved as one
+    // multi-right-hand-side solve on an instance of that size.
     bool admit(Admission* a) {
         for (auto it = queue.begin(); it != queue.end();) {
             Request* r = *it;
             Cached* c = find(r->key);
             if (c) {
-                for (auto& i : c->inst)
-                    if (!i.busy) {
-                        i.busy = true;
-                        *a = Admission{r, c, i.prob, 0};
-                        queue.erase(it);
-                        return true;
+                std::vector<std::deque<Request*>::iterator> grp{it};
+                if (max_group > 1 && r->opts.use_graph == 2 && r->opts.krylov != GLLS_KRYLOV_GMRES)
+                    for (auto jt = std::next(it); jt != queue.end() && (int)grp.size() < max_group; ++jt)
+                        if ((*jt)->key == r->key && (*jt)->gp == r->gp && same_opts((*jt)->opts, r->opts))
+                            grp.push_back(jt);
+                int g = 1;
+                while (2 * g <= (int)grp.size()) g *= 2;
+                for (; g >= 1; g /= 2) {
+                    Instance* idle = nullptr;
+                    for (auto& i : c->inst)
+                        if (!i.busy && i.nrhs == g) {
+                            idle = &i;
+                            break;
+                        }
+                    size_t need = 0;
+                    if (!idle) {
+                        need = c->instance_bytes * (size_t)g;
+                        if (!make_room(need, c)) continue;
+                        resident += need;
+                        ++c->cloning;
+                    } else {
+                        idle->busy = true;
                     }
-                if (make_room(c->instance_bytes, c)) {
-                    resident += c->instance_bytes;
-                    ++c->cloning;
-                    *a = Admission{r, c, nullptr, c->instance_bytes};
-                    queue.erase(it);
+                    *a = Admission{{}, c, idle ? idle->prob : nullptr, g, need};
+                    for (int k = 0; k < g; ++k) a->rs.push_back(*grp[k]);
+                    // one pass over the queue (erasing inside a deque invalidates its iterators)
+                    queue.erase(std::remove_if(queue.begin(), queue.end(),
+                                               [&](Request* q) {
+                                                   return std::find(a->rs.begin(), a->rs.end(), q) != a->rs.end();
+                                               }),
+                                queue.end());
                     return true;
                 }
                 ++it;
@@ -212,7 +254,7 @@ struct glls_server {
             if (!make_room(r->estimate, nullptr)) return false;
             resident += r->estimate;
             creating.push_back(r->key);
-            *a = Admission{r, nullptr, nullptr, r->estimate};
+            *a = Admission{{r}, nullptr, nullptr, 1, r->estimate};
             queue.erase(it);
             return true;
         }
@@ -223,26 +265,32 @@ struct glls_server {
         cudaSetDevice(device);
         cudaStream_t stream = nullptr;
         cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+        std::vector<double> F, U;                 // staging of a group's right-hand sides and solutions
+        std::vector<glls_stats> st_all;
         for (;;) {
             Admission a;
             {
                 std::unique_lock<std::mutex> lock(m);
                 cv_work.wait(lock, [&] { return stop || admit(&a); });
-                if (!a.r) break;
-                a.r->state = 1;
-                a.r->started = Clock::now();
-                ++running;
+                if (a.rs.empty()) break;
+                for (Request* q : a.rs) {
+                    q->state = 1;
+                    q->started = Clock::now();
+                }
+                running += a.rs.size();
             }
-            Request* r = a.r;
+            Request* r = a.rs.front();
+            const int g = (int)a.rs.size();
             Cached* mesh = a.mesh;
             glls_problem* prob = a.prob;
             glls_status st = GLLS_OK;
             double setup_ms = 0.0;
+            int setup_kind = prob ? 0 : mesh ? 2 : 1;
             if (!prob && mesh) {
-                // all instances of the resident mesh are busy: a clone shares its mesh data
+                // no idle instance of this size: a clone shares the mesh data
                 glls_problem* base = mesh->inst.front().prob;
                 auto t0 = Clock::now();
-                st = glls_problem_clone(base, &prob);
+                st = glls_problem_clone_nrhs(base, a.nrhs, &prob);
                 setup_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
                 std::lock_guard<std::mutex> lock(m);
                 --mesh->cloning;
@@ -252,9 +300,11 @@ struct glls_server {
                     glls_problem_info(prob, &inf);
                     Instance in;
                     in.prob = prob;
+                    in.nrhs = a.nrhs;
+                    in.bytes = inf.instance_bytes;
                     in.busy = true;
                     mesh->inst.push_back(in);
-                    resident += mesh->instance_bytes;
+                    resident += in.bytes;
                     ++clones;
                 }
             } else if (!prob) {
@@ -277,6 +327,7 @@ struct glls_server {
                     c.shared_bytes = inf.device_bytes - inf.instance_bytes;
                     Instance in;
                     in.prob = prob;
+                    in.bytes = inf.instance_bytes;
                     in.busy = true;
                     c.inst.push_back(in);
                     c.last_used = Clock::now();
@@ -287,10 +338,32 @@ struct glls_server {
             }
             // a new resident mesh or instance can admit waiting requests now
             if (!a.prob) cv_work.notify_all();
-            glls_stats stats{};
-            if (st == GLLS_OK) st = glls_set_rhs(prob, r->f.data(), 0, stream);
-            if (st == GLLS_OK && !r->g.empty()) st = glls_set_dirichlet(prob, r->g.data(), 0, stream);
-            if (st == GLLS_OK) st = glls_solve(prob, &r->opts, r->u, 0, stream, &stats);
+            st_all.assign(g, glls_stats{});
+            if (g == 1) {
+                if (st == GLLS_OK) st = glls_set_rhs(prob, r->fp, 0, stream);
+                if (st == GLLS_OK && r->gp) st = glls_set_dirichlet(prob, r->gp, 0, stream);
+                if (st == GLLS_OK) st = glls_solve(prob, &r->opts, r->u, 0, stream, st_all.data());
+                st_all[0].status = st;
+            } else {
+                const size_t N = (size_t)r->N;
+                try {
+                    F.resize(N * g);
+                    U.resize(N * g);
+                } catch (const std::bad_alloc&) {
+                    st = GLLS_ERR_OOM;
+                }
+                if (st == GLLS_OK) {
+                    for (int k = 0; k < g; ++k) std::memcpy(&F[N * k], a.rs[k]->fp, sizeof(double) * N);
+                    st = glls_set_rhs(prob, F.data(), 0, stream);
+                }
+                if (st == GLLS_OK && r->gp) st = glls_set_dirichlet(prob, r->gp, 0, stream);
+                if (st == GLLS_OK) {
+                    glls_solve(prob, &r->opts, U.data(), 0, stream, st_all.data());   // per-RHS status in st_all
+                    for (int k = 0; k < g; ++k) std::memcpy(a.rs[k]->u, &U[N * k], sizeof(double) * N);
+                } else {
+                    for (auto& x : st_all) x.status = st;
+                }
+            }
             {
                 std::lock_guard<std::mutex> lock(m);
                 if (mesh) {
@@ -298,15 +371,23 @@ struct glls_server {
                         if (i.prob == prob) i.busy = false;
                     mesh->last_used = Clock::now();
                 }
-                r->finished = Clock::now();
-                stats.setup_ms = setup_ms;
-                stats.solve_ms = std::chrono::duration<double, std::milli>(r->finished - r->submitted).count();
-                stats.status = st;
-                r->stats = stats;
-                r->status = st;
-                r->state = 2;
-                --running;
-                if (st == GLLS_OK) ++completed; else ++failed;
+                const auto done = Clock::now();
+                for (int k = 0; k < g; ++k) {
+                    Request* q = a.rs[k];
+                    glls_stats& s = st_all[k];
+                    q->finished = done;
+                    s.setup_ms = k == 0 ? setup_ms : 0.0;
+                    s.setup_kind = k == 0 ? setup_kind : 0;
+                    s.group = g;
+                    s.queue_ms = std::chrono::duration<double, std::milli>(q->started - q->submitted).count();
+                    s.solve_ms = std::chrono::duration<double, std::milli>(q->finished - q->submitted).count();
+                    q->stats = s;
+                    q->status = (glls_status)s.status;
+                    q->state = 2;
+                    if (s.status == GLLS_OK) ++completed; else ++failed;
+                }
+                running -= g;
+                grouped += g > 1 ? g : 0;
             }
             cv_done.notify_all();
             cv_work.notify_all();
@@ -366,13 +447,22 @@ static std::shared_ptr<MeshRec> make_mesh(glls_server* S, const glls_mesh_desc* 
     return m;
 }
 
+// copy = true: f and g are copied now; else the request reads the caller's
+// buffers when it runs.
 static glls_status enqueue(glls_server* S, std::shared_ptr<const MeshRec> m, const double* f, const double* g,
-                           const glls_solve_opts* opts, double* u, unsigned long long* ticket) {
+                           const glls_solve_opts* opts, double* u, unsigned long long* ticket, bool copy) {
     auto r = std::make_unique<Request>();
     r->mesh = m;
     r->N = m->N;
-    r->f.assign(f, f + m->N);
-    if (g) r->g.assign(g, g + m->N);
+    if (copy) {
+        r->f.assign(f, f + m->N);
+        if (g) r->g.assign(g, g + m->N);
+        r->fp = r->f.data();
+        r->gp = g ? r->g.data() : nullptr;
+    } else {
+        r->fp = f;
+        r->gp = g;
+    }
     r->desc = m->desc;
     r->opts = *opts;
     r->u = u;
@@ -402,7 +492,7 @@ glls_status glls_submit(glls_server* S, const glls_mesh_desc* mesh, const double
         return GLLS_ERR_OOM;
     }
     if (!m) return st;
-    return enqueue(S, m, f, g, opts, u, ticket);
+    return enqueue(S, m, f, g, opts, u, ticket, true);
 }
 
 glls_status glls_server_register(glls_server* S, const glls_mesh_desc* mesh, unsigned long long* mesh_id) {
@@ -432,7 +522,7 @@ glls_status glls_submit_mesh(glls_server* S, unsigned long long mesh_id, const d
         m = it->second;
     }
     try {
-        return enqueue(S, m, f, g, opts, u, ticket);
+        return enqueue(S, m, f, g, opts, u, ticket, false);
     } catch (const std::bad_alloc&) {
         return GLLS_ERR_OOM;
     }
@@ -454,6 +544,13 @@ glls_status glls_poll(glls_server* S, unsigned long long ticket, int wait, glls_
     return st;
 }
 
+glls_status glls_server_set_max_group(glls_server* S, int max_group) {
+    if (!S || max_group < 1 || max_group > 64) return GLLS_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(S->m);
+    S->max_group = max_group;
+    return GLLS_OK;
+}
+
 glls_status glls_server_info_get(glls_server* S, glls_server_info* out) {
     if (!S || !out) return GLLS_ERR_INVALID;
     std::lock_guard<std::mutex> lock(S->m);
@@ -469,6 +566,7 @@ glls_status glls_server_info_get(glls_server* S, glls_server_info* out) {
     int inst = 0;
     for (const auto& c : S->cache) inst += (int)c.inst.size();
     out->cached_instances = inst;
+    out->grouped = S->grouped;
     return GLLS_OK;
 }
 

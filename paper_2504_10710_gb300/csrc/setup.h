@@ -70,8 +70,12 @@ std::vector<double> interpolation(int p_from, int p_to);   // [(p_to+1) x (p_fro
 std::vector<int> order_chain(int p_fine, bool multi_element);
 
 // Builds all levels (index 0 = coarsest).  Returns "" on success or an error message.
+// phase_ms (optional, 4 entries) accumulates the wall time of the set-up
+// phases: coarse-level coordinates, geometry factors, line data (bands and
+// line blocks), transfers.
 std::string build_levels(int dim, const int nelem[3], int p_fine, const double* coords,
-                         int smoother, int restriction, std::vector<LevelHost>& levels);
+                         int smoother, int restriction, std::vector<LevelHost>& levels,
+                         double* phase_ms = nullptr);
 // coarse_solver: 0 automatic (block-CR depth from a cost model, 0 levels =
 // dense), 1 dense A_0^-1, 2 block CR with cr_levels levels (clamped to what
 // the block count allows; 0 = the model's depth, at least one level).

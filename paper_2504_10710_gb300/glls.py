@@ -38,21 +38,22 @@ class SolveOpts(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("setup_ms", C.c_double),
-                ("solve_ms", C.c_double), ("status", C.c_int), ("kernels", C.c_longlong)]
+                ("solve_ms", C.c_double), ("status", C.c_int), ("kernels", C.c_longlong),
+                ("queue_ms", C.c_double), ("setup_kind", C.c_int), ("group", C.c_int)]
 
 
 class Info(C.Structure):
     _fields_ = [("dim", C.c_int), ("levels", C.c_int), ("order", C.c_int * 8), ("nodes", (C.c_int * 3) * 8),
                 ("ndof", C.c_longlong * 8), ("coarse_unknowns", C.c_longlong), ("device_bytes", C.c_size_t),
                 ("coarse_cr_levels", C.c_int), ("coarse_dense_unknowns", C.c_longlong),
-                ("instance_bytes", C.c_size_t), ("nrhs", C.c_int)]
+                ("instance_bytes", C.c_size_t), ("nrhs", C.c_int), ("setup_phase_ms", C.c_double * 6)]
 
 
 class ServerInfo(C.Structure):
     _fields_ = [("submitted", C.c_ulonglong), ("completed", C.c_ulonglong), ("failed", C.c_ulonglong),
                 ("queued", C.c_ulonglong), ("running", C.c_ulonglong), ("resident_bytes", C.c_size_t),
                 ("budget_bytes", C.c_size_t), ("cached_problems", C.c_int), ("cached_instances", C.c_int),
-                ("clones", C.c_ulonglong)]
+                ("clones", C.c_ulonglong), ("grouped", C.c_ulonglong)]
 
 
 class GllsError(RuntimeError):
@@ -79,6 +80,9 @@ def lib():
             "glls_problem_create_nrhs": [C.POINTER(MeshDesc), i, C.POINTER(vp)],
             "glls_problem_info": [vp, C.POINTER(Info)],
             "glls_problem_clone": [vp, C.POINTER(vp)],
+            "glls_solve_batch_worklist": [C.POINTER(vp), i, C.POINTER(SolveOpts), C.POINTER(vp), i, vp,
+                                          C.POINTER(Stats)],
+            "glls_problem_clone_nrhs": [vp, C.c_int, C.POINTER(vp)],
             "glls_set_dirichlet": [vp, vp, i, vp],
             "glls_set_rhs": [vp, vp, i, vp],
             "glls_solve": [vp, C.POINTER(SolveOpts), vp, i, vp, C.POINTER(Stats)],
@@ -93,6 +97,7 @@ def lib():
             "glls_server_info_get": [vp, C.POINTER(ServerInfo)],
             "glls_cancel": [vp, C.c_ulonglong],
             "glls_server_register": [vp, C.POINTER(MeshDesc), C.POINTER(C.c_ulonglong)],
+            "glls_server_set_max_group": [vp, C.c_int],
             "glls_submit_mesh": [vp, C.c_ulonglong, vp, vp, C.POINTER(SolveOpts), vp, C.POINTER(C.c_ulonglong)],
             "glls_apply_partials_f64": [vp, i, vp, vp, vp, i, C.POINTER(i), vp],
         }
@@ -168,12 +173,14 @@ class Problem:
         self.info = self._info()
         self.N = int(self.info.ndof[self.info.levels - 1])
 
-    def clone(self):
-        """A problem on the same mesh sharing its read-only device data."""
+    def clone(self, nrhs=None):
+        """A problem on the same mesh sharing its read-only device data (with
+        nrhs right-hand sides; default: as this one)."""
         h = C.c_void_p()
-        _check(lib().glls_problem_clone(self.h, C.byref(h)))
+        nrhs = self.nrhs if nrhs is None else nrhs
+        _check(lib().glls_problem_clone_nrhs(self.h, nrhs, C.byref(h)))
         c = Problem.__new__(Problem)
-        c.h, c.dim, c._coords, c.nrhs = h, self.dim, self._coords, self.nrhs
+        c.h, c.dim, c._coords, c.nrhs = h, self.dim, self._coords, nrhs
         c.info = c._info()
         c.N = self.N
         return c
@@ -297,15 +304,18 @@ class Problem:
         _check(lib().glls_lift_f64(self.h, _ptr(f), _ptr(g), _ptr(f0), _stream(stream)))
 
 
-def solve_batch(problems, outs, o: SolveOpts, stream=None, raise_on_error=True):
+def solve_batch(problems, outs, o: SolveOpts, stream=None, raise_on_error=True, worklist=False):
     """Solve several problems in one graph launch; outs: numpy host arrays
-    (or torch CUDA float64 tensors), one per problem.  Returns the stats."""
+    (or torch CUDA float64 tensors), one per problem.  worklist=True: the
+    work-list kernels (glls_solve_batch_worklist), else one graph branch per
+    problem.  Returns the stats."""
     n = len(problems)
     hs = (C.c_void_p * n)(*[p.h.value for p in problems])
     on_device = 0 if isinstance(outs[0], np.ndarray) else 1
     ptrs = (C.c_void_p * n)(*[(o_.ctypes.data if on_device == 0 else o_.data_ptr()) for o_ in outs])
     st = (Stats * n)()
-    status = lib().glls_solve_batch(hs, n, C.byref(o), ptrs, on_device, _stream(stream), st)
+    fn = lib().glls_solve_batch_worklist if worklist else lib().glls_solve_batch
+    status = fn(hs, n, C.byref(o), ptrs, on_device, _stream(stream), st)
     if raise_on_error:
         _check(status)
     return list(st)
@@ -365,6 +375,10 @@ class Server:
         self._keep[t.value] = out          # the output buffer must outlive the request
         return t.value
 
+    def set_max_group(self, k):
+        """Solve up to k queued requests of one mesh together (see glls_server_set_max_group)."""
+        _check(lib().glls_server_set_max_group(self.h, k))
+
     def register(self, dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE):
         """Registers a mesh; returns its id for submit_mesh."""
         desc, coords = mesh_desc(dim, nelem, order, coords, smoother, restriction)
@@ -380,7 +394,7 @@ class Server:
         _check(lib().glls_submit_mesh(self.h, mesh_id, f.ctypes.data_as(C.c_void_p),
                                       None if g is None else g.ctypes.data_as(C.c_void_p), C.byref(o),
                                       out.ctypes.data_as(C.c_void_p), C.byref(t)))
-        self._keep[t.value] = out
+        self._keep[t.value] = (out, f, g)        # read by the request when it runs
         return t.value
 
     def poll(self, ticket, wait=False):

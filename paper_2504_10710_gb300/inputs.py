@@ -126,29 +126,71 @@ def identity_map(*X):
 # --------------------------------------------------------------------------
 # right-hand sides and Dirichlet data
 # --------------------------------------------------------------------------
+_CHUNK = 1 << 20
+
+
+def _sine_harmonics(t: np.ndarray, kmax: int, out: np.ndarray, tmp: np.ndarray) -> np.ndarray:
+    """out[k] = sin(pi k t) for k = 0..kmax by the recurrence
+    sin((k+1) a) = 2 cos(a) sin(k a) - sin((k-1) a), a = pi t (in place)."""
+    n = t.size
+    h = out[:, :n]
+    c2 = tmp[:n]
+    h[0] = 0.0
+    np.multiply(t, np.pi, out=c2)
+    np.sin(c2, out=h[1])
+    np.cos(c2, out=c2)
+    c2 *= 2.0
+    for k in range(2, kmax + 1):
+        np.multiply(c2, h[k - 1], out=h[k])
+        h[k] -= h[k - 2]
+    return h
+
+
+def _fourier_sum(coords, a, ks, kmax):
+    """sum_k a[k] prod_axis sin(pi ks[k, axis] x_axis), evaluated in chunks
+    of nodes with the sine harmonics of each coordinate tabulated once
+    (buffers reused across chunks)."""
+    shape = np.shape(coords[0])
+    flat = [np.ascontiguousarray(c, dtype=np.float64).reshape(-1) for c in coords]
+    out = np.empty(flat[0].size, dtype=np.float64)
+    ch = min(_CHUNK, max(1, out.size))
+    tabs = [np.empty((kmax + 1, ch)) for _ in flat]
+    tmp, term = np.empty(ch), np.empty(ch)
+    for s0 in range(0, out.size, ch):
+        n = min(out.size, s0 + ch) - s0
+        h = [_sine_harmonics(c[s0:s0 + n], kmax, tb, tmp) for c, tb in zip(flat, tabs)]
+        acc = out[s0:s0 + n]
+        acc[:] = 0.0
+        t = term[:n]
+        for k in range(len(a)):
+            np.multiply(h[0][ks[k][0]], a[k], out=t)
+            for ax in range(1, len(flat)):
+                t *= h[ax][ks[k][ax]]
+            acc += t
+    return out.reshape(shape)
+
+
 def fourier_rhs_2d(rng: np.random.Generator, nmodes: int = 16, kmax: int = 8):
+    """f = sum of nmodes products sin(pi m x) sin(pi n y), a ~ N(0, 1),
+    m, n ~ U{1..kmax}."""
     a = rng.standard_normal(nmodes)
     m = rng.integers(1, kmax + 1, nmodes)
     n = rng.integers(1, kmax + 1, nmodes)
+    ks = np.stack([m, n], axis=1)
 
     def f(x, y):
-        out = np.zeros_like(x, dtype=np.float64)
-        for k in range(nmodes):
-            out += a[k] * np.sin(np.pi * m[k] * x) * np.sin(np.pi * n[k] * y)
-        return out
+        return _fourier_sum((x, y), a, ks, kmax)
     return f, dict(a=a.tolist(), m=m.tolist(), n=n.tolist())
 
 
 def fourier_rhs_3d(rng: np.random.Generator, nmodes: int = 16, kmax: int = 8):
+    """f = sum of nmodes products sin(pi k1 x) sin(pi k2 y) sin(pi k3 z),
+    a ~ N(0, 1), k ~ U{1..kmax}^3."""
     a = rng.standard_normal(nmodes)
     ks = rng.integers(1, kmax + 1, (nmodes, 3))
 
     def f(x, y, z):
-        out = np.zeros_like(x, dtype=np.float64)
-        for k in range(nmodes):
-            out += (a[k] * np.sin(np.pi * ks[k, 0] * x) * np.sin(np.pi * ks[k, 1] * y)
-                    * np.sin(np.pi * ks[k, 2] * z))
-        return out
+        return _fourier_sum((x, y, z), a, ks, kmax)
     return f, dict(a=a.tolist(), k=ks.tolist())
 
 

@@ -274,3 +274,125 @@ def test_server_cancel_queued_request():
     assert not outs[2].any()
     assert srv.info().completed == 2
     srv.close()
+
+
+def test_server_registered_meshes_match_single_solves():
+    """Meshes registered once and solved by id (the request reads the caller's
+    f and g when it runs): results equal single solves; the first request on
+    a mesh reports its set-up (setup_kind 1), concurrent ones on the same
+    mesh a clone (2) or a resident instance (0); queue time is within the
+    latency."""
+    o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_MIXED)
+    wls = [MIX[0], MIX[3], MIX[2]]
+    reqs = [(wl,) + _request(wl) for wl in wls]
+    srv = glls.Server(budget_bytes=8 << 30, slots=3)
+    ids = [srv.register(wl.dim, wl.nelem, wl.order, c) for wl, c, _, _ in reqs]
+    assert len(set(ids)) == len(ids)
+    fs = {k: [f * (1.0 + 0.25 * j) for j in range(3)] for k, (_, _, f, _) in enumerate(reqs)}
+    outs, tickets = [], []
+    for j in range(3):
+        for k, (wl, c, f, g) in enumerate(reqs):
+            out = np.full(f.size, np.nan)
+            outs.append((k, j, out))
+            tickets.append(srv.submit_mesh(ids[k], fs[k][j], g, o, out))
+    kinds = {k: [] for k in range(len(reqs))}
+    for (k, j, _), t in zip(outs, tickets):
+        st, stats = srv.poll(t, wait=True)
+        assert st == glls.OK and stats.rel_residual <= 1e-10
+        assert 0.0 <= stats.queue_ms <= stats.solve_ms
+        kinds[k].append(stats.setup_kind)
+        if stats.setup_kind:
+            assert stats.setup_ms > 0.0
+    for k in kinds:
+        assert kinds[k].count(1) == 1 and set(kinds[k]) <= {0, 1, 2}
+    with pytest.raises(glls.GllsError):
+        srv.submit_mesh(987654, reqs[0][2], None, o, np.zeros(reqs[0][2].size))
+    srv.close()
+    for k, j, out in outs:
+        wl, c, _, g = reqs[k]
+        assert _rel(out, _alone(wl, c, fs[k][j], g, o)) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [glls.PREC_MIXED, glls.PREC_FP64], ids=["mixed", "fp64"])
+def test_server_groups_same_mesh_requests_into_one_multi_rhs_solve(prec):
+    """With grouping on, queued requests of one resident mesh with the same
+    Dirichlet data are solved together as one multi-right-hand-side solve
+    (group sizes are powers of two); each result equals its solve alone."""
+    o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=prec)
+    wl = MIX[1]
+    coords, f, g = _request(wl)
+    srv = glls.Server(budget_bytes=8 << 30, slots=1)
+    srv.set_max_group(4)
+    mid = srv.register(wl.dim, wl.nelem, wl.order, coords)
+    fs = [f * (1.0 + 0.3 * j) - 0.1 * j for j in range(7)]
+    outs = [np.full(f.size, np.nan) for _ in fs]
+    tickets = [srv.submit_mesh(mid, fk, g, o, out) for fk, out in zip(fs, outs)]
+    groups = []
+    for t in tickets:
+        st, stats = srv.poll(t, wait=True)
+        assert st == glls.OK and stats.rel_residual <= 1e-10
+        groups.append(stats.group)
+    inf = srv.info()
+    srv.close()
+    assert set(groups) <= {1, 2, 4} and max(groups) > 1, groups
+    assert inf.grouped == sum(1 for k in groups if k > 1)
+    for fk, out in zip(fs, outs):
+        assert _rel(out, _alone(wl, coords, fk, g, o)) < 1e-10
+
+
+# uneven 2-D problems: several order chains (8-4-2-1, 6-3-1, 5-2-1, 4-2-1),
+# two of them with more than one problem, ragged element counts
+WORKLIST = [inputs.random2d((9, 7), 6, amp=0.1, seed=61), inputs.random2d((16, 12), 8, amp=0.15, seed=62),
+            inputs.random2d((4, 5), 5, amp=0.05, seed=63), inputs.random2d((10, 6), 4, amp=0.1, seed=64),
+            inputs.random2d((6, 8), 6, amp=0.1, seed=65), inputs.random2d((21, 19), 8, amp=0.1, seed=66),
+            inputs.random2d((3, 2), 5, amp=0.1, seed=67)]
+
+
+@pytest.mark.parametrize("prec", [glls.PREC_FP64, glls.PREC_MIXED], ids=["fp64", "mixed"])
+def test_worklist_batch_equals_single_solves(prec):
+    """The work-list batch (one launch per step over all problems of an order
+    chain) gives each problem its single-solve result and iteration count;
+    a second call reuses the cached plan."""
+    o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=prec)
+    setups = [_setup(wl) for wl in WORKLIST]
+    probs = [s[0] for s in setups]
+    alone = []
+    for prob in probs:
+        u = np.zeros(prob.N)
+        st = prob.solve(u, o)
+        alone.append((u, st.iterations))
+    for rep in range(2):
+        outs = [np.full(p.N, np.nan) for p in probs]
+        stats = glls.solve_batch(probs, outs, o, worklist=True)
+        # FP64: the same kernels in the same order (up to the order of the
+        # seam atomics); mixed: FP32 rounding of the cycle, as between two
+        # single mixed solves
+        tol = 1e-12 if prec == glls.PREC_FP64 else 1e-8
+        for (u, its), out, st in zip(alone, outs, stats):
+            assert st.status == glls.OK and st.rel_residual <= 1e-10
+            assert abs(st.iterations - its) <= 1
+            assert _rel(out, u) < tol
+        assert stats[0].kernels > 0
+    for p in probs:
+        p.close()
+
+
+def test_worklist_batch_device_outputs_and_refusals():
+    o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_MIXED)
+    probs = [_setup(wl)[0] for wl in WORKLIST[:3]]
+    outs = [torch.zeros(p.N, dtype=torch.float64, device="cuda") for p in probs]
+    stats = glls.solve_batch(probs, outs, o, worklist=True)
+    for p, out, st in zip(probs, outs, stats):
+        u = np.zeros(p.N)
+        p.solve(u, o)
+        assert st.status == glls.OK and _rel(out.cpu().numpy(), u) < 1e-8
+    # 3-D problems and GMRES are refused (the graph-branch batch takes them)
+    p3 = _setup(inputs.random3d((3, 3, 2), 4, amp=0.1, seed=24))[0]
+    with pytest.raises(glls.GllsError) as ei:
+        glls.solve_batch([probs[0], p3], [np.zeros(probs[0].N), np.zeros(p3.N)], o, worklist=True)
+    assert ei.value.status == glls.ERR_INVALID
+    with pytest.raises(glls.GllsError):
+        glls.solve_batch(probs, [np.zeros(p.N) for p in probs],
+                         glls.opts(tol=1e-10, krylov=glls.KRYLOV_GMRES), worklist=True)
+    for p in probs + [p3]:
+        p.close()
