@@ -62,7 +62,7 @@ def parse():
                     help="as --profile, on the 3-D 16^3 p = 7 workload with one right-hand side")
     ap.add_argument("--serving-only", action="store_true",
                     help="only the serving-stream measurement (prints its JSON object)")
-    ap.add_argument("--probe", choices=["line2d", "line3d", "apply64", "setup"],
+    ap.add_argument("--probe", choices=["line2d", "line3d", "apply64", "setup", "apply3d_multi"],
                     help="launch one kernel a few times on its workload, nothing else (small ncu captures): "
                          "line2d / line3d = the fine-level FP32 line update (MODE 1) of every axis after one "
                          "apply, on the 2-D bench workload / the 3-D 16^3 p = 7 workload; apply64 = the 2-D "
@@ -804,6 +804,25 @@ def probe(name, reps=3):
     import __graft_entry__
     from paper_2504_10710_gb300 import glls, inputs
     __graft_entry__.build()
+    if name == "apply3d_multi":
+        # the 3-D fine-level FP32 apply for 32 stacked vectors (geometry read
+        # once per launch), then for one vector
+        wl = inputs.terrain3d(nrhs=1)
+        prob, _ = glls.problem_for(wl, glls.SMOOTHER_GLL)
+        L = prob.levels - 1
+        shape = prob.level_shape(L)
+        k = 32
+        xs = torch.cat([_interior_random(torch, shape, torch.float32) for _ in range(k)])
+        ys = torch.zeros_like(xs)
+        for _ in range(reps):
+            prob.apply_multi(L, xs, ys, k)
+        x1, y1 = xs[:xs.numel() // k].clone(), torch.zeros(xs.numel() // k, dtype=torch.float32, device="cuda")
+        for _ in range(reps):
+            prob.apply(L, x1, y1)
+        torch.cuda.synchronize()
+        print(json.dumps({"probe": name, "workload": wl.name, "nrhs": k, "reps": reps}))
+        prob.close()
+        return
     if name == "setup":
         meshes, _ = inputs.serving_stream(nreq=10)
         wls = [inputs.terrain2d(), inputs.terrain3d(nrhs=1)] + [w for w in meshes if w.dim == 3]

@@ -314,6 +314,12 @@ glls_status glls_apply_partials_f64(glls_problem* prob, int level, const double*
                                     int capacity, int* count, void* stream);
 glls_status glls_apply_f64(glls_problem* prob, int level, const double* x, double* y, void* stream);
 glls_status glls_apply_f32(glls_problem* prob, int level, const float* x, float* y, void* stream);
+/* y = A_l x for nrhs vectors at once (x, y: nrhs x N_l values, vector j at
+ * j N_l), in one launch with the vector fastest in the CTA order, so the
+ * geometry factors of each element are read from HBM once for all nrhs
+ * (the multi-right-hand-side apply of the solve). */
+glls_status glls_apply_multi_f64(glls_problem* prob, int level, const double* x, double* y, int nrhs, void* stream);
+glls_status glls_apply_multi_f32(glls_problem* prob, int level, const float* x, float* y, int nrhs, void* stream);
 
 /* x = B_s^-1 g: every interior grid line along axis s solved by cyclic
  * reduction (Def. 3.2, Cor. 3.9); x is written on interior nodes only.  The

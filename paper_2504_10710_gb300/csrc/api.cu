@@ -2050,6 +2050,17 @@ glls_status glls_apply_partials_f64(glls_problem* P, int level, const double* x,
 }
 
 #define LEVEL_OPS(SUF, T)                                                                                      \
+    glls_status glls_apply_multi_##SUF(glls_problem* P, int level, const T* x, T* y, int nrhs, void* stream) {  \
+        glls_status s = check_level(P, level, false);                                                           \
+        if (s != GLLS_OK) return s;                                                                             \
+        if (!x || !y || nrhs < 1 || nrhs > 4096) return fail(GLLS_ERR_INVALID, "null vector or bad nrhs");      \
+        DeviceScope scope(P->device);                                                                           \
+        CK(scope.err);                                                                                          \
+        CK(launch_apply<T>(levels_of<T>(P)[level].dev, x, y, true, (cudaStream_t)stream, false, nullptr,        \
+                           nullptr, nullptr, nrhs));                                                            \
+        CK(cudaGetLastError());                                                                                 \
+        return GLLS_OK;                                                                                         \
+    }                                                                                                           \
     glls_status glls_apply_##SUF(glls_problem* P, int level, const T* x, T* y, void* stream) {                  \
         glls_status s = check_level(P, level, false);                                                           \
         if (s != GLLS_OK) return s;                                                                             \

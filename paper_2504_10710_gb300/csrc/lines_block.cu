@@ -70,6 +70,18 @@ int sm_count() {
 // shared-memory index with one pad word per 32
 __device__ __forceinline__ int padk(int k) { return k + (k >> 5); }
 
+// Asynchronous global -> shared copy of one value (cp.async, no register
+// held while it is in flight), and the wait for all of this thread's copies.
+template <typename T>
+__device__ __forceinline__ void cp_async(T* sdst, const T* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Vertex system of one line (E - 1 unknowns; vertex k is line unknown
 // (k + 1) p - 1), right-hand side c_k = g_v - dr[k] - dl[k + 1], operator
 // from shared memory (vb: diagonal and coupling to the next vertex per
@@ -135,7 +147,8 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
     const long long ntask = A.ntask;
     T* sg = reinterpret_cast<T*>(smem_raw);   // [LPC][span]: g, then z / nu, then B^-1 g
     T* sx = sg + LPC * span;                  // [LPC][span]: x on entry (MODE 1, 2)
-    T* sdl = sx + LPC * span;                 // [LPC][E]: w_L . g_I per segment
+    T* sy = sx + LPC * span;                  // [LPC][span]: y on entry (MODE 1)
+    T* sdl = sy + LPC * span;                 // [LPC][E]: w_L . g_I per segment
     T* sdr = sdl + LPC * E;                   // [LPC][E]: w_R . g_I
     T* svb = sdr + LPC * E;                   // [LPC][2 (E - 1)]: vertex systems
     T* sz = svb + 2 * LPC * (E - 1);          // [LPC][span]: z accumulation (P = 0)
@@ -164,10 +177,11 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
             }
         }
     }
-    // line values, staged without divisions: x-lines are walked along the
-    // line by whole warps (coalesced along x); strided directions by threads
-    // that each keep one line of the CTA and step over its rows, adjacent
-    // threads on adjacent lines (coalesced across the lines)
+    // line values, staged without divisions by asynchronous copies (every
+    // copy of the tile in flight at once): x-lines are walked along the line
+    // by whole warps (coalesced along x); strided directions by threads that
+    // each keep one line of the CTA and step over its rows, adjacent threads
+    // on adjacent lines (coalesced across the lines)
     const bool contig = A.contiguous != 0;
     const int nthr = blockDim.x, nwarp = nthr >> 5;
     const int rows_per_pass = nthr / LPC;     // strided: rows covered per pass
@@ -175,12 +189,10 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
     const bool s_active = !contig && sw < Wc && sk0 < rows_per_pass;
     const int s_base = s_active ? line_base(sw) : 0;
     auto stage = [&](int w, int k, int node) {
-        T v;
-        if (mode == 0) v = A.g[node];
-        else if (mode == 1) v = A.r[node] - A.y[node];
-        else v = A.r[node];
-        sg[w * span + padk(k)] = v;
-        if (mode == 1 || mode == 2) sx[w * span + padk(k)] = A.x[node];
+        const int o = w * span + padk(k);
+        cp_async(sg + o, (mode == 0 ? A.g : A.r) + node);
+        if (mode == 1) cp_async(sy + o, A.y + node);
+        if (mode == 1 || mode == 2) cp_async(sx + o, A.x + node);
     };
     if (contig) {
         for (int w = tid >> 5; w < Wc; w += nwarp) {
@@ -196,9 +208,14 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
     if (E > 1) {
         const T* vsrc = reinterpret_cast<const T*>(A.vband + (long long)l0 * (E - 1));
         const int nvb = 2 * Wc * (E - 1);
-        for (int i = tid; i < nvb; i += nthr) svb[i] = __ldg(vsrc + i);
+        for (int i = tid; i < nvb; i += nthr) cp_async(svb + i, vsrc + i);
     }
+    cp_async_wait_all();
     __syncthreads();
+    if (mode == 1) {          // g = r - y (pad slots hold unused values)
+        for (int i = tid; i < Wc * span; i += nthr) sg[i] -= sy[i];
+        __syncthreads();
+    }
 
     // ---- segments: z = K_I^-1 g_I and the two vertex dots
     T z[SegOp<T, P>::MI];
@@ -336,7 +353,7 @@ __global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 ||
 
 template <typename T, int P>
 size_t block_smem(int lpc, int span, int E) {
-    return sizeof(T) * ((size_t)lpc * span * (P == 0 ? 3 : 2) + 2 * (size_t)lpc * E + 2 * (size_t)lpc * (E - 1));
+    return sizeof(T) * ((size_t)lpc * span * (P == 0 ? 4 : 3) + 2 * (size_t)lpc * E + 2 * (size_t)lpc * (E - 1));
 }
 
 // Orders 2..8 are compiled for vertex chunks of 1 and 2 per lane (lines of up

@@ -103,6 +103,7 @@ def lib():
         }
         for suf, real in (("f64", d), ("f32", C.c_float)):
             sig[f"glls_apply_{suf}"] = [vp, i, vp, vp, vp]
+            sig[f"glls_apply_multi_{suf}"] = [vp, i, vp, vp, i, vp]
             sig[f"glls_line_solve_{suf}"] = [vp, i, i, vp, vp, vp]
             sig[f"glls_smooth_{suf}"] = [vp, i, i, real, vp, vp, vp]
             sig[f"glls_line_update_{suf}"] = [vp, i, i, real, vp, vp, vp, vp]
@@ -262,6 +263,11 @@ class Problem:
 
     def apply(self, level, x, y, stream=None):
         _check(getattr(lib(), f"glls_apply_{self._suffix(x)}")(self.h, level, _ptr(x), _ptr(y), _stream(stream)))
+
+    def apply_multi(self, level, x, y, nrhs, stream=None):
+        """y = A_l x for nrhs stacked vectors in one launch."""
+        _check(getattr(lib(), f"glls_apply_multi_{self._suffix(x)}")(self.h, level, _ptr(x), _ptr(y), nrhs,
+                                                                      _stream(stream)))
 
     def apply_partials(self, level, x, y, partials, stream=None):
         """FP64 y += A x with the fused per-CTA x.(A x) partials (y zero on

@@ -155,3 +155,27 @@ def test_terrain3d_full_size_32_rhs_in_one_problem():
         res = np.linalg.norm((f0 - fine.apply(w))[fine.interior]) / np.linalg.norm(f0[fine.interior])
         assert res <= 2e-10, (j, res)
     prob.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("dims", [((5, 4), 8), ((3, 3, 2), 7), ((4, 3, 2), 3)], ids=["2d_p8", "3d_p7", "3d_p3"])
+def test_apply_multi_equals_single_applies(dtype, dims):
+    """glls_apply_multi on k stacked vectors (one launch, the operator read
+    once) equals k single applies, every level."""
+    nelem, p = dims
+    wl = inputs.random2d(nelem, p, amp=0.1, seed=41) if len(nelem) == 2 else inputs.random3d(nelem, p, seed=41)
+    prob, _ = glls.problem_for(wl)
+    k = 5
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    for level in range(prob.levels):
+        n = int(np.prod(prob.level_shape(level)))
+        X = torch.randn(k * n, dtype=dtype, device="cuda", generator=gen)
+        Y = torch.zeros_like(X)
+        prob.apply_multi(level, X, Y, k)
+        for j in range(k):
+            y1 = torch.zeros(n, dtype=dtype, device="cuda")
+            prob.apply(level, X[j * n:(j + 1) * n].contiguous(), y1)
+            scale = float(y1.abs().max())
+            tol = 1e-13 if dtype == torch.float64 else 2e-6
+            assert float((Y[j * n:(j + 1) * n] - y1).abs().max()) <= tol * scale
+    prob.close()
