@@ -99,22 +99,19 @@ __device__ __forceinline__ void apply_p_body(const DevLevel<T>& L, const T* __re
             for (int c = 0; c < NC; ++c) gk[it][c] = __ldg(L.G + c * EN + gq);
         }
     }
-    // the x gather in the same round trip as G: each thread derives its
-    // element's first node itself instead of waiting for sbase
+    for (int t = threadIdx.x; t < N1 * N1; t += 256) {
+        sD[t] = L.D[t];
+        if constexpr (VEC) sDT[t] = L.D[(t % N1) * N1 + t / N1];
+    }
+    __syncthreads();
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
         const int t = threadIdx.x + 256 * it;
         if (t < total) {
             const int el = t / NLOC, q = t - el * NLOC;
-            const int e = e0 + el, ne0 = L.ne[0], ne1 = L.ne[1];
-            const int ex = e % ne0, ey = (e / ne0) % ne1, ez = DIM == 3 ? e / (ne0 * ne1) : 0;
             const int i = q % N1, j = (q / N1) % N1, k = DIM == 3 ? q / (N1 * N1) : 0;
-            sx[t] = x[((ez * P) * n1 + ey * P) * n0 + ex * P + (k * n1 + j) * n0 + i];
+            sx[t] = x[sbase[el] + (k * n1 + j) * n0 + i];
         }
-    }
-    for (int t = threadIdx.x; t < N1 * N1; t += 256) {
-        sD[t] = L.D[t];
-        if constexpr (VEC) sDT[t] = L.D[(t % N1) * N1 + t / N1];
     }
     __syncthreads();
 

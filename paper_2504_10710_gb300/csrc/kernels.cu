@@ -326,9 +326,10 @@ __device__ __forceinline__ void coarse_body(long long n, long long ld, const lon
     using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
     // each lane keeps U row chunks in flight (independent loads and partial
     // sums), so a row costs about one memory latency instead of one per chunk
-    constexpr int U = 8;
+    constexpr int U = sizeof(T) == 4 ? 16 : 8;
     const long long nvec = ld / V;
     for (long long row = bx * wpb + warp; row < n; row += nbx * wpb) {
+        const long long out = lane == 0 ? index[reduced_pos(row, m, H)] : 0;   // in flight with the row
         const Vec* a = reinterpret_cast<const Vec*>(inv + row * ld);
         T part[U];
 #pragma unroll
@@ -354,7 +355,7 @@ __device__ __forceinline__ void coarse_body(long long n, long long ld, const lon
 #pragma unroll
         for (int u = 0; u < U; ++u) s += part[u];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) e[index[reduced_pos(row, m, H)]] = s;
+        if (lane == 0) e[out] = s;
     }
 }
 
@@ -710,7 +711,17 @@ constexpr int kVecU = 4;
 // valid in thread 0.
 __device__ __forceinline__ double sum_partials(const double* part, int n, double* red) {
     double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(part + i);
+    int i = threadIdx.x;
+    const int b = blockDim.x;
+    for (; i + 3 * b < n; i += 4 * b) {      // four loads in flight, added in the same order
+        const double a0 = __ldcg(part + i), a1 = __ldcg(part + i + b), a2 = __ldcg(part + i + 2 * b),
+                     a3 = __ldcg(part + i + 3 * b);
+        s += a0;
+        s += a1;
+        s += a2;
+        s += a3;
+    }
+    for (; i < n; i += b) s += __ldcg(part + i);
     return block_sum(s, red);
 }
 
@@ -776,19 +787,10 @@ __device__ __forceinline__ void fcg_update_body(double* __restrict__ x, double* 
     const bool active = S[S_DONE] == 0.0;
     __shared__ double red[32];
     __shared__ double sh[3];
-    const double pq = sum_partials(ppq, npq, red);
-    const double rz = sum_partials(prz, nrz, red);
-    if (threadIdx.x == 0) {
-        sh[0] = rz / pq;                    // FP64 division once per block
-        sh[1] = pq;
-        sh[2] = rz;
-    }
-    __syncthreads();
-    const double alpha = sh[0];
-    double s = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; active && i0 < n; i0 += kVecU * stride) {
-        double xv[kVecU], rv[kVecU], pv[kVecU], qv[kVecU];
+    const long long ifirst = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double xv[kVecU], rv[kVecU], pv[kVecU], qv[kVecU];
+    auto load = [&](long long i0) {
 #pragma unroll
         for (int u = 0; u < kVecU; ++u) {
             const long long i = i0 + u * stride;
@@ -800,6 +802,21 @@ __device__ __forceinline__ void fcg_update_body(double* __restrict__ x, double* 
                 qv[u] = q[i];
             }
         }
+    };
+    // the first trip's vectors are in flight while the partials are summed
+    if (active) load(ifirst);
+    const double pq = sum_partials(ppq, npq, red);
+    const double rz = sum_partials(prz, nrz, red);
+    if (threadIdx.x == 0) {
+        sh[0] = rz / pq;                    // FP64 division once per block
+        sh[1] = pq;
+        sh[2] = rz;
+    }
+    __syncthreads();
+    const double alpha = sh[0];
+    double s = 0.0;
+    for (long long i0 = ifirst; active && i0 < n; i0 += kVecU * stride) {
+        if (i0 != ifirst) load(i0);
 #pragma unroll
         for (int u = 0; u < kVecU; ++u) {
             const long long i = i0 + u * stride;
@@ -848,14 +865,10 @@ __device__ __forceinline__ void fcg_direction_body(double* __restrict__ p, const
     if (S[S_DONE] != 0.0) return;           // stopped: p is no longer used
     __shared__ double red[32];
     __shared__ double sh_beta;
-    const double rz_new = sum_partials(prz, nd, red);
-    const double zq = sum_partials(pzq, nd, red);
-    if (threadIdx.x == 0) sh_beta = flexible ? -S[S_ALPHA] * zq / S[S_RZ] : rz_new / S[S_RZ];
-    __syncthreads();
-    const double beta = sh_beta;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += kVecU * stride) {
-        double zv[kVecU], pv[kVecU];
+    const long long ifirst = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double zv[kVecU], pv[kVecU];
+    auto load = [&](long long i0) {
 #pragma unroll
         for (int u = 0; u < kVecU; ++u) {
             const long long i = i0 + u * stride;
@@ -865,6 +878,15 @@ __device__ __forceinline__ void fcg_direction_body(double* __restrict__ p, const
                 pv[u] = p[i];
             }
         }
+    };
+    load(ifirst);      // in flight while the partials are summed
+    const double rz_new = sum_partials(prz, nd, red);
+    const double zq = sum_partials(pzq, nd, red);
+    if (threadIdx.x == 0) sh_beta = flexible ? -S[S_ALPHA] * zq / S[S_RZ] : rz_new / S[S_RZ];
+    __syncthreads();
+    const double beta = sh_beta;
+    for (long long i0 = ifirst; i0 < n; i0 += kVecU * stride) {
+        if (i0 != ifirst) load(i0);
 #pragma unroll
         for (int u = 0; u < kVecU; ++u) {
             const long long i = i0 + u * stride;

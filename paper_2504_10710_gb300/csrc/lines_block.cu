@@ -27,6 +27,7 @@
 // compile-time order (2..8); P = 0 takes the order at run time, reads its
 // operator from global memory inside the loops and accumulates K_I^-1 g_I in
 // shared memory.
+#include "async_copy.cuh"
 #include "cr_warp.cuh"
 #include "device.cuh"
 
@@ -70,17 +71,7 @@ int sm_count() {
 // shared-memory index with one pad word per 32
 __device__ __forceinline__ int padk(int k) { return k + (k >> 5); }
 
-// Asynchronous global -> shared copy of one value (cp.async, no register
-// held while it is in flight), and the wait for all of this thread's copies.
-template <typename T>
-__device__ __forceinline__ void cp_async(T* sdst, const T* gsrc) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-    if constexpr (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 
 // Vertex system of one line (E - 1 unknowns; vertex k is line unknown
 // (k + 1) p - 1), right-hand side c_k = g_v - dr[k] - dl[k + 1], operator
