@@ -110,7 +110,7 @@ __device__ __forceinline__ bool on_bd(int I, int J, int K, const int n[3]) {
 // small levels still spread over many CTAs per SM.  Two resident CTAs per SM
 // bound the registers (at most 128 per thread).
 template <typename T, int P, bool DOT>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     apply_eo3_kernel(DevLevel<T> L, const __grid_constant__ EoParams<T, P + 1> M, const T* __restrict__ x,
                      T* __restrict__ y, int mask, double* dot, double* part, unsigned* ticket, int epb, int nrhs) {
     using S = EoShape<T, P + 1>;
