@@ -151,8 +151,8 @@ def run_ours(args, rank, world):
     prob.set_dirichlet(g_d, stream)
     tiles = prob.autotune()          # line-solve tiles per level / precision / direction (set-up, untimed)
     if args.roofline_only:
-        print(json.dumps({"roofline": line_roofline(prob, glls, torch),
-                          "roofline_fp64_apply": fp64_apply_roofline(prob, glls, torch),
+        print(json.dumps({"roofline": fp64_apply_roofline(prob, glls, torch),
+                          "roofline_line_update": line_roofline(prob, glls, torch),
                           "roofline_hbm": smoother_rooflines(prob, glls, torch, inputs, flush)}))
         sys.exit(0)
     kernels = [0]
@@ -249,8 +249,8 @@ def run_ours(args, rank, world):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)), "n": int(lat.size),
                        "what": "end to end through glls_set_rhs/set_dirichlet/solve with host buffers"},
         "clocks": clk,
-        "roofline": roof,
-        "roofline_fp64_apply": roof64,
+        "roofline": roof64,
+        "roofline_line_update": roof,
         "roofline_hbm": roof_hbm,
         "gpu_launches": int(launches),
         "line_tiles": {f"l{l}_{pn}_ax{a}": c for (l, pn, a), (c, _us) in sorted(tiles.items()) if pn == "f32"},
@@ -353,9 +353,10 @@ def _fp64_peak_gflops(torch):
 
 
 def fp64_apply_roofline(prob, glls, torch):
-    """The FP64 fine-level stiffness apply of the outer iteration, in the
-    form the solve launches it: y = A p with the per-CTA partials of p.(A p)
-    fused (flexible CG's p.Ap).  FP64-ALU bound.  FLOPs per launch from the
+    """The bench workload's top kernel in the ncu launch list (13 % of the
+    solve): the FP64 fine-level stiffness apply of the outer iteration, in
+    the form the solve launches it: y = A p with the per-CTA partials of
+    p.(A p) fused (flexible CG's p.Ap).  FP64-ALU bound.  FLOPs per launch from the
     sum-factorised algorithm: per element 4 (p+1)^3 FMA for the four 1-D
     contraction sweeps and 4 (p+1)^2 for the geometric factors, plus 2 (p+1)^2
     for the dot, 2 FLOP per FMA."""
@@ -381,7 +382,7 @@ def fp64_apply_roofline(prob, glls, torch):
 
 
 def line_roofline(prob, glls, torch):
-    """The bench workload's top kernel in the ncu launch list: the FP32 line
+    """The bench workload's second kernel in the ncu launch list: the FP32 line
     update of the fine level (line_block_kernel<float, 8>, MODE 1: x += alpha
     B_s^-1 (r - y) after y = A x), timed as the solve launches it, by graph
     replay (the level stays L2-resident, as inside a solve).  Algorithmic
