@@ -230,6 +230,7 @@ def run_ours(args, rank, world):
                                                          "latency_ms", "latency_resident_ms", "service_ms",
                                                          "grouping")}
     batch = batch_run(glls, inputs, torch) if not args.no_batch else None
+    smoothers = smoother_compare(glls, inputs, torch)
     multirhs = multirhs_run(glls, inputs, torch) if not args.no_batch else None
 
     # whole-job throughput: all ranks' DOF over the slowest rank's time
@@ -249,6 +250,7 @@ def run_ours(args, rank, world):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)), "n": int(lat.size),
                        "what": "end to end through glls_set_rhs/set_dirichlet/solve with host buffers"},
         "clocks": clk,
+        "smoothers": smoothers,
         "roofline": roof64,
         "roofline_line_update": roof,
         "roofline_hbm": roof_hbm,
@@ -497,6 +499,40 @@ def smoother_rooflines(prob, glls, torch, inputs, flush, large=True):
         if pb is not prob:
             pb.close()
     return {"peak_source": src, "kernels": out}
+
+
+def smoother_compare(glls, inputs, torch, reps=10):
+    """The bench workload (2-D 64x64, p = 8) with each line smoother the
+    library offers, mixed precision, gamma = 1, to 1e-10: the Def. 3.2 line
+    blocks at the paper's alpha = 2/3 (the default), the band-1 part of the
+    GLL line systems at alpha = 0.5 (the largest that converges on this
+    deformed grid) and the FEM line systems at the paper's alpha = 0.16.
+    Iterations and CUDA-event time per solve (outputs on the device)."""
+    wl = inputs.terrain2d()
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, sm, alpha in (("gll_line_blocks", glls.SMOOTHER_GLL, 2.0 / 3.0),
+                            ("gll_band1", glls.SMOOTHER_GLL_BAND1, 0.5),
+                            ("fem", glls.SMOOTHER_FEM, 0.16)):
+        prob, coords = glls.problem_for(wl, sm, glls.RESTRICT_TRANSPOSE)
+        prob.set_rhs(wl.sample_rhs(coords)[0])
+        prob.set_dirichlet(wl.sample_dirichlet(coords))
+        u = torch.zeros(prob.N, dtype=torch.float64, device="cuda")
+        o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=alpha, precision=glls.PREC_MIXED, max_iter=300)
+        for _ in range(3):
+            st = prob.solve(u, o, stream, raise_on_error=False)
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = prob.solve(u, o, stream, raise_on_error=False)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        out[name] = {"alpha": alpha, "iterations": int(st.iterations), "converged": st.status == glls.OK,
+                     "ms_per_solve": float(np.median(ms)), "dof_per_s": prob.N / (float(np.median(ms)) / 1e3)}
+        prob.close()
+    return out
 
 
 def multirhs_run(glls, inputs, torch, reps=3):

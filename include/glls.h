@@ -224,9 +224,12 @@ glls_status glls_solve_batch_worklist(glls_problem* const* probs, int n, const g
                                       double* const* u, int on_device, void* stream, glls_stats* stats);
 
 /* Autotuner: for every level >= 1, precision and direction, time the line
- * solve with 2, 4, 8 and (FP32 only) 16 lines per CTA on the problem's own
- * data and keep the fastest.  chosen / best_us (optional): levels x 2 (FP32, FP64) x 3 entries,
- * index (level * 2 + precision) * 3 + axis, the chosen tile and its time in
+ * solve on the problem's own data with each candidate number of lines per
+ * CTA and keep the fastest: for the Def. 3.2 line blocks (GLL smoother)
+ * 1, 2, 4, 8, 16 (at most 256 element segments per CTA) or 0, the launch
+ * heuristic; for the band-1 and FEM line kernels 2, 4, 8 and (FP32 only) 16.
+ * chosen / best_us (optional): levels x 2 (FP32, FP64) x 3 entries,
+ * index (level * 2 + precision) * 3 + axis, the chosen value and its time in
  * microseconds per launch.  Cached graphs are rebuilt on the next solve.
  * Synchronous. */
 glls_status glls_autotune(glls_problem* prob, int* chosen, float* best_us);

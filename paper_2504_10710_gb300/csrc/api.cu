@@ -704,16 +704,22 @@ glls_status tune_levels(glls_problem* P, std::vector<LevelStore<T>>& Ls, int pre
     cudaEvent_t a = nullptr, b = nullptr;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));
-    // lines per CTA: 16 only in FP32 (launch_line_warp falls back to 8 otherwise)
+    // band-1 lines per CTA: 16 only in FP32 (launch_line_warp falls back to 8
+    // otherwise); line blocks: the launch heuristic (0) or 1..16 lines, at
+    // most 256 segment tasks per CTA
     const int cand[4] = {2, 4, 8, 16};
     const int ncand = sizeof(T) == 4 ? 4 : 3;
+    const int bcand[6] = {0, 1, 2, 4, 8, 16};
     for (size_t l = 1; l < Ls.size(); ++l)
         for (int s = 0; s < Ls[l].dev.dim; ++s) {
             float best = 1e30f;
-            int pick = 4;
-            for (int ci = 0; ci < ncand; ++ci) {
-                const int c = cand[ci];
-                Ls[l].dev.lpb[s] = c;
+            const bool blocks = Ls[l].dev.blk[s] != nullptr;
+            int pick = blocks ? 0 : 4;
+            for (int ci = 0; ci < (blocks ? 6 : ncand); ++ci) {
+                const int c = blocks ? bcand[ci] : cand[ci];
+                if (blocks && c * Ls[l].dev.ne[s] > 256) continue;
+                if (blocks) Ls[l].dev.lbc[s] = c;
+                else Ls[l].dev.lpb[s] = c;
                 for (int w = 0; w < 3; ++w)
                     launch_line_solve<T>(Ls[l].dev, s, 0, Ls[l].r, nullptr, nullptr, Ls[l].t2, T(1), st);
                 CK(cudaEventRecord(a, st));
@@ -725,7 +731,8 @@ glls_status tune_levels(glls_problem* P, std::vector<LevelStore<T>>& Ls, int pre
                 CK(cudaEventElapsedTime(&ms, a, b));
                 if (ms < best) { best = ms; pick = c; }
             }
-            Ls[l].dev.lpb[s] = pick;
+            if (blocks) Ls[l].dev.lbc[s] = pick;
+            else Ls[l].dev.lpb[s] = pick;
             const size_t k = (l * 2 + prec) * 3 + s;
             if (chosen) chosen[k] = pick;
             if (best_us) best_us[k] = best * 100.f;   // 10 launches: ms * 1000 / 10

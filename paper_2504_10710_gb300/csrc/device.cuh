@@ -87,7 +87,8 @@ struct DevLevel {
     // (diag, off[s]) interleaved per direction: one 8/16-byte load per node
     const typename Vec2Of<T>::type* band[3] = {nullptr, nullptr, nullptr};
     DevBand<T> P[3], R[3];
-    int lpb[3] = {4, 4, 4};   // line-solve tile (lines per CTA) per direction, set by the autotuner
+    int lpb[3] = {4, 4, 4};   // band-1 line-solve tile (lines per CTA) per direction, set by the autotuner
+    int lbc[3] = {0, 0, 0};   // line-block lines per CTA per direction, set by the autotuner (0: launch heuristic)
     // Def. 3.2 line blocks condensed per element segment (GLL smoother, p >= 2;
     // null otherwise): blk[s] [ncoef][nlines * ne[s]] = packed K_I^-1, w_L,
     // w_R per segment; vband[s] [nlines][ne[s] - 1] = vertex Schur complement

@@ -351,11 +351,16 @@ size_t block_smem(int lpc, int span, int E) {
 // to 65 elements); longer lines and other orders take the run-time order.
 template <typename T, int P, int CV>
 bool launch_pc(BlockLineArgs<T> A, cudaStream_t st) {
-    // lines per CTA: at most 256 segment tasks and 16 lines, fewer while the
-    // level would have less than about four CTAs per SM (small levels are
-    // latency bound: more, smaller CTAs run their phases side by side)
-    int lpc = std::min(kMaxLinesPerCta, std::max(1, kBlockThreads / A.E));
-    while (lpc > 1 && (long long)(A.nlines + lpc - 1) / lpc * A.nrhs < 4 * sm_count()) lpc /= 2;
+    // lines per CTA: at most 256 segment tasks and 16 lines; the autotuner's
+    // choice for the level and direction when it has made one (A.lpc > 0),
+    // else fewer while the level would have less than about four CTAs per SM
+    // (small levels are latency bound: more, smaller CTAs run their phases
+    // side by side)
+    const int most = std::min(kMaxLinesPerCta, std::max(1, kBlockThreads / A.E));
+    int lpc = most;
+    if (A.lpc > 0) lpc = std::min(A.lpc, most);
+    else
+        while (lpc > 1 && (long long)(A.nlines + lpc - 1) / lpc * A.nrhs < 4 * sm_count()) lpc /= 2;
     while (lpc > 1 && block_smem<T, P>(lpc, A.span, A.E) > kMaxDynSmemBytes) lpc /= 2;
     const size_t smem = block_smem<T, P>(lpc, A.span, A.E);
     if (smem > kMaxDynSmemBytes) return false;
@@ -446,7 +451,7 @@ int make_args(BlockLineArgs<T>& A, const DevLevel<T>& L, int s, int mode, const 
     A.p = L.p;
     A.span = (A.n - 1) + ((A.n - 1) >> 5) + 1;
     A.span = (A.span + 3) / 4 * 4;
-    A.lpc = 1;
+    A.lpc = L.lbc[s];                  // 0: the launch heuristic
     const int nv = A.E - 1;
     A.cv = nv <= 32 ? 1 : (nv <= 64 ? 2 : (nv <= 128 ? 4 : 8));
     A.alpha = alpha;

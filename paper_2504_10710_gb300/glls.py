@@ -241,8 +241,9 @@ class Problem:
         return st[0] if self.nrhs == 1 else list(st)
 
     def autotune(self):
-        """Pick the line-solve tile per level/precision/direction by timing;
-        returns {(level, 'f32'|'f64', axis): (lines_per_cta, us_per_launch)}."""
+        """Pick the lines per CTA of the line solve per level/precision/direction
+        by timing (line blocks: 0 = the launch heuristic, or 1..16; band-1:
+        2..16); returns {(level, 'f32'|'f64', axis): (choice, us_per_launch)}."""
         n = self.levels * 2 * 3
         ch = (C.c_int * n)()
         us = (C.c_float * n)()

@@ -148,14 +148,19 @@ def test_server_poll_without_waiting():
     srv.close()
 
 
-def test_autotune_picks_valid_tiles_and_keeps_results():
+@pytest.mark.parametrize("smoother", [glls.SMOOTHER_GLL, glls.SMOOTHER_GLL_BAND1], ids=["blocks", "band1"])
+def test_autotune_picks_valid_tiles_and_keeps_results(smoother):
     wl = MIX[1]
-    prob, coords, f, g = _setup(wl)
+    prob, coords = glls.problem_for(wl, smoother)
+    f, g = wl.sample_rhs(coords)[0], wl.sample_dirichlet(coords)
+    prob.set_rhs(f)
+    prob.set_dirichlet(g)
     o = glls.opts(tol=1e-10, gamma=1, alpha=0.5)
     before = np.zeros(prob.N)
     st0 = prob.solve(before, o)
     tiles = prob.autotune()
-    assert tiles and all(c in (2, 4, 8, 16) and us > 0 for c, us in tiles.values())
+    # GLL line blocks: 0 (launch heuristic) or 1..16 lines per CTA
+    assert tiles and all(c in (0, 1, 2, 4, 8, 16) and us > 0 for c, us in tiles.values())
     after = np.zeros(prob.N)
     st1 = prob.solve(after, o)            # graphs are re-captured with the chosen tiles
     assert _rel(after, before) < 1e-10 and abs(st1.iterations - st0.iterations) <= 1
