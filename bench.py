@@ -62,7 +62,7 @@ def parse():
                     help="as --profile, on the 3-D 16^3 p = 7 workload with one right-hand side")
     ap.add_argument("--serving-only", action="store_true",
                     help="only the serving-stream measurement (prints its JSON object)")
-    ap.add_argument("--probe", choices=["line2d", "line3d", "apply64", "setup", "apply3d_multi"],
+    ap.add_argument("--probe", choices=["line2d", "line3d", "apply64", "setup", "apply3d_multi", "batch_passes"],
                     help="launch one kernel a few times on its workload, nothing else (small ncu captures): "
                          "line2d / line3d = the fine-level FP32 line update (MODE 1) of every axis after one "
                          "apply, on the 2-D bench workload / the 3-D 16^3 p = 7 workload; apply64 = the 2-D "
@@ -849,6 +849,36 @@ def probe(name, reps=3):
     import __graft_entry__
     from paper_2504_10710_gb300 import glls, inputs
     __graft_entry__.build()
+    if name == "batch_passes":
+        # the batched uneven workload with the iteration cap at 1, 2, 4, 8:
+        # the fixed cost and the cost per pass of each batch form
+        ws = inputs.batch_uneven()
+        probs = []
+        for w in ws:
+            pr, coords = glls.problem_for(w, glls.SMOOTHER_GLL)
+            pr.set_rhs(w.sample_rhs(coords)[0])
+            pr.set_dirichlet(w.sample_dirichlet(coords))
+            probs.append(pr)
+        outs = [torch.zeros(p.N, dtype=torch.float64, device="cuda") for p in probs]
+        stream = torch.cuda.current_stream()
+        res = {}
+        for form in ("branches", "worklist"):
+            for cap in (1, 2, 4, 8, 300):
+                o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED, max_iter=cap)
+                glls.solve_batch(probs, outs, o, stream, raise_on_error=False, worklist=form == "worklist")
+                ms = []
+                for _ in range(3):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    glls.solve_batch(probs, outs, o, stream, raise_on_error=False, worklist=form == "worklist")
+                    b.record(stream)
+                    b.synchronize()
+                    ms.append(a.elapsed_time(b))
+                res[f"{form}_cap{cap}"] = float(np.median(ms))
+        print(json.dumps({"probe": name, "ms": res}))
+        for p in probs:
+            p.close()
+        return
     if name == "apply3d_multi":
         # the 3-D fine-level FP32 apply for 32 stacked vectors (geometry read
         # once per launch), then for one vector
