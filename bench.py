@@ -62,7 +62,8 @@ def parse():
                     help="as --profile, on the 3-D 16^3 p = 7 workload with one right-hand side")
     ap.add_argument("--serving-only", action="store_true",
                     help="only the serving-stream measurement (prints its JSON object)")
-    ap.add_argument("--probe", choices=["line2d", "line3d", "apply64", "setup", "apply3d_multi", "batch_passes"],
+    ap.add_argument("--probe", choices=["line2d", "line3d", "apply64", "setup", "apply3d_multi", "batch_passes",
+                                        "batch_worklist"],
                     help="launch one kernel a few times on its workload, nothing else (small ncu captures): "
                          "line2d / line3d = the fine-level FP32 line update (MODE 1) of every axis after one "
                          "apply, on the 2-D bench workload / the 3-D 16^3 p = 7 workload; apply64 = the 2-D "
@@ -849,6 +850,27 @@ def probe(name, reps=3):
     import __graft_entry__
     from paper_2504_10710_gb300 import glls, inputs
     __graft_entry__.build()
+    if name == "batch_worklist":
+        # the batched uneven workload's work-list form with two passes of its
+        # loop captured inline (GLLS_WORKLIST_PASSES), so that ncu lists the
+        # list kernels of those passes; not a solve to tolerance
+        os.environ["GLLS_WORKLIST_PASSES"] = "2"
+        ws = inputs.batch_uneven()
+        probs = []
+        for w in ws:
+            pr, coords = glls.problem_for(w, glls.SMOOTHER_GLL)
+            pr.set_rhs(w.sample_rhs(coords)[0])
+            pr.set_dirichlet(w.sample_dirichlet(coords))
+            probs.append(pr)
+        outs = [torch.zeros(p.N, dtype=torch.float64, device="cuda") for p in probs]
+        o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=glls.PREC_MIXED, max_iter=300)
+        for _ in range(reps):
+            glls.solve_batch(probs, outs, o, raise_on_error=False, worklist=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"probe": name, "problems": len(probs), "reps": reps}))
+        for p in probs:
+            p.close()
+        return
     if name == "batch_passes":
         # the batched uneven workload with the iteration cap at 1, 2, 4, 8:
         # the fixed cost and the cost per pass of each batch form

@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstddef>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -1168,6 +1169,12 @@ std::string build_group(WlGroup& G, const glls_solve_opts& o) {
         ApplyItem<double> ai{F, P->pk, P->qk, ppq, nullptr};
         ap.put(ai, apply_list_blocks(F.p, F.E), (int)j);
     }
+    // CTAs per problem of the outer-Krylov kernels: enough for the largest
+    // problem of the group (about 16 values per thread), not kDotBlocks for
+    // every one: each CTA also sums all of its problem's partials
+    long long nmax = 1;
+    for (glls_problem* P : G.probs) nmax = std::max(nmax, P->N);
+    const int fcg_blocks = (int)std::min<long long>(kDotBlocks, std::max<long long>(16, (nmax + 4095) / 4096));
     for (int step : {0, 1, -1, 2}) {
         if (step == -1) {
             G.body.push_back(ap);
@@ -1177,6 +1184,7 @@ std::string build_group(WlGroup& G, const glls_solve_opts& o) {
         r.kind = WL_FCG;
         r.step = step;
         r.dbl = true;
+        r.blocks = fcg_blocks;
         for (size_t j = 0; j < items.size(); ++j) {
             const FcgItem& it = items[j];
             const unsigned char* b = reinterpret_cast<const unsigned char*>(&it);
@@ -1249,7 +1257,7 @@ cudaError_t replay(const WlRecord& r, const unsigned char* base, int flexible, c
                 launch_coarse_list<float>((const CoarseItem<float>*)items, start, r.nitems, r.blocks, r.smem, st);
             break;
         default:
-            launch_fcg_list(r.step, (const FcgItem*)items, r.nitems, flexible, st);
+            launch_fcg_list(r.step, (const FcgItem*)items, r.nitems, flexible, r.blocks, st);
     }
     if (!ok) return cudaErrorInvalidConfiguration;
     return cudaGetLastError();
@@ -1258,6 +1266,12 @@ cudaError_t replay(const WlRecord& r, const unsigned char* base, int flexible, c
 // Captures the whole batched solve of W (all groups as graph branches).
 cudaError_t capture_plan(WlPlan* W, const glls_solve_opts* o) {
     unsigned char* base = static_cast<unsigned char*>(W->dev);
+    // GLLS_WORKLIST_PASSES=k (profiling aid): k passes of the loop body
+    // captured inline instead of the device-side loop, so that a profiler
+    // that does not list kernels inside conditional nodes sees them; the
+    // solve then stops after k iterations
+    const char* up = std::getenv("GLLS_WORKLIST_PASSES");
+    const int unroll = up ? std::max(0, std::atoi(up)) : 0;
     const int flexible = o->krylov == GLLS_KRYLOV_FCG ? 1 : 0;
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> joins(W->groups.size(), nullptr);
@@ -1277,35 +1291,46 @@ cudaError_t capture_plan(WlPlan* W, const glls_solve_opts* o) {
             e = cudaMemcpyAsync(S + (size_t)j * S_COUNT, P->S, sizeof(double) * S_COUNT, cudaMemcpyDeviceToDevice,
                                 G.s1);
         }
-        cudaStreamCaptureStatus stt;
-        cudaGraph_t capg = nullptr;
-        cudaGraphConditionalHandle handle = 0;
-        if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(G.s1, &stt, nullptr, &capg, nullptr, nullptr, nullptr);
-        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, capg, 0, cudaGraphCondAssignDefault);
-        if (e != cudaSuccess) break;
-        launch_solve_init(S, handle, o->tol, o->max_iter, G.s1, n);
-        const cudaGraphNode_t* deps = nullptr;
-        size_t ndeps = 0;
-        e = cudaStreamGetCaptureInfo(G.s1, &stt, nullptr, &capg, &deps, nullptr, &ndeps);
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = handle;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t cnode = nullptr;
-        if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, capg, deps, nullptr, ndeps, &cp);
-        if (e == cudaSuccess)
-            e = cudaStreamUpdateCaptureDependencies(G.s1, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-        if (e == cudaSuccess) {
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            e = cudaStreamBeginCaptureToGraph(G.s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
+        if (unroll > 0) {
+            // profiling form: `unroll` passes of the body inline, no
+            // conditional node (ncu lists the kernels of the passes)
+            launch_solve_init(S, 0, o->tol, o->max_iter, G.s1, n, false);
+            for (int k = 0; k < unroll && e == cudaSuccess; ++k) {
                 for (const WlRecord& r : G.body)
-                    if (e == cudaSuccess) e = replay(r, base, flexible, G.s2);
-                launch_solve_cond(S, handle, o->max_iter, G.s2, n);
-                cudaError_t e2 = cudaStreamEndCapture(G.s2, &body);
-                if (e == cudaSuccess) e = e2;
-                if (e == cudaSuccess) G.kernels_iter = count_kernel_nodes(body);
+                    if (e == cudaSuccess) e = replay(r, base, flexible, G.s1);
+                launch_solve_cond(S, 0, o->max_iter, G.s1, n, false);
+            }
+        } else {
+            cudaStreamCaptureStatus stt;
+            cudaGraph_t capg = nullptr;
+            cudaGraphConditionalHandle handle = 0;
+            if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(G.s1, &stt, nullptr, &capg, nullptr, nullptr, nullptr);
+            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, capg, 0, cudaGraphCondAssignDefault);
+            if (e != cudaSuccess) break;
+            launch_solve_init(S, handle, o->tol, o->max_iter, G.s1, n);
+            const cudaGraphNode_t* deps = nullptr;
+            size_t ndeps = 0;
+            e = cudaStreamGetCaptureInfo(G.s1, &stt, nullptr, &capg, &deps, nullptr, &ndeps);
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = handle;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cnode = nullptr;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, capg, deps, nullptr, ndeps, &cp);
+            if (e == cudaSuccess)
+                e = cudaStreamUpdateCaptureDependencies(G.s1, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+            if (e == cudaSuccess) {
+                cudaGraph_t body = cp.conditional.phGraph_out[0];
+                e = cudaStreamBeginCaptureToGraph(G.s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (const WlRecord& r : G.body)
+                        if (e == cudaSuccess) e = replay(r, base, flexible, G.s2);
+                    launch_solve_cond(S, handle, o->max_iter, G.s2, n);
+                    cudaError_t e2 = cudaStreamEndCapture(G.s2, &body);
+                    if (e == cudaSuccess) e = e2;
+                    if (e == cudaSuccess) G.kernels_iter = count_kernel_nodes(body);
+                }
             }
         }
         for (int j = 0; j < n && e == cudaSuccess; ++j) {   // u = w + v; the scalars back to the problem

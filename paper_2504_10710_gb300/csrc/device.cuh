@@ -203,7 +203,9 @@ void launch_coarse_list(const CoarseItem<T>* items, const int* start, int nitems
 template <typename T>
 void launch_bcr_list(bool forward, int l, const BcrItem<T>* items, const int* start, int nitems, int blocks,
                      size_t smem, cudaStream_t st);
-void launch_fcg_list(int step, const FcgItem* items, int nitems, int flexible, cudaStream_t st);
+// blocks: CTAs per item (<= kDotBlocks), the same for every item: each item's
+// partial sums of r.z, z.q and r.r have that many entries
+void launch_fcg_list(int step, const FcgItem* items, int nitems, int flexible, int blocks, cudaStream_t st);
 template <typename T>
 size_t line_block_item_bytes();
 template <typename T>
@@ -360,7 +362,11 @@ void launch_scale_by_norm(double* out, const double* in, const double* nrm2, lon
 // Device-side solve loop: after S_RR0 is computed, initialise S and set the
 // WHILE handle (r0 != 0); at the end of each iteration count it and set the
 // handle to (r.r > tol^2 r0.r0, it < maxit, no breakdown).
-void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st, int nrhs = 1);
-void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st, int nrhs = 1);
+// set_cond = false: update the scalars without setting the conditional
+// (unrolled loops captured without a conditional node)
+void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st, int nrhs = 1,
+                       bool set_cond = true);
+void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st, int nrhs = 1,
+                       bool set_cond = true);
 
 }  // namespace glls

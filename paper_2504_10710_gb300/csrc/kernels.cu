@@ -971,7 +971,8 @@ __global__ void scale_by_norm_kernel(double* __restrict__ out, const double* __r
 // ends every outer iteration.
 // With several right-hand sides the loop runs while any of them is still
 // iterating; each one stops (S_DONE, S_ITS) when it converges or breaks down.
-__global__ void solve_init_kernel(double* S0, cudaGraphConditionalHandle h, double tol, int maxit, int nrhs) {
+__global__ void solve_init_kernel(double* S0, cudaGraphConditionalHandle h, double tol, int maxit, int nrhs,
+                                  int set_cond) {
     grid_dep_sync();
     if (threadIdx.x != 0) return;
     bool go = false;
@@ -997,10 +998,10 @@ __global__ void solve_init_kernel(double* S0, cudaGraphConditionalHandle h, doub
         }
         go = go || S[S_DONE] == 0.0;
     }
-    cudaGraphSetConditional(h, go && maxit > 0 ? 1u : 0u);
+    if (set_cond) cudaGraphSetConditional(h, go && maxit > 0 ? 1u : 0u);
 }
 
-__global__ void solve_cond_kernel(double* S0, cudaGraphConditionalHandle h, int maxit, int nrhs) {
+__global__ void solve_cond_kernel(double* S0, cudaGraphConditionalHandle h, int maxit, int nrhs, int set_cond) {
     grid_dep_sync();
     if (threadIdx.x != 0) return;
     bool any = false;
@@ -1022,7 +1023,7 @@ __global__ void solve_cond_kernel(double* S0, cudaGraphConditionalHandle h, int 
             any = true;
         }
     }
-    cudaGraphSetConditional(h, any && it < (double)maxit ? 1u : 0u);
+    if (set_cond) cudaGraphSetConditional(h, any && it < (double)maxit ? 1u : 0u);
 }
 
 // f and f0 hold nrhs vectors; mass and y (A v of the shared lifting) one.
@@ -1249,9 +1250,9 @@ void launch_bcr_list(bool forward, int l, const BcrItem<T>* items, const int* st
     launch_k(bcr_list_kernel<T>, blocks, 256, smem, st, items, start, nitems, l, forward ? 1 : 0);
 }
 
-void launch_fcg_list(int step, const FcgItem* items, int nitems, int flexible, cudaStream_t st) {
+void launch_fcg_list(int step, const FcgItem* items, int nitems, int flexible, int blocks, cudaStream_t st) {
     if (nitems < 1) return;
-    launch_k(fcg_list_kernel, dim3(kDotBlocks, nitems), 256, 0, st, items, step, flexible);
+    launch_k(fcg_list_kernel, dim3(blocks, nitems), 256, 0, st, items, step, flexible);
 }
 
 template bool transfer2_list_config<float>(const DevBand<float>&, const DevBand<float>&, const int*, int*, int*, int*,
@@ -1357,12 +1358,14 @@ void launch_scale_by_norm(double* out, const double* in, const double* nrm2, lon
     launch_k(scale_by_norm_kernel, grid_for(n), 256, 0, st, out, in, nrm2, n);
 }
 
-void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st, int nrhs) {
-    launch_k(solve_init_kernel, 1, 32, 0, st, S, h, tol, maxit, nrhs);
+void launch_solve_init(double* S, cudaGraphConditionalHandle h, double tol, int maxit, cudaStream_t st, int nrhs,
+                       bool set_cond) {
+    launch_k(solve_init_kernel, 1, 32, 0, st, S, h, tol, maxit, nrhs, set_cond ? 1 : 0);
 }
 
-void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st, int nrhs) {
-    launch_k(solve_cond_kernel, 1, 32, 0, st, S, h, maxit, nrhs);
+void launch_solve_cond(double* S, cudaGraphConditionalHandle h, int maxit, cudaStream_t st, int nrhs,
+                       bool set_cond) {
+    launch_k(solve_cond_kernel, 1, 32, 0, st, S, h, maxit, nrhs, set_cond ? 1 : 0);
 }
 
 void launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t st, int nrhs, bool x_shared) {

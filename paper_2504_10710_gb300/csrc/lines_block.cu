@@ -143,6 +143,10 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
     T* sdr = sdl + LPC * E;                   // [LPC][E]: w_R . g_I
     T* svb = sdr + LPC * E;                   // [LPC][2 (E - 1)]: vertex systems
     T* sz = svb + 2 * LPC * (E - 1);          // [LPC][span]: z accumulation (P = 0)
+    // orders above 8 keep the segment operators in shared memory (too many
+    // for registers): the run-time order, and compile-time orders 9..12
+    constexpr bool SMOP = P == 0 || P > 8;
+    T* sop = P == 0 ? sz + LPC * span : sz;   // [ncoef][blockDim]: segment operators (SMOP)
     const int l0 = bx * LPC;
     const int Wc = min(LPC, A.nlines - l0);
     const int tid = threadIdx.x;
@@ -156,8 +160,8 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
     const bool has_task = tid < ntk;
     const int tw = has_task ? tid / E : 0, te = has_task ? tid - tw * E : 0;
     const T* bp = A.blk + ((long long)(l0 + tw) * E + te);
-    SegOp<T, P> op;
-    if constexpr (P > 0) {
+    SegOp<T, SMOP ? 2 : P> op;            // registers (orders 2..8 only)
+    if constexpr (P > 0 && !SMOP) {
         if (has_task) {
 #pragma unroll
             for (int c = 0; c < SegOp<T, P>::NPK; ++c) op.t[c] = __ldg(bp + (long long)c * ntask);
@@ -168,6 +172,28 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
             }
         }
     }
+    if constexpr (SMOP) {
+        // the thread's segment operator is copied to shared memory with the
+        // line values and read from there in the loops
+        if (has_task) {
+            const int ncoef = npk + 2 * mi;
+            for (int c = 0; c < ncoef; ++c) cp_async(sop + c * blockDim.x + tid, bp + (long long)c * ntask);
+        }
+    }
+    auto opc = [&](int c) { return sop[c * blockDim.x + tid]; };   // coefficient c of this thread's segment (SMOP)
+    auto op_t = [&](int c) -> T {
+        if constexpr (SMOP) return opc(c);
+        else return op.t[c];
+    };
+    auto op_wl = [&](int i) -> T {
+        if constexpr (SMOP) return opc(npk + i);
+        else return op.wl[i];
+    };
+    auto op_wr = [&](int i) -> T {
+        if constexpr (SMOP) return opc(npk + mi + i);
+        else return op.wr[i];
+    };
+
     // line values, staged without divisions by asynchronous copies (every
     // copy of the tile in flight at once): x-lines are walked along the line
     // by whole warps (coalesced along x); strided directions by threads that
@@ -209,7 +235,7 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
     }
 
     // ---- segments: z = K_I^-1 g_I and the two vertex dots
-    T z[SegOp<T, P>::MI];
+    T z[P > 1 ? P - 1 : 1];
     if (has_task) {
         T* line = sg + tw * span;
         const int base = te * p;   // line unknown of the segment's first interior node
@@ -226,14 +252,14 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
             for (int i = 0; i < P - 1; ++i)
 #pragma unroll
                 for (int j = i; j < P - 1; ++j) {
-                    const T t = op.t[c++];
+                    const T t = op_t(c++);
                     z[i] += t * gi[j];
                     if (j != i) z[j] += t * gi[i];
                 }
 #pragma unroll
             for (int i = 0; i < P - 1; ++i) {
-                dl += op.wl[i] * gi[i];
-                dr += op.wr[i] * gi[i];
+                dl += op_wl(i) * gi[i];
+                dr += op_wr(i) * gi[i];
             }
         } else {
             T* zz = sz + tw * span;
@@ -243,14 +269,14 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
                 const T gi_ = line[padk(base + i)];
                 T zi = T(0);
                 for (int j = i; j < mi; ++j) {
-                    const T t = __ldg(bp + (long long)c * ntask);
+                    const T t = opc(c);
                     ++c;
                     zi += t * line[padk(base + j)];
                     if (j != i) zz[padk(base + j)] += t * gi_;
                 }
                 zz[padk(base + i)] += zi;
-                dl += __ldg(bp + (long long)(npk + i) * ntask) * gi_;
-                dr += __ldg(bp + (long long)(npk + mi + i) * ntask) * gi_;
+                dl += opc(npk + i) * gi_;
+                dr += opc(npk + mi + i) * gi_;
             }
         }
         // each task reads and writes only its own segment's interior nodes
@@ -285,11 +311,11 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
         const T nr = te < E - 1 ? line[padk(base + mi)] : T(0);
         if constexpr (P > 0) {
 #pragma unroll
-            for (int i = 0; i < P - 1; ++i) line[padk(base + i)] = z[i] - (op.wl[i] * nl + op.wr[i] * nr);
+            for (int i = 0; i < P - 1; ++i) line[padk(base + i)] = z[i] - (op_wl(i) * nl + op_wr(i) * nr);
         } else {
             for (int i = 0; i < mi; ++i) {
-                const T wl = __ldg(bp + (long long)(npk + i) * ntask);
-                const T wr = __ldg(bp + (long long)(npk + mi + i) * ntask);
+                const T wl = opc(npk + i);
+                const T wr = opc(npk + mi + i);
                 line[padk(base + i)] -= wl * nl + wr * nr;
             }
         }
@@ -325,7 +351,7 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
 }
 
 template <typename T, int P, int CV>
-__global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 || P == 0 ? 3 : 4))
+__global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P >= 8 || P == 0 ? 3 : 4))
     line_block_kernel(BlockLineArgs<T> A) {
     grid_dep_sync();
     line_block_body<T, P, CV>(A, blockIdx.x);
@@ -334,7 +360,7 @@ __global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 ||
 // Work-list form: item j (one problem's level, direction and vectors) owns
 // the CTAs [start[j], start[j + 1]).
 template <typename T, int P, int CV>
-__global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P == 8 || P == 0 ? 3 : 4))
+__global__ void __launch_bounds__(kBlockThreads, sizeof(T) == 8 ? 2 : (P >= 8 || P == 0 ? 3 : 4))
     line_block_list_kernel(const BlockLineArgs<T>* __restrict__ items, const int* __restrict__ start, int nitems) {
     grid_dep_sync();
     const int j = work_item(start, nitems, blockIdx.x);
@@ -347,8 +373,16 @@ size_t block_smem(int lpc, int span, int E) {
     return sizeof(T) * ((size_t)lpc * span * (P == 0 ? 4 : 3) + 2 * (size_t)lpc * E + 2 * (size_t)lpc * (E - 1));
 }
 
-// Orders 2..8 are compiled for vertex chunks of 1 and 2 per lane (lines of up
-// to 65 elements); longer lines and other orders take the run-time order.
+// Shared memory of the run-time-order instance's segment operators for a
+// block of `threads` threads at order p.
+template <typename T>
+size_t op_smem(int p, int threads) {
+    const size_t mi = (size_t)(p - 1);
+    return sizeof(T) * (mi * (mi + 1) / 2 + 2 * mi) * (size_t)threads;
+}
+
+// Orders 2..12 are compiled for vertex chunks of 1 and 2 per lane (lines of
+// up to 65 elements); longer lines and other orders take the run-time order.
 template <typename T, int P, int CV>
 bool launch_pc(BlockLineArgs<T> A, cudaStream_t st) {
     // lines per CTA: at most 256 segment tasks and 16 lines; the autotuner's
@@ -361,11 +395,15 @@ bool launch_pc(BlockLineArgs<T> A, cudaStream_t st) {
     if (A.lpc > 0) lpc = std::min(A.lpc, most);
     else
         while (lpc > 1 && (long long)(A.nlines + lpc - 1) / lpc * A.nrhs < 4 * sm_count()) lpc /= 2;
-    while (lpc > 1 && block_smem<T, P>(lpc, A.span, A.E) > kMaxDynSmemBytes) lpc /= 2;
-    const size_t smem = block_smem<T, P>(lpc, A.span, A.E);
+    auto thr = [&](int c) { return std::min(kBlockThreads, std::max(32, (c * A.E + 31) / 32 * 32)); };
+    auto sm = [&](int c) {
+        return block_smem<T, P>(c, A.span, A.E) + (P == 0 || P > 8 ? op_smem<T>(A.p, thr(c)) : 0);
+    };
+    while (lpc > 1 && sm(lpc) > kMaxDynSmemBytes) lpc /= 2;
+    const size_t smem = sm(lpc);
     if (smem > kMaxDynSmemBytes) return false;
     A.lpc = lpc;
-    const int threads = std::min(kBlockThreads, std::max(32, (lpc * A.E + 31) / 32 * 32));
+    const int threads = thr(lpc);
     const long long blocks = (long long)(A.nlines + lpc - 1) / lpc * A.nrhs;
     if (blocks > 0x7fffffffLL) return false;
     return launch_k(line_block_kernel<T, P, CV>, (unsigned)blocks, threads, smem, st, A) == cudaSuccess;
@@ -413,7 +451,8 @@ bool set_attr_p() {
 template <typename T>
 bool set_attr_t() {
     return set_attr_p<T, 0>() && set_attr_p<T, 2>() && set_attr_p<T, 3>() && set_attr_p<T, 4>() &&
-           set_attr_p<T, 5>() && set_attr_p<T, 6>() && set_attr_p<T, 7>() && set_attr_p<T, 8>();
+           set_attr_p<T, 5>() && set_attr_p<T, 6>() && set_attr_p<T, 7>() && set_attr_p<T, 8>() &&
+           set_attr_p<T, 9>() && set_attr_p<T, 10>() && set_attr_p<T, 11>() && set_attr_p<T, 12>();
 }
 
 }  // namespace
@@ -514,12 +553,16 @@ int line_block_list_item(const DevLevel<T>& L, int s, int mode, const T* g, cons
     BlockLineArgs<T> A;
     const int k = make_args<T>(A, L, s, mode, g, r, y, x, alpha, 1);
     if (k <= 0) return k;
+    // the run-time-order instance also holds the segment operators of a
+    // block of up to kBlockThreads threads (the list's block is the largest
+    // of its items')
+    auto sm1 = [&](int c) { return block_smem<T, 0>(c, A.span, A.E) + op_smem<T>(A.p, kBlockThreads); };
     int lpc = std::min(kMaxLinesPerCta, std::max(1, kBlockThreads / A.E));
-    while (lpc > 1 && block_smem<T, 0>(lpc, A.span, A.E) > kMaxDynSmemBytes) lpc /= 2;
-    if (block_smem<T, 0>(lpc, A.span, A.E) > kMaxDynSmemBytes) return -1;
+    while (lpc > 1 && sm1(lpc) > kMaxDynSmemBytes) lpc /= 2;
+    if (sm1(lpc) > kMaxDynSmemBytes) return -1;
     A.lpc = lpc;
-    smem[0] = block_smem<T, 2>(lpc, A.span, A.E);
-    smem[1] = block_smem<T, 0>(lpc, A.span, A.E);
+    smem[0] = block_smem<T, 2>(lpc, A.span, A.E) + (A.p > 8 ? op_smem<T>(A.p, kBlockThreads) : 0);
+    smem[1] = sm1(lpc);
     *threads = std::min(kBlockThreads, std::max(32, (lpc * A.E + 31) / 32 * 32));
     *blocks = (A.nlines + lpc - 1) / lpc;
     *cv = A.cv;
@@ -529,7 +572,7 @@ int line_block_list_item(const DevLevel<T>& L, int s, int mode, const T* g, cons
 
 // Whether launch_line_block_list(p, cv, ...) runs the order-specialised
 // instance (smem[0] of the items) or the run-time-order one (smem[1]).
-bool line_block_list_specialised(int p, int cv) { return p >= 2 && p <= 8 && cv <= 2; }
+bool line_block_list_specialised(int p, int cv) { return p >= 2 && p <= 12 && cv <= 2; }
 
 // One launch over the items (all of order p; cv: the largest vertex chunk of
 // the items).
@@ -545,6 +588,10 @@ bool launch_line_block_list(int p, int cv, const void* items, const int* start, 
         case 6: return launch_list_p<T, 6>(cv, items, start, nitems, blocks, threads, smem, st);
         case 7: return launch_list_p<T, 7>(cv, items, start, nitems, blocks, threads, smem, st);
         case 8: return launch_list_p<T, 8>(cv, items, start, nitems, blocks, threads, smem, st);
+        case 9: return launch_list_p<T, 9>(cv, items, start, nitems, blocks, threads, smem, st);
+        case 10: return launch_list_p<T, 10>(cv, items, start, nitems, blocks, threads, smem, st);
+        case 11: return launch_list_p<T, 11>(cv, items, start, nitems, blocks, threads, smem, st);
+        case 12: return launch_list_p<T, 12>(cv, items, start, nitems, blocks, threads, smem, st);
         default: return launch_list_p<T, 0>(cv, items, start, nitems, blocks, threads, smem, st);
     }
 }
@@ -574,6 +621,10 @@ bool launch_line_block(const DevLevel<T>& L, int s, int mode, const T* g, const 
         case 6: return launch_p<T, 6>(A, st);
         case 7: return launch_p<T, 7>(A, st);
         case 8: return launch_p<T, 8>(A, st);
+        case 9: return launch_p<T, 9>(A, st);
+        case 10: return launch_p<T, 10>(A, st);
+        case 11: return launch_p<T, 11>(A, st);
+        case 12: return launch_p<T, 12>(A, st);
         default: return launch_p<T, 0>(A, st);
     }
 }

@@ -346,11 +346,14 @@ def test_server_groups_same_mesh_requests_into_one_multi_rhs_solve(prec):
 
 
 # uneven 2-D problems: several order chains (8-4-2-1, 6-3-1, 5-2-1, 4-2-1),
-# two of them with more than one problem, ragged element counts
+# two of them with more than one problem, ragged element counts,
+# and orders above 8 (the run-time-order line-block instance: 12-6-3-1 and
+# 10-5-2-1 next to 5-2-1)
 WORKLIST = [inputs.random2d((9, 7), 6, amp=0.1, seed=61), inputs.random2d((16, 12), 8, amp=0.15, seed=62),
             inputs.random2d((4, 5), 5, amp=0.05, seed=63), inputs.random2d((10, 6), 4, amp=0.1, seed=64),
             inputs.random2d((6, 8), 6, amp=0.1, seed=65), inputs.random2d((21, 19), 8, amp=0.1, seed=66),
-            inputs.random2d((3, 2), 5, amp=0.1, seed=67)]
+            inputs.random2d((3, 2), 5, amp=0.1, seed=67), inputs.random2d((7, 5), 12, amp=0.1, seed=68),
+            inputs.random2d((5, 9), 10, amp=0.15, seed=69), inputs.random2d((4, 4), 12, amp=0.05, seed=70)]
 
 
 @pytest.mark.parametrize("prec", [glls.PREC_FP64, glls.PREC_MIXED], ids=["fp64", "mixed"])

@@ -86,6 +86,10 @@ CASES = [
     ("2d_70x3_p4_blocks", lambda: inputs.random2d((70, 3), 4, amp=0.1, seed=17), "gll", "transpose"),
     ("3d_3x2x4_p7_blocks", lambda: inputs.random3d((3, 2, 4), 7, amp=0.1, seed=18), "gll", "transpose"),
     ("3d_2x2x2_p5_blocks", lambda: inputs.random3d((2, 2, 2), 5, amp=0.15, seed=19), "gll", "transpose"),
+    # orders 9..12: compile-time line-block instances with the operators in shared memory
+    ("2d_4x3_p10_blocks", lambda: inputs.random2d((4, 3), 10, amp=0.1, seed=21), "gll", "transpose"),
+    ("2d_3x2_p12_blocks", lambda: inputs.random2d((3, 2), 12, amp=0.15, seed=22), "gll", "transpose"),
+    ("2d_single_p9_blocks", lambda: inputs.table1_problem3(9), "gll", "interp"),
 ]
 
 
