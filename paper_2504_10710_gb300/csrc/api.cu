@@ -498,9 +498,10 @@ void outer_iteration(glls_problem* P, const glls_solve_opts* o, cudaStream_t st)
     double* ppq = prr + (long long)k * kDotBlocks;
     const int npq = apply_dot_partials<double>(P->L64[L].dev);
     launch_dots_rz_zq(P->rk, P->zk, mixed ? P->z32 : nullptr, P->qk, N, prz, pzq, st, k);
-    launch_fcg_direction(P->pk, P->zk, N, prz, pzq, kDotBlocks, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, st, k);
+    const int nb = fcg_blocks(N);            // the dots' CTAs: partials of r.z, z.q, r.r per right-hand side
+    launch_fcg_direction(P->pk, P->zk, N, prz, pzq, nb, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, st, k);
     launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st, true, P->S + S_PQ, ppq, nullptr, k);
-    launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, ppq, npq, prz, kDotBlocks, prr, P->S, P->ticket,
+    launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, ppq, npq, prz, nb, prr, P->S, P->ticket,
                       mixed ? P->r32 : nullptr, st, k);
 }
 
@@ -1174,7 +1175,7 @@ std::string build_group(WlGroup& G, const glls_solve_opts& o) {
     // every one: each CTA also sums all of its problem's partials
     long long nmax = 1;
     for (glls_problem* P : G.probs) nmax = std::max(nmax, P->N);
-    const int fcg_blocks = (int)std::min<long long>(kDotBlocks, std::max<long long>(16, (nmax + 4095) / 4096));
+    const int nblk = fcg_blocks(nmax);
     for (int step : {0, 1, -1, 2}) {
         if (step == -1) {
             G.body.push_back(ap);
@@ -1184,7 +1185,7 @@ std::string build_group(WlGroup& G, const glls_solve_opts& o) {
         r.kind = WL_FCG;
         r.step = step;
         r.dbl = true;
-        r.blocks = fcg_blocks;
+        r.blocks = nblk;
         for (size_t j = 0; j < items.size(); ++j) {
             const FcgItem& it = items[j];
             const unsigned char* b = reinterpret_cast<const unsigned char*>(&it);

@@ -315,6 +315,14 @@ void launch_zero_boundary(T* v, const int n[3], int dim, cudaStream_t st, int nr
 // S[slot0] (and S[slot1]).  `ticket` is a zero-initialised counter that the
 // kernel resets.
 constexpr int kDotBlocks = 304;   // 2 x 152 SMs
+// CTAs per right-hand side of the outer-iteration kernels (dots, direction,
+// update) for vectors of n values: about 16 values per thread, between 16
+// and kDotBlocks (each CTA also sums all of the apply's partials, so more
+// CTAs than the vector needs cost more than they hide)
+inline int fcg_blocks(long long n) {
+    const long long b = (n + 4095) / 4096;
+    return (int)(b < 16 ? 16 : b > kDotBlocks ? kDotBlocks : b);
+}
 constexpr int kMaxReduceBlocks = 8192;
 void launch_dots(const double* a0, const double* b0, const double* a1, const double* b1, int ndots,
                  long long n, double* part, double* S, int slot0, int slot1, unsigned* ticket, cudaStream_t st, int nrhs = 1);

@@ -1316,18 +1316,18 @@ void launch_dots(const double* a0, const double* b0, const double* a1, const dou
 void launch_fcg_update(double* x, double* r, const double* p, const double* q, long long n, const double* ppq,
                        int npq, const double* prz, int nrz, double* prr, double* S, unsigned* ticket, float* r32,
                        cudaStream_t st, int nrhs) {
-    launch_k(fcg_update_kernel, dim3(kDotBlocks, nrhs), 256, 0, st, x, r, p, q, n, ppq, npq, prz, nrz, prr, S, ticket,
-             r32);
+    // nrz: the dots' CTA count, the same grid here (prr gets one partial per CTA)
+    launch_k(fcg_update_kernel, dim3(nrz, nrhs), 256, 0, st, x, r, p, q, n, ppq, npq, prz, nrz, prr, S, ticket, r32);
 }
 
 void launch_dots_rz_zq(const double* r, double* z, const float* z32, double* q, long long n, double* prz, double* pzq,
                        cudaStream_t st, int nrhs) {
-    launch_k(dots_rz_zq_kernel, dim3(kDotBlocks, nrhs), 256, 0, st, r, z, z32, q, n, prz, pzq);
+    launch_k(dots_rz_zq_kernel, dim3(fcg_blocks(n), nrhs), 256, 0, st, r, z, z32, q, n, prz, pzq);
 }
 
 void launch_fcg_direction(double* p, const double* z, long long n, const double* prz, const double* pzq, int nd,
                           const double* S, int flexible, cudaStream_t st, int nrhs) {
-    launch_k(fcg_direction_kernel, dim3(kDotBlocks, nrhs), 256, 0, st, p, z, n, prz, pzq, nd, S, flexible);
+    launch_k(fcg_direction_kernel, dim3(nd, nrhs), 256, 0, st, p, z, n, prz, pzq, nd, S, flexible);
 }
 
 void launch_lift_rhs(const double* mass, const double* f, const double* y, double* f0, const int n[3], int dim,
