@@ -172,15 +172,18 @@ __device__ __forceinline__ void line_block_body(BlockLineArgs<T> A, int blk) {
             }
         }
     }
+    // operator rows are as long as this launch item's own thread count (a
+    // work-list block may be larger; its extra threads have no segment)
+    const int opstride = min(kBlockThreads, max(32, (LPC * E + 31) / 32 * 32));
     if constexpr (SMOP) {
         // the thread's segment operator is copied to shared memory with the
         // line values and read from there in the loops
         if (has_task) {
             const int ncoef = npk + 2 * mi;
-            for (int c = 0; c < ncoef; ++c) cp_async(sop + c * blockDim.x + tid, bp + (long long)c * ntask);
+            for (int c = 0; c < ncoef; ++c) cp_async(sop + c * opstride + tid, bp + (long long)c * ntask);
         }
     }
-    auto opc = [&](int c) { return sop[c * blockDim.x + tid]; };   // coefficient c of this thread's segment (SMOP)
+    auto opc = [&](int c) { return sop[c * opstride + tid]; };   // coefficient c of this thread's segment (SMOP)
     auto op_t = [&](int c) -> T {
         if constexpr (SMOP) return opc(c);
         else return op.t[c];
@@ -553,17 +556,17 @@ int line_block_list_item(const DevLevel<T>& L, int s, int mode, const T* g, cons
     BlockLineArgs<T> A;
     const int k = make_args<T>(A, L, s, mode, g, r, y, x, alpha, 1);
     if (k <= 0) return k;
-    // the run-time-order instance also holds the segment operators of a
-    // block of up to kBlockThreads threads (the list's block is the largest
-    // of its items')
-    auto sm1 = [&](int c) { return block_smem<T, 0>(c, A.span, A.E) + op_smem<T>(A.p, kBlockThreads); };
+    // the run-time-order instance and orders 9..12 also hold the segment
+    // operators of the item's own threads
+    auto thr = [&](int c) { return std::min(kBlockThreads, std::max(32, (c * A.E + 31) / 32 * 32)); };
+    auto sm1 = [&](int c) { return block_smem<T, 0>(c, A.span, A.E) + op_smem<T>(A.p, thr(c)); };
     int lpc = std::min(kMaxLinesPerCta, std::max(1, kBlockThreads / A.E));
     while (lpc > 1 && sm1(lpc) > kMaxDynSmemBytes) lpc /= 2;
     if (sm1(lpc) > kMaxDynSmemBytes) return -1;
     A.lpc = lpc;
-    smem[0] = block_smem<T, 2>(lpc, A.span, A.E) + (A.p > 8 ? op_smem<T>(A.p, kBlockThreads) : 0);
+    smem[0] = block_smem<T, 2>(lpc, A.span, A.E) + (A.p > 8 ? op_smem<T>(A.p, thr(lpc)) : 0);
     smem[1] = sm1(lpc);
-    *threads = std::min(kBlockThreads, std::max(32, (lpc * A.E + 31) / 32 * 32));
+    *threads = thr(lpc);
     *blocks = (A.nlines + lpc - 1) / lpc;
     *cv = A.cv;
     std::memcpy(item, &A, sizeof(A));
