@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--serving-only", action="store_true",
                     help="only the serving-stream measurement (prints its JSON object)")
     ap.add_argument("--probe", choices=["line2d", "line3d", "apply64", "setup", "apply3d_multi", "batch_passes",
-                                        "batch_worklist"],
+                                        "batch_worklist", "summation", "apply_ff"],
                     help="launch one kernel a few times on its workload, nothing else (small ncu captures): "
                          "line2d / line3d = the fine-level FP32 line update (MODE 1) of every axis after one "
                          "apply, on the 2-D bench workload / the 3-D 16^3 p = 7 workload; apply64 = the 2-D "
@@ -220,6 +220,7 @@ def run_ours(args, rank, world):
     # HBM (bench workload and 3-D)
     roof = line_roofline(prob, glls, torch)
     roof64 = fp64_apply_roofline(prob, glls, torch)
+    roof_ff = ff_apply_roofline(prob, glls, torch)
     roof_hbm = smoother_rooflines(prob, glls, torch, inputs, flush)
     serving = serving_run(glls, inputs) if not args.no_serving else None
     if serving is not None:
@@ -232,6 +233,7 @@ def run_ours(args, rank, world):
                                                          "grouping")}
     batch = batch_run(glls, inputs, torch) if not args.no_batch else None
     smoothers = smoother_compare(glls, inputs, torch)
+    summation = summation_compare(glls, inputs, torch)
     multirhs = multirhs_run(glls, inputs, torch) if not args.no_batch else None
 
     # whole-job throughput: all ranks' DOF over the slowest rank's time
@@ -252,7 +254,9 @@ def run_ours(args, rank, world):
                        "what": "end to end through glls_set_rhs/set_dirichlet/solve with host buffers"},
         "clocks": clk,
         "smoothers": smoothers,
+        "summation": summation,
         "roofline": roof64,
+        "roofline_outer_apply_ff": roof_ff,
         "roofline_line_update": roof,
         "roofline_hbm": roof_hbm,
         "gpu_launches": int(launches),
@@ -382,6 +386,40 @@ def fp64_apply_roofline(prob, glls, torch):
                            "(MEASURED_PEAKS.json sm_max_mhz); no FP64 peak is measured",
             "note": "FMA counted as 2 FLOP; 50 launches replayed from a CUDA graph, CUDA events; y is not "
                     "re-zeroed between the timed launches (same work)"}
+
+
+def ff_apply_roofline(prob, glls, torch):
+    """The outer iteration's apply as the mixed-precision solve launches it:
+    q = A p with the p.(A p) partials in float-float arithmetic
+    (apply_ff_kernel<8>), timed by graph replay.  Bound by the FP32 pipe:
+    the algorithm's FP32 instructions per element node are 12 per float-float
+    multiply-add (one product, three fused multiply-adds, the six of the
+    two-sum, two adds) over 2 (p+1) + 4 + 2 (p+1) of them, plus 3 per
+    renormalisation (five), i.e. 48 (p+1) + 63; the peak is 128 FP32 lanes
+    per SM per clock.  The FP64 work (splitting p, joining q, the dot) is a
+    few operations per node beside it."""
+    L = prob.levels - 1
+    shape = prob.level_shape(L)
+    p, E = prob.info.order[L], 64 * 64
+    x = _interior_random(torch, shape, torch.float64)
+    y = torch.zeros_like(x)
+    part = torch.zeros(8192, dtype=torch.float64, device="cuda")
+    ms = _time_graph(torch, lambda s: prob.apply_partials(L, x, y, part, s, ff=True))
+    ops = float(E * (p + 1) ** 2 * (48 * (p + 1) + 63))
+    ach = ops / (ms / 1e3) / 1e9
+    peaks, _ = _peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = 128.0 * sms * mhz / 1e3
+    return {"bound": "alu", "kernel": f"apply_ff_kernel<{p}> (fine-level outer apply with the fused p.Ap partials "
+                                      "in float-float arithmetic, as launched by the mixed-precision solve)",
+            "achieved": ach, "peak": peak, "unit": "G FP32-instructions/s", "frac": ach / peak,
+            "traffic": _traffic(f"apply_ff_kernel<{p}>", "terrain2d_64x64_p8"),
+            "ms_per_launch": ms, "algorithmic_fp32_instructions": ops,
+            "peak_source": f"derived: 128 FP32 lanes/clk/SM x {sms} SMs (device properties) x {mhz:.0f} MHz "
+                           "(MEASURED_PEAKS.json sm_max_mhz)",
+            "note": "an instruction (FMA included) counted once; 50 launches replayed from a CUDA graph, CUDA "
+                    "events; y is not re-zeroed between the timed launches (same work)"}
 
 
 def line_roofline(prob, glls, torch):
@@ -532,6 +570,44 @@ def smoother_compare(glls, inputs, torch, reps=10):
             ms.append(a.elapsed_time(b))
         out[name] = {"alpha": alpha, "iterations": int(st.iterations), "converged": st.status == glls.OK,
                      "ms_per_solve": float(np.median(ms)), "dof_per_s": prob.N / (float(np.median(ms)) / 1e3)}
+        prob.close()
+    return out
+
+
+def summation_compare(glls, inputs, torch, reps=10):
+    """The bench workload (2-D 64x64, p = 8, line blocks, alpha = 2/3, to
+    1e-10) with the two direct stiffness summations: atomic (the default) and
+    coloured (bitwise reproducible: one launch per element colour of the
+    node-per-thread apply).  Mixed and FP64; iterations, CUDA-event time per
+    solve, and whether repeated coloured solves gave the same bits."""
+    wl = inputs.terrain2d()
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, summ in (("atomic", glls.SUM_ATOMIC), ("colored", glls.SUM_COLORED)):
+        prob, coords = glls.problem_for(wl, glls.SMOOTHER_GLL, glls.RESTRICT_TRANSPOSE, summation=summ)
+        prob.set_rhs(wl.sample_rhs(coords)[0])
+        prob.set_dirichlet(wl.sample_dirichlet(coords))
+        for pname, prec in (("mixed", glls.PREC_MIXED), ("fp64", glls.PREC_FP64)):
+            u = torch.zeros(prob.N, dtype=torch.float64, device="cuda")
+            first = None
+            o = glls.opts(tol=1e-10, gamma=GAMMA, alpha=ALPHA, precision=prec, max_iter=300)
+            same = True
+            for _ in range(3):
+                st = prob.solve(u, o, stream, raise_on_error=False)
+                if first is None:
+                    first = u.clone()
+                same = same and bool(torch.equal(u, first))
+            ms = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                st = prob.solve(u, o, stream, raise_on_error=False)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+                same = same and bool(torch.equal(u, first))
+            out[f"{name}_{pname}"] = {"iterations": int(st.iterations), "converged": st.status == glls.OK,
+                                      "ms_per_solve": float(np.median(ms)), "same_bits_every_solve": same}
         prob.close()
     return out
 
@@ -850,6 +926,9 @@ def probe(name, reps=3):
     import __graft_entry__
     from paper_2504_10710_gb300 import glls, inputs
     __graft_entry__.build()
+    if name == "summation":
+        print(json.dumps({"probe": name, "summation": summation_compare(glls, inputs, torch)}))
+        return
     if name == "batch_worklist":
         # the batched uneven workload's work-list form with two passes of its
         # loop captured inline (GLLS_WORKLIST_PASSES), so that ncu lists the
@@ -941,6 +1020,32 @@ def probe(name, reps=3):
     prob, _ = glls.problem_for(wl, glls.SMOOTHER_GLL, glls.RESTRICT_TRANSPOSE)
     L = prob.levels - 1
     shape = prob.level_shape(L)
+    if name == "apply_ff":
+        # the float-float outer apply launched reps times, then both outer
+        # applies timed by graph replay
+        x = _interior_random(torch, shape, torch.float64)
+        y = torch.zeros_like(x)
+        part = torch.zeros(8192, dtype=torch.float64, device="cuda")
+        for _ in range(reps):
+            y.zero_()
+            prob.apply_partials(L, x, y, part, ff=True)
+        torch.cuda.synchronize()
+        out = {"probe": name, "ff": ff_apply_roofline(prob, glls, torch),
+               "fp64": fp64_apply_roofline(prob, glls, torch)}
+        prob.close()
+        # 3-D 16^3, p = 7: both outer applies by graph replay
+        w3 = inputs.terrain3d(nrhs=1)
+        p3, _ = glls.problem_for(w3, glls.SMOOTHER_GLL, glls.RESTRICT_TRANSPOSE)
+        L3 = p3.levels - 1
+        x3 = _interior_random(torch, p3.level_shape(L3), torch.float64)
+        y3 = torch.zeros_like(x3)
+        part3 = torch.zeros(1 << 16, dtype=torch.float64, device="cuda")
+        out["ms_3d_16x16x16_p7"] = {
+            "ff": _time_graph(torch, lambda s: p3.apply_partials(L3, x3, y3, part3, s, ff=True)),
+            "fp64": _time_graph(torch, lambda s: p3.apply_partials(L3, x3, y3, part3, s))}
+        p3.close()
+        print(json.dumps(out))
+        return
     if name == "apply64":
         x = _interior_random(torch, shape, torch.float64)
         y = torch.zeros_like(x)

@@ -80,6 +80,20 @@ enum { GLLS_KRYLOV_FCG = 0, GLLS_KRYLOV_PCG = 1, GLLS_KRYLOV_GMRES = 2 };
  * slowest axis (lines in 2-D, planes in 3-D) and refuses blocks of more than
  * 2048 unknowns. */
 enum { GLLS_COARSE_AUTO = 0, GLLS_COARSE_DENSE = 1, GLLS_COARSE_BLOCK_CR = 2 };
+/* Direct stiffness summation of the operator applies (the sum over elements of
+ * A = sum_e Q_e^T A_e Q_e, Sec. 2):
+ *   ATOMIC   one launch; nodes shared by elements are accumulated with atomic
+ *            adds, so their summation order, and with it the last bits of an
+ *            FP32 or FP64 result, follows the GPU's scheduling.
+ *   COLORED  one launch per element colour (the 2^dim parity classes of the
+ *            element coordinates, no two elements of a class share a node)
+ *            in a fixed order: every shared node sums its contributions in the
+ *            same order on every run.  A solve is then the same bits alone, in
+ *            a graph-branch batch and in the serving loop, at the cost of the
+ *            node-per-thread apply kernel (not the specialised ones) and 2^dim
+ *            launches per apply.  Work-list batches refuse such problems, and
+ *            the serving loop does not group their requests. */
+enum { GLLS_SUM_ATOMIC = 0, GLLS_SUM_COLORED = 1 };
 
 typedef struct glls_problem glls_problem;   /* opaque, library-owned */
 
@@ -97,6 +111,7 @@ typedef struct {
     int device;           /* CUDA device ordinal */
     int coarse_solver;    /* GLLS_COARSE_* (0 = AUTO) */
     int coarse_cr_levels; /* block-CR levels for GLLS_COARSE_BLOCK_CR (0 = automatic) */
+    int summation;        /* GLLS_SUM_* (0 = ATOMIC) */
 } glls_mesh_desc;
 
 typedef struct {
@@ -315,6 +330,17 @@ glls_status glls_cancel(glls_server* server, unsigned long long ticket);
  * capacity is smaller. */
 glls_status glls_apply_partials_f64(glls_problem* prob, int level, const double* x, double* y, double* partials,
                                     int capacity, int* count, void* stream);
+/* The same product and partials computed in float-float arithmetic (each
+ * value a pair of FP32 numbers, about 48 significant bits: Knuth's two-sum and
+ * the FMA exact product), as the mixed-precision solve's outer iteration runs
+ * it for solves with tol >= 1e-12 (GB300 runs FP32 at 64 times its FP64
+ * rate).  x and y are FP64 as above; the relative rounding is near 2^-44 per
+ * contraction instead of 2^-53.  Only the finest level of a problem with
+ * 2 <= p <= 16 (2-D) or 2 <= p <= 8 (3-D, even-odd line sweeps) and
+ * GLLS_SUM_ATOMIC (else GLLS_ERR_INVALID without device work); *count is this
+ * kernel's partial count (in 2-D the same as glls_apply_partials_f64's). */
+glls_status glls_apply_partials_ff(glls_problem* prob, int level, const double* x, double* y, double* partials,
+                                   int capacity, int* count, void* stream);
 glls_status glls_apply_f64(glls_problem* prob, int level, const double* x, double* y, void* stream);
 glls_status glls_apply_f32(glls_problem* prob, int level, const float* x, float* y, void* stream);
 /* y = A_l x for nrhs vectors at once (x, y: nrhs x N_l values, vector j at

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libglls.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "apply.cu", "apply_col.cu", "apply_eo.cu", "lines.cu", "lines_block.cu", "api.cu", "server.cu", "setup.cpp"]
+SOURCES = ["kernels.cu", "apply.cu", "apply_col.cu", "apply_eo.cu", "apply_ff.cu", "lines.cu", "lines_block.cu", "api.cu", "server.cu", "setup.cpp"]
 
 
 def _nvcc() -> str:

@@ -474,6 +474,12 @@ glls_status check_opts(const glls_solve_opts* o) {
     return GLLS_OK;
 }
 
+// Dot partials written by launch_apply for L (coloured summation runs the
+// node-per-thread kernel and a separate dot over kDotBlocks CTAs).
+static int dot_partials_of(const DevLevel<double>& L) {
+    return L.colored ? kDotBlocks : apply_dot_partials<double>(L);
+}
+
 // Body of one outer iteration (4 launches besides the gamma-cycle):
 //   z = M r                      (FP32 cycle on r32 = float(r) in mixed precision)
 //   partials of r.z and z.q      (z = double(z32); q reset to 0 after reading)
@@ -496,11 +502,15 @@ void outer_iteration(glls_problem* P, const glls_solve_opts* o, cudaStream_t st)
     double* pzq = prz + (long long)k * kDotBlocks;
     double* prr = pzq + (long long)k * kDotBlocks;
     double* ppq = prr + (long long)k * kDotBlocks;
-    const int npq = apply_dot_partials<double>(P->L64[L].dev);
+    // mixed precision: q = A p in float-float arithmetic where the level allows
+    // it (apply_ff.cu), else in FP64
+    const bool ff = mixed && o->tol >= kFfMinTol && apply_ff_supported(P->L64[L].dev);
+    const int npq = ff ? apply_ff_partials(P->L64[L].dev) : dot_partials_of(P->L64[L].dev);
     launch_dots_rz_zq(P->rk, P->zk, mixed ? P->z32 : nullptr, P->qk, N, prz, pzq, st, k);
     const int nb = fcg_blocks(N);            // the dots' CTAs: partials of r.z, z.q, r.r per right-hand side
     launch_fcg_direction(P->pk, P->zk, N, prz, pzq, nb, P->S, o->krylov == GLLS_KRYLOV_FCG ? 1 : 0, st, k);
-    launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st, true, P->S + S_PQ, ppq, nullptr, k);
+    if (ff) launch_apply_ff(P->L64[L].dev, P->pk, P->qk, true, ppq, st, k);
+    else launch_apply<double>(P->L64[L].dev, P->pk, P->qk, true, st, true, P->S + S_PQ, ppq, nullptr, k);
     launch_fcg_update(P->xk, P->rk, P->pk, P->qk, N, ppq, npq, prz, nb, prr, P->S, P->ticket,
                       mixed ? P->r32 : nullptr, st, k);
 }
@@ -869,6 +879,7 @@ struct WlRecord {
     bool dbl = false;                  // FP64 items
     int p = 0, cv = 1, wb = 0, ty = 0, l = 0, step = 0;
     bool mask = false, dot = false, add = false;
+    bool ff = false;                   // the float-float form of the FP64 outer apply
     int blocks = 0, threads = 256, nitems = 0;
     size_t smem = 0;
     std::vector<unsigned char> items;  // host copy of the item array
@@ -1156,6 +1167,7 @@ std::string build_group(WlGroup& G, const glls_solve_opts& o) {
     ap.dbl = true;
     ap.mask = true;
     ap.dot = true;
+    ap.ff = mixed && o.tol >= kFfMinTol;     // the outer apply in float-float where every item allows it
     for (size_t j = 0; j < G.probs.size(); ++j) {
         glls_problem* P = G.probs[j];
         const DevLevel<double>& F = P->L64[L].dev;
@@ -1167,6 +1179,7 @@ std::string build_group(WlGroup& G, const glls_solve_opts& o) {
                    P->N, prz, pzq, prr, ppq, apply_list_blocks(F.p, F.E), nullptr, P->ticket};
         items.push_back(it);
         ap.p = F.p;
+        ap.ff = ap.ff && F.dim == 2 && apply_ff_supported(F);
         ApplyItem<double> ai{F, P->pk, P->qk, ppq, nullptr};
         ap.put(ai, apply_list_blocks(F.p, F.E), (int)j);
     }
@@ -1225,6 +1238,10 @@ cudaError_t replay(const WlRecord& r, const unsigned char* base, int flexible, c
     bool ok = true;
     switch (r.kind) {
         case WL_APPLY:
+            if (r.ff) {
+                ok = launch_apply_ff_list(r.p, (const ApplyItem<double>*)items, start, r.nitems, r.blocks, r.mask, st);
+                break;
+            }
             ok = r.dbl ? launch_apply_list<double>(r.p, (const ApplyItem<double>*)items, start, r.nitems, r.blocks,
                                                    r.mask, r.dot, st)
                        : launch_apply_list<float>(r.p, (const ApplyItem<float>*)items, start, r.nitems, r.blocks,
@@ -1447,6 +1464,8 @@ static glls_status problem_create(const glls_mesh_desc* desc, int nrhs, glls_pro
         return fail(GLLS_ERR_INVALID, "bad smoother");
     if (desc->restriction != GLLS_RESTRICT_TRANSPOSE && desc->restriction != GLLS_RESTRICT_INTERP)
         return fail(GLLS_ERR_INVALID, "bad restriction");
+    if (desc->summation != GLLS_SUM_ATOMIC && desc->summation != GLLS_SUM_COLORED)
+        return fail(GLLS_ERR_INVALID, "bad summation");
     if (desc->smoother == GLLS_SMOOTHER_GLL && desc->order >= 2)
         for (int a = 0; a < desc->dim; ++a)
             if (!line_block_supported(desc->nelem[a] * desc->order - 1, desc->nelem[a]))
@@ -1512,6 +1531,22 @@ static glls_status problem_create(const glls_mesh_desc* desc, int nrhs, glls_pro
     if (st != GLLS_OK) return st;
     st = upload_levels<float>(P.get(), H, P->L32);
     if (st != GLLS_OK) return st;
+    for (auto& l : P->L64) l.dev.colored = desc->summation == GLLS_SUM_COLORED;
+    for (auto& l : P->L32) l.dev.colored = desc->summation == GLLS_SUM_COLORED;
+    {
+        // float-float outer apply: the FP32 rounding remainders of the finest
+        // level's FP64 geometric factors (the FP32 level holds the rounded
+        // values)
+        const size_t lf = H.size() - 1;
+        DevLevel<double>& F64 = P->L64[lf].dev;
+        if (F64.p >= 2 && F64.p <= (F64.dim == 2 ? 16 : 8)) {
+            const std::vector<double>& G = H[lf].G;
+            std::vector<float> lo(G.size());
+            for (size_t i = 0; i < G.size(); ++i) lo[i] = (float)(G[i] - (double)(float)G[i]);
+            CK(P->upload(&F64.Glo, lo));
+            F64.Ghi = P->L32[lf].dev.G;
+        }
+    }
     st = upload_coarse<double>(P.get(), C, P->C64);
     if (st == GLLS_OK) st = upload_coarse<float>(P.get(), C, P->C32);
     if (st != GLLS_OK) return st;
@@ -1828,6 +1863,7 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
         // vectors in each precision; transfer bands
         total += 12.0 * ((double)ncomp * E * nloc + (1 + d) * (double)N + (p + 1) * (p + 1)) + 12.0 * 5 * N;
         total += 24.0 * d * (double)N;
+        if (c == 0 && p >= 2 && p <= (d == 2 ? 16 : 8)) total += 4.0 * ncomp * E * nloc;   // float-float G remainders
         total += 2.0 * d * (12.0 * (2 * p + 2) * (double)(ne[0] * p + 1) + 4.0 * (ne[0] * p + 1));
         if (desc->smoother == GLLS_SMOOTHER_GLL && p >= 2) {
             // condensed line blocks: per segment (p-1)p/2 + 2(p-1) values, per vertex 2 (FP64 + FP32)
@@ -1976,6 +2012,9 @@ glls_status glls_solve_batch_worklist(glls_problem* const* probs, int n, const g
         if (probs[i]->device != dev) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: problems on different devices");
         if (!probs[i]->has_rhs) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: right-hand side not set");
         if (probs[i]->nrhs != 1) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: one right-hand side per problem");
+        if (probs[i]->L64.back().dev.colored)
+            return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: coloured summation (GLLS_SUM_COLORED) is not "
+                                          "in the work-list kernels; use glls_solve_batch");
         for (int j = 0; j < i; ++j)
             if (probs[j] == probs[i]) return fail(GLLS_ERR_INVALID, "glls_solve_batch_worklist: a problem appears twice");
     }
@@ -2072,12 +2111,33 @@ glls_status glls_apply_partials_f64(glls_problem* P, int level, const double* x,
     if (s != GLLS_OK) return s;
     if (!x || !y || !partials || !count) return fail(GLLS_ERR_INVALID, "null argument");
     const DevLevel<double>& L = P->L64[level].dev;
-    const int n = apply_dot_partials<double>(L);
+    const int n = dot_partials_of(L);
     *count = n;
     if (capacity < n) return fail(GLLS_ERR_INVALID, "partials: need " + std::to_string(n) + " entries");
     DeviceScope scope(P->device);
     CK(scope.err);
     launch_apply<double>(L, x, y, true, (cudaStream_t)stream, true, partials, partials, nullptr);
+    CK(cudaGetLastError());
+    return GLLS_OK;
+}
+
+// The same product in float-float arithmetic, as the mixed-precision outer
+// iteration launches it where the level allows (apply_ff.cu).
+glls_status glls_apply_partials_ff(glls_problem* P, int level, const double* x, double* y, double* partials,
+                                   int capacity, int* count, void* stream) {
+    glls_status s = check_level(P, level, false);
+    if (s != GLLS_OK) return s;
+    if (!x || !y || !partials || !count) return fail(GLLS_ERR_INVALID, "null argument");
+    const DevLevel<double>& L = P->L64[level].dev;
+    if (!apply_ff_supported(L))
+        return fail(GLLS_ERR_INVALID, "float-float apply: the finest level of a problem with 2 <= p <= 16 (2-D) "
+                                      "or 2 <= p <= 8 (3-D) and atomic summation only");
+    const int n = apply_ff_partials(L);
+    *count = n;
+    if (capacity < n) return fail(GLLS_ERR_INVALID, "partials: need " + std::to_string(n) + " entries");
+    DeviceScope scope(P->device);
+    CK(scope.err);
+    if (!launch_apply_ff(L, x, y, true, partials, (cudaStream_t)stream, 1)) return fail(GLLS_ERR_CUDA, "launch failed");
     CK(cudaGetLastError());
     return GLLS_OK;
 }

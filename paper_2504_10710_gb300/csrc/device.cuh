@@ -89,6 +89,12 @@ struct DevLevel {
     DevBand<T> P[3], R[3];
     int lpb[3] = {4, 4, 4};   // band-1 line-solve tile (lines per CTA) per direction, set by the autotuner
     int lbc[3] = {0, 0, 0};   // line-block lines per CTA per direction, set by the autotuner (0: launch heuristic)
+    int colored = 0;          // direct stiffness summation by element colours (bitwise reproducible; see launch_apply)
+    // float-float form of G (finest FP64 level, 2-D 2 <= p <= 16, 3-D
+    // 2 <= p <= 8; null elsewhere): Ghi = the FP32 level's G (the FP64 factors rounded to
+    // nearest), Glo = their FP32 rounding remainders (apply_ff.cu)
+    const float* Ghi = nullptr;
+    const float* Glo = nullptr;
     // Def. 3.2 line blocks condensed per element segment (GLL smoother, p >= 2;
     // null otherwise): blk[s] [ncoef][nlines * ne[s]] = packed K_I^-1, w_L,
     // w_R per segment; vband[s] [nlines][ne[s] - 1] = vertex Schur complement
@@ -191,6 +197,19 @@ int apply_list_blocks(int p, long long E);
 template <typename T>
 bool launch_apply_list(int p, const ApplyItem<T>* items, const int* start, int nitems, int blocks, bool mask,
                        bool dot, cudaStream_t st);
+// Float-float outer apply with p.(A p) partials (apply_ff.cu): the finest
+// level of 2-D problems with 2 <= p <= 16 and of 3-D problems with
+// 2 <= p <= 8 (false elsewhere).  y seams zero on entry.
+bool apply_ff_supported(const DevLevel<double>& L);
+int apply_ff_partials(const DevLevel<double>& L);   // dot partials (CTAs) per right-hand side
+bool launch_apply_ff(const DevLevel<double>& L, const double* x, double* y, bool mask, double* part,
+                     cudaStream_t st, int nrhs);
+bool launch_apply_ff_list(int p, const ApplyItem<double>* items, const int* start, int nitems, int blocks, bool mask,
+                          cudaStream_t st);
+// The float-float apply serves solves with tol >= kFfMinTol: its rounding
+// (about 2^-44 relative per contraction) parts the recurrence residual from
+// the true one near 1e-13.
+constexpr double kFfMinTol = 1e-12;
 template <typename T>
 bool transfer2_list_config(const DevBand<T>& M0, const DevBand<T>& M1, const int nout[3], int* gx, int* gy,
                            int* wb, int* ty, size_t* smem);

@@ -44,9 +44,43 @@ __device__ __forceinline__ bool on_boundary(long long g, const int n[3], int dim
 // ---------------------------------------------------------------------------
 // stiffness apply
 // ---------------------------------------------------------------------------
+// Element e of a launch: the e-th element in lexicographic order, or with
+// colour >= 0 the e-th element (lexicographic within the colour) whose
+// coordinate parities (ex & 1, ey & 1, ez & 1) are the bits of colour.
+// Elements of one colour are at least two apart along some axis, so no two of
+// them share a node.
+template <int DIM>
+__device__ __forceinline__ void element_coords(long long e, const int* ne, int colour, long long& ex, long long& ey,
+                                               long long& ez) {
+    if (colour < 0) {
+        ex = e % ne[0];
+        ey = (e / ne[0]) % ne[1];
+        ez = DIM == 3 ? e / ((long long)ne[0] * ne[1]) : 0;
+        return;
+    }
+    const int cx = colour & 1, cy = (colour >> 1) & 1, cz = (colour >> 2) & 1;
+    const long long m0 = (ne[0] - cx + 1) / 2, m1 = (ne[1] - cy + 1) / 2;
+    ex = 2 * (e % m0) + cx;
+    ey = 2 * ((e / m0) % m1) + cy;
+    ez = DIM == 3 ? 2 * (e / (m0 * m1)) + cz : 0;
+}
+
+// Elements of colour c (as above) on a grid of ne elements per axis.
+inline long long colour_elements(const int* ne, int dim, int c) {
+    long long n = 1;
+    for (int a = 0; a < dim; ++a) n *= (ne[a] - ((c >> a) & 1) + 1) / 2;
+    return n;
+}
+
+// y = A x over the elements of the launch.  colour < 0: all elements, seam
+// nodes accumulated with atomics (their summation order follows the
+// scheduling).  colour >= 0: the elements of one colour, seam nodes updated
+// with a plain read-add-write (no other element of the launch touches them);
+// the 2^dim colour launches in order 0, 1, ... add every seam node's
+// contributions in a fixed order, so y is the same bits on every run.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) apply_kernel(DevLevel<T> L, const T* __restrict__ x, T* __restrict__ y,
-                                                    int mask, int epc, int nrhs) {
+                                                    int mask, int epc, int nrhs, int colour, long long nelem) {
     grid_dep_sync();
     // right-hand side fastest in the CTA order (see device.cuh)
     const int rhs = blockIdx.x % nrhs;
@@ -60,15 +94,15 @@ __global__ void __launch_bounds__(256) apply_kernel(DevLevel<T> L, const T* __re
     T* sw = sx + epc * nloc;
     for (int t = threadIdx.x; t < n1 * n1; t += blockDim.x) sD[t] = L.D[t];
     const long long e0 = bx * epc;
-    const int ecount = (int)min((long long)epc, L.E - e0);
+    const int ecount = (int)min((long long)epc, nelem - e0);
     const int total = ecount * nloc;
     const long long EN = L.E * nloc;
 
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int el = t / nloc, q = t - el * nloc;
-        const long long e = e0 + el;
         const int i = q % n1, j = (q / n1) % n1, k = DIM == 3 ? q / (n1 * n1) : 0;
-        const long long ex = e % L.ne[0], ey = (e / L.ne[0]) % L.ne[1], ez = DIM == 3 ? e / ((long long)L.ne[0] * L.ne[1]) : 0;
+        long long ex, ey, ez;
+        element_coords<DIM>(e0 + el, L.ne, colour, ex, ey, ez);
         const long long g = ((ez * p + k) * L.n[1] + (ey * p + j)) * L.n[0] + (ex * p + i);
         sx[t] = x[g];
     }
@@ -85,7 +119,9 @@ __global__ void __launch_bounds__(256) apply_kernel(DevLevel<T> L, const T* __re
             gr[1] += sD[j * n1 + m] * xe[(k * n1 + m) * n1 + i];
             if (DIM == 3) gr[2] += sD[k * n1 + m] * xe[(m * n1 + j) * n1 + i];
         }
-        const long long gq = (e0 + el) * nloc + q;
+        long long ex, ey, ez;
+        element_coords<DIM>(e0 + el, L.ne, colour, ex, ey, ez);
+        const long long gq = ((ez * L.ne[1] + ey) * L.ne[0] + ex) * nloc + q;   // geometry factors of the element
         if (DIM == 2) {
             const T g00 = L.G[gq], g01 = L.G[EN + gq], g11 = L.G[2 * EN + gq];
             sw[t] = g00 * gr[0] + g01 * gr[1];
@@ -102,7 +138,6 @@ __global__ void __launch_bounds__(256) apply_kernel(DevLevel<T> L, const T* __re
 
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int el = t / nloc, q = t - el * nloc;
-        const long long e = e0 + el;
         const int i = q % n1, j = (q / n1) % n1, k = DIM == 3 ? q / (n1 * n1) : 0;
         const T* w0 = sw + el * nloc;
         const T* w1 = sw + epc * nloc + el * nloc;
@@ -113,14 +148,16 @@ __global__ void __launch_bounds__(256) apply_kernel(DevLevel<T> L, const T* __re
             v += sD[m * n1 + j] * w1[(k * n1 + m) * n1 + i];
             if (DIM == 3) v += sD[m * n1 + k] * w2[(m * n1 + j) * n1 + i];
         }
-        const long long ex = e % L.ne[0], ey = (e / L.ne[0]) % L.ne[1], ez = DIM == 3 ? e / ((long long)L.ne[0] * L.ne[1]) : 0;
+        long long ex, ey, ez;
+        element_coords<DIM>(e0 + el, L.ne, colour, ex, ey, ez);
         const long long g = ((ez * p + k) * L.n[1] + (ey * p + j)) * L.n[0] + (ex * p + i);
         const bool inner = i > 0 && i < p && j > 0 && j < p && (DIM == 2 || (k > 0 && k < p));
         if (inner) {
             y[g] = v;
         } else {
             if (mask && on_boundary(g, L.n, DIM)) continue;
-            atomicAdd(&y[g], v);
+            if (colour < 0) atomicAdd(&y[g], v);
+            else y[g] += v;
         }
     }
 }
@@ -1088,15 +1125,24 @@ cudaError_t launch_apply(const DevLevel<T>& L, const T* x, T* y, bool mask, cuda
         const cudaError_t e = cudaMemsetAsync(y, 0, sizeof(T) * L.N * nrhs, st);
         if (e != cudaSuccess) return e;
     }
-    if (launch_apply_fixed<T>(L, x, y, mask, dot, part, ticket, st, nrhs)) return cudaSuccess;
+    // coloured summation: the node-per-thread kernel once per element colour
+    if (!L.colored && launch_apply_fixed<T>(L, x, y, mask, dot, part, ticket, st, nrhs)) return cudaSuccess;
     int epc = 256 / L.nloc;
     if (epc < 1) epc = 1;
-    const long long blocks = (L.E + epc - 1) / epc * nrhs;
     const size_t smem = sizeof(T) * (L.n1 * L.n1 + (size_t)epc * L.nloc * (1 + L.dim));
-    if (L.dim == 2) {
-        launch_k(apply_kernel<T, 2>, (unsigned)blocks, 256, smem, st, L, x, y, mask ? 1 : 0, epc, nrhs);
-    } else {
-        launch_k(apply_kernel<T, 3>, (unsigned)blocks, 256, smem, st, L, x, y, mask ? 1 : 0, epc, nrhs);
+    const int ncolour = L.colored ? 1 << L.dim : 1;
+    for (int c = 0; c < ncolour; ++c) {
+        const int colour = L.colored ? c : -1;
+        const long long nelem = L.colored ? colour_elements(L.ne, L.dim, c) : L.E;
+        if (nelem == 0) continue;
+        const long long blocks = (nelem + epc - 1) / epc * nrhs;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        const cudaError_t e =
+            L.dim == 2 ? launch_k(apply_kernel<T, 2>, (unsigned)blocks, 256, smem, st, L, x, y, mask ? 1 : 0, epc,
+                                  nrhs, colour, nelem)
+                       : launch_k(apply_kernel<T, 3>, (unsigned)blocks, 256, smem, st, L, x, y, mask ? 1 : 0, epc,
+                                  nrhs, colour, nelem);
+        if (e != cudaSuccess) return e;
     }
     // orders outside the specialised range: x.(A x) as a separate product
     if (dot) {

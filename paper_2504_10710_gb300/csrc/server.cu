@@ -26,14 +26,14 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 struct MeshKey {
-    int dim = 0, order = 0, smoother = 0, restriction = 0, coarse_solver = 0, coarse_cr_levels = 0;
+    int dim = 0, order = 0, smoother = 0, restriction = 0, coarse_solver = 0, coarse_cr_levels = 0, summation = 0;
     int nelem[3] = {1, 1, 1};
     size_t ncoords = 0;
     unsigned long long hash = 0;
     bool operator==(const MeshKey& o) const {
         return dim == o.dim && order == o.order && smoother == o.smoother && restriction == o.restriction &&
                coarse_solver == o.coarse_solver && coarse_cr_levels == o.coarse_cr_levels &&
-               nelem[0] == o.nelem[0] && nelem[1] == o.nelem[1] && nelem[2] == o.nelem[2] &&
+               summation == o.summation && nelem[0] == o.nelem[0] && nelem[1] == o.nelem[1] && nelem[2] == o.nelem[2] &&
                ncoords == o.ncoords && hash == o.hash;
     }
 };
@@ -207,7 +207,9 @@ struct glls_server {
             Cached* c = find(r->key);
             if (c) {
                 std::vector<std::deque<Request*>::iterator> grp{it};
-                if (max_group > 1 && r->opts.use_graph == 2 && r->opts.krylov != GLLS_KRYLOV_GMRES)
+                // (coloured-summation meshes promise single-solve bits: not grouped)
+                if (max_group > 1 && r->opts.use_graph == 2 && r->opts.krylov != GLLS_KRYLOV_GMRES &&
+                    r->key.summation == GLLS_SUM_ATOMIC)
                     for (auto jt = std::next(it); jt != queue.end() && (int)grp.size() < max_group; ++jt)
                         if ((*jt)->key == r->key && (*jt)->gp == r->gp && same_opts((*jt)->opts, r->opts))
                             grp.push_back(jt);
@@ -441,6 +443,7 @@ static std::shared_ptr<MeshRec> make_mesh(glls_server* S, const glls_mesh_desc* 
     m->key.restriction = mesh->restriction;
     m->key.coarse_solver = mesh->coarse_solver;
     m->key.coarse_cr_levels = mesh->coarse_cr_levels;
+    m->key.summation = mesh->summation;
     for (int a = 0; a < 3; ++a) m->key.nelem[a] = a < mesh->dim ? mesh->nelem[a] : 1;
     m->key.ncoords = m->coords.size();
     m->key.hash = fnv1a(m->coords.data(), sizeof(double) * m->coords.size());

@@ -22,12 +22,14 @@ SMOOTHER_GLL, SMOOTHER_FEM, SMOOTHER_GLL_BAND1 = 0, 1, 2
 RESTRICT_TRANSPOSE, RESTRICT_INTERP = 0, 1
 KRYLOV_FCG, KRYLOV_PCG, KRYLOV_GMRES = 0, 1, 2
 COARSE_AUTO, COARSE_DENSE, COARSE_BLOCK_CR = 0, 1, 2
+SUM_ATOMIC, SUM_COLORED = 0, 1
 
 
 class MeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("nelem", C.c_int * 3), ("order", C.c_int),
                 ("coords", C.POINTER(C.c_double)), ("smoother", C.c_int), ("restriction", C.c_int),
-                ("device", C.c_int), ("coarse_solver", C.c_int), ("coarse_cr_levels", C.c_int)]
+                ("device", C.c_int), ("coarse_solver", C.c_int), ("coarse_cr_levels", C.c_int),
+                ("summation", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -100,6 +102,7 @@ def lib():
             "glls_server_set_max_group": [vp, C.c_int],
             "glls_submit_mesh": [vp, C.c_ulonglong, vp, vp, C.POINTER(SolveOpts), vp, C.POINTER(C.c_ulonglong)],
             "glls_apply_partials_f64": [vp, i, vp, vp, vp, i, C.POINTER(i), vp],
+            "glls_apply_partials_ff": [vp, i, vp, vp, vp, i, C.POINTER(i), vp],
         }
         for suf, real in (("f64", d), ("f32", C.c_float)):
             sig[f"glls_apply_{suf}"] = [vp, i, vp, vp, vp]
@@ -162,9 +165,9 @@ class Problem:
     """Owns a ``glls_problem``: mesh levels resident on the device."""
 
     def __init__(self, dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE,
-                 device=0, coarse_solver=COARSE_AUTO, coarse_cr_levels=0, nrhs=1):
+                 device=0, coarse_solver=COARSE_AUTO, coarse_cr_levels=0, nrhs=1, summation=SUM_ATOMIC):
         desc, coords = mesh_desc(dim, nelem, order, coords, smoother, restriction, device, coarse_solver,
-                                 coarse_cr_levels)
+                                 coarse_cr_levels, summation)
         self._coords = coords
         h = C.c_void_p()
         _check(lib().glls_problem_create_nrhs(C.byref(desc), nrhs, C.byref(h)))
@@ -270,12 +273,13 @@ class Problem:
         _check(getattr(lib(), f"glls_apply_multi_{self._suffix(x)}")(self.h, level, _ptr(x), _ptr(y), nrhs,
                                                                       _stream(stream)))
 
-    def apply_partials(self, level, x, y, partials, stream=None):
+    def apply_partials(self, level, x, y, partials, stream=None, ff=False):
         """FP64 y += A x with the fused per-CTA x.(A x) partials (y zero on
-        entry); returns the number of partials written."""
+        entry); returns the number of partials written.  ff=True: the
+        float-float form the mixed-precision outer iteration runs."""
         n = C.c_int()
-        _check(lib().glls_apply_partials_f64(self.h, level, _ptr(x), _ptr(y), _ptr(partials), partials.numel(),
-                                             C.byref(n), _stream(stream)))
+        fn = lib().glls_apply_partials_ff if ff else lib().glls_apply_partials_f64
+        _check(fn(self.h, level, _ptr(x), _ptr(y), _ptr(partials), partials.numel(), C.byref(n), _stream(stream)))
         return n.value
 
     def line_solve(self, level, axis, g, x, stream=None):
@@ -346,11 +350,11 @@ def solve_multi(problem, F, g, o: SolveOpts, clones=None):
 
 
 def mesh_desc(dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0,
-              coarse_solver=COARSE_AUTO, coarse_cr_levels=0):
+              coarse_solver=COARSE_AUTO, coarse_cr_levels=0, summation=SUM_ATOMIC):
     coords = np.ascontiguousarray(coords, dtype=np.float64)
     ne = (C.c_int * 3)(*(list(nelem) + [1] * (3 - len(nelem))))
     return MeshDesc(dim, ne, order, coords.ctypes.data_as(C.POINTER(C.c_double)), smoother, restriction,
-                    device, coarse_solver, coarse_cr_levels), coords
+                    device, coarse_solver, coarse_cr_levels, summation), coords
 
 
 def estimate_bytes(dim, nelem, order, coords, coarse_solver=COARSE_AUTO, coarse_cr_levels=0):
@@ -370,8 +374,8 @@ class Server:
         self._keep = {}
 
     def submit(self, dim, nelem, order, coords, f, g, o: SolveOpts, out, smoother=SMOOTHER_GLL,
-               restriction=RESTRICT_TRANSPOSE):
-        desc, coords = mesh_desc(dim, nelem, order, coords, smoother, restriction)
+               restriction=RESTRICT_TRANSPOSE, summation=SUM_ATOMIC):
+        desc, coords = mesh_desc(dim, nelem, order, coords, smoother, restriction, summation=summation)
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
         assert out.dtype == np.float64 and out.flags.c_contiguous
@@ -386,9 +390,10 @@ class Server:
         """Solve up to k queued requests of one mesh together (see glls_server_set_max_group)."""
         _check(lib().glls_server_set_max_group(self.h, k))
 
-    def register(self, dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE):
+    def register(self, dim, nelem, order, coords, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE,
+                 summation=SUM_ATOMIC):
         """Registers a mesh; returns its id for submit_mesh."""
-        desc, coords = mesh_desc(dim, nelem, order, coords, smoother, restriction)
+        desc, coords = mesh_desc(dim, nelem, order, coords, smoother, restriction, summation=summation)
         mid = C.c_ulonglong()
         _check(lib().glls_server_register(self.h, C.byref(desc), C.byref(mid)))
         return mid.value
@@ -438,10 +443,10 @@ class Server:
 
 
 def problem_for(workload, smoother=SMOOTHER_GLL, restriction=RESTRICT_TRANSPOSE, device=0,
-                coarse_solver=COARSE_AUTO, coarse_cr_levels=0, nrhs=1):
+                coarse_solver=COARSE_AUTO, coarse_cr_levels=0, nrhs=1, summation=SUM_ATOMIC):
     """Problem of a workload description, with nodes placed at the library's
     own GLL points."""
     xi, _ = gll(workload.order)
     coords = workload.coords(xi)
     return Problem(workload.dim, workload.nelem, workload.order, coords, smoother, restriction, device,
-                   coarse_solver, coarse_cr_levels, nrhs), coords
+                   coarse_solver, coarse_cr_levels, nrhs, summation), coords
