@@ -24,7 +24,6 @@
 // parameters, the three line directions of an element through shared memory.
 #include "device.cuh"
 #include "ff.cuh"
-#include "reduce.cuh"
 #include "setup.h"
 
 #include <algorithm>
@@ -33,6 +32,22 @@
 
 namespace glls {
 namespace {
+
+// Block sum of one FP64 value per thread (blockDim.x <= 256, a multiple of
+// 32) with few FP64 adds: the values go through shared memory, lane l of
+// warp 0 adds values l, l + 32, ... in that order, then warp 0's shuffle
+// tree.  A shuffle tree over every warp would cost each thread five FP64
+// adds, which on GB300's FP64 pipe is a visible share of these kernels.
+__device__ __forceinline__ double block_sum_lean(double v, double* sv) {
+    sv[threadIdx.x] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += sv[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;   // valid in thread 0
+}
 
 template <int P>
 __device__ __forceinline__ void apply_ff_body(const DevLevel<double>& L, const double* __restrict__ x,
@@ -141,8 +156,8 @@ __device__ __forceinline__ void apply_ff_body(const DevLevel<double>& L, const d
             atomicAdd(&y[g], vd);
         }
     }
-    __shared__ double red[32];
-    const double tsum = block_sum(local, red);
+    __shared__ double sv[256];
+    const double tsum = block_sum_lean(local, sv);
     if (threadIdx.x == 0) part[(long long)rhs * nbx + bx] = tsum;
 }
 
@@ -194,10 +209,13 @@ bool launch_ff_list(int p, const ApplyItem<double>* items, const int* start, int
 
 // ---- 3-D, even-odd line sweeps ---------------------------------------------
 
-// Elements per CTA: at most 256 threads, and no more elements than keep about
-// eight CTAs per SM on the level (152 SMs).
+// Elements per CTA: at most 192 threads (three CTAs per SM at 96 registers
+// a thread; with two CTAs of 256 threads the kernel ran at 128 registers and
+// 18 % warp occupancy), and no more elements than keep about eight CTAs per
+// SM on the level (152 SMs).
+constexpr int kEoFfThreads = 192;
 int eo_ff_epb(int p, long long E) {
-    const long long most = 256 / ((p + 1) * (p + 1));
+    const long long most = kEoFfThreads / ((p + 1) * (p + 1));
     const long long fill = E / (152 * 8);
     return (int)std::max(1LL, std::min(most, fill));
 }
@@ -253,7 +271,7 @@ __device__ __forceinline__ void eo_line_ff(const EoMatFF<N>& M, const ffloat (&u
 template <int N>
 struct EoShapeFF {
     static constexpr int NP = N * N, NLOC = NP * N;
-    static constexpr int EPB = 256 / NP;
+    static constexpr int EPB = kEoFfThreads / NP;
     static constexpr int RS = N == 8 ? 9 : N == 7 ? 7 : N == 6 ? 9 : N;
     static constexpr int PS = N == 3 ? 9 : N == 4 ? 19 : N == 5 ? 25 : N == 6 ? 54 : N == 7 ? 52 : N == 8 ? 72 : 89;
     static constexpr int ES = N == 3 ? 27 : N == 4 ? 76 : N == 5 ? 125 : N == 6 ? 324 : N == 7 ? 369 : N == 8 ? 576 : 801;
@@ -263,7 +281,7 @@ struct EoShapeFF {
 // and the r-line (j, k) = (a, b) and s-line (i, k) = (a, b) through shared
 // memory (X: x, U, V: the r and s work buffers).
 template <int P>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(kEoFfThreads, 3)
     apply_eo3_ff_kernel(DevLevel<double> L, const __grid_constant__ EoParamsFF<P + 1> M, const double* __restrict__ x,
                         double* __restrict__ y, int mask, double* part, int epb, int nrhs) {
     using S = EoShapeFF<P + 1>;
@@ -378,8 +396,8 @@ __global__ void __launch_bounds__(256, 2)
             }
         }
     }
-    __shared__ double red[32];
-    const double tsum = block_sum(local, red);
+    __shared__ double sv[kEoFfThreads];
+    const double tsum = block_sum_lean(local, sv);
     if (tid == 0) part[(long long)rhs * nbx + bx] = tsum;
 }
 
