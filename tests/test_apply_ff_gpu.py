@@ -77,6 +77,30 @@ def test_ff_apply_and_partials_match_oracle(case):
     prob.close()
 
 
+@pytest.mark.parametrize("scale", [1e-20, 1e-8, 1e8, 1e25], ids=lambda v: f"x{v:g}")
+@pytest.mark.parametrize("mk", [lambda: inputs.random2d((5, 4), 6, amp=0.1, seed=44),
+                                lambda: inputs.random3d((3, 2, 2), 7, amp=0.1, seed=45)], ids=["2d", "3d"])
+def test_ff_apply_scaled_inputs(mk, scale):
+    """The conversions between FP64 and float pairs across the FP32 exponent
+    range: p scaled by 1e-20 .. 1e25 gives A p scaled the same, to the same
+    relative accuracy."""
+    wl = mk()
+    prob, coords = glls.problem_for(wl)
+    lv = Level(wl.dim, wl.nelem, wl.order, coords)
+    rng = np.random.default_rng(9)
+    x = np.where(lv.interior, rng.standard_normal(lv.shape), 0.0) * scale
+    L = prob.levels - 1
+    part = torch.zeros(1 << 16, dtype=torch.float64, device="cuda")
+    y = torch.zeros(lv.N, dtype=torch.float64, device="cuda")
+    n = prob.apply_partials(L, torch.tensor(x.ravel(), dtype=torch.float64, device="cuda"), y, part, ff=True)
+    torch.cuda.synchronize()
+    ref = lv.apply(x)
+    assert _rel(y.cpu().numpy().reshape(lv.shape), ref) < TOL_FF
+    rdot = float(np.vdot(x, ref))
+    assert abs(float(part[:n].sum()) - rdot) <= 1e-12 * abs(rdot)
+    prob.close()
+
+
 def test_ff_apply_refusals():
     part = torch.zeros(1 << 12, dtype=torch.float64, device="cuda")
     # a coarse level (the float-float factors are kept for the finest level only)
