@@ -91,8 +91,11 @@ enum { GLLS_COARSE_AUTO = 0, GLLS_COARSE_DENSE = 1, GLLS_COARSE_BLOCK_CR = 2 };
  *            same order on every run.  A solve is then the same bits alone, in
  *            a graph-branch batch and in the serving loop, at the cost of the
  *            node-per-thread apply kernel (not the specialised ones) and 2^dim
- *            launches per apply.  Work-list batches refuse such problems, and
- *            the serving loop does not group their requests. */
+ *            launches per apply.  A multi-right-hand-side solve gives each
+ *            right-hand side the bits of its single solve (every kernel does
+ *            the same arithmetic per right-hand side), so grouped requests in
+ *            the serving loop keep them too.  Work-list batches refuse such
+ *            problems. */
 enum { GLLS_SUM_ATOMIC = 0, GLLS_SUM_COLORED = 1 };
 
 typedef struct glls_problem glls_problem;   /* opaque, library-owned */

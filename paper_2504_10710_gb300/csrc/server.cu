@@ -207,9 +207,7 @@ struct glls_server {
             Cached* c = find(r->key);
             if (c) {
                 std::vector<std::deque<Request*>::iterator> grp{it};
-                // (coloured-summation meshes promise single-solve bits: not grouped)
-                if (max_group > 1 && r->opts.use_graph == 2 && r->opts.krylov != GLLS_KRYLOV_GMRES &&
-                    r->key.summation == GLLS_SUM_ATOMIC)
+                if (max_group > 1 && r->opts.use_graph == 2 && r->opts.krylov != GLLS_KRYLOV_GMRES)
                     for (auto jt = std::next(it); jt != queue.end() && (int)grp.size() < max_group; ++jt)
                         if ((*jt)->key == r->key && (*jt)->gp == r->gp && same_opts((*jt)->opts, r->opts))
                             grp.push_back(jt);

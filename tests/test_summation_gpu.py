@@ -128,8 +128,8 @@ def test_colored_solve_matches_atomic_solve():
 
 def test_server_colored_results_same_bits_alone_and_in_the_mix():
     """Concurrent requests on registered coloured meshes (clones, several
-    slots, grouping switched on) return exactly the bits of the solve alone,
-    and are never grouped."""
+    slots, grouping into multi-right-hand-side solves switched on) return
+    exactly the bits of the solve alone."""
     o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_MIXED)
     reqs = [_colored(wl) for wl in SOLVE_MIX[:3]]
     alone = []
@@ -150,10 +150,8 @@ def test_server_colored_results_same_bits_alone_and_in_the_mix():
             tickets.append(srv.submit_mesh(ids[k], f, g, o, out))
     for t in tickets:
         st, stats = srv.poll(t, wait=True)
-        assert st == glls.OK and stats.group <= 1
-    inf = srv.info()
+        assert st == glls.OK
     srv.close()
-    assert inf.grouped == 0
     for k, out in outs:
         assert np.array_equal(out, alone[k])
 
@@ -163,3 +161,64 @@ def test_bad_summation_is_refused():
     with pytest.raises(glls.GllsError) as ei:
         glls.problem_for(wl, summation=2)
     assert ei.value.status == glls.ERR_INVALID
+
+
+@pytest.mark.parametrize("prec", [glls.PREC_FP64, glls.PREC_MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("mk", [lambda: inputs.random2d((7, 5), 6, amp=0.1, seed=96, nrhs=3),
+                                lambda: inputs.random3d((3, 2, 2), 5, amp=0.1, seed=97, nrhs=4)],
+                         ids=["2d_7x5_p6_x3", "3d_3x2x2_p5_x4"])
+def test_colored_nrhs_solve_same_bits_as_single_solves(mk, prec):
+    """With coloured summation every kernel of a multi-right-hand-side solve
+    does, for each right-hand side, the arithmetic of a single solve in the
+    same order (right-hand sides only add CTAs): each result is the bits of
+    its single solve."""
+    wl = mk()
+    prob, coords = glls.problem_for(wl, nrhs=wl.nrhs, summation=glls.SUM_COLORED)
+    F = np.ascontiguousarray(wl.sample_rhs(coords).reshape(wl.nrhs, -1))
+    g = wl.sample_dirichlet(coords).ravel()
+    prob.set_rhs(F)
+    prob.set_dirichlet(g)
+    o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=prec)
+    U = np.zeros((wl.nrhs, prob.N))
+    stats = prob.solve(U, o)
+    single = glls.problem_for(wl, summation=glls.SUM_COLORED)[0]
+    single.set_dirichlet(g)
+    for j in range(wl.nrhs):
+        single.set_rhs(F[j])
+        u1 = np.zeros(prob.N)
+        s1 = single.solve(u1, o)
+        assert stats[j].iterations == s1.iterations
+        assert np.array_equal(U[j], u1), (j, np.abs(U[j] - u1).max())
+    single.close()
+    prob.close()
+
+
+def test_server_groups_colored_requests_with_single_solve_bits():
+    """One slot and grouping on: queued requests of a coloured mesh are solved
+    together as multi-right-hand-side solves, and each result is the bits of
+    its right-hand side solved alone."""
+    o = glls.opts(tol=1e-10, gamma=1, alpha=2.0 / 3.0, precision=glls.PREC_MIXED)
+    wl = SOLVE_MIX[1]
+    prob, coords, f, g = _colored(wl)
+    fs = [f * (1.0 + 0.3 * j) - 0.1 * j for j in range(6)]
+    alone = []
+    for fk in fs:
+        prob.set_rhs(fk)
+        u = np.zeros(prob.N)
+        assert prob.solve(u, o).status == glls.OK
+        alone.append(u)
+    prob.close()
+    srv = glls.Server(budget_bytes=8 << 30, slots=1)
+    srv.set_max_group(4)
+    mid = srv.register(wl.dim, wl.nelem, wl.order, coords, summation=glls.SUM_COLORED)
+    outs = [np.full(f.size, np.nan) for _ in fs]
+    tickets = [srv.submit_mesh(mid, fk, g, o, out) for fk, out in zip(fs, outs)]
+    groups = []
+    for t in tickets:
+        st, stats = srv.poll(t, wait=True)
+        assert st == glls.OK
+        groups.append(stats.group)
+    srv.close()
+    assert max(groups) > 1, groups
+    for out, u in zip(outs, alone):
+        assert np.array_equal(out, u)
