@@ -52,7 +52,16 @@ typedef enum {
     GLLS_ERR_BUDGET = -7
 } glls_status;
 
-enum { GLLS_PREC_FP64 = 0, GLLS_PREC_MIXED = 1 };          /* gamma-cycle in FP64, or FP32 */
+/* Precision of a solve:
+ *   FP64   everything in FP64;
+ *   MIXED  the gamma-cycle in FP32 and, for tol >= 1e-12, the outer apply in
+ *          float-float arithmetic (glls_apply_partials_ff); the outer Krylov
+ *          vectors, dots and updates stay FP64.  The residuals and directions
+ *          must stay inside the FP32 exponent range (about 1e-38 .. 3e38 in
+ *          magnitude): data far outside it overflows or underflows in the
+ *          cycle and the solve reports GLLS_ERR_BREAKDOWN; scale it, or use
+ *          FP64. */
+enum { GLLS_PREC_FP64 = 0, GLLS_PREC_MIXED = 1 };
 /* Line systems of the line smoother (Def. 3.2):
  *   GLL        the line blocks R A_p P, i.e. every coupling of A_p between two
  *              nodes of the grid line (half-bandwidth p; solved exactly by
