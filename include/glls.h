@@ -47,7 +47,9 @@ typedef enum {
     GLLS_ERR_OOM = -2,            /* device or host allocation failed */
     GLLS_ERR_CUDA = -3,           /* a CUDA runtime call failed */
     GLLS_ERR_NOT_CONVERGED = -4,  /* max_iter reached; last iterate returned */
-    GLLS_ERR_BREAKDOWN = -5,      /* p.Ap <= 0, NaN/Inf, zero pivot, bad Jacobian */
+    GLLS_ERR_BREAKDOWN = -5,      /* p.Ap <= 0, NaN/Inf, zero pivot, bad Jacobian; a solve that
+                                     breaks down clears the problem's work vectors before it
+                                     returns, so the next solve starts clean */
     GLLS_ERR_TIMEOUT = -6,
     GLLS_ERR_BUDGET = -7
 } glls_status;

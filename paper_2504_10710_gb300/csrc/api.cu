@@ -1432,6 +1432,31 @@ glls_status make_plan(glls_problem* const* probs, int n, const glls_solve_opts* 
     return GLLS_OK;
 }
 
+// After a breakdown the instance's work vectors can hold Inf or NaN where the
+// solve kernels rely on zeros they never write (boundary entries of the level
+// iterates, which a prolongation of an infinite coarse value turns into 0 *
+// Inf; the seam entries of the apply scratch).  They are cleared so that the
+// next solve, in either precision, starts from the state set-up left.
+template <typename T>
+void clear_level_vectors(std::vector<LevelStore<T>>& Ls, int nrhs, cudaStream_t st) {
+    for (auto& l : Ls) {
+        const size_t bytes = sizeof(T) * (size_t)(l.dev.N * nrhs);
+        T* vs[] = {l.r, l.x, l.y, l.t1, l.t2};
+        for (T* v : vs) cudaMemsetAsync(v, 0, bytes, st);
+    }
+}
+
+void clear_work_vectors(glls_problem* P, cudaStream_t st) {
+    const long long NK = P->N * P->nrhs;
+    double* vd[] = {P->xk, P->rk, P->pk, P->qk, P->zk};
+    for (double* v : vd) cudaMemsetAsync(v, 0, sizeof(double) * NK, st);
+    float* vf[] = {P->r32, P->z32};
+    for (float* v : vf) cudaMemsetAsync(v, 0, sizeof(float) * NK, st);
+    clear_level_vectors(P->L64, P->nrhs, st);
+    clear_level_vectors(P->L32, P->nrhs, st);
+    cudaStreamSynchronize(st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1820,6 +1845,10 @@ glls_status glls_solve(glls_problem* P, const glls_solve_opts* o, double* u, int
     const int k = P ? P->nrhs : 1;
     if (stats) std::memset(stats, 0, sizeof(*stats) * k);
     const glls_status r = solve_impl(P, o, u, on_device, stream, stats);
+    if (r == GLLS_ERR_BREAKDOWN) {
+        DeviceScope scope(P->device);
+        if (scope.err == cudaSuccess) clear_work_vectors(P, (cudaStream_t)stream);
+    }
     if (stats) {
         if (k == 1) {
             stats[0].status = r;
@@ -1992,6 +2021,7 @@ glls_status glls_solve_batch(glls_problem* const* probs, int n, const glls_solve
     glls_status worst = GLLS_OK;
     for (int i = 0; i < n; ++i) {
         glls_status r = solve_result(probs[i], probs[i]->hostS, stats ? &stats[i] : nullptr, t_ms);
+        if (r == GLLS_ERR_BREAKDOWN) clear_work_vectors(probs[i], st);
         if (r != GLLS_OK && worst == GLLS_OK) worst = r;
     }
     if (worst == GLLS_ERR_BREAKDOWN) fail(worst, "breakdown in at least one problem of the batch");
@@ -2068,6 +2098,7 @@ glls_status glls_solve_batch_worklist(glls_problem* const* probs, int n, const g
     glls_status worst = GLLS_OK;
     for (int i = 0; i < n; ++i) {
         glls_status r = solve_result(probs[i], probs[i]->hostS, stats ? &stats[i] : nullptr, t_ms);
+        if (r == GLLS_ERR_BREAKDOWN) clear_work_vectors(probs[i], st);
         if (r != GLLS_OK && worst == GLLS_OK) worst = r;
     }
     if (stats) {

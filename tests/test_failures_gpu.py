@@ -131,3 +131,26 @@ def test_entry_points_restore_the_callers_device():
     c.close()
     assert torch.cuda.current_device() == dev_before
     prob.close()
+
+
+@pytest.mark.parametrize("scale", [1e40, 1e-50], ids=["x1e40", "x1e-50"])
+def test_mixed_solve_outside_fp32_range_reports_breakdown(scale):
+    """Data far outside the FP32 exponent range: the mixed solve (FP32 cycle,
+    float-float outer apply) reports a breakdown instead of a wrong answer;
+    the same problem then solves the same data in FP64, and ordinary data in
+    mixed precision (the breakdown's Inf/NaN do not stay in its work
+    vectors)."""
+    wl, prob, coords = _problem()
+    f = np.asarray(wl.sample_rhs(coords)[0], dtype=np.float64)
+    prob.set_rhs(f * scale)
+    prob.set_dirichlet(np.zeros(prob.N))
+    u = np.zeros(prob.N)
+    st = prob.solve(u, glls.opts(tol=1e-10, precision=glls.PREC_MIXED), raise_on_error=False)
+    assert st.status == glls.ERR_BREAKDOWN, st.status
+    st = prob.solve(u, glls.opts(tol=1e-10, precision=glls.PREC_FP64))
+    assert st.status == glls.OK and np.isfinite(u).all()
+    prob.set_rhs(f)
+    for use_graph in (2, 0):
+        st = prob.solve(u, glls.opts(tol=1e-10, precision=glls.PREC_MIXED, use_graph=use_graph))
+        assert st.status == glls.OK and np.isfinite(u).all()
+    prob.close()
