@@ -1433,10 +1433,10 @@ glls_status make_plan(glls_problem* const* probs, int n, const glls_solve_opts* 
 }
 
 // After a breakdown the instance's work vectors can hold Inf or NaN where the
-// solve kernels rely on zeros they never write (boundary entries of the level
-// iterates, which a prolongation of an infinite coarse value turns into 0 *
-// Inf; the seam entries of the apply scratch).  They are cleared so that the
-// next solve, in either precision, starts from the state set-up left.
+// solve kernels rely on zeros they never write (set-up leaves them zero: for
+// instance boundary entries of the level iterates, where a prolongation of an
+// infinite coarse value gives 0 * Inf).  They are cleared so that the next
+// solve, in either precision, starts from the state set-up left.
 template <typename T>
 void clear_level_vectors(std::vector<LevelStore<T>>& Ls, int nrhs, cudaStream_t st) {
     for (auto& l : Ls) {
