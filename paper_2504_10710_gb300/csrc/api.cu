@@ -1877,7 +1877,7 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
     std::vector<int> chain = order_chain(desc->order, multi);
     const int ncomp = d == 2 ? 3 : 6;
     double total = 0.0;
-    long long Nfine = 0, Ncoarse = 0, n0 = 1;
+    long long Nfine = 0, n0 = 1;
     for (size_t c = 0; c < chain.size(); ++c) {
         const int p = chain[c];
         long long N = 1, nloc = 1, inner = 1;
@@ -1887,7 +1887,7 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
             inner *= ne[a] * p - 1;
         }
         if (c == 0) Nfine = N;
-        if (c + 1 == chain.size()) { Ncoarse = N; n0 = inner; }
+        if (c + 1 == chain.size()) n0 = inner;
         // G, diag, off, D in FP64 + FP32; packed (diag, off) pairs per direction; five level
         // vectors in each precision; transfer bands
         total += 12.0 * ((double)ncomp * E * nloc + (1 + d) * (double)N + (p + 1) * (p + 1)) + 12.0 * 5 * N;
@@ -1925,7 +1925,6 @@ glls_status glls_estimate_bytes(const glls_mesh_desc* desc, size_t* bytes) {
     total += 8.0 * n0 + (double)nr * (8.0 * ld64 + 4.0 * ld32);
     total += 8.0 * (11.0 * Nfine) + 8.0 * Nfine + 8.0 * std::max<double>(2 * kMaxReduceBlocks, E + 1) + 64.0;
     total += 4.0 * 2.0 * Nfine;                                          // r32, z32
-    (void)Ncoarse;
     *bytes = (size_t)total;
     return GLLS_OK;
 }

@@ -1093,14 +1093,6 @@ __global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x
         y[i] += a * x[x_shared ? i % n : i];
 }
 
-// One element per thread (more loads in flight than a grid-stride loop);
-// the partial-sum buffer holds up to kMaxReduceBlocks entries per dot.
-inline int reduce_grid(long long n) {
-    long long b = (n + 255) / 256;
-    if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
-    return (int)(b < 1 ? 1 : b);
-}
-
 inline int grid_for(long long n, int threads = 256) {
     long long b = (n + threads - 1) / threads;
     if (b > 152LL * 16) b = 152LL * 16;
