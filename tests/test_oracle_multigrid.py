@@ -147,7 +147,8 @@ TABLE1_CASES = [
     ("FEM", P1, 8, range(1, 9), 1), ("FEM", P1, 16, range(1, 9), 1), ("FEM", P1, 32, range(1, 9), 1),
     ("FEM", P3, 8, range(1, 9), 1), ("FEM", P3, 16, range(1, 9), 1),
     ("GLL", P1, 8, range(1, 9), 1), ("GLL", P1, 16, range(1, 9), 1), ("GLL", P1, 32, range(1, 9), 2),
-    ("GLL", P1, 64, range(1, 4), (3, 1, 1)),
+    # (gamma = 6..8 take 28-93 s each in the oracle: measured once, 7 6 6 for the printed 6 5 5)
+    ("GLL", P1, 64, range(1, 6), (3, 1, 1, 1, 1)),
     ("GLL", P3, 8, range(1, 9), 2),
 ]
 
